@@ -1,0 +1,70 @@
+"""Element matrices A_e of Eq. 16 for the two element types of Section 2.3.3.
+
+Oracle code (test infrastructure only).  Every function here is pinned by
+tests/test_oracle_elements.py against closed forms: the unit right tetrahedron,
+the unit cube, exact gradient energy for affine fields, and the hourglass
+null-space of the one-point hexahedron.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+# Trilinear hex8 shape functions N_n = (1 + s_x xi)(1 + s_y eta)(1 + s_z zeta) / 8,
+# corner n having natural coordinates s_n in {-1, +1}^3 (bottom face
+# counter-clockwise, then top face).
+HEX8_NATURAL = np.array([[-1, -1, -1], [1, -1, -1], [1, 1, -1], [-1, 1, -1],
+                         [-1, -1, 1], [1, -1, 1], [1, 1, 1], [-1, 1, 1]], dtype=np.float64)
+
+
+def hex8_dN_dxi_centre() -> np.ndarray:
+    """dN_n/dxi_j at xi = eta = zeta = 0, as a (3, 8) array: s_n,j / 8."""
+    return HEX8_NATURAL.T / 8.0
+
+
+def hex8_reduced(xe: np.ndarray):
+    """One-point (reduced integration) hexahedron, Eq. 14 and Eq. 16.
+
+    xe: (..., 8, 3) corner coordinates.  J_ij = sum_n x_n,i dN_n/dxi_j is taken
+    at the element centre, the single integration point; B = J^-T dN/dxi gives
+    the temperature gradient matrix; A = 8 det(J) B^T B.  Returns (A, detJ,
+    V_e) with V_e = 8 det J (the reference cube has volume 8)."""
+    dN = hex8_dN_dxi_centre()                                  # (3, 8)
+    J = np.einsum("...ni,jn->...ij", xe, dN)                   # (..., 3, 3)
+    detJ = np.linalg.det(J)
+    B = np.einsum("...ji,jn->...in", np.linalg.inv(J), dN)    # J^-T dN: (..., 3, 8)
+    A = 8.0 * detJ[..., None, None] * np.einsum("...in,...im->...nm", B, B)
+    return A, detJ, 8.0 * detJ
+
+
+def tet4_linear(xe: np.ndarray):
+    """Linear tetrahedron, Eq. 15 and Eq. 16.
+
+    xe: (..., 4, 3).  With the edge matrix E = [x1-x0, x2-x0, x3-x0] (as
+    columns), the barycentric gradients of corners 1..3 are the rows of E^-1
+    and the gradient of corner 0 is minus their sum.  V_tet = det(E) / 6 and
+    A = V_tet B^T B.  Returns (A, det(E), V_tet)."""
+    E = np.swapaxes(xe[..., 1:, :] - xe[..., :1, :], -1, -2)    # (..., 3, 3) columns = edges
+    detE = np.linalg.det(E)
+    G = np.linalg.inv(E)                                       # rows = grad lambda_1..3
+    B = np.concatenate([-G.sum(axis=-2, keepdims=True), G], axis=-2)   # (..., 4, 3)
+    V = detE / 6.0
+    A = V[..., None, None] * np.einsum("...ni,...mi->...nm", B, B)
+    return A, detE, V
+
+
+def element_matrices(elem_type: int, xyz: np.ndarray, conn: np.ndarray):
+    """A_e, the orientation determinant and V_e for every element of a mesh.
+
+    Raises ValueError for an element with det <= 0 (inverted or degenerate),
+    which the method cannot use (Algorithm 1, pre-computation)."""
+    xe = xyz[conn]
+    if elem_type == 8:
+        A, det, V = hex8_reduced(xe)
+    elif elem_type == 4:
+        A, det, V = tet4_linear(xe)
+    else:
+        raise ValueError(f"unknown element type {elem_type}")
+    bad = np.nonzero(~(det > 0))[0]
+    if len(bad):
+        raise ValueError(f"element {int(bad[0])} has non-positive Jacobian determinant")
+    return A, det, V

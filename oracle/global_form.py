@@ -1,0 +1,143 @@
+"""Global assembled form of the FED-FEM step, Eq. 7-8 with lumped C (Section 2.3.4).
+
+Oracle code (test infrastructure only).  Per time step (Algorithm 1, the
+time-stepping block, taken in its global matrix form):
+
+1. k at every node from the nodal temperature, k_e = mean of the element's
+   nodal k (Eq. 13);
+2. K = sum_e k_e A_e assembled into one global sparse matrix (Eq. 11);
+3. C_i = V_i rho(T_i) c(T_i) (lumped, Section 2.3.4);
+4. R = -K T + beta (T_a - T) + Q + hA (T_inf - T), beta_i = w_b c_b V_i
+   (the pre-computed K_b and Q_b of Section 2.3.5 in difference form);
+5. T <- T + dt R / C on free nodes (Eq. 8, Eq. 19); Dirichlet nodes keep
+   their initial value (Eq. 3).
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+
+from .elements import element_matrices
+
+
+def lumped_volumes(conn: np.ndarray, V_e: np.ndarray, n_nodes: int) -> np.ndarray:
+    """V_i = sum over elements containing i of V_e / (nodes per element)."""
+    nv = conn.shape[1]
+    V = np.zeros(n_nodes)
+    np.add.at(V, conn.ravel(), np.repeat(V_e / nv, nv))
+    return V
+
+
+def lumped_face_areas(xyz: np.ndarray, faces: np.ndarray, n_nodes: int) -> np.ndarray:
+    """A_i = sum over boundary faces containing i of (face area) / (face nodes).
+
+    Triangles: |(x1-x0) x (x2-x0)| / 2.  Quadrilaterals: |d1 x d2| / 2 with the
+    two diagonals d1 = x2-x0, d2 = x3-x1 (exact for planar quadrilaterals)."""
+    A = np.zeros(n_nodes)
+    if len(faces) == 0:
+        return A
+    x = xyz[faces]
+    if faces.shape[1] == 3:
+        area = 0.5 * np.linalg.norm(np.cross(x[:, 1] - x[:, 0], x[:, 2] - x[:, 0]), axis=1)
+    elif faces.shape[1] == 4:
+        area = 0.5 * np.linalg.norm(np.cross(x[:, 2] - x[:, 0], x[:, 3] - x[:, 1]), axis=1)
+    else:
+        raise ValueError("faces must have 3 or 4 nodes")
+    np.add.at(A, faces.ravel(), np.repeat(area / faces.shape[1], faces.shape[1]))
+    return A
+
+
+def gaussian_density(xyz: np.ndarray, sources) -> np.ndarray:
+    """Q_r(x_i) = sum_s peak_s exp(-|x_i - x0_s|^2 / (2 sigma_s^2)), W/m^3."""
+    q = np.zeros(len(xyz))
+    for s in sources:
+        r2 = np.sum((xyz - np.asarray(s.x0)) ** 2, axis=1)
+        q += s.peak * np.exp(-r2 / (2.0 * s.sigma ** 2))
+    return q
+
+
+class Oracle:
+    """Plain FP64 global-matrix stepper for one :class:`synth.problem.Problem`."""
+
+    def __init__(self, problem):
+        p = problem
+        self.p = p
+        N = p.n_nodes
+        self.N = N
+        self.conn = np.asarray(p.conn, dtype=np.int64)
+        self.A_e, self.det_e, self.V_e = element_matrices(p.elem_type, p.xyz, self.conn)
+        self.V = lumped_volumes(self.conn, self.V_e, N)
+        self.hA = p.conv_h * lumped_face_areas(p.xyz, np.asarray(p.conv_faces, dtype=np.int64), N)
+        self.beta = p.perfusion.w_b * p.perfusion.c_b * self.V
+        qr = gaussian_density(p.xyz, p.sources)
+        if p.q_r is not None:
+            qr = qr + np.asarray(p.q_r, dtype=np.float64)
+        self.Q = self.V * (p.perfusion.Q_m + qr)
+        if len(p.flux_nodes):
+            np.add.at(self.Q, np.asarray(p.flux_nodes, dtype=np.int64), np.asarray(p.flux_q, dtype=np.float64))
+        self.free = np.ones(N, dtype=bool)
+        self.free[np.asarray(p.dirichlet_nodes, dtype=np.int64)] = False
+        # sparsity pattern of K: one entry per (row, col) pair met in any element
+        nv = self.conn.shape[1]
+        rows = np.repeat(self.conn, nv, axis=1).ravel()
+        cols = np.tile(self.conn, (1, nv)).ravel()
+        key = rows * N + cols
+        uniq, self._slot = np.unique(key, return_inverse=True)
+        self._rows = uniq // N
+        self._cols = uniq % N
+        self.indptr = np.searchsorted(self._rows, np.arange(N + 1))
+
+    # --- material laws (linear in T, Section 3.1.6) -------------------------
+    def k_of(self, T):
+        m = self.p.material
+        return m.k0 + m.dk * (T - m.T_ref)
+
+    def rho_of(self, T):
+        m = self.p.material
+        return m.rho0 + m.drho * (T - m.T_ref)
+
+    def c_of(self, T):
+        m = self.p.material
+        return m.c0 + m.dc * (T - m.T_ref)
+
+    # --- Eq. 11 and Eq. 13: global conduction matrix at the current field ---
+    def element_conductivity(self, T):
+        return self.k_of(T)[self.conn].mean(axis=1)
+
+    def assemble_K(self, k_e) -> sp.csr_matrix:
+        vals = (k_e[:, None, None] * self.A_e).ravel()
+        data = np.bincount(self._slot, weights=vals, minlength=len(self._rows))
+        return sp.csr_matrix((data, self._cols, self.indptr), shape=(self.N, self.N))
+
+    def conduction_load(self, K: sp.csr_matrix, T) -> np.ndarray:
+        """(K T)_i evaluated row by row as sum_j K_ij (T_j - T_i)."""
+        contrib = K.data * (T[self._cols] - T[self._rows])
+        return np.bincount(self._rows, weights=contrib, minlength=self.N)
+
+    def initial_field(self) -> np.ndarray:
+        T = self.p.T0_array()
+        if len(self.p.dirichlet_nodes):
+            T[np.asarray(self.p.dirichlet_nodes, dtype=np.int64)] = self.p.dirichlet_T
+        return T
+
+    def rate(self, T) -> np.ndarray:
+        """R = -K(T) T + beta (T_a - T) + Q + hA (T_inf - T)  (W per node)."""
+        K = self.assemble_K(self.element_conductivity(T))
+        F = self.conduction_load(K, T)
+        pf = self.p.perfusion
+        return -F + self.beta * (pf.T_a - T) + self.Q + self.hA * (self.p.conv_T_inf - T)
+
+    def capacitance(self, T) -> np.ndarray:
+        return self.V * self.rho_of(T) * self.c_of(T)
+
+    def step(self, T, dt: float) -> np.ndarray:
+        """One explicit Euler step (Eq. 6, Eq. 8) with lumped C."""
+        Tn = T + dt * self.rate(T) / self.capacitance(T)
+        Tn[~self.free] = T[~self.free]
+        return Tn
+
+    def run(self, dt: float, n_steps: int, T=None) -> np.ndarray:
+        T = self.initial_field() if T is None else np.array(T, dtype=np.float64)
+        for _ in range(n_steps):
+            T = self.step(T, dt)
+        return T
