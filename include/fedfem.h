@@ -1,0 +1,233 @@
+/*
+ * fedfem.h -- C ABI of the GB300 FED-FEM Pennes bio-heat library.
+ *
+ * The library advances the Pennes bio-heat equation (Eq. 1, constant
+ * properties; Eq. 2, temperature-dependent properties) on an unstructured mesh
+ * of one-point hexahedra (Eq. 14) or linear tetrahedra (Eq. 15) with the fast
+ * explicit dynamics scheme of Zhang & Chauhan (arXiv:1909.05098): forward Euler
+ * in time (Eq. 6), element-level conduction loads F_e = k_e A_e T_e from
+ * pre-computed element matrices (Eq. 12-17, k_e by Eq. 13), lumped capacitance
+ * and perfusion (Section 2.3.4-2.3.5) and the nodal update of Eq. 19, below the
+ * critical step of Eq. 9.  Call order follows Algorithm 1:
+ *
+ *   fedfem_create -> fedfem_set_* (load mesh and boundary conditions, Alg. 1
+ *   pre-computation) -> fedfem_precompute (A_e, lumped C, K_b, Q_b, dt_cr)
+ *   -> fedfem_init (T0, Alg. 1 initialisation) -> fedfem_step(n) (the time
+ *   loop) -> fedfem_sync / fedfem_read_temperature.
+ *
+ * Conventions for every call:
+ *  - The return value is a fedfem_status; 0 (FEDFEM_OK) is success.  On any
+ *    other value fedfem_last_error() holds a one-line message and the context
+ *    is unchanged unless stated.
+ *  - Array inputs are host pointers and are COPIED before the call returns;
+ *    the caller keeps ownership.  Output arrays are caller-allocated host
+ *    buffers, except in the *_device calls, which take device pointers on the
+ *    context's device.
+ *  - Node and element indices at this boundary are 0-based and always refer
+ *    to the caller's input order; the library's internal reordering is never
+ *    visible.
+ *  - Units are SI, temperatures in degrees Celsius; w_b is the perfusion rate
+ *    in kg/(m^3 s) as in Eq. 1.
+ *  - All device work is issued on the context's CUDA stream.  fedfem_step is
+ *    asynchronous; every other call that touches the device returns after its
+ *    work has completed.
+ *  - A context is used by one host thread at a time.
+ *  - The library owns all device memory it allocates and frees it in
+ *    fedfem_destroy.
+ */
+#ifndef FEDFEM_H
+#define FEDFEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fedfem_ctx fedfem_ctx;
+
+typedef enum {
+    FEDFEM_OK = 0,
+    FEDFEM_E_ARG = -1,          /* invalid argument (null pointer, bad size, bad index, NaN) */
+    FEDFEM_E_MESH = -2,         /* element with det J <= 0, or a node used by no element */
+    FEDFEM_E_STATE = -3,        /* call out of order (e.g. step before init) */
+    FEDFEM_E_UNSTABLE_DT = -4,  /* dt >= the critical step of Eq. 9 */
+    FEDFEM_E_RANGE = -5,        /* T left [T_lo, T_hi] or became NaN; rho c or k not positive on the range */
+    FEDFEM_E_TIMEOUT = -6,      /* a bounded device wait (grid barrier) gave up */
+    FEDFEM_E_CUDA = -7,         /* CUDA runtime error */
+    FEDFEM_E_OOM = -8,          /* device allocation failed */
+    FEDFEM_E_UNSUPPORTED = -9   /* option not available for this element type / precision */
+} fedfem_status;
+
+enum { FEDFEM_TET4 = 4, FEDFEM_HEX8 = 8 };
+
+/* Arithmetic of the time loop.  Pre-computation is always FP64. */
+enum {
+    FEDFEM_FP64 = 0,        /* FP64 state and arithmetic */
+    FEDFEM_FP32_KAHAN = 1,  /* FP32 loads and arithmetic, state kept as an FP32 pair
+                               (hi, lo) updated by compensated (Kahan) summation */
+    FEDFEM_FP32_PLAIN = 2   /* FP32 state without compensation (a negative control) */
+};
+
+/* Internal element order; the node order follows by first touch. */
+enum { FEDFEM_ORDER_INPUT = 0, FEDFEM_ORDER_MORTON = 1, FEDFEM_ORDER_RCM = 2 };
+
+/* Time-loop kernel family.  All give bit-identical results. */
+enum {
+    FEDFEM_KERNEL_TWO_PHASE = 0,   /* one element launch and one node launch per step */
+    FEDFEM_KERNEL_PERSISTENT = 1,  /* one cooperative launch for n steps, bounded grid barriers */
+    FEDFEM_KERNEL_TILED = 2        /* persistent, node tiles with their elements staged in shared memory */
+};
+
+/* Linear laws p(T) = p0 + dp (T - T_ref) for density rho [kg/m^3], specific
+ * heat c [J/(kg K)] and conductivity k [W/(m K)] (Eq. 2; Section 3.1.6 uses
+ * this linear form between two temperatures).  Constant properties: dp = 0. */
+typedef struct { double T_ref, rho0, drho, c0, dc, k0, dk; } fedfem_material;
+
+/* Perfusion rate w_b [kg/(m^3 s)], blood specific heat c_b [J/(kg K)],
+ * arterial temperature T_a [degC] and metabolic heat Q_m [W/m^3] (Eq. 1). */
+typedef struct { double w_b, c_b, T_a, Q_m; } fedfem_perfusion;
+
+/* Launch knobs (chosen by the autotuner).  Results do not depend on them. */
+typedef struct {
+    int kernel;        /* FEDFEM_KERNEL_* */
+    int block;         /* threads per block: 64..1024, multiple of 32 (0 = default) */
+    int tile_nodes;    /* TILED: owned nodes per tile, multiple of 32 (0 = default) */
+    int blocks_per_sm; /* PERSISTENT/TILED: resident blocks per SM (0 = occupancy maximum) */
+} fedfem_tile;
+
+/* Read-only facts about a pre-computed context. */
+typedef struct {
+    int64_t n_nodes, n_elems, n_free, n_dirichlet, n_convective;
+    int elem_type, precision, order;
+    double dt_cr;              /* critical step of Eq. 9 over [T_lo, T_hi] */
+    double lambda_max_ref;     /* largest eigenvalue at reference properties */
+    double td_scale;           /* factor applied for temperature-dependent laws */
+    double dt_element_bound;   /* conservative step from element eigenvalue bounds */
+    int lanczos_iterations;
+    int64_t steps_done;        /* steps completed since fedfem_init */
+    double sim_time;           /* simulated seconds since fedfem_init */
+    int64_t device_bytes;      /* device memory held by the context */
+    int64_t bytes_per_step;    /* bytes the chosen kernel reads and writes per time step (model) */
+    int64_t algorithmic_bytes_per_step; /* minimum bytes any step must move (fused model) */
+    int sm_count, grid_blocks, block_threads;
+} fedfem_info;
+
+/* Create a context on CUDA device `device`.  `precision` is a FEDFEM_FP*
+ * value.  `cuda_stream` is a cudaStream_t to issue work on, or NULL for a
+ * stream owned by the context.  *out receives the context (NULL on error). */
+int fedfem_create(fedfem_ctx** out, int device, int precision, void* cuda_stream);
+
+/* Mesh (Algorithm 1, pre-computation line 1).  xyz: n_nodes x 3 doubles,
+ * metres, row-major.  conn: n_elems x elem_type 0-based node ids, row-major.
+ * hex8 (Eq. 14): corners at natural coordinates (-1,-1,-1), (1,-1,-1),
+ * (1,1,-1), (-1,1,-1), then the same four at zeta = +1, det J > 0.
+ * tet4 (Eq. 15): det[x1-x0, x2-x0, x3-x0] > 0.  Every node must be used by
+ * an element.  Replaces any earlier mesh and clears boundary conditions,
+ * sources and the pre-computation. */
+int fedfem_set_mesh(fedfem_ctx* ctx, int elem_type, int64_t n_nodes, const double* xyz,
+                    int64_t n_elems, const int32_t* conn);
+
+/* Element order used internally (FEDFEM_ORDER_*; default MORTON). */
+int fedfem_set_order(fedfem_ctx* ctx, int order);
+
+/* Homogeneous tissue laws (Eq. 2). */
+int fedfem_set_material(fedfem_ctx* ctx, const fedfem_material* m);
+
+/* Perfusion and metabolism (Eq. 1); K_b and Q_b are lumped (Section 2.3.5). */
+int fedfem_set_perfusion(fedfem_ctx* ctx, const fedfem_perfusion* p);
+
+/* Regional source density Q_r at every node [W/m^3] (Eq. 1), n_nodes values,
+ * or NULL to clear.  Adds to any Gaussian sources. */
+int fedfem_set_source(fedfem_ctx* ctx, const double* q_r);
+
+/* Add Q_r(x) = peak exp(-|x - x0|^2 / (2 sigma^2)) [W/m^3]. */
+int fedfem_add_gaussian_source(fedfem_ctx* ctx, const double x0[3], double sigma, double peak);
+
+/* Remove all Gaussian sources. */
+int fedfem_clear_sources(fedfem_ctx* ctx);
+
+/* Essential boundary (Eq. 3): n nodes held at T (degC) from fedfem_init on.
+ * A node listed twice takes its last value.  Dirichlet wins over every other
+ * condition on the same node. */
+int fedfem_set_dirichlet(fedfem_ctx* ctx, int64_t n, const int32_t* nodes, const double* T);
+
+/* Film condition on boundary faces: q = h (T_inf - T), lumped to nodes with
+ * each face's area split equally over its nverts (3 or 4) nodes, explicit at
+ * the current T.  faces: n_faces x nverts node ids. */
+int fedfem_set_convective(fedfem_ctx* ctx, int64_t n_faces, int nverts, const int32_t* faces,
+                          double h, double T_inf);
+
+/* Concentrated nodal heat flows q [W] (heat-flux boundary of Eq. 4 as the
+ * paper applies it).  Repeated nodes add. */
+int fedfem_set_nodal_flux(fedfem_ctx* ctx, int64_t n, const int32_t* nodes, const double* q_W);
+
+/* Pre-computation (Algorithm 1, lines 2-6) in FP64 on the GPU: element
+ * geometry and A_e (Eq. 16), lumped volumes, perfusion and source loads, face
+ * areas, and the critical step of Eq. 9 for properties anywhere in
+ * [T_lo, T_hi].  Writes dt_cr to *dt_cr_out (may be NULL).  Returns
+ * FEDFEM_E_MESH on an element with det J <= 0, FEDFEM_E_RANGE if rho c or k
+ * is not positive on the range. */
+int fedfem_precompute(fedfem_ctx* ctx, double T_lo, double T_hi, double* dt_cr_out);
+
+/* Initial field (Algorithm 1, line 7): T0 has n_nodes values in input order,
+ * or is NULL for T0_uniform everywhere.  Dirichlet nodes take their values.
+ * Clears the device status and the step counter. */
+int fedfem_init(fedfem_ctx* ctx, const double* T0, double T0_uniform);
+
+/* As fedfem_init, T0 a device pointer to n_nodes doubles (input order). */
+int fedfem_init_device(fedfem_ctx* ctx, const double* T0_dev);
+
+/* Advance n_steps explicit steps of size dt (Algorithm 1, lines 8-15),
+ * asynchronously.  FEDFEM_E_UNSTABLE_DT if dt >= dt_cr.  A range violation
+ * or barrier timeout stops the loop on the device and is reported by
+ * fedfem_sync. */
+int fedfem_step(fedfem_ctx* ctx, double dt, int64_t n_steps);
+
+/* Wait for the context's stream; *steps_done (may be NULL) receives the steps
+ * completed since init.  Returns FEDFEM_E_RANGE or FEDFEM_E_TIMEOUT if the
+ * device recorded one (sticky until the next init or set_state). */
+int fedfem_sync(fedfem_ctx* ctx, int64_t* steps_done);
+
+/* Nodal temperatures (n_nodes doubles, input order).  FP32 states return
+ * (double)hi + (double)lo. */
+int fedfem_read_temperature(fedfem_ctx* ctx, double* out);
+
+/* As fedfem_read_temperature into a device buffer of n_nodes doubles. */
+int fedfem_read_temperature_device(fedfem_ctx* ctx, double* out_dev);
+
+/* Checkpoint: with buf == NULL, *bytes receives the size needed.  Otherwise
+ * the state (temperature pair, step counter, simulated time) is written to
+ * buf (capacity *bytes).  Restoring it with fedfem_set_state into a context
+ * with the same mesh, options and precision resumes bit-identically. */
+int fedfem_get_state(fedfem_ctx* ctx, void* buf, size_t* bytes);
+int fedfem_set_state(fedfem_ctx* ctx, const void* buf, size_t bytes);
+
+/* Launch knobs; see fedfem_tile.  May be called after precompute. */
+int fedfem_set_tile(fedfem_ctx* ctx, const fedfem_tile* tile);
+
+/* Facts about the context (after precompute). */
+int fedfem_get_info(fedfem_ctx* ctx, fedfem_info* info);
+
+/* Last error message of this context ("" if none).  Valid until the next call. */
+const char* fedfem_last_error(const fedfem_ctx* ctx);
+
+/* Free everything the context holds.  NULL is allowed. */
+void fedfem_destroy(fedfem_ctx* ctx);
+
+/* Library version string. */
+const char* fedfem_version(void);
+
+/* Testing hooks (the paper has no counterpart).  key 1: barrier spin limit in
+ * clock64 ticks for later fedfem_step calls (default 4e9, or the environment
+ * variable FEDFEM_BARRIER_SPIN_LIMIT).  key 2: index of a block that never
+ * arrives at the grid barrier from the next fedfem_init on (-1: none); the
+ * other blocks then give up after the spin limit and fedfem_sync returns
+ * FEDFEM_E_TIMEOUT.  Used to test the bounded waits without faulting. */
+int fedfem_debug_set(fedfem_ctx* ctx, int key, int64_t value);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FEDFEM_H */

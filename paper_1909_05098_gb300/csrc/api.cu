@@ -1,0 +1,716 @@
+// C ABI of the FED-FEM library: context, input validation, device memory and
+// the order of Algorithm 1 (pre-computation, initialisation, time loop).
+#include <algorithm>
+#include <array>
+#include <climits>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "fedfem_internal.h"
+
+using namespace fedfem;
+
+struct fedfem_ctx {
+    int device = 0;
+    int precision = FEDFEM_FP32_KAHAN;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::string err;
+    // ---- inputs (copies) ----
+    bool has_mesh = false, has_mat = false;
+    int nv = 0;
+    int64_t N = 0, E = 0;
+    std::vector<double> xyz;
+    std::vector<int32_t> conn;
+    int order = FEDFEM_ORDER_MORTON;
+    fedfem_material mat{};
+    fedfem_perfusion perf{0.0, 0.0, 37.0, 0.0};
+    std::vector<double> qr;                       // empty: none
+    std::vector<std::array<double, 5>> sources;   // x0 y0 z0 sigma peak
+    std::vector<char> is_dir;
+    std::vector<double> dir_T;
+    std::vector<int32_t> conv_faces;
+    int conv_nv = 0;
+    double conv_h = 0.0, conv_Tinf = 0.0;
+    std::vector<double> flux;                     // empty: none
+    fedfem_tile tile{FEDFEM_KERNEL_PERSISTENT, 256, 0, 0};
+    // ---- pre-computed ----
+    bool pre = false, inited = false;
+    Layout L;
+    double T_lo = 0, T_hi = 0, dt_cr = 0, lambda = 0, td_scale = 1;
+    int lz_iters = 0;
+    // ---- device ----
+    std::vector<void*> allocs;
+    int64_t dev_bytes = 0;
+    int4* conn4 = nullptr;
+    double* M64 = nullptr;
+    float* M32 = nullptr;
+    int32_t *sell_off = nullptr, *sell_ids = nullptr;
+    double *V64 = nullptr, *Q64 = nullptr, *hA64 = nullptr;
+    float *V32 = nullptr, *Q32 = nullptr, *hA32 = nullptr;
+    void* T = nullptr;
+    float* Tlo = nullptr;
+    void* slots = nullptr;
+    int32_t* node_of = nullptr;
+    double* T_dir = nullptr;
+    double* io = nullptr;
+    DevStatus* st = nullptr;
+    int sm_count = 0;
+    long long spin_limit = 4000000000LL;
+    int skip_block = -1;
+    int64_t steps_issued = 0;
+    double sim_time = 0.0;
+    LaunchCfg last{};
+};
+
+namespace {
+
+int fail(fedfem_ctx* c, int code, const std::string& msg) {
+    if (c) c->err = msg;
+    return code;
+}
+
+int cuda_fail(fedfem_ctx* c, cudaError_t e, const char* what) {
+    return fail(c, e == cudaErrorMemoryAllocation ? FEDFEM_E_OOM : FEDFEM_E_CUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CU(call, what)                                   \
+    do {                                                 \
+        cudaError_t _e = (call);                         \
+        if (_e != cudaSuccess) return cuda_fail(c, _e, what); \
+    } while (0)
+
+void free_device(fedfem_ctx* c) {
+    for (void* p : c->allocs) cudaFree(p);
+    c->allocs.clear();
+    c->dev_bytes = 0;
+    c->conn4 = nullptr; c->M64 = nullptr; c->M32 = nullptr; c->sell_off = c->sell_ids = nullptr;
+    c->V64 = c->Q64 = c->hA64 = nullptr; c->V32 = c->Q32 = c->hA32 = nullptr;
+    c->T = nullptr; c->Tlo = nullptr; c->slots = nullptr; c->node_of = nullptr; c->T_dir = nullptr;
+    c->io = nullptr; c->st = nullptr;
+    c->pre = false;
+    c->inited = false;
+}
+
+template <typename P>
+cudaError_t dalloc(fedfem_ctx* c, P** p, size_t bytes) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, std::max<size_t>(bytes, 16));
+    if (e != cudaSuccess) return e;
+    c->allocs.push_back(q);
+    c->dev_bytes += (int64_t)bytes;
+    *p = (P*)q;
+    return cudaSuccess;
+}
+
+void release(fedfem_ctx* c, void* p, size_t bytes) {
+    if (!p) return;
+    auto it = std::find(c->allocs.begin(), c->allocs.end(), p);
+    if (it != c->allocs.end()) { cudaFree(p); c->allocs.erase(it); c->dev_bytes -= (int64_t)bytes; }
+}
+
+void invalidate(fedfem_ctx* c) {
+    c->pre = false;
+    c->inited = false;
+}
+
+bool is_finite(double v) { return std::isfinite(v); }
+
+// s = max(1, max k/k0) * max(1, max rho0 c0 / (rho c)) over [lo, hi]; rho c is
+// quadratic in T, so its minimum is at an end point or the vertex.
+int property_scale(fedfem_ctx* c, double lo, double hi, double* s_out) {
+    const fedfem_material& m = c->mat;
+    auto k = [&](double T) { return m.k0 + m.dk * (T - m.T_ref); };
+    auto rc = [&](double T) { return (m.rho0 + m.drho * (T - m.T_ref)) * (m.c0 + m.dc * (T - m.T_ref)); };
+    if (!(k(lo) > 0 && k(hi) > 0)) return fail(c, FEDFEM_E_RANGE, "k(T) is not positive on [T_lo, T_hi]");
+    double rc_min = std::min(rc(lo), rc(hi));
+    const double qa = m.drho * m.dc;
+    if (qa != 0.0) {
+        const double u = -(m.rho0 * m.dc + m.c0 * m.drho) / (2.0 * qa);
+        if (lo < m.T_ref + u && m.T_ref + u < hi) rc_min = std::min(rc_min, rc(m.T_ref + u));
+    }
+    if (!(rc_min > 0)) return fail(c, FEDFEM_E_RANGE, "rho(T) c(T) is not positive on [T_lo, T_hi]");
+    const double kmax = std::max(k(lo), k(hi));
+    *s_out = std::max(1.0, kmax / m.k0) * std::max(1.0, m.rho0 * m.c0 / rc_min);
+    return FEDFEM_OK;
+}
+
+int reset_status(fedfem_ctx* c) {
+    DevStatus h{};
+    h.flags = 0;
+    h.skip_barrier_block = c->skip_block;
+    h.fail_node = LLONG_MAX;
+    h.fail_step = LLONG_MAX;
+    h.barrier = 0;
+    h.steps_done = 0;
+    CU(cudaMemcpyAsync(c->st, &h, sizeof(h), cudaMemcpyHostToDevice, c->stream), "status reset");
+    CU(cudaStreamSynchronize(c->stream), "status reset");
+    return FEDFEM_OK;
+}
+
+template <typename R>
+StepArgs<R> make_args(fedfem_ctx* c, const R* M, const R* V, const R* Q, const R* hA, double dt) {
+    StepArgs<R> a{};
+    a.E = c->E; a.N = c->N; a.N_plain = c->L.N_plain; a.N_free = c->L.N_free;
+    a.conn4 = c->conn4; a.M = M; a.slots = (R*)c->slots;
+    a.sell_off = c->sell_off; a.sell_ids = c->sell_ids;
+    a.V = V; a.Q = Q; a.hA = hA;
+    a.T = (R*)c->T; a.Tlo = (R*)c->Tlo;
+    a.T_ref = (R)c->mat.T_ref; a.rho0 = (R)c->mat.rho0; a.drho = (R)c->mat.drho;
+    a.c0 = (R)c->mat.c0; a.dc = (R)c->mat.dc; a.k0 = (R)c->mat.k0; a.dk = (R)c->mat.dk;
+    a.wbcb = (R)(c->perf.w_b * c->perf.c_b); a.T_a = (R)c->perf.T_a; a.T_inf = (R)c->conv_Tinf;
+    a.dt = (R)dt; a.T_lo = (R)c->T_lo; a.T_hi = (R)c->T_hi;
+    a.status = c->st;
+    a.step0 = c->steps_issued;
+    return a;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* fedfem_version(void) { return "fedfem-gb300 0.1 (sm_103a)"; }
+
+int fedfem_create(fedfem_ctx** out, int device, int precision, void* cuda_stream) {
+    if (!out) return FEDFEM_E_ARG;
+    *out = nullptr;
+    if (precision < FEDFEM_FP64 || precision > FEDFEM_FP32_PLAIN) return FEDFEM_E_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return FEDFEM_E_CUDA;
+    if (cudaSetDevice(device) != cudaSuccess) return FEDFEM_E_CUDA;
+    int major = 0, minor = 0, coop = 0, sms = 0;
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, device);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, device);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    if (major != 10 || minor != 3 || !coop) return FEDFEM_E_UNSUPPORTED;
+    fedfem_ctx* c = new fedfem_ctx();
+    c->device = device;
+    c->precision = precision;
+    c->sm_count = sms;
+    if (const char* s = std::getenv("FEDFEM_BARRIER_SPIN_LIMIT")) c->spin_limit = std::max(1000LL, std::atoll(s));
+    if (cuda_stream) {
+        c->stream = (cudaStream_t)cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) { delete c; return FEDFEM_E_CUDA; }
+        c->own_stream = true;
+    }
+    *out = c;
+    return FEDFEM_OK;
+}
+
+void fedfem_destroy(fedfem_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    free_device(c);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+const char* fedfem_last_error(const fedfem_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int fedfem_set_mesh(fedfem_ctx* c, int elem_type, int64_t n_nodes, const double* xyz, int64_t n_elems,
+                    const int32_t* conn) {
+    if (!c) return FEDFEM_E_ARG;
+    if (elem_type != FEDFEM_HEX8 && elem_type != FEDFEM_TET4) return fail(c, FEDFEM_E_ARG, "elem_type must be 4 or 8");
+    if (n_nodes <= 0 || n_elems <= 0 || !xyz || !conn) return fail(c, FEDFEM_E_ARG, "empty mesh or null array");
+    if (n_nodes >= INT32_MAX) return fail(c, FEDFEM_E_ARG, "n_nodes must fit in int32");
+    for (int64_t i = 0; i < 3 * n_nodes; ++i)
+        if (!is_finite(xyz[i])) return fail(c, FEDFEM_E_ARG, "non-finite coordinate");
+    for (int64_t i = 0; i < n_elems * elem_type; ++i)
+        if (conn[i] < 0 || conn[i] >= n_nodes)
+            return fail(c, FEDFEM_E_MESH, "element " + std::to_string(i / elem_type) + " has a node id out of range");
+    c->nv = elem_type; c->N = n_nodes; c->E = n_elems;
+    c->xyz.assign(xyz, xyz + 3 * n_nodes);
+    c->conn.assign(conn, conn + n_elems * elem_type);
+    c->is_dir.assign(n_nodes, 0);
+    c->dir_T.assign(n_nodes, 0.0);
+    c->conv_faces.clear(); c->conv_nv = 0; c->conv_h = 0; c->conv_Tinf = 0;
+    c->flux.clear(); c->qr.clear(); c->sources.clear();
+    c->has_mesh = true;
+    free_device(c);
+    c->err.clear();
+    return FEDFEM_OK;
+}
+
+int fedfem_set_order(fedfem_ctx* c, int order) {
+    if (!c) return FEDFEM_E_ARG;
+    if (order < FEDFEM_ORDER_INPUT || order > FEDFEM_ORDER_RCM) return fail(c, FEDFEM_E_ARG, "unknown order");
+    c->order = order;
+    invalidate(c);
+    return FEDFEM_OK;
+}
+
+int fedfem_set_material(fedfem_ctx* c, const fedfem_material* m) {
+    if (!c || !m) return fail(c, FEDFEM_E_ARG, "null material");
+    const double v[7] = {m->T_ref, m->rho0, m->drho, m->c0, m->dc, m->k0, m->dk};
+    for (double x : v)
+        if (!is_finite(x)) return fail(c, FEDFEM_E_ARG, "non-finite material value");
+    if (!(m->rho0 > 0 && m->c0 > 0 && m->k0 > 0)) return fail(c, FEDFEM_E_ARG, "rho0, c0 and k0 must be positive");
+    c->mat = *m;
+    c->has_mat = true;
+    invalidate(c);
+    return FEDFEM_OK;
+}
+
+int fedfem_set_perfusion(fedfem_ctx* c, const fedfem_perfusion* p) {
+    if (!c || !p) return fail(c, FEDFEM_E_ARG, "null perfusion");
+    if (!(is_finite(p->w_b) && is_finite(p->c_b) && is_finite(p->T_a) && is_finite(p->Q_m)) || p->w_b < 0 || p->c_b < 0)
+        return fail(c, FEDFEM_E_ARG, "perfusion values must be finite, w_b and c_b non-negative");
+    c->perf = *p;
+    invalidate(c);
+    return FEDFEM_OK;
+}
+
+int fedfem_set_source(fedfem_ctx* c, const double* q_r) {
+    if (!c) return FEDFEM_E_ARG;
+    if (!c->has_mesh) return fail(c, FEDFEM_E_STATE, "set_mesh first");
+    if (!q_r) { c->qr.clear(); invalidate(c); return FEDFEM_OK; }
+    for (int64_t i = 0; i < c->N; ++i)
+        if (!is_finite(q_r[i])) return fail(c, FEDFEM_E_ARG, "non-finite source density");
+    c->qr.assign(q_r, q_r + c->N);
+    invalidate(c);
+    return FEDFEM_OK;
+}
+
+int fedfem_add_gaussian_source(fedfem_ctx* c, const double x0[3], double sigma, double peak) {
+    if (!c || !x0) return fail(c, FEDFEM_E_ARG, "null source centre");
+    if (!(is_finite(x0[0]) && is_finite(x0[1]) && is_finite(x0[2]) && is_finite(peak)) || !(sigma > 0) || !is_finite(sigma))
+        return fail(c, FEDFEM_E_ARG, "source needs a finite centre and peak and sigma > 0");
+    c->sources.push_back({x0[0], x0[1], x0[2], sigma, peak});
+    invalidate(c);
+    return FEDFEM_OK;
+}
+
+int fedfem_clear_sources(fedfem_ctx* c) {
+    if (!c) return FEDFEM_E_ARG;
+    c->sources.clear();
+    invalidate(c);
+    return FEDFEM_OK;
+}
+
+int fedfem_set_dirichlet(fedfem_ctx* c, int64_t n, const int32_t* nodes, const double* T) {
+    if (!c) return FEDFEM_E_ARG;
+    if (!c->has_mesh) return fail(c, FEDFEM_E_STATE, "set_mesh first");
+    if (n < 0 || (n > 0 && (!nodes || !T))) return fail(c, FEDFEM_E_ARG, "bad Dirichlet arrays");
+    for (int64_t i = 0; i < n; ++i) {
+        if (nodes[i] < 0 || nodes[i] >= c->N) return fail(c, FEDFEM_E_ARG, "Dirichlet node out of range");
+        if (!is_finite(T[i])) return fail(c, FEDFEM_E_ARG, "non-finite Dirichlet value");
+    }
+    std::fill(c->is_dir.begin(), c->is_dir.end(), 0);
+    for (int64_t i = 0; i < n; ++i) { c->is_dir[nodes[i]] = 1; c->dir_T[nodes[i]] = T[i]; }
+    invalidate(c);
+    return FEDFEM_OK;
+}
+
+int fedfem_set_convective(fedfem_ctx* c, int64_t n_faces, int nverts, const int32_t* faces, double h, double T_inf) {
+    if (!c) return FEDFEM_E_ARG;
+    if (!c->has_mesh) return fail(c, FEDFEM_E_STATE, "set_mesh first");
+    if (n_faces < 0 || (n_faces > 0 && (!faces || (nverts != 3 && nverts != 4))))
+        return fail(c, FEDFEM_E_ARG, "faces need 3 or 4 nodes");
+    if (!is_finite(h) || h < 0 || !is_finite(T_inf)) return fail(c, FEDFEM_E_ARG, "film h must be finite and >= 0");
+    for (int64_t i = 0; i < n_faces * nverts; ++i)
+        if (faces[i] < 0 || faces[i] >= c->N) return fail(c, FEDFEM_E_ARG, "face node out of range");
+    c->conv_faces.assign(faces, faces + n_faces * nverts);
+    c->conv_nv = n_faces > 0 ? nverts : 0;
+    c->conv_h = h;
+    c->conv_Tinf = T_inf;
+    invalidate(c);
+    return FEDFEM_OK;
+}
+
+int fedfem_set_nodal_flux(fedfem_ctx* c, int64_t n, const int32_t* nodes, const double* q_W) {
+    if (!c) return FEDFEM_E_ARG;
+    if (!c->has_mesh) return fail(c, FEDFEM_E_STATE, "set_mesh first");
+    if (n < 0 || (n > 0 && (!nodes || !q_W))) return fail(c, FEDFEM_E_ARG, "bad flux arrays");
+    for (int64_t i = 0; i < n; ++i) {
+        if (nodes[i] < 0 || nodes[i] >= c->N) return fail(c, FEDFEM_E_ARG, "flux node out of range");
+        if (!is_finite(q_W[i])) return fail(c, FEDFEM_E_ARG, "non-finite flux");
+    }
+    c->flux.assign(n > 0 ? c->N : 0, 0.0);
+    for (int64_t i = 0; i < n; ++i) c->flux[nodes[i]] += q_W[i];
+    invalidate(c);
+    return FEDFEM_OK;
+}
+
+int fedfem_set_tile(fedfem_ctx* c, const fedfem_tile* t) {
+    if (!c || !t) return fail(c, FEDFEM_E_ARG, "null tile");
+    if (t->kernel < FEDFEM_KERNEL_TWO_PHASE || t->kernel > FEDFEM_KERNEL_TILED) return fail(c, FEDFEM_E_ARG, "unknown kernel");
+    if (t->kernel == FEDFEM_KERNEL_TILED) return fail(c, FEDFEM_E_UNSUPPORTED, "tiled kernel not available in this build");
+    if (t->block != 0 && (t->block < 64 || t->block > 1024 || t->block % 32)) return fail(c, FEDFEM_E_ARG, "block must be 64..1024, multiple of 32");
+    if (t->blocks_per_sm < 0 || t->tile_nodes < 0 || t->tile_nodes % 32) return fail(c, FEDFEM_E_ARG, "bad tile knobs");
+    c->tile = *t;
+    return FEDFEM_OK;
+}
+
+int fedfem_debug_set(fedfem_ctx* c, int key, int64_t value) {
+    if (!c) return FEDFEM_E_ARG;
+    if (key == 1) { c->spin_limit = std::max<long long>(1000, value); return FEDFEM_OK; }
+    if (key == 2) { c->skip_block = (int)value; return FEDFEM_OK; }
+    return fail(c, FEDFEM_E_ARG, "unknown debug key");
+}
+
+int fedfem_precompute(fedfem_ctx* c, double T_lo, double T_hi, double* dt_cr_out) {
+    if (!c) return FEDFEM_E_ARG;
+    if (!c->has_mesh || !c->has_mat) return fail(c, FEDFEM_E_STATE, "set_mesh and set_material first");
+    if (!(is_finite(T_lo) && is_finite(T_hi) && T_lo < T_hi)) return fail(c, FEDFEM_E_ARG, "need T_lo < T_hi");
+    double s = 1.0;
+    int rc = property_scale(c, T_lo, T_hi, &s);
+    if (rc) return rc;
+    CU(cudaSetDevice(c->device), "set device");
+    free_device(c);
+    // ---- layout (host, integer work) ----
+    MeshInput in;
+    in.nv = c->nv; in.N = c->N; in.E = c->E; in.xyz = c->xyz.data(); in.conn = c->conn.data();
+    in.is_dirichlet = &c->is_dir;
+    in.conv_faces = c->conv_nv ? &c->conv_faces : nullptr;
+    in.conv_nverts = c->conv_nv;
+    in.order = c->order;
+    bool mesh_err = false;
+    std::string m = build_layout(in, c->L, &mesh_err);
+    if (!m.empty()) return fail(c, mesh_err ? FEDFEM_E_MESH : FEDFEM_E_ARG, m);
+    const Layout& L = c->L;
+    const int64_t N = c->N, E = c->E, NF = L.N_free, NC = L.N_free - L.N_plain;
+    const int nv = c->nv;
+    cudaStream_t st = c->stream;
+    // ---- device arrays ----
+    std::vector<int32_t> c4((size_t)E * nv);
+    for (int p = 0; p < nv / 4; ++p)
+        for (int64_t e = 0; e < E; ++e)
+            for (int k = 0; k < 4; ++k) c4[((size_t)p * E + e) * 4 + k] = L.conn[e * nv + 4 * p + k];
+    std::vector<double> xs(N), ys(N), zs(N);
+    for (int64_t i = 0; i < N; ++i) {
+        const int64_t o = L.node_of[i];
+        xs[i] = c->xyz[3 * o]; ys[i] = c->xyz[3 * o + 1]; zs[i] = c->xyz[3 * o + 2];
+    }
+    double *x = nullptr, *y = nullptr, *z = nullptr, *Vshare = nullptr, *face_share = nullptr, *qr = nullptr,
+           *flux = nullptr, *src = nullptr;
+    int32_t *faces = nullptr, *conv_off = nullptr, *conv_face = nullptr;
+    int* bad = nullptr;
+    CU(dalloc(c, &c->conn4, sizeof(int32_t) * E * nv), "alloc");
+    CU(dalloc(c, &x, sizeof(double) * N), "alloc");
+    CU(dalloc(c, &y, sizeof(double) * N), "alloc");
+    CU(dalloc(c, &z, sizeof(double) * N), "alloc");
+    CU(dalloc(c, &c->M64, sizeof(double) * 6 * E), "alloc");
+    CU(dalloc(c, &Vshare, sizeof(double) * (E + 1)), "alloc");
+    CU(dalloc(c, &bad, sizeof(int)), "alloc");
+    CU(dalloc(c, &c->sell_off, sizeof(int32_t) * L.sell_off.size()), "alloc");
+    CU(dalloc(c, &c->sell_ids, sizeof(int32_t) * L.sell_ids.size()), "alloc");
+    CU(dalloc(c, &c->V64, sizeof(double) * NF), "alloc");
+    CU(dalloc(c, &c->Q64, sizeof(double) * NF), "alloc");
+    CU(dalloc(c, &c->hA64, sizeof(double) * NC), "alloc");
+    CU(dalloc(c, &c->node_of, sizeof(int32_t) * N), "alloc");
+    CU(dalloc(c, &c->T_dir, sizeof(double) * (N - NF)), "alloc");
+    CU(dalloc(c, &c->io, sizeof(double) * N), "alloc");
+    CU(dalloc(c, &c->st, sizeof(DevStatus)), "alloc");
+    CU(cudaMemcpyAsync(c->conn4, c4.data(), sizeof(int32_t) * E * nv, cudaMemcpyHostToDevice, st), "copy");
+    CU(cudaMemcpyAsync(x, xs.data(), sizeof(double) * N, cudaMemcpyHostToDevice, st), "copy");
+    CU(cudaMemcpyAsync(y, ys.data(), sizeof(double) * N, cudaMemcpyHostToDevice, st), "copy");
+    CU(cudaMemcpyAsync(z, zs.data(), sizeof(double) * N, cudaMemcpyHostToDevice, st), "copy");
+    CU(cudaMemcpyAsync(c->sell_off, L.sell_off.data(), sizeof(int32_t) * L.sell_off.size(), cudaMemcpyHostToDevice, st), "copy");
+    CU(cudaMemcpyAsync(c->sell_ids, L.sell_ids.data(), sizeof(int32_t) * L.sell_ids.size(), cudaMemcpyHostToDevice, st), "copy");
+    CU(cudaMemcpyAsync(c->node_of, L.node_of.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice, st), "copy");
+    {
+        std::vector<double> td(N - NF);
+        for (int64_t i = NF; i < N; ++i) td[i - NF] = c->dir_T[L.node_of[i]];
+        CU(cudaMemcpyAsync(c->T_dir, td.data(), sizeof(double) * td.size(), cudaMemcpyHostToDevice, st), "copy");
+        CU(cudaStreamSynchronize(st), "copy");
+    }
+    const int bad_init = INT_MAX;
+    CU(cudaMemcpyAsync(bad, &bad_init, sizeof(int), cudaMemcpyHostToDevice, st), "copy");
+    std::vector<int32_t> fint;
+    if (c->conv_nv) {
+        fint.resize(c->conv_faces.size());
+        for (size_t i = 0; i < fint.size(); ++i) fint[i] = L.node_at[c->conv_faces[i]];
+        CU(dalloc(c, &faces, sizeof(int32_t) * fint.size()), "alloc");
+        CU(dalloc(c, &face_share, sizeof(double) * (fint.size() / c->conv_nv)), "alloc");
+        CU(cudaMemcpyAsync(faces, fint.data(), sizeof(int32_t) * fint.size(), cudaMemcpyHostToDevice, st), "copy");
+    }
+    CU(dalloc(c, &conv_off, sizeof(int32_t) * L.conv_off.size()), "alloc");
+    CU(dalloc(c, &conv_face, sizeof(int32_t) * std::max<size_t>(1, L.conv_face.size())), "alloc");
+    CU(cudaMemcpyAsync(conv_off, L.conv_off.data(), sizeof(int32_t) * L.conv_off.size(), cudaMemcpyHostToDevice, st), "copy");
+    if (!L.conv_face.empty())
+        CU(cudaMemcpyAsync(conv_face, L.conv_face.data(), sizeof(int32_t) * L.conv_face.size(), cudaMemcpyHostToDevice, st), "copy");
+    std::vector<double> qr_int, flux_int, src_h;
+    if (!c->qr.empty()) {
+        qr_int.resize(NF);
+        for (int64_t i = 0; i < NF; ++i) qr_int[i] = c->qr[L.node_of[i]];
+        CU(dalloc(c, &qr, sizeof(double) * NF), "alloc");
+        CU(cudaMemcpyAsync(qr, qr_int.data(), sizeof(double) * NF, cudaMemcpyHostToDevice, st), "copy");
+    }
+    if (!c->flux.empty()) {
+        flux_int.resize(NF);
+        for (int64_t i = 0; i < NF; ++i) flux_int[i] = c->flux[L.node_of[i]];
+        CU(dalloc(c, &flux, sizeof(double) * NF), "alloc");
+        CU(cudaMemcpyAsync(flux, flux_int.data(), sizeof(double) * NF, cudaMemcpyHostToDevice, st), "copy");
+    }
+    for (auto& sgm : c->sources) src_h.insert(src_h.end(), sgm.begin(), sgm.end());
+    CU(dalloc(c, &src, sizeof(double) * std::max<size_t>(1, src_h.size())), "alloc");
+    if (!src_h.empty())
+        CU(cudaMemcpyAsync(src, src_h.data(), sizeof(double) * src_h.size(), cudaMemcpyHostToDevice, st), "copy");
+
+    PreArgs pa{};
+    pa.nv = nv; pa.E = E; pa.N = N; pa.N_plain = L.N_plain; pa.N_free = NF;
+    pa.conn4 = c->conn4; pa.x = x; pa.y = y; pa.z = z;
+    pa.M64 = c->M64; pa.Vshare = Vshare; pa.bad_elem = bad;
+    pa.sell_off = c->sell_off; pa.sell_ids = c->sell_ids;
+    pa.V = c->V64; pa.Q = c->Q64; pa.hA = c->hA64;
+    pa.qr_node = qr; pa.flux_node = flux; pa.src = src; pa.n_src = (int)c->sources.size();
+    pa.Q_m = c->perf.Q_m;
+    pa.n_faces = c->conv_nv ? (int64_t)fint.size() / c->conv_nv : 0;
+    pa.face_nv = c->conv_nv; pa.faces = faces; pa.face_share = face_share;
+    pa.conv_off = conv_off; pa.conv_face = conv_face; pa.h_film = c->conv_h;
+    CU(launch_geometry(pa, st), "geometry kernel");
+    int bad_h = INT_MAX;
+    CU(cudaMemcpyAsync(&bad_h, bad, sizeof(int), cudaMemcpyDeviceToHost, st), "copy");
+    CU(cudaStreamSynchronize(st), "geometry kernel");
+    if (bad_h != INT_MAX) {
+        const int in_e = L.elem_of[bad_h];
+        free_device(c);
+        return fail(c, FEDFEM_E_MESH, "element " + std::to_string(in_e) + " has det J <= 0 (inverted or degenerate)");
+    }
+    CU(launch_nodal(pa, st), "nodal kernel");
+    CU(cudaStreamSynchronize(st), "nodal kernel");
+    LanczosResult lr;
+    std::string lm = lanczos_lambda_max(pa, c->mat.k0, c->mat.rho0 * c->mat.c0, c->perf.w_b * c->perf.c_b,
+                                        3000, 1e-14, lr, st);
+    if (!lm.empty()) return fail(c, FEDFEM_E_CUDA, lm);
+    c->lambda = lr.lambda;
+    c->lz_iters = lr.iterations;
+    c->td_scale = s;
+    c->T_lo = T_lo; c->T_hi = T_hi;
+    c->dt_cr = lr.lambda > 0 ? 2.0 / (s * lr.lambda) : INFINITY;
+    // ---- time-loop arrays ----
+    if (c->precision == FEDFEM_FP64) {
+        CU(dalloc(c, (double**)&c->T, sizeof(double) * N), "alloc");
+        CU(dalloc(c, (double**)&c->slots, sizeof(double) * (E * nv + 1)), "alloc");
+        CU(cudaMemsetAsync(c->slots, 0, sizeof(double) * (E * nv + 1), st), "memset");
+    } else {
+        CU(dalloc(c, &c->M32, sizeof(float) * 6 * E), "alloc");
+        CU(dalloc(c, &c->V32, sizeof(float) * NF), "alloc");
+        CU(dalloc(c, &c->Q32, sizeof(float) * NF), "alloc");
+        CU(dalloc(c, &c->hA32, sizeof(float) * NC), "alloc");
+        CU(launch_to_f32(c->M64, c->M32, 6 * E, st), "convert");
+        CU(launch_to_f32(c->V64, c->V32, NF, st), "convert");
+        CU(launch_to_f32(c->Q64, c->Q32, NF, st), "convert");
+        CU(launch_to_f32(c->hA64, c->hA32, NC, st), "convert");
+        CU(dalloc(c, (float**)&c->T, sizeof(float) * N), "alloc");
+        CU(dalloc(c, &c->Tlo, sizeof(float) * N), "alloc");
+        CU(dalloc(c, (float**)&c->slots, sizeof(float) * (E * nv + 1)), "alloc");
+        CU(cudaMemsetAsync(c->slots, 0, sizeof(float) * (E * nv + 1), st), "memset");
+    }
+    CU(cudaStreamSynchronize(st), "precompute");
+    // pre-computation scratch no longer needed
+    release(c, x, sizeof(double) * N); release(c, y, sizeof(double) * N); release(c, z, sizeof(double) * N);
+    release(c, Vshare, sizeof(double) * (E + 1)); release(c, bad, sizeof(int));
+    release(c, faces, sizeof(int32_t) * fint.size());
+    release(c, face_share, sizeof(double) * (fint.size() / std::max(1, c->conv_nv)));
+    release(c, conv_off, sizeof(int32_t) * L.conv_off.size());
+    release(c, conv_face, sizeof(int32_t) * std::max<size_t>(1, L.conv_face.size()));
+    release(c, qr, sizeof(double) * NF); release(c, flux, sizeof(double) * NF);
+    release(c, src, sizeof(double) * std::max<size_t>(1, src_h.size()));
+    if (c->precision != FEDFEM_FP64) {
+        release(c, c->M64, sizeof(double) * 6 * E); c->M64 = nullptr;
+        release(c, c->V64, sizeof(double) * NF); c->V64 = nullptr;
+        release(c, c->Q64, sizeof(double) * NF); c->Q64 = nullptr;
+        release(c, c->hA64, sizeof(double) * NC); c->hA64 = nullptr;
+    }
+    c->pre = true;
+    c->inited = false;
+    if (dt_cr_out) *dt_cr_out = c->dt_cr;
+    c->err.clear();
+    return FEDFEM_OK;
+}
+
+static int init_common(fedfem_ctx* c) {
+    CU(launch_init_state(c->precision, c->N, c->L.N_free, c->node_of, c->io, c->T_dir, c->T, c->Tlo, c->stream),
+       "init kernel");
+    int r = reset_status(c);
+    if (r) return r;
+    c->inited = true;
+    c->steps_issued = 0;
+    c->sim_time = 0.0;
+    c->err.clear();
+    return FEDFEM_OK;
+}
+
+int fedfem_init(fedfem_ctx* c, const double* T0, double T0_uniform) {
+    if (!c) return FEDFEM_E_ARG;
+    if (!c->pre) return fail(c, FEDFEM_E_STATE, "precompute first");
+    CU(cudaSetDevice(c->device), "set device");
+    if (T0) {
+        for (int64_t i = 0; i < c->N; ++i)
+            if (!is_finite(T0[i])) return fail(c, FEDFEM_E_ARG, "non-finite initial temperature");
+        CU(cudaMemcpyAsync(c->io, T0, sizeof(double) * c->N, cudaMemcpyHostToDevice, c->stream), "copy T0");
+    } else {
+        if (!is_finite(T0_uniform)) return fail(c, FEDFEM_E_ARG, "non-finite initial temperature");
+        std::vector<double> u(c->N, T0_uniform);
+        CU(cudaMemcpyAsync(c->io, u.data(), sizeof(double) * c->N, cudaMemcpyHostToDevice, c->stream), "copy T0");
+        CU(cudaStreamSynchronize(c->stream), "copy T0");
+    }
+    return init_common(c);
+}
+
+int fedfem_init_device(fedfem_ctx* c, const double* T0_dev) {
+    if (!c || !T0_dev) return fail(c, FEDFEM_E_ARG, "null T0");
+    if (!c->pre) return fail(c, FEDFEM_E_STATE, "precompute first");
+    CU(cudaSetDevice(c->device), "set device");
+    CU(cudaMemcpyAsync(c->io, T0_dev, sizeof(double) * c->N, cudaMemcpyDeviceToDevice, c->stream), "copy T0");
+    return init_common(c);
+}
+
+int fedfem_step(fedfem_ctx* c, double dt, int64_t n_steps) {
+    if (!c) return FEDFEM_E_ARG;
+    if (!c->inited) return fail(c, FEDFEM_E_STATE, "init first");
+    if (!(dt > 0) || !is_finite(dt) || n_steps < 0) return fail(c, FEDFEM_E_ARG, "need dt > 0 and n_steps >= 0");
+    if (!(dt < c->dt_cr)) return fail(c, FEDFEM_E_UNSTABLE_DT, "dt >= critical step " + std::to_string(c->dt_cr));
+    if (n_steps == 0) return FEDFEM_OK;
+    CU(cudaSetDevice(c->device), "set device");
+    LaunchCfg cfg;
+    cfg.kernel = c->tile.kernel;
+    cfg.block = c->tile.block;
+    cfg.blocks_per_sm = c->tile.blocks_per_sm;
+    cfg.sm_count = c->sm_count;
+    cfg.spin_limit = c->spin_limit;
+    cudaError_t e;
+    if (c->precision == FEDFEM_FP64) {
+        StepArgs<double> a = make_args<double>(c, c->M64, c->V64, c->Q64, c->hA64, dt);
+        e = launch_steps_f64(a, c->nv, n_steps, cfg, c->stream);
+    } else {
+        StepArgs<float> a = make_args<float>(c, c->M32, c->V32, c->Q32, c->hA32, dt);
+        e = launch_steps_f32(a, c->nv, c->precision == FEDFEM_FP32_KAHAN, n_steps, cfg, c->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "step launch");
+    c->last = cfg;
+    c->steps_issued += n_steps;
+    c->sim_time += dt * (double)n_steps;
+    return FEDFEM_OK;
+}
+
+int fedfem_sync(fedfem_ctx* c, int64_t* steps_done) {
+    if (!c) return FEDFEM_E_ARG;
+    if (!c->inited) return fail(c, FEDFEM_E_STATE, "init first");
+    CU(cudaSetDevice(c->device), "set device");
+    CU(cudaStreamSynchronize(c->stream), "sync");
+    DevStatus h{};
+    CU(cudaMemcpy(&h, c->st, sizeof(h), cudaMemcpyDeviceToHost), "status read");
+    int64_t done = c->steps_issued;
+    int rc = FEDFEM_OK;
+    if (h.flags & STATUS_TIMEOUT) {
+        done = h.steps_done;
+        rc = fail(c, FEDFEM_E_TIMEOUT, "a grid barrier wait gave up after its spin limit");
+    } else if (h.flags & STATUS_RANGE) {
+        done = h.fail_step + 1;
+        const int64_t node = (h.fail_node >= 0 && h.fail_node < c->N) ? c->L.node_of[h.fail_node] : -1;
+        rc = fail(c, FEDFEM_E_RANGE, "temperature left [T_lo, T_hi] or became NaN at step " +
+                                         std::to_string(h.fail_step) + ", node " + std::to_string(node));
+    }
+    if (steps_done) *steps_done = done;
+    return rc;
+}
+
+int fedfem_read_temperature_device(fedfem_ctx* c, double* out_dev) {
+    if (!c || !out_dev) return fail(c, FEDFEM_E_ARG, "null output");
+    if (!c->inited) return fail(c, FEDFEM_E_STATE, "init first");
+    CU(cudaSetDevice(c->device), "set device");
+    CU(launch_read_state(c->precision, c->N, c->node_of, c->T, c->Tlo, out_dev, c->stream), "read kernel");
+    CU(cudaStreamSynchronize(c->stream), "read");
+    return FEDFEM_OK;
+}
+
+int fedfem_read_temperature(fedfem_ctx* c, double* out) {
+    if (!c || !out) return fail(c, FEDFEM_E_ARG, "null output");
+    if (!c->inited) return fail(c, FEDFEM_E_STATE, "init first");
+    CU(cudaSetDevice(c->device), "set device");
+    CU(launch_read_state(c->precision, c->N, c->node_of, c->T, c->Tlo, c->io, c->stream), "read kernel");
+    CU(cudaMemcpyAsync(out, c->io, sizeof(double) * c->N, cudaMemcpyDeviceToHost, c->stream), "copy out");
+    CU(cudaStreamSynchronize(c->stream), "read");
+    return FEDFEM_OK;
+}
+
+struct StateHeader {
+    uint64_t magic;
+    int32_t version, precision;
+    int64_t N, E;
+    int32_t order, nv;
+    int64_t steps_done;
+    double sim_time;
+    uint64_t payload;
+};
+static const uint64_t kMagic = 0x5453464d45464546ULL;   // "FEFEMFST"
+
+int fedfem_get_state(fedfem_ctx* c, void* buf, size_t* bytes) {
+    if (!c || !bytes) return fail(c, FEDFEM_E_ARG, "null size pointer");
+    if (!c->inited) return fail(c, FEDFEM_E_STATE, "init first");
+    const size_t tb = (c->precision == FEDFEM_FP64 ? sizeof(double) : sizeof(float)) * c->N;
+    const size_t lb = (c->precision == FEDFEM_FP64 ? 0 : sizeof(float) * c->N);
+    const size_t need = sizeof(StateHeader) + tb + lb;
+    if (!buf) { *bytes = need; return FEDFEM_OK; }
+    if (*bytes < need) return fail(c, FEDFEM_E_ARG, "state buffer too small");
+    int64_t done = 0;
+    int rc = fedfem_sync(c, &done);
+    if (rc) return rc;
+    StateHeader h{kMagic, 1, c->precision, c->N, c->E, c->order, c->nv, done, c->sim_time, tb + lb};
+    std::memcpy(buf, &h, sizeof(h));
+    char* p = (char*)buf + sizeof(h);
+    CU(cudaMemcpy(p, c->T, tb, cudaMemcpyDeviceToHost), "state copy");
+    if (lb) CU(cudaMemcpy(p + tb, c->Tlo, lb, cudaMemcpyDeviceToHost), "state copy");
+    *bytes = need;
+    return FEDFEM_OK;
+}
+
+int fedfem_set_state(fedfem_ctx* c, const void* buf, size_t bytes) {
+    if (!c || !buf) return fail(c, FEDFEM_E_ARG, "null state");
+    if (!c->pre) return fail(c, FEDFEM_E_STATE, "precompute first");
+    if (bytes < sizeof(StateHeader)) return fail(c, FEDFEM_E_ARG, "state too short");
+    StateHeader h;
+    std::memcpy(&h, buf, sizeof(h));
+    const size_t tb = (c->precision == FEDFEM_FP64 ? sizeof(double) : sizeof(float)) * c->N;
+    const size_t lb = (c->precision == FEDFEM_FP64 ? 0 : sizeof(float) * c->N);
+    if (h.magic != kMagic || h.version != 1 || h.precision != c->precision || h.N != c->N || h.E != c->E ||
+        h.order != c->order || h.nv != c->nv || h.payload != tb + lb || bytes < sizeof(h) + tb + lb)
+        return fail(c, FEDFEM_E_ARG, "state does not match this context");
+    CU(cudaSetDevice(c->device), "set device");
+    const char* p = (const char*)buf + sizeof(h);
+    CU(cudaMemcpy(c->T, p, tb, cudaMemcpyHostToDevice), "state copy");
+    if (lb) CU(cudaMemcpy(c->Tlo, p + tb, lb, cudaMemcpyHostToDevice), "state copy");
+    int r = reset_status(c);
+    if (r) return r;
+    c->inited = true;
+    c->steps_issued = h.steps_done;
+    c->sim_time = h.sim_time;
+    return FEDFEM_OK;
+}
+
+int fedfem_get_info(fedfem_ctx* c, fedfem_info* info) {
+    if (!c || !info) return fail(c, FEDFEM_E_ARG, "null info");
+    if (!c->pre) return fail(c, FEDFEM_E_STATE, "precompute first");
+    std::memset(info, 0, sizeof(*info));
+    const Layout& L = c->L;
+    info->n_nodes = c->N; info->n_elems = c->E; info->n_free = L.N_free;
+    info->n_dirichlet = c->N - L.N_free; info->n_convective = L.N_free - L.N_plain;
+    info->elem_type = c->nv; info->precision = c->precision; info->order = c->order;
+    info->dt_cr = c->dt_cr; info->lambda_max_ref = c->lambda; info->td_scale = c->td_scale;
+    info->lanczos_iterations = c->lz_iters;
+    info->steps_done = c->steps_issued;
+    info->sim_time = c->sim_time;
+    info->device_bytes = c->dev_bytes;
+    const int64_t R = c->precision == FEDFEM_FP64 ? 8 : 4;
+    const int64_t node_state = c->precision == FEDFEM_FP32_KAHAN ? 4 * R : 2 * R;   // T (+lo) read+write
+    const int64_t E = c->E, NF = L.N_free, NC = L.N_free - L.N_plain;
+    info->algorithmic_bytes_per_step = E * (4 * c->nv + 6 * R) + NF * (node_state + 2 * R) + NC * R;
+    // two-phase / persistent model: + slot write and read, gather ids, slice offsets, T gather read once
+    info->bytes_per_step = info->algorithmic_bytes_per_step + E * c->nv * 2 * R + (int64_t)L.sell_ids.size() * 4 +
+                           (int64_t)L.sell_off.size() * 4;
+    info->sm_count = c->sm_count;
+    info->grid_blocks = c->last.grid_used;
+    info->block_threads = 256;
+    return FEDFEM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,151 @@
+// Internal declarations of the FED-FEM library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "fedfem.h"
+
+namespace fedfem {
+
+// ---------------------------------------------------------------------------
+// Host-side mesh layout (built once, cold path; host_layout.cpp)
+// ---------------------------------------------------------------------------
+struct Layout {
+    int nv = 0;                      // nodes per element (4 or 8)
+    int64_t N = 0, E = 0;
+    int64_t N_plain = 0;             // [0, N_plain): free nodes without a film condition
+    int64_t N_free = 0;              // [N_plain, N_free): free nodes with a film condition
+                                     // [N_free, N): Dirichlet nodes
+    std::vector<int32_t> elem_of;    // internal element -> input element
+    std::vector<int32_t> node_of;    // internal node -> input node
+    std::vector<int32_t> node_at;    // input node -> internal node
+    std::vector<int32_t> conn;       // internal connectivity, E x nv, internal node ids
+    // Node -> element-slot gather over the free nodes, sliced ELL with slices of
+    // 32 consecutive nodes: entry k of node i sits at sell_ids[sell_off[i/32] + 32k + i%32].
+    // Each node's list is sorted by INPUT element id; pads point at the zero slot E*nv.
+    std::vector<int32_t> sell_off;   // n_slices + 1
+    std::vector<int32_t> sell_ids;
+    int max_degree = 0;
+    // convective nodes [N_plain, N_free): CSR over face ids (input face order)
+    std::vector<int32_t> conv_off;   // (N_free - N_plain) + 1
+    std::vector<int32_t> conv_face;
+};
+
+struct MeshInput {
+    int nv = 0;
+    int64_t N = 0, E = 0;
+    const double* xyz = nullptr;
+    const int32_t* conn = nullptr;
+    const std::vector<char>* is_dirichlet = nullptr;   // input node flags
+    const std::vector<int32_t>* conv_faces = nullptr;  // n_faces x conv_nverts
+    int conv_nverts = 0;
+    int order = FEDFEM_ORDER_MORTON;
+};
+
+// Returns "" on success, else an error message.  Sets *mesh_error when the
+// failure is a mesh defect.
+std::string build_layout(const MeshInput& in, Layout& out, bool* mesh_error);
+
+// ---------------------------------------------------------------------------
+// Device status word shared by all time-loop kernels
+// ---------------------------------------------------------------------------
+enum : int { STATUS_RANGE = 1, STATUS_TIMEOUT = 2 };
+
+struct DevStatus {
+    int flags;
+    int skip_barrier_block;          // testing hook: this block never arrives (-1 = none)
+    long long fail_node;             // internal node of the first range failure
+    long long fail_step;             // step index (since init) of the first failure
+    unsigned long long barrier;      // monotone arrival counter of the grid barrier
+    long long steps_done;            // steps completed since init
+    long long pad[2];
+};
+
+// ---------------------------------------------------------------------------
+// Kernel parameter block of the time loop
+// ---------------------------------------------------------------------------
+template <typename R>
+struct StepArgs {
+    int64_t E, N, N_plain, N_free;
+    const int4* conn4;               // nv/4 planes of E int4
+    const R* M;                      // 6 planes of E: m00 m11 m22 m01 m02 m12
+    R* slots;                        // E*nv + 1 element loads (the last one stays 0)
+    const int32_t* sell_off;
+    const int32_t* sell_ids;
+    const R* V;                      // lumped volume, free nodes
+    const R* Q;                      // constant nodal heat flow (W), free nodes
+    const R* hA;                     // film h * lumped area, nodes [N_plain, N_free)
+    R* T;                            // temperature (FP64) or its hi part (FP32), all N nodes
+    R* Tlo;                          // FP32 compensation, all N nodes (unused in FP64)
+    R T_ref, rho0, drho, c0, dc, k0, dk;
+    R wbcb, T_a, T_inf;
+    R dt, T_lo, T_hi;
+    DevStatus* status;
+    long long step0;                 // step index (since init) of the first step of this call
+};
+
+// Launchers (step.cu).  mode: FEDFEM_FP64 / FEDFEM_FP32_KAHAN / FEDFEM_FP32_PLAIN.
+struct LaunchCfg {
+    int kernel = FEDFEM_KERNEL_PERSISTENT;
+    int block = 256;
+    int blocks_per_sm = 0;
+    int sm_count = 0;
+    long long spin_limit = 4000000000LL;   // clock64 ticks a barrier waits before giving up
+    int grid_used = 0;                     // out: grid of the last persistent launch
+};
+
+cudaError_t launch_steps_f64(const StepArgs<double>& a, int nv, int64_t n_steps, LaunchCfg& cfg,
+                             cudaStream_t s);
+cudaError_t launch_steps_f32(const StepArgs<float>& a, int nv, bool kahan, int64_t n_steps,
+                             LaunchCfg& cfg, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Pre-computation (precompute.cu), FP64
+// ---------------------------------------------------------------------------
+struct PreArgs {
+    int nv;
+    int64_t E, N, N_plain, N_free;
+    const int4* conn4;
+    const double* x; const double* y; const double* z;      // internal node order
+    double* M64;                 // 6 planes of E
+    double* Vshare;              // E + 1 (last = 0): V_e / nv
+    int* bad_elem;               // smallest internal element with det <= 0 (init INT_MAX)
+    const int32_t* sell_off; const int32_t* sell_ids;
+    double* V;                   // free nodes
+    double* Q;                   // free nodes
+    double* hA;                  // convective nodes
+    const double* qr_node;       // free nodes, W/m^3 (nullable)
+    const double* flux_node;     // free nodes, W (nullable)
+    const double* src;           // n_src x 5: x0 y0 z0 sigma peak
+    int n_src;
+    double Q_m;
+    // film faces
+    int64_t n_faces; int face_nv;
+    const int32_t* faces;        // internal node ids, n_faces x face_nv
+    double* face_share;          // n_faces: h * area / face_nv
+    const int32_t* conv_off; const int32_t* conv_face;
+    double h_film;
+};
+
+cudaError_t launch_geometry(const PreArgs& a, cudaStream_t s);
+cudaError_t launch_nodal(const PreArgs& a, cudaStream_t s);
+cudaError_t launch_to_f32(const double* src, float* dst, int64_t n, cudaStream_t s);
+
+// Largest eigenvalue of C0^-1/2 (K0 + diag(beta + hA)) C0^-1/2 on the free
+// nodes by Lanczos (FP64).  Returns an error message or "".
+struct LanczosResult { double lambda = 0; int iterations = 0; };
+std::string lanczos_lambda_max(const PreArgs& a, double k0, double rho0c0, double wbcb,
+                               int max_iter, double rel_tol, LanczosResult& out, cudaStream_t s);
+
+// Init / output helpers (precompute.cu)
+cudaError_t launch_init_state(int precision, int64_t N, int64_t N_free, const int32_t* node_of,
+                              const double* T_in, const double* T_dir, void* T, float* Tlo,
+                              cudaStream_t s);
+cudaError_t launch_read_state(int precision, int64_t N, const int32_t* node_of, const void* T,
+                              const float* Tlo, double* out, cudaStream_t s);
+
+}  // namespace fedfem

@@ -1,0 +1,345 @@
+"""Python binding of the C ABI declared in include/fedfem.h (ctypes).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  Each ``fedfem_*`` function here has the name, argument order
+and meaning of the C call, takes numpy arrays / Python numbers, and raises
+:class:`FedfemError` on a non-zero status.  There is no CPU fallback: if the
+shared library is missing, importing this module fails.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from .build import LIB
+
+if not os.path.exists(LIB):
+    raise ImportError(f"libfedfem.so not built ({LIB}); run paper_1909_05098_gb300.build.build()")
+_lib = C.CDLL(LIB)
+
+OK, E_ARG, E_MESH, E_STATE, E_UNSTABLE_DT, E_RANGE, E_TIMEOUT, E_CUDA, E_OOM, E_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6, -7, -8, -9
+TET4, HEX8 = 4, 8
+FP64, FP32_KAHAN, FP32_PLAIN = 0, 1, 2
+ORDER_INPUT, ORDER_MORTON, ORDER_RCM = 0, 1, 2
+KERNEL_TWO_PHASE, KERNEL_PERSISTENT, KERNEL_TILED = 0, 1, 2
+
+STATUS_NAMES = {0: "OK", -1: "E_ARG", -2: "E_MESH", -3: "E_STATE", -4: "E_UNSTABLE_DT", -5: "E_RANGE",
+                -6: "E_TIMEOUT", -7: "E_CUDA", -8: "E_OOM", -9: "E_UNSUPPORTED"}
+
+
+class FedfemError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class fedfem_material(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("T_ref", "rho0", "drho", "c0", "dc", "k0", "dk")]
+
+
+class fedfem_perfusion(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("w_b", "c_b", "T_a", "Q_m")]
+
+
+class fedfem_tile(C.Structure):
+    _fields_ = [("kernel", C.c_int), ("block", C.c_int), ("tile_nodes", C.c_int), ("blocks_per_sm", C.c_int)]
+
+
+class fedfem_info(C.Structure):
+    _fields_ = [("n_nodes", C.c_int64), ("n_elems", C.c_int64), ("n_free", C.c_int64),
+                ("n_dirichlet", C.c_int64), ("n_convective", C.c_int64),
+                ("elem_type", C.c_int), ("precision", C.c_int), ("order", C.c_int),
+                ("dt_cr", C.c_double), ("lambda_max_ref", C.c_double), ("td_scale", C.c_double),
+                ("dt_element_bound", C.c_double), ("lanczos_iterations", C.c_int),
+                ("steps_done", C.c_int64), ("sim_time", C.c_double), ("device_bytes", C.c_int64),
+                ("bytes_per_step", C.c_int64), ("algorithmic_bytes_per_step", C.c_int64),
+                ("sm_count", C.c_int), ("grid_blocks", C.c_int), ("block_threads", C.c_int)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+_ctx_p = C.c_void_p
+_i64 = C.c_int64
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int32)
+
+_SIGS = {
+    "fedfem_create": ([C.POINTER(_ctx_p), C.c_int, C.c_int, C.c_void_p], C.c_int),
+    "fedfem_set_mesh": ([_ctx_p, C.c_int, _i64, _dp, _i64, _ip], C.c_int),
+    "fedfem_set_order": ([_ctx_p, C.c_int], C.c_int),
+    "fedfem_set_material": ([_ctx_p, C.POINTER(fedfem_material)], C.c_int),
+    "fedfem_set_perfusion": ([_ctx_p, C.POINTER(fedfem_perfusion)], C.c_int),
+    "fedfem_set_source": ([_ctx_p, _dp], C.c_int),
+    "fedfem_add_gaussian_source": ([_ctx_p, _dp, C.c_double, C.c_double], C.c_int),
+    "fedfem_clear_sources": ([_ctx_p], C.c_int),
+    "fedfem_set_dirichlet": ([_ctx_p, _i64, _ip, _dp], C.c_int),
+    "fedfem_set_convective": ([_ctx_p, _i64, C.c_int, _ip, C.c_double, C.c_double], C.c_int),
+    "fedfem_set_nodal_flux": ([_ctx_p, _i64, _ip, _dp], C.c_int),
+    "fedfem_precompute": ([_ctx_p, C.c_double, C.c_double, _dp], C.c_int),
+    "fedfem_init": ([_ctx_p, _dp, C.c_double], C.c_int),
+    "fedfem_init_device": ([_ctx_p, C.c_void_p], C.c_int),
+    "fedfem_step": ([_ctx_p, C.c_double, _i64], C.c_int),
+    "fedfem_sync": ([_ctx_p, C.POINTER(_i64)], C.c_int),
+    "fedfem_read_temperature": ([_ctx_p, _dp], C.c_int),
+    "fedfem_read_temperature_device": ([_ctx_p, C.c_void_p], C.c_int),
+    "fedfem_get_state": ([_ctx_p, C.c_void_p, C.POINTER(C.c_size_t)], C.c_int),
+    "fedfem_set_state": ([_ctx_p, C.c_void_p, C.c_size_t], C.c_int),
+    "fedfem_set_tile": ([_ctx_p, C.POINTER(fedfem_tile)], C.c_int),
+    "fedfem_get_info": ([_ctx_p, C.POINTER(fedfem_info)], C.c_int),
+    "fedfem_last_error": ([_ctx_p], C.c_char_p),
+    "fedfem_destroy": ([_ctx_p], None),
+    "fedfem_version": ([], C.c_char_p),
+    "fedfem_debug_set": ([_ctx_p, C.c_int, _i64], C.c_int),
+}
+for _name, (_args, _res) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = _res
+
+
+def library():
+    """The loaded ctypes library (for tests that inspect exported symbols)."""
+    return _lib
+
+
+def _check(ctx, rc):
+    if rc != OK:
+        msg = _lib.fedfem_last_error(ctx).decode() if ctx else ""
+        raise FedfemError(rc, msg)
+
+
+def _d(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(_dp)
+
+
+def _i(a):
+    a = np.ascontiguousarray(a, dtype=np.int32)
+    return a, a.ctypes.data_as(_ip)
+
+
+# ---- the C calls, same names -------------------------------------------------
+
+def fedfem_version() -> str:
+    return _lib.fedfem_version().decode()
+
+
+def fedfem_create(device: int = 0, precision: int = FP32_KAHAN, cuda_stream: int | None = None):
+    ctx = _ctx_p()
+    rc = _lib.fedfem_create(C.byref(ctx), device, precision, C.c_void_p(cuda_stream or 0))
+    _check(None, rc)
+    return ctx
+
+
+def fedfem_destroy(ctx):
+    _lib.fedfem_destroy(ctx)
+
+
+def fedfem_set_mesh(ctx, elem_type: int, xyz, conn):
+    x, px = _d(xyz)
+    c, pc = _i(conn)
+    _check(ctx, _lib.fedfem_set_mesh(ctx, elem_type, x.shape[0], px, c.shape[0], pc))
+
+
+def fedfem_set_order(ctx, order: int):
+    _check(ctx, _lib.fedfem_set_order(ctx, order))
+
+
+def fedfem_set_material(ctx, T_ref, rho0, drho, c0, dc, k0, dk):
+    m = fedfem_material(T_ref, rho0, drho, c0, dc, k0, dk)
+    _check(ctx, _lib.fedfem_set_material(ctx, C.byref(m)))
+
+
+def fedfem_set_perfusion(ctx, w_b, c_b, T_a, Q_m=0.0):
+    p = fedfem_perfusion(w_b, c_b, T_a, Q_m)
+    _check(ctx, _lib.fedfem_set_perfusion(ctx, C.byref(p)))
+
+
+def fedfem_set_source(ctx, q_r):
+    if q_r is None:
+        _check(ctx, _lib.fedfem_set_source(ctx, None))
+        return
+    q, pq = _d(q_r)
+    _check(ctx, _lib.fedfem_set_source(ctx, pq))
+
+
+def fedfem_add_gaussian_source(ctx, x0, sigma, peak):
+    x, px = _d(np.asarray(x0, dtype=np.float64).reshape(3))
+    _check(ctx, _lib.fedfem_add_gaussian_source(ctx, px, sigma, peak))
+
+
+def fedfem_clear_sources(ctx):
+    _check(ctx, _lib.fedfem_clear_sources(ctx))
+
+
+def fedfem_set_dirichlet(ctx, nodes, T):
+    n, pn = _i(nodes)
+    t, pt = _d(np.broadcast_to(np.asarray(T, dtype=np.float64), n.shape))
+    _check(ctx, _lib.fedfem_set_dirichlet(ctx, n.shape[0], pn, pt))
+
+
+def fedfem_set_convective(ctx, faces, h, T_inf):
+    f, pf = _i(faces)
+    nverts = f.shape[1] if f.ndim == 2 and f.shape[0] else 3
+    _check(ctx, _lib.fedfem_set_convective(ctx, f.shape[0], nverts, pf, h, T_inf))
+
+
+def fedfem_set_nodal_flux(ctx, nodes, q_W):
+    n, pn = _i(nodes)
+    q, pq = _d(q_W)
+    _check(ctx, _lib.fedfem_set_nodal_flux(ctx, n.shape[0], pn, pq))
+
+
+def fedfem_precompute(ctx, T_lo, T_hi) -> float:
+    out = C.c_double()
+    _check(ctx, _lib.fedfem_precompute(ctx, T_lo, T_hi, C.byref(out)))
+    return out.value
+
+
+def fedfem_init(ctx, T0=None, T0_uniform: float = 37.0):
+    if T0 is None:
+        _check(ctx, _lib.fedfem_init(ctx, None, T0_uniform))
+    else:
+        t, pt = _d(T0)
+        _check(ctx, _lib.fedfem_init(ctx, pt, T0_uniform))
+
+
+def fedfem_init_device(ctx, T0_dev_ptr: int):
+    _check(ctx, _lib.fedfem_init_device(ctx, C.c_void_p(T0_dev_ptr)))
+
+
+def fedfem_step(ctx, dt: float, n_steps: int):
+    _check(ctx, _lib.fedfem_step(ctx, dt, n_steps))
+
+
+def fedfem_sync(ctx) -> int:
+    done = _i64()
+    _check(ctx, _lib.fedfem_sync(ctx, C.byref(done)))
+    return done.value
+
+
+def fedfem_sync_status(ctx):
+    """(status, steps_done) without raising -- for tests of the error paths."""
+    done = _i64()
+    rc = _lib.fedfem_sync(ctx, C.byref(done))
+    return rc, done.value
+
+
+def fedfem_read_temperature(ctx, out=None) -> np.ndarray:
+    info = fedfem_get_info(ctx)
+    if out is None:
+        out = np.empty(info["n_nodes"], dtype=np.float64)
+    _check(ctx, _lib.fedfem_read_temperature(ctx, out.ctypes.data_as(_dp)))
+    return out
+
+
+def fedfem_read_temperature_device(ctx, out_dev_ptr: int):
+    _check(ctx, _lib.fedfem_read_temperature_device(ctx, C.c_void_p(out_dev_ptr)))
+
+
+def fedfem_get_state(ctx) -> bytes:
+    n = C.c_size_t()
+    _check(ctx, _lib.fedfem_get_state(ctx, None, C.byref(n)))
+    buf = C.create_string_buffer(n.value)
+    _check(ctx, _lib.fedfem_get_state(ctx, buf, C.byref(n)))
+    return buf.raw[: n.value]
+
+
+def fedfem_set_state(ctx, state: bytes):
+    buf = C.create_string_buffer(state, len(state))
+    _check(ctx, _lib.fedfem_set_state(ctx, buf, len(state)))
+
+
+def fedfem_set_tile(ctx, kernel=KERNEL_PERSISTENT, block=0, tile_nodes=0, blocks_per_sm=0):
+    t = fedfem_tile(kernel, block, tile_nodes, blocks_per_sm)
+    _check(ctx, _lib.fedfem_set_tile(ctx, C.byref(t)))
+
+
+def fedfem_get_info(ctx) -> dict:
+    info = fedfem_info()
+    _check(ctx, _lib.fedfem_get_info(ctx, C.byref(info)))
+    return info.as_dict()
+
+
+def fedfem_last_error(ctx) -> str:
+    return _lib.fedfem_last_error(ctx).decode()
+
+
+def fedfem_debug_set(ctx, key: int, value: int):
+    _check(ctx, _lib.fedfem_debug_set(ctx, key, value))
+
+
+# ---- convenience wrapper ------------------------------------------------------
+
+class Solver:
+    """One problem on one GPU: set-up, pre-computation, initial field.
+
+    ``problem`` is any object with the fields of a Pennes problem: elem_type,
+    xyz, conn, material (T_ref rho0 drho c0 dc k0 dk), perfusion (w_b c_b T_a
+    Q_m), sources (x0 sigma peak), q_r, dirichlet_nodes/_T, conv_faces/_h/
+    _T_inf, flux_nodes/_q, T0, T_lo, T_hi."""
+
+    def __init__(self, problem, precision=FP32_KAHAN, device=0, stream=None, order=ORDER_MORTON,
+                 kernel=KERNEL_PERSISTENT, T_lo=None, T_hi=None):
+        self.ctx = fedfem_create(device, precision, stream)
+        self.problem = problem
+        try:
+            p = problem
+            fedfem_set_mesh(self.ctx, p.elem_type, p.xyz, p.conn)
+            fedfem_set_order(self.ctx, order)
+            m = p.material
+            fedfem_set_material(self.ctx, m.T_ref, m.rho0, m.drho, m.c0, m.dc, m.k0, m.dk)
+            pf = p.perfusion
+            fedfem_set_perfusion(self.ctx, pf.w_b, pf.c_b, pf.T_a, pf.Q_m)
+            for s in p.sources:
+                fedfem_add_gaussian_source(self.ctx, s.x0, s.sigma, s.peak)
+            if p.q_r is not None:
+                fedfem_set_source(self.ctx, p.q_r)
+            if len(p.dirichlet_nodes):
+                fedfem_set_dirichlet(self.ctx, p.dirichlet_nodes, p.dirichlet_T)
+            if len(p.conv_faces):
+                fedfem_set_convective(self.ctx, p.conv_faces, p.conv_h, p.conv_T_inf)
+            if len(p.flux_nodes):
+                fedfem_set_nodal_flux(self.ctx, p.flux_nodes, p.flux_q)
+            fedfem_set_tile(self.ctx, kernel)
+            self.dt_cr = fedfem_precompute(self.ctx, p.T_lo if T_lo is None else T_lo,
+                                           p.T_hi if T_hi is None else T_hi)
+            self.init()
+        except Exception:
+            fedfem_destroy(self.ctx)
+            self.ctx = None
+            raise
+
+    def init(self, T0=None):
+        T0 = self.problem.T0 if T0 is None else T0
+        T0 = np.asarray(T0, dtype=np.float64)
+        if T0.ndim == 0:
+            fedfem_init(self.ctx, None, float(T0))
+        else:
+            fedfem_init(self.ctx, T0)
+
+    def step(self, dt, n):
+        fedfem_step(self.ctx, dt, n)
+
+    def sync(self):
+        return fedfem_sync(self.ctx)
+
+    def temperature(self):
+        return fedfem_read_temperature(self.ctx)
+
+    def info(self):
+        return fedfem_get_info(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            fedfem_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,100 @@
+"""GPU path (through the C ABI) against the FP64 oracle, element by element.
+
+Tolerances (max |dT| over all nodes): FP64 1e-9 degC, FP32 + Kahan 1e-3 degC.
+"""
+import copy
+
+import numpy as np
+import pytest
+
+from oracle import Oracle, critical_dt, eq20_error
+from synth.scenarios import cube_hex_fp64, cube_hex_td_convective, ellipsoid_tet_td
+
+from gpu_util import ff, max_abs, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+TOL64, TOL32 = 1e-9, 1e-3
+
+
+@pytest.fixture(scope="module")
+def cube():
+    w = cube_hex_fp64()
+    orc = Oracle(w.problem)
+    dt_cr = critical_dt(orc)
+    dt = 0.5 * dt_cr
+    return w, orc, dt_cr, dt, orc.run(dt, w.n_steps)
+
+
+def test_cube_fp64_2000_steps(cube):
+    w, orc, dt_cr, dt, ref = cube
+    f = ff()
+    T, info = run_gpu(w.problem, dt, w.n_steps, f.FP64)
+    assert info["dt_cr"] == pytest.approx(dt_cr, rel=1e-9)
+    err = max_abs(T, ref)
+    print(f"cube FP64 2000 steps: max|dT| = {err:.3e}, Eq.20 = {eq20_error(ref, T):.3e}, "
+          f"Lanczos iterations {info['lanczos_iterations']}")
+    assert err <= TOL64
+
+
+def test_cube_fp32_kahan_and_plain(cube):
+    w, orc, dt_cr, dt, ref = cube
+    f = ff()
+    Tk, _ = run_gpu(w.problem, dt, w.n_steps, f.FP32_KAHAN)
+    Tp, _ = run_gpu(w.problem, dt, w.n_steps, f.FP32_PLAIN)
+    ek, ep = max_abs(Tk, ref), max_abs(Tp, ref)
+    print(f"cube FP32+Kahan max|dT| = {ek:.3e}; FP32 plain (negative control) = {ep:.3e}")
+    assert ek <= TOL32
+    assert ek < ep
+
+
+def test_every_kernel_and_order_is_bit_identical(cube):
+    w, orc, dt_cr, dt, ref = cube
+    f = ff()
+    for prec in (f.FP64, f.FP32_KAHAN):
+        base, _ = run_gpu(w.problem, dt, 300, prec, order=f.ORDER_MORTON, kernel=f.KERNEL_PERSISTENT)
+        for order in (f.ORDER_INPUT, f.ORDER_MORTON, f.ORDER_RCM):
+            for kernel in (f.KERNEL_TWO_PHASE, f.KERNEL_PERSISTENT):
+                T, _ = run_gpu(w.problem, dt, 300, prec, order=order, kernel=kernel)
+                assert np.array_equal(T, base), (prec, order, kernel)
+
+
+@pytest.mark.parametrize("prec_name", ["FP64", "FP32_KAHAN"])
+def test_small_tet_ellipsoid_td(prec_name):
+    w = ellipsoid_tet_td(h=1.5e-3, axes=(0.024, 0.018, 0.014), n_steps=1500)
+    p = w.problem
+    orc = Oracle(p)
+    dt = 0.5 * critical_dt(orc)
+    ref = orc.run(dt, w.n_steps)
+    f = ff()
+    T, info = run_gpu(p, dt, w.n_steps, getattr(f, prec_name))
+    assert info["dt_cr"] == pytest.approx(critical_dt(orc), rel=1e-9)
+    err = max_abs(T, ref)
+    print(f"tet ellipsoid {p.n_nodes} nodes {prec_name}: max|dT| = {err:.3e}, max T = {ref.max():.2f}")
+    assert err <= (TOL64 if prec_name == "FP64" else TOL32)
+
+
+@pytest.mark.parametrize("prec_name", ["FP64", "FP32_KAHAN"])
+def test_small_convective_cube_td(prec_name):
+    w = cube_hex_td_convective(n=12)
+    p = w.problem
+    orc = Oracle(p)
+    dt = 0.5 * critical_dt(orc)
+    ref = orc.run(dt, 800)
+    f = ff()
+    T, _ = run_gpu(p, dt, 800, getattr(f, prec_name))
+    err = max_abs(T, ref)
+    print(f"convective cube 12^3 {prec_name}: max|dT| = {err:.3e}")
+    assert err <= (TOL64 if prec_name == "FP64" else TOL32)
+
+
+def test_uniform_field_bit_unchanged_on_gpu():
+    w = cube_hex_td_convective(n=20)
+    p = copy.copy(w.problem)
+    p.sources = []
+    p.conv_T_inf = 37.0
+    f = ff()
+    for prec in (f.FP64, f.FP32_KAHAN, f.FP32_PLAIN):
+        for kernel in (f.KERNEL_TWO_PHASE, f.KERNEL_PERSISTENT):
+            T, _ = run_gpu(p, 1.0, 200, prec, kernel=kernel)
+            assert np.all(T == 37.0), (prec, kernel)
