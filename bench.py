@@ -1,0 +1,395 @@
+"""Throughput of the FED-FEM explicit step on GB300 (one JSON line on stdout).
+
+Workload: the 128^3 hex8 cube (2,146,689 nodes, 2,097,152 elements) with
+temperature-dependent k(T), c(T), perfusion, a Gaussian source, a film
+condition on one face and Dirichlet on the other five; FP32 state with Kahan
+compensation; the persistent multi-step kernel.  One bench step is one
+``fedfem_step`` call that advances ``--steps-per-launch`` explicit time steps
+(Algorithm 1, lines 8-15) on the device.  Metric: node-steps/s (nodes x time
+steps / second), whole job.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (global assembled K, Eq. 7-8) on a
+bounded sample of the same workload on the host cores.  Multi-GPU (torchrun):
+every rank runs an independent replica (the single-mesh path has no
+data-parallel split), value = all ranks' node-steps / max rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOAD_N = 128
+STEPS_PER_LAUNCH = 100
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--steps-per-launch", type=int, default=STEPS_PER_LAUNCH)
+    ap.add_argument("--n", type=int, default=WORKLOAD_N, help="cube edge in elements")
+    ap.add_argument("--kernel", default="persistent", choices=["two_phase", "persistent", "tiled"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload_name(n):
+    return (f"hex8 cube {n}^3 elements ({(n + 1) ** 3} nodes), h=1 mm, T-dependent k,c, perfusion, "
+            f"Gaussian source, film h=10 on z-max, Dirichlet on 5 faces, FP32+Kahan")
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (replicas)
+# ---------------------------------------------------------------------------
+
+def dist_init(n_gpus):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if _cuda_ok() else "gloo"
+        dist.init_process_group(backend=backend)
+    return rank, world, local
+
+
+def _cuda_ok():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def reduce_max(x, world, device=None):
+    """Max of a float over ranks (the job's time is its slowest rank's)."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate(units_per_rank, seconds_per_rank):
+    """Whole-job throughput: all ranks' units over the slowest rank's time."""
+    return float(sum(units_per_rank)) / float(max(seconds_per_rank))
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if re.match(r"^[0-9.]+$", r[1])]
+        mx = [float(r[2]) for r in rows if re.match(r"^[0-9.]+$", r[2])]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def clocks_rejected(c):
+    bad = {"hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"}
+    if set(c.get("reasons", [])) & bad:
+        return True
+    if c.get("sm_mhz") and c.get("sm_max_mhz") and c["sm_mhz"] < 0.5 * c["sm_max_mhz"] and not c["reasons"]:
+        return True
+    return False
+
+
+# ---------------------------------------------------------------------------
+# roofline inputs
+# ---------------------------------------------------------------------------
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        if d.get("hbm_gbs"):
+            return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    csrc = os.path.join(ROOT, "paper_1909_05098_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_name, n, steps_per_launch):
+    """DRAM bytes per time step of `kernel_name` on the n^3 workload from the
+    committed ncu summary, scaled to one launch; None if the summary is absent
+    or was taken on different kernel sources."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    e = d.get(kernel_name)
+    if not e or e.get("source_hash") != kernel_source_hash():
+        return None
+    per_step = e["dram_bytes_per_step_full"] if e.get("n") != n else e["dram_bytes_per_step"]
+    return per_step * steps_per_launch
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the oracle, bounded sample
+# ---------------------------------------------------------------------------
+
+def cpu_baseline(budget_s=12.0, n_sample=64):
+    from oracle import Oracle
+    from synth.scenarios import cube_hex_td_convective
+    w = cube_hex_td_convective(n=n_sample)
+    orc = Oracle(w.problem)
+    T = orc.initial_field()
+    dt = 1.0
+    steps = 0
+    t0 = time.perf_counter()
+    while True:
+        T = orc.step(T, dt)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or steps >= 200:
+            break
+    return {"value": w.problem.n_nodes * steps / el, "unit": "node-steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"FP64 oracle (global K(T) assembled each step, Eq. 7-8), {steps} steps of the same recipe "
+                      f"on a {n_sample}^3-element cube ({w.problem.n_nodes} nodes), single host thread, "
+                      f"{el:.1f} s"}
+
+
+# ---------------------------------------------------------------------------
+# reference arm
+# ---------------------------------------------------------------------------
+
+def run_reference(args):
+    rank, world, _ = int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), 0
+    if rank != 0:
+        return
+    from oracle import Oracle
+    from synth.scenarios import cube_hex_td_convective
+    n_sample = 48
+    w = cube_hex_td_convective(n=n_sample)
+    orc = Oracle(w.problem)
+    T = orc.initial_field()
+    per = 2   # oracle time steps per bench step (bounded sample)
+    for _ in range(args.warmup):
+        for _ in range(per):
+            T = orc.step(T, 1.0)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for _ in range(per):
+            T = orc.step(T, 1.0)
+    el = time.perf_counter() - t0
+    value = w.problem.n_nodes * per * args.steps / el
+    sample = (f"FP64 oracle on a {n_sample}^3-element cube of the same recipe ({w.problem.n_nodes} nodes), "
+              f"{per} time steps per bench step, single host thread")
+    print(json.dumps({
+        "impl": "reference", "metric": "node-steps/s", "value": value, "unit": "node-steps/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(args.n), "sample_nodes": w.problem.n_nodes},
+        "cpu_baseline": {"value": value, "unit": "node-steps/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "node-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_init(args.gpus)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1909_05098_gb300.build import build
+    if rank == 0 or world == 1:
+        build()
+    barrier(world)
+    build()
+    from paper_1909_05098_gb300 import fedfem as ff
+    from synth.scenarios import cube_hex_td_convective
+
+    kernel = {"two_phase": ff.KERNEL_TWO_PHASE, "persistent": ff.KERNEL_PERSISTENT,
+              "tiled": ff.KERNEL_TILED}[args.kernel]
+    S = args.steps_per_launch
+    w = cube_hex_td_convective(n=args.n)
+    p = w.problem
+    stream = torch.cuda.Stream(device=dev)
+    solver = ff.Solver(p, precision=ff.FP32_KAHAN, device=local, stream=stream.cuda_stream, kernel=kernel)
+    info = solver.info()
+    dt = 0.5 * solver.dt_cr
+    N = info["n_nodes"]
+
+    def timed(K):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        barrier(world)
+        torch.cuda.synchronize()
+        for a, b in ev:
+            a.record(stream)
+            solver.step(dt, S)
+            b.record(stream)
+        solver.sync()
+        torch.cuda.synchronize()
+        barrier(world)
+        per = [a.elapsed_time(b) for a, b in ev]
+        return ev[0][0].elapsed_time(ev[-1][1]) / 1e3, per
+
+    for _ in range(args.warmup):
+        solver.step(dt, S)
+    solver.sync()
+    clk = ClockSampler(local)
+    clk.start()
+    total_s, per_launch_ms = timed(args.steps)
+    clocks = clk.stop()
+    note = None
+    if clocks_rejected(clocks):
+        note = f"first timed region rejected (clocks {clocks}); re-measured once"
+        clk.start()
+        total_s, per_launch_ms = timed(args.steps)
+        clocks = clk.stop()
+    t_max = reduce_max(total_s, world, dev)
+    units_rank = N * S * args.steps
+    value = units_rank * world / t_max
+    ms_per_step = 1e3 * t_max / args.steps
+    steps_done = solver.sync()
+
+    # error of this FP32+Kahan run against an FP64 GPU run of the same steps
+    # (the FP64 path is pinned to the oracle by the parity tests)
+    T32 = solver.temperature()
+    ref64 = ff.Solver(p, precision=ff.FP64, device=local, stream=stream.cuda_stream, kernel=kernel)
+    ref64.step(dt, steps_done)
+    ref64.sync()
+    max_err = float(np.max(np.abs(T32 - ref64.temperature())))
+    ref64.close()
+
+    # end to end through the C ABI with pinned host buffers: H2D of T0, S steps, D2H of T
+    T0 = torch.full((N,), float(p.T0), dtype=torch.float64).pin_memory()
+    out = torch.empty((N,), dtype=torch.float64).pin_memory()
+    ctx = solver.ctx
+    for _ in range(2):
+        ff._check(ctx, ff._lib.fedfem_init(ctx, ff.C.cast(T0.data_ptr(), ff._dp), 0.0))
+        ff.fedfem_step(ctx, dt, S)
+        ff._check(ctx, ff._lib.fedfem_read_temperature(ctx, ff.C.cast(out.data_ptr(), ff._dp)))
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ff._check(ctx, ff._lib.fedfem_init(ctx, ff.C.cast(T0.data_ptr(), ff._dp), 0.0))
+        ff.fedfem_step(ctx, dt, S)
+        ff._check(ctx, ff._lib.fedfem_read_temperature(ctx, ff.C.cast(out.data_ptr(), ff._dp)))
+    e2e_s = reduce_max(time.perf_counter() - t0, world, dev)
+    e2e_value = units_rank * world / e2e_s
+
+    alg_bytes_launch = info["algorithmic_bytes_per_step"] * S
+    launch_s = float(np.mean(per_launch_ms)) / 1e3
+    peak, peak_src = measured_peak()
+    achieved = alg_bytes_launch / launch_s / 1e9
+    traffic = ncu_traffic(f"persistent_fp32_kahan_hex8" if kernel == ff.KERNEL_PERSISTENT else args.kernel,
+                          args.n, S)
+    solver.close()
+    if rank != 0:
+        return
+    line = {
+        "metric": "node-steps/s", "value": value, "unit": "node-steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": workload_name(args.n), "nodes": N, "elements": info["n_elems"],
+                   "time_steps_per_bench_step": S, "kernel": args.kernel, "precision": "FP32+Kahan",
+                   "dt_s": dt, "dt_cr_s": solver.dt_cr,
+                   "l2": f"inputs larger than L2: {info['bytes_per_step'] / 1e6:.0f} MB moved per time step",
+                   "parallelism": f"replicas x{world}"},
+        "sim_s_per_wall_s": dt * S * args.steps / t_max,
+        "max_err_vs_fp64_C": max_err,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback 6.8 TB/s",
+                     "algorithmic_bytes_per_launch": alg_bytes_launch,
+                     "model_bytes_per_launch": info["bytes_per_step"] * S,
+                     "model_gbs": info["bytes_per_step"] * S / launch_s / 1e9},
+        "e2e": {"value": e2e_value, "unit": "node-steps/s", "h2d_bytes_per_step": int(T0.numel() * 8),
+                "d2h_bytes_per_step": int(out.numel() * 8)},
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+    }
+    if note:
+        line["note"] = note
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()
