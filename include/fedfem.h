@@ -219,6 +219,46 @@ void fedfem_destroy(fedfem_ctx* ctx);
 /* Library version string. */
 const char* fedfem_version(void);
 
+/* Explicit steps that allocate nothing (the paper has no counterpart).
+ *
+ * For callers that may not allocate device memory themselves or through this
+ * library -- code running inside another framework's memory pool, a
+ * real-time loop that forbids allocation after start-up, or a plug-in that
+ * must not call cudaMalloc/cudaFree.  There is no context: the caller passes
+ * the mesh, the gather structure and the temperature as its own device
+ * buffers, and every temporary (element loads, element matrices, lumped
+ * volumes and loads) lives in one fixed device array inside the library
+ * (about 18.3 MB, held by every GPU that loads the library until the process
+ * exits).  Nothing is allocated or freed by the call.
+ *
+ * Runs n_steps explicit FP64 steps (Eq. 17 with k_e of Eq. 13, Eq. 19) on the
+ * CURRENT CUDA device, on `cuda_stream` (NULL = legacy default stream), and
+ * returns after they have completed.  The element matrices and lumped volumes
+ * are recomputed at the start of every call.
+ *   xyz_dev     n_nodes x 3 coordinates (m), row-major
+ *   conn_dev    n_elems x elem_type node ids, as in fedfem_set_mesh
+ *   row_ptr_dev n_nodes + 1 offsets into slot_dev
+ *   slot_dev    for node i, entries row_ptr[i] .. row_ptr[i+1]-1 are
+ *               e * elem_type + corner for every (element e, corner) that is
+ *               node i, sorted by e (this fixes the summation order)
+ *   q_r_dev     n_nodes source densities (W/m^3) or NULL; loads are
+ *               V_i (Q_m + q_r[i]) with V_i the lumped volume
+ *   held_dev    n_nodes bytes, 1 = Dirichlet node kept at its value in T, or NULL
+ *   T_dev       n_nodes temperatures, updated in place
+ * No film condition or nodal flux; no range check.
+ * Limits: n_elems <= 131072 and n_nodes <= 160000; larger meshes get
+ * FEDFEM_E_ARG ("beyond the fixed scratch") without touching the device.
+ * FEDFEM_E_MESH: an element had det J <= 0 (T is then not meaningful).
+ * All calls share the one array and it keeps the last call's contents; two
+ * calls whose work overlaps on the GPU (other streams or other host threads)
+ * race.  The first call on each device looks up the array's device address;
+ * make that first call before any stream capture. */
+int fedfem_step_static(int elem_type, int64_t n_nodes, int64_t n_elems, const double* xyz_dev,
+                       const int32_t* conn_dev, const int32_t* row_ptr_dev, const int32_t* slot_dev,
+                       const fedfem_material* mat, const fedfem_perfusion* perf, const double* q_r_dev,
+                       const unsigned char* held_dev, double dt, int64_t n_steps, double* T_dev,
+                       void* cuda_stream);
+
 /* Testing hooks (the paper has no counterpart).  key 1: barrier spin limit in
  * clock64 ticks for later fedfem_step calls (default 4e9, or the environment
  * variable FEDFEM_BARRIER_SPIN_LIMIT).  key 2: index of a block that never

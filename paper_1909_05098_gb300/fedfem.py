@@ -93,6 +93,9 @@ _SIGS = {
     "fedfem_destroy": ([_ctx_p], None),
     "fedfem_version": ([], C.c_char_p),
     "fedfem_debug_set": ([_ctx_p, C.c_int, _i64], C.c_int),
+    "fedfem_step_static": ([C.c_int, _i64, _i64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                            C.POINTER(fedfem_material), C.POINTER(fedfem_perfusion), C.c_void_p, C.c_void_p,
+                            C.c_double, _i64, C.c_void_p, C.c_void_p], C.c_int),
 }
 for _name, (_args, _res) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -270,6 +273,21 @@ def fedfem_last_error(ctx) -> str:
 
 def fedfem_debug_set(ctx, key: int, value: int):
     _check(ctx, _lib.fedfem_debug_set(ctx, key, value))
+
+
+def fedfem_step_static(elem_type, n_nodes, n_elems, xyz_dev, conn_dev, row_ptr_dev, slot_dev, material,
+                       perfusion, q_r_dev, held_dev, dt, n_steps, T_dev, cuda_stream=0):
+    """Allocation-free explicit steps on caller-owned device buffers (raw
+    device pointers as ints; q_r_dev / held_dev may be 0).  material and
+    perfusion are (T_ref, rho0, drho, c0, dc, k0, dk) and (w_b, c_b, T_a, Q_m)."""
+    m = fedfem_material(*material)
+    p = fedfem_perfusion(*perfusion)
+    rc = _lib.fedfem_step_static(elem_type, n_nodes, n_elems, C.c_void_p(xyz_dev), C.c_void_p(conn_dev),
+                                 C.c_void_p(row_ptr_dev), C.c_void_p(slot_dev), C.byref(m), C.byref(p),
+                                 C.c_void_p(q_r_dev or 0), C.c_void_p(held_dev or 0), dt, n_steps,
+                                 C.c_void_p(T_dev), C.c_void_p(cuda_stream or 0))
+    if rc != OK:
+        raise FedfemError(rc, "fedfem_step_static")
 
 
 # ---- convenience wrapper ------------------------------------------------------
