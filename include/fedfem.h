@@ -77,7 +77,8 @@ enum { FEDFEM_ORDER_INPUT = 0, FEDFEM_ORDER_MORTON = 1, FEDFEM_ORDER_RCM = 2 };
 enum {
     FEDFEM_KERNEL_TWO_PHASE = 0,   /* one element launch and one node launch per step */
     FEDFEM_KERNEL_PERSISTENT = 1,  /* one cooperative launch for n steps, bounded grid barriers */
-    FEDFEM_KERNEL_TILED = 2        /* persistent, node tiles with their elements staged in shared memory */
+    FEDFEM_KERNEL_TILED = 2,       /* persistent, node tiles: T and element loads in shared memory, no global slots */
+    FEDFEM_KERNEL_TILED_STAGED = 3 /* as TILED, each tile's constant data streamed into shared memory by bulk copies */
 };
 
 /* Linear laws p(T) = p0 + dp (T - T_ref) for density rho [kg/m^3], specific
@@ -218,6 +219,41 @@ void fedfem_destroy(fedfem_ctx* ctx);
 
 /* Library version string. */
 const char* fedfem_version(void);
+
+/* Sizes of the layout fedfem_plan_layout returns. */
+typedef struct {
+    int64_t n_nodes, n_elems;
+    int64_t n_plain, n_free;      /* node ranges: [0,n_plain) plain free, [n_plain,n_free) film, rest Dirichlet */
+    int64_t n_slices, n_gather;   /* sliced-ELL gather over the free nodes */
+    int max_degree;
+    int tile_nodes;               /* owned nodes per tile (0: no tiles requested) */
+    int64_t n_tiles, n_tile_elems, n_halo, n_tile_gather, n_tile_slice_off;
+    int max_tile_local, max_tile_elems;
+} fedfem_layout_info;
+
+/* Host-only planning (no device work): the internal order and the gather
+ * structures that fedfem_precompute and the tiled kernel build for this mesh.
+ * For inspection and tests.  Call once with every array NULL to get the sizes
+ * in *info, then again with caller-allocated arrays:
+ *   node_of[n_nodes]       internal node -> input node
+ *   elem_of[n_elems]       internal element -> input element
+ *   slice_off[n_slices+1], gather[n_gather]: node i (internal, free) receives
+ *       the element loads gather[slice_off[i/32] + 32k + i%32], k = 0.., each
+ *       entry internal_element * elem_type + corner, pads = n_elems * elem_type,
+ *       in input element order (the summation order of every kernel)
+ *   tile_elem_off[n_tiles+1], tile_elems[n_tile_elems] (internal elements),
+ *   tile_lconn[n_tile_elems * elem_type] (tile-local node ids: owned nodes
+ *       first, then tile_halo), tile_halo_off[n_tiles+1], tile_halo[n_halo],
+ *   tile_gather_base[n_tiles], tile_slice_off[n_tile_slice_off],
+ *   tile_gather[n_tile_gather] (corner * tile_elements + j; pad = elem_type * tile_elements).
+ * tile_nodes <= 0 requests no tiles.  Mesh / Dirichlet / face arguments as in
+ * the set_* calls.  Returns FEDFEM_E_MESH / FEDFEM_E_ARG on bad input. */
+int fedfem_plan_layout(int elem_type, int64_t n_nodes, const double* xyz, int64_t n_elems, const int32_t* conn,
+                       int order, int64_t n_dirichlet, const int32_t* dirichlet_nodes, int64_t n_faces, int nverts,
+                       const int32_t* faces, int tile_nodes, fedfem_layout_info* info, int32_t* node_of,
+                       int32_t* elem_of, int32_t* slice_off, int32_t* gather, int32_t* tile_elem_off,
+                       int32_t* tile_elems, uint16_t* tile_lconn, int32_t* tile_halo_off, int32_t* tile_halo,
+                       int32_t* tile_gather_base, int32_t* tile_slice_off, uint16_t* tile_gather);
 
 /* Explicit steps that allocate nothing (the paper has no counterpart).
  *

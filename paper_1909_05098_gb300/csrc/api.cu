@@ -52,7 +52,18 @@ struct fedfem_ctx {
     double *V64 = nullptr, *Q64 = nullptr, *hA64 = nullptr;
     float *V32 = nullptr, *Q32 = nullptr, *hA32 = nullptr;
     void* T = nullptr;
+    void* T2 = nullptr;
     float* Tlo = nullptr;
+    // ---- tiled kernel (built on first use) ----
+    bool tiles_ok = false;
+    int tiles_B = 0;
+    Tiles tiles_host;          // host copy kept for the traffic model
+    std::vector<void*> tile_allocs;
+    unsigned char* t_blocks = nullptr;
+    int64_t* t_block_off = nullptr;
+    int64_t t_block_bytes = 0;
+    int t_max_block = 0, t_max_local = 0, t_fs_words = 0;
+    size_t t_smem = 0;
     void* slots = nullptr;
     int32_t* node_of = nullptr;
     double* T_dir = nullptr;
@@ -84,13 +95,22 @@ int cuda_fail(fedfem_ctx* c, cudaError_t e, const char* what) {
         if (_e != cudaSuccess) return cuda_fail(c, _e, what); \
     } while (0)
 
+void free_tiles(fedfem_ctx* c) {
+    for (void* p : c->tile_allocs) cudaFree(p);
+    c->tile_allocs.clear();
+    c->tiles_ok = false;
+    c->tiles_B = 0;
+    c->tiles_host = Tiles();
+}
+
 void free_device(fedfem_ctx* c) {
+    free_tiles(c);
     for (void* p : c->allocs) cudaFree(p);
     c->allocs.clear();
     c->dev_bytes = 0;
     c->conn4 = nullptr; c->M64 = nullptr; c->M32 = nullptr; c->sell_off = c->sell_ids = nullptr;
     c->V64 = c->Q64 = c->hA64 = nullptr; c->V32 = c->Q32 = c->hA32 = nullptr;
-    c->T = nullptr; c->Tlo = nullptr; c->slots = nullptr; c->node_of = nullptr; c->T_dir = nullptr;
+    c->T = nullptr; c->T2 = nullptr; c->Tlo = nullptr; c->slots = nullptr; c->node_of = nullptr; c->T_dir = nullptr;
     c->io = nullptr; c->st = nullptr;
     c->pre = false;
     c->inited = false;
@@ -159,7 +179,7 @@ StepArgs<R> make_args(fedfem_ctx* c, const R* M, const R* V, const R* Q, const R
     a.conn4 = c->conn4; a.M = M; a.slots = (R*)c->slots;
     a.sell_off = c->sell_off; a.sell_ids = c->sell_ids;
     a.V = V; a.Q = Q; a.hA = hA;
-    a.T = (R*)c->T; a.Tlo = (R*)c->Tlo;
+    a.T = (R*)c->T; a.T2 = (R*)c->T2; a.Tlo = (R*)c->Tlo;
     a.T_ref = (R)c->mat.T_ref; a.rho0 = (R)c->mat.rho0; a.drho = (R)c->mat.drho;
     a.c0 = (R)c->mat.c0; a.dc = (R)c->mat.dc; a.k0 = (R)c->mat.k0; a.dk = (R)c->mat.dk;
     a.wbcb = (R)(c->perf.w_b * c->perf.c_b); a.T_a = (R)c->perf.T_a; a.T_inf = (R)c->conv_Tinf;
@@ -169,9 +189,188 @@ StepArgs<R> make_args(fedfem_ctx* c, const R* M, const R* V, const R* Q, const R
     return a;
 }
 
+template <typename P>
+cudaError_t talloc(fedfem_ctx* c, P** p, size_t bytes) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, std::max<size_t>(bytes, 16));
+    if (e != cudaSuccess) return e;
+    c->tile_allocs.push_back(q);
+    *p = (P*)q;
+    return cudaSuccess;
+}
+
+// bytes of tile t's packed block (see TileArgs)
+int64_t tile_block_bytes(const Tiles& t, int64_t i, size_t rs) {
+    const int64_t ne = t.e_off[i + 1] - t.e_off[i], ne_pad = (ne + 7) / 8 * 8;
+    const int64_t nh = t.h_off[i + 1] - t.h_off[i];
+    const int64_t G = (i + 1 < t.n_tiles ? t.g_base[i + 1] : (int64_t)t.gat.size()) - t.g_base[i];
+    int64_t b = 16 + 6 * ne_pad * (int64_t)rs + ne_pad * t.nv * 2 + G * 2 + (nh + 3) / 4 * 4 * 4 +
+                (t.spt + 1 + 3) / 4 * 4 * 4;
+    return (b + 15) / 16 * 16;
+}
+
+size_t tile_smem(const Tiles& t, size_t rs, int* max_block, int* fs_words, bool staged) {
+    int64_t mb = 0, max_ne_pad = 0;
+    for (int64_t i = 0; i < t.n_tiles; ++i) {
+        mb = std::max(mb, tile_block_bytes(t, i, rs));
+        max_ne_pad = std::max<int64_t>(max_ne_pad, (t.e_off[i + 1] - t.e_off[i] + 7) / 8 * 8);
+    }
+    *max_block = (int)mb;
+    *fs_words = (int)(t.nv * max_ne_pad + 1);
+    const size_t b = (staged ? 128 + 2 * (size_t)mb : 0) + rs * ((size_t)t.max_local + *fs_words);
+    return (b + 15) / 16 * 16;
+}
+
+// Tiles for the tiled kernels.  Default size: 256 owned hex nodes (128 tet
+// nodes; halved in FP64) per tile, then adjusted so the tile count is a whole
+// number of waves of the resident grid (every block gets the same number of
+// tiles).  Each tile's constant data is packed into one 16-byte-aligned block.
+int plan_tiles(fedfem_ctx* c) {
+    if (c->tiles_ok) return FEDFEM_OK;
+    const bool staged = c->tile.kernel == FEDFEM_KERNEL_TILED_STAGED;
+    const size_t rs = c->precision == FEDFEM_FP64 ? sizeof(double) : sizeof(float);
+    const int64_t NF = c->L.N_free;
+    if (NF == 0) return fail(c, FEDFEM_E_ARG, "no free nodes");
+    int B = c->tile.tile_nodes;
+    Tiles t;
+    std::string m;
+    int mb = 0, fw = 0;
+    if (B <= 0) {
+        int B0 = c->nv == 8 ? 256 : 128;
+        if (c->precision == FEDFEM_FP64) B0 /= 2;
+        B0 = (int)std::max<int64_t>(32, std::min<int64_t>(B0, ((NF + 31) / 32) * 32));
+        m = build_tiles(c->L, B0, t);
+        if (!m.empty()) return fail(c, FEDFEM_E_ARG, m);
+        size_t smem = tile_smem(t, rs, &mb, &fw, staged);
+        int per_sm = tiled_blocks_per_sm(c->precision, c->nv, staged, smem);
+        if (c->tile.blocks_per_sm > 0) per_sm = std::min(per_sm, c->tile.blocks_per_sm);
+        if (per_sm < 1) return fail(c, FEDFEM_E_UNSUPPORTED, "tile does not fit in shared memory");
+        const int64_t grid = (int64_t)per_sm * c->sm_count;
+        const int64_t waves = std::max<int64_t>(1, (int64_t)std::llround((double)NF / ((double)B0 * grid)));
+        B = (int)(((NF + waves * grid - 1) / (waves * grid) + 31) / 32 * 32);
+        if (B > 2 * B0 || waves * grid * 32 > NF * 4) B = B0;   // small meshes: keep the default size
+    }
+    if (t.B != B) {
+        m = build_tiles(c->L, B, t);
+        if (!m.empty()) return fail(c, FEDFEM_E_ARG, m);
+    }
+    const size_t smem = tile_smem(t, rs, &mb, &fw, staged);
+    if (tiled_blocks_per_sm(c->precision, c->nv, staged, smem) < 1)
+        return fail(c, FEDFEM_E_UNSUPPORTED, "tile does not fit in shared memory; use smaller tile_nodes");
+    free_tiles(c);
+    cudaStream_t st = c->stream;
+    // element matrices back to the host once, to pack them per tile
+    const int64_t E = c->E;
+    std::vector<unsigned char> Mh(rs * 6 * E);
+    CU(cudaMemcpyAsync(Mh.data(), c->precision == FEDFEM_FP64 ? (void*)c->M64 : (void*)c->M32, rs * 6 * E,
+                       cudaMemcpyDeviceToHost, st), "tile pack");
+    CU(cudaStreamSynchronize(st), "tile pack");
+    std::vector<int64_t> off(t.n_tiles + 1, 0);
+    for (int64_t i = 0; i < t.n_tiles; ++i) off[i + 1] = off[i] + tile_block_bytes(t, i, rs);
+    std::vector<unsigned char> blob(off[t.n_tiles], 0);
+    for (int64_t i = 0; i < t.n_tiles; ++i) {
+        unsigned char* b = blob.data() + off[i];
+        const int64_t e0 = t.e_off[i], ne = t.e_off[i + 1] - e0, ne_pad = (ne + 7) / 8 * 8;
+        const int64_t h0 = t.h_off[i], nh = t.h_off[i + 1] - h0;
+        const int64_t g0 = t.g_base[i];
+        const int64_t G = (i + 1 < t.n_tiles ? t.g_base[i + 1] : (int64_t)t.gat.size()) - g0;
+        const int32_t hdr[4] = {(int32_t)ne, (int32_t)ne_pad, (int32_t)nh, (int32_t)G};
+        std::memcpy(b, hdr, 16);
+        unsigned char* Mb = b + 16;
+        for (int q = 0; q < 6; ++q)
+            for (int64_t j = 0; j < ne; ++j)
+                std::memcpy(Mb + rs * (q * ne_pad + j), Mh.data() + rs * (q * E + t.e_glob[e0 + j]), rs);
+        uint16_t* lc = (uint16_t*)(Mb + rs * 6 * ne_pad);
+        std::memcpy(lc, t.lconn.data() + e0 * t.nv, sizeof(uint16_t) * ne * t.nv);
+        uint16_t* g = lc + t.nv * ne_pad;
+        std::memcpy(g, t.gat.data() + g0, sizeof(uint16_t) * G);
+        int32_t* h = (int32_t*)(g + G);
+        std::memcpy(h, t.halo.data() + h0, sizeof(int32_t) * nh);
+        int32_t* so = h + (nh + 3) / 4 * 4;
+        std::memcpy(so, t.s_off.data() + i * (t.spt + 1), sizeof(int32_t) * (t.spt + 1));
+    }
+    CU(talloc(c, &c->t_blocks, blob.size()), "tile alloc");
+    CU(talloc(c, &c->t_block_off, sizeof(int64_t) * off.size()), "tile alloc");
+    CU(cudaMemcpyAsync(c->t_blocks, blob.data(), blob.size(), cudaMemcpyHostToDevice, st), "tile copy");
+    CU(cudaMemcpyAsync(c->t_block_off, off.data(), sizeof(int64_t) * off.size(), cudaMemcpyHostToDevice, st),
+       "tile copy");
+    CU(cudaStreamSynchronize(st), "tile build");
+    c->t_block_bytes = (int64_t)blob.size();
+    c->t_max_block = mb;
+    c->t_max_local = t.max_local;
+    c->t_fs_words = fw;
+    c->t_smem = smem;
+    c->tiles_B = t.B;
+    c->tiles_host = std::move(t);
+    c->tiles_ok = true;
+    return FEDFEM_OK;
+}
+
+template <typename R>
+TileArgs<R> make_tile_args(fedfem_ctx* c) {
+    TileArgs<R> t{};
+    const Tiles& h = c->tiles_host;
+    t.n_tiles = h.n_tiles; t.B = h.B; t.spt = h.spt; t.nv = h.nv;
+    t.blocks = c->t_blocks; t.block_off = c->t_block_off;
+    t.max_block = c->t_max_block; t.max_local = c->t_max_local; t.fs_words = c->t_fs_words;
+    t.smem_bytes = c->t_smem;
+    t.staged = c->tile.kernel == FEDFEM_KERNEL_TILED_STAGED;
+    return t;
+}
+
 }  // namespace
 
 extern "C" {
+
+int fedfem_plan_layout(int elem_type, int64_t n_nodes, const double* xyz, int64_t n_elems, const int32_t* conn,
+                       int order, int64_t n_dirichlet, const int32_t* dirichlet_nodes, int64_t n_faces, int nverts,
+                       const int32_t* faces, int tile_nodes, fedfem_layout_info* info, int32_t* node_of,
+                       int32_t* elem_of, int32_t* slice_off, int32_t* gather, int32_t* tile_elem_off,
+                       int32_t* tile_elems, uint16_t* tile_lconn, int32_t* tile_halo_off, int32_t* tile_halo,
+                       int32_t* tile_gather_base, int32_t* tile_slice_off, uint16_t* tile_gather) {
+    if (!info || !xyz || !conn || n_nodes <= 0 || n_elems <= 0) return FEDFEM_E_ARG;
+    if (elem_type != FEDFEM_HEX8 && elem_type != FEDFEM_TET4) return FEDFEM_E_ARG;
+    if (order < FEDFEM_ORDER_INPUT || order > FEDFEM_ORDER_RCM) return FEDFEM_E_ARG;
+    if (n_dirichlet < 0 || (n_dirichlet > 0 && !dirichlet_nodes)) return FEDFEM_E_ARG;
+    if (n_faces < 0 || (n_faces > 0 && (!faces || (nverts != 3 && nverts != 4)))) return FEDFEM_E_ARG;
+    std::vector<char> dir(n_nodes, 0);
+    for (int64_t i = 0; i < n_dirichlet; ++i) {
+        if (dirichlet_nodes[i] < 0 || dirichlet_nodes[i] >= n_nodes) return FEDFEM_E_ARG;
+        dir[dirichlet_nodes[i]] = 1;
+    }
+    std::vector<int32_t> fv;
+    if (n_faces > 0) {
+        fv.assign(faces, faces + n_faces * nverts);
+        for (int32_t v : fv)
+            if (v < 0 || v >= n_nodes) return FEDFEM_E_ARG;
+    }
+    MeshInput in;
+    in.nv = elem_type; in.N = n_nodes; in.E = n_elems; in.xyz = xyz; in.conn = conn;
+    in.is_dirichlet = &dir; in.conv_faces = n_faces > 0 ? &fv : nullptr; in.conv_nverts = n_faces > 0 ? nverts : 0;
+    in.order = order;
+    Layout L;
+    bool mesh_err = false;
+    std::string m = build_layout(in, L, &mesh_err);
+    if (!m.empty()) return mesh_err ? FEDFEM_E_MESH : FEDFEM_E_ARG;
+    Tiles t;
+    if (tile_nodes > 0) {
+        m = build_tiles(L, tile_nodes, t);
+        if (!m.empty()) return FEDFEM_E_ARG;
+    }
+    std::memset(info, 0, sizeof(*info));
+    info->n_nodes = n_nodes; info->n_elems = n_elems; info->n_plain = L.N_plain; info->n_free = L.N_free;
+    info->n_slices = (int64_t)L.sell_off.size() - 1; info->n_gather = (int64_t)L.sell_ids.size();
+    info->max_degree = L.max_degree;
+    info->tile_nodes = tile_nodes > 0 ? tile_nodes : 0;
+    info->n_tiles = t.n_tiles; info->n_tile_elems = (int64_t)t.e_glob.size(); info->n_halo = (int64_t)t.halo.size();
+    info->n_tile_gather = (int64_t)t.gat.size(); info->n_tile_slice_off = (int64_t)t.s_off.size();
+    info->max_tile_local = t.max_local; info->max_tile_elems = t.max_elems;
+    auto put = [](auto* dst, const auto& v) { if (dst && !v.empty()) std::memcpy(dst, v.data(), v.size() * sizeof(v[0])); };
+    put(node_of, L.node_of); put(elem_of, L.elem_of); put(slice_off, L.sell_off); put(gather, L.sell_ids);
+    put(tile_elem_off, t.e_off); put(tile_elems, t.e_glob); put(tile_lconn, t.lconn); put(tile_halo_off, t.h_off);
+    put(tile_halo, t.halo); put(tile_gather_base, t.g_base); put(tile_slice_off, t.s_off); put(tile_gather, t.gat);
+    return FEDFEM_OK;
+}
 
 const char* fedfem_version(void) { return "fedfem-gb300 0.1 (sm_103a)"; }
 
@@ -340,10 +539,12 @@ int fedfem_set_nodal_flux(fedfem_ctx* c, int64_t n, const int32_t* nodes, const 
 
 int fedfem_set_tile(fedfem_ctx* c, const fedfem_tile* t) {
     if (!c || !t) return fail(c, FEDFEM_E_ARG, "null tile");
-    if (t->kernel < FEDFEM_KERNEL_TWO_PHASE || t->kernel > FEDFEM_KERNEL_TILED) return fail(c, FEDFEM_E_ARG, "unknown kernel");
-    if (t->kernel == FEDFEM_KERNEL_TILED) return fail(c, FEDFEM_E_UNSUPPORTED, "tiled kernel not available in this build");
+    if (t->kernel < FEDFEM_KERNEL_TWO_PHASE || t->kernel > FEDFEM_KERNEL_TILED_STAGED) return fail(c, FEDFEM_E_ARG, "unknown kernel");
     if (t->block != 0 && (t->block < 64 || t->block > 1024 || t->block % 32)) return fail(c, FEDFEM_E_ARG, "block must be 64..1024, multiple of 32");
     if (t->blocks_per_sm < 0 || t->tile_nodes < 0 || t->tile_nodes % 32) return fail(c, FEDFEM_E_ARG, "bad tile knobs");
+    if (t->tile_nodes != c->tile.tile_nodes || t->blocks_per_sm != c->tile.blocks_per_sm ||
+        (t->kernel == FEDFEM_KERNEL_TILED_STAGED) != (c->tile.kernel == FEDFEM_KERNEL_TILED_STAGED))
+        free_tiles(c);
     c->tile = *t;
     return FEDFEM_OK;
 }
@@ -488,6 +689,7 @@ int fedfem_precompute(fedfem_ctx* c, double T_lo, double T_hi, double* dt_cr_out
     // ---- time-loop arrays ----
     if (c->precision == FEDFEM_FP64) {
         CU(dalloc(c, (double**)&c->T, sizeof(double) * N), "alloc");
+        CU(dalloc(c, (double**)&c->T2, sizeof(double) * N), "alloc");
         CU(dalloc(c, (double**)&c->slots, sizeof(double) * (E * nv + 1)), "alloc");
         CU(cudaMemsetAsync(c->slots, 0, sizeof(double) * (E * nv + 1), st), "memset");
     } else {
@@ -500,6 +702,7 @@ int fedfem_precompute(fedfem_ctx* c, double T_lo, double T_hi, double* dt_cr_out
         CU(launch_to_f32(c->Q64, c->Q32, NF, st), "convert");
         CU(launch_to_f32(c->hA64, c->hA32, NC, st), "convert");
         CU(dalloc(c, (float**)&c->T, sizeof(float) * N), "alloc");
+        CU(dalloc(c, (float**)&c->T2, sizeof(float) * N), "alloc");
         CU(dalloc(c, &c->Tlo, sizeof(float) * N), "alloc");
         CU(dalloc(c, (float**)&c->slots, sizeof(float) * (E * nv + 1)), "alloc");
         CU(cudaMemsetAsync(c->slots, 0, sizeof(float) * (E * nv + 1), st), "memset");
@@ -527,9 +730,16 @@ int fedfem_precompute(fedfem_ctx* c, double T_lo, double T_hi, double* dt_cr_out
     return FEDFEM_OK;
 }
 
+static int mirror_T(fedfem_ctx* c) {
+    const size_t rs = c->precision == FEDFEM_FP64 ? sizeof(double) : sizeof(float);
+    CU(cudaMemcpyAsync(c->T2, c->T, rs * c->N, cudaMemcpyDeviceToDevice, c->stream), "mirror");
+    return FEDFEM_OK;
+}
+
 static int init_common(fedfem_ctx* c) {
     CU(launch_init_state(c->precision, c->N, c->L.N_free, c->node_of, c->io, c->T_dir, c->T, c->Tlo, c->stream),
        "init kernel");
+    if (int r = mirror_T(c)) return r;
     int r = reset_status(c);
     if (r) return r;
     c->inited = true;
@@ -578,7 +788,17 @@ int fedfem_step(fedfem_ctx* c, double dt, int64_t n_steps) {
     cfg.sm_count = c->sm_count;
     cfg.spin_limit = c->spin_limit;
     cudaError_t e;
-    if (c->precision == FEDFEM_FP64) {
+    if (cfg.kernel == FEDFEM_KERNEL_TILED || cfg.kernel == FEDFEM_KERNEL_TILED_STAGED) {
+        if (int r = plan_tiles(c)) return r;
+        if (c->precision == FEDFEM_FP64) {
+            StepArgs<double> a = make_args<double>(c, c->M64, c->V64, c->Q64, c->hA64, dt);
+            e = launch_tiled_f64(a, make_tile_args<double>(c), n_steps, cfg, c->stream);
+        } else {
+            StepArgs<float> a = make_args<float>(c, c->M32, c->V32, c->Q32, c->hA32, dt);
+            e = launch_tiled_f32(a, make_tile_args<float>(c), c->precision == FEDFEM_FP32_KAHAN, n_steps, cfg,
+                                 c->stream);
+        }
+    } else if (c->precision == FEDFEM_FP64) {
         StepArgs<double> a = make_args<double>(c, c->M64, c->V64, c->Q64, c->hA64, dt);
         e = launch_steps_f64(a, c->nv, n_steps, cfg, c->stream);
     } else {
@@ -679,6 +899,7 @@ int fedfem_set_state(fedfem_ctx* c, const void* buf, size_t bytes) {
     const char* p = (const char*)buf + sizeof(h);
     CU(cudaMemcpy(c->T, p, tb, cudaMemcpyHostToDevice), "state copy");
     if (lb) CU(cudaMemcpy(c->Tlo, p + tb, lb, cudaMemcpyHostToDevice), "state copy");
+    if (int m = mirror_T(c)) return m;
     int r = reset_status(c);
     if (r) return r;
     c->inited = true;
@@ -707,6 +928,12 @@ int fedfem_get_info(fedfem_ctx* c, fedfem_info* info) {
     // two-phase / persistent model: + slot write and read, gather ids, slice offsets, T gather read once
     info->bytes_per_step = info->algorithmic_bytes_per_step + E * c->nv * 2 * R + (int64_t)L.sell_ids.size() * 4 +
                            (int64_t)L.sell_off.size() * 4;
+    if ((c->tile.kernel == FEDFEM_KERNEL_TILED || c->tile.kernel == FEDFEM_KERNEL_TILED_STAGED) && c->tiles_ok) {
+        const Tiles& t = c->tiles_host;
+        // every packed block once, halo values, owned T read; then T written, lo read+write, V, Q, hA
+        const int64_t node_rest = NF * (node_state - R + 2 * R) + NC * R;
+        info->bytes_per_step = c->t_block_bytes + (int64_t)t.halo.size() * R + NF * R + node_rest;
+    }
     info->sm_count = c->sm_count;
     info->grid_blocks = c->last.grid_used;
     info->block_threads = 256;

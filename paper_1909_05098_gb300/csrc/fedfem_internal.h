@@ -35,6 +35,26 @@ struct Layout {
     std::vector<int32_t> conv_face;
 };
 
+// Tiles of the tiled time loop: tile t owns free nodes [t*B, min((t+1)*B, N_free))
+// and holds every element touching one of them (elements on a tile edge are
+// computed by each tile that touches them).  Local node ids: owned nodes
+// first (l = i - t*B), then the halo nodes in global order.
+struct Tiles {
+    int B = 0, nv = 0, spt = 0;            // owned nodes per tile, corners, slices per tile (B/32)
+    int64_t n_tiles = 0;
+    std::vector<int32_t> e_off;            // n_tiles + 1, into the tile-element arrays
+    std::vector<int32_t> e_glob;           // internal element id of each tile element
+    std::vector<uint16_t> lconn;           // nv local node ids per tile element
+    std::vector<int32_t> h_off;            // n_tiles + 1
+    std::vector<int32_t> halo;             // global node ids
+    std::vector<int32_t> g_base;           // n_tiles: first gather entry of the tile
+    std::vector<int32_t> s_off;            // n_tiles * (spt + 1): slice offsets relative to g_base
+    std::vector<uint16_t> gat;             // corner * ne_pad + j, pad = nv * ne_pad (a zero cell); ne_pad = ne rounded up to 8
+    int max_local = 0, max_elems = 0;
+};
+
+std::string build_tiles(const Layout& L, int B, Tiles& out);
+
 struct MeshInput {
     int nv = 0;
     int64_t N = 0, E = 0;
@@ -80,6 +100,7 @@ struct StepArgs {
     const R* Q;                      // constant nodal heat flow (W), free nodes
     const R* hA;                     // film h * lumped area, nodes [N_plain, N_free)
     R* T;                            // temperature (FP64) or its hi part (FP32), all N nodes
+    R* T2;                           // second buffer of the tiled kernel (same layout as T)
     R* Tlo;                          // FP32 compensation, all N nodes (unused in FP64)
     R T_ref, rho0, drho, c0, dc, k0, dk;
     R wbcb, T_a, T_inf;
@@ -97,6 +118,32 @@ struct LaunchCfg {
     long long spin_limit = 4000000000LL;   // clock64 ticks a barrier waits before giving up
     int grid_used = 0;                     // out: grid of the last persistent launch
 };
+
+// Packed per-tile blocks of the tiled kernel, each 16-byte aligned and copied
+// whole into shared memory by one bulk (TMA) copy:
+//   int32 header {ne, ne_pad, nh, G}; M: 6 planes of ne_pad R;
+//   local connectivity: ne_pad x nv uint16; gather: G uint16 (G multiple of 32);
+//   halo ids: nh int32 (padded to 4); slice offsets: spt + 1 int32 (padded to 4).
+template <typename R>
+struct TileArgs {
+    int64_t n_tiles;
+    int B, spt, nv;
+    const unsigned char* blocks;
+    const int64_t* block_off;        // n_tiles + 1 byte offsets
+    int max_block;                   // bytes, multiple of 16
+    int max_local;                   // R words of staged temperatures
+    int fs_words;                    // R words of element loads (nv * max ne_pad + 1)
+    int staged;                      // 1: blocks bulk-copied into shared-memory stages; 0: read from global
+    size_t smem_bytes;
+};
+
+cudaError_t launch_tiled_f64(const StepArgs<double>& a, const TileArgs<double>& t, int64_t n_steps,
+                             LaunchCfg& cfg, cudaStream_t s);
+cudaError_t launch_tiled_f32(const StepArgs<float>& a, const TileArgs<float>& t, bool kahan, int64_t n_steps,
+                             LaunchCfg& cfg, cudaStream_t s);
+// occupancy (blocks per SM) of the tiled kernel for a shared-memory size
+int tiled_blocks_per_sm(int precision, int nv, int staged, size_t smem_bytes);
+int tiled_threads();
 
 cudaError_t launch_steps_f64(const StepArgs<double>& a, int nv, int64_t n_steps, LaunchCfg& cfg,
                              cudaStream_t s);

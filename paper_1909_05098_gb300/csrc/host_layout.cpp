@@ -263,3 +263,96 @@ std::string build_layout(const MeshInput& in, Layout& L, bool* mesh_error) {
 }
 
 }  // namespace fedfem
+
+namespace fedfem {
+
+std::string build_tiles(const Layout& L, int B, Tiles& T) {
+    T = Tiles();
+    const int nv = L.nv;
+    const int64_t NF = L.N_free;
+    if (B <= 0 || B % 32) return "tile size must be a positive multiple of 32";
+    T.B = B; T.nv = nv; T.spt = B / 32;
+    T.n_tiles = (NF + B - 1) / B;
+    T.e_off.assign(T.n_tiles + 1, 0);
+    T.h_off.assign(T.n_tiles + 1, 0);
+    T.g_base.assign(std::max<int64_t>(T.n_tiles, 1), 0);
+    T.s_off.assign(T.n_tiles * (T.spt + 1), 0);
+    std::vector<int32_t> elems, local_of(L.N, -1), halo;
+    std::vector<int32_t> touched;
+    for (int64_t t = 0; t < T.n_tiles; ++t) {
+        const int64_t base = t * B, own = std::min<int64_t>(B, NF - base);
+        // elements touching the owned nodes, from the nodes' slot lists
+        elems.clear();
+        for (int64_t i = base; i < base + own; ++i) {
+            const int64_t s = i / 32, lane = i % 32;
+            const int w = (L.sell_off[s + 1] - L.sell_off[s]) / 32;
+            for (int k = 0; k < w; ++k) {
+                const int32_t slot = L.sell_ids[L.sell_off[s] + 32 * k + lane];
+                if (slot < L.E * nv) elems.push_back(slot / nv);
+            }
+        }
+        std::sort(elems.begin(), elems.end());
+        elems.erase(std::unique(elems.begin(), elems.end()), elems.end());
+        const int64_t ne = (int64_t)elems.size();
+        if (ne * nv + 1 > 65535) return "tile has too many elements for 16-bit gather entries; use smaller tiles";
+        // local numbering: owned first, then halo in global order
+        touched.clear();
+        for (int32_t e : elems)
+            for (int k = 0; k < nv; ++k) {
+                const int32_t g = L.conn[(int64_t)e * nv + k];
+                if (g < base || g >= base + own) touched.push_back(g);
+            }
+        std::sort(touched.begin(), touched.end());
+        touched.erase(std::unique(touched.begin(), touched.end()), touched.end());
+        const int64_t nl = own + (int64_t)touched.size();
+        if (nl > 65535) return "tile has too many local nodes for 16-bit ids; use smaller tiles";
+        for (int64_t l = 0; l < own; ++l) local_of[base + l] = (int32_t)l;
+        for (size_t h = 0; h < touched.size(); ++h) local_of[touched[h]] = (int32_t)(own + h);
+        for (int32_t e : elems) {
+            T.e_glob.push_back(e);
+            for (int k = 0; k < nv; ++k) T.lconn.push_back((uint16_t)local_of[L.conn[(int64_t)e * nv + k]]);
+        }
+        T.halo.insert(T.halo.end(), touched.begin(), touched.end());
+        // gather lists of the owned nodes, in the global (input element) order
+        const int64_t gb = (int64_t)T.gat.size();
+        if (gb > INT32_MAX) return "gather lists too large";
+        T.g_base[t] = (int32_t)gb;
+        int32_t* so = &T.s_off[t * (T.spt + 1)];
+        const int64_t ne_pad = (ne + 7) / 8 * 8;
+        if (ne_pad * nv + 1 > 65535) return "tile has too many elements for 16-bit gather entries; use smaller tiles";
+        const uint16_t pad = (uint16_t)(nv * ne_pad);
+        int32_t cur = 0;
+        for (int s = 0; s < T.spt; ++s) {
+            so[s] = cur;
+            const int64_t i0 = base + 32 * s;
+            if (i0 >= base + own) continue;
+            const int64_t gs = i0 / 32;      // global slice (B is a multiple of 32)
+            const int w = (L.sell_off[gs + 1] - L.sell_off[gs]) / 32;
+            for (int k = 0; k < w; ++k)
+                for (int lane = 0; lane < 32; ++lane) {
+                    const int64_t i = i0 + lane;
+                    uint16_t v = pad;
+                    if (i < base + own) {
+                        const int32_t slot = L.sell_ids[L.sell_off[gs] + 32 * k + lane];
+                        if (slot < L.E * nv) {
+                            const int32_t e = slot / nv, corner = slot % nv;
+                            const int64_t j = std::lower_bound(elems.begin(), elems.end(), e) - elems.begin();
+                            v = (uint16_t)(corner * ne_pad + j);
+                        }
+                    }
+                    T.gat.push_back(v);
+                }
+            cur += 32 * w;
+        }
+        so[T.spt] = cur;
+        for (int64_t l = 0; l < own; ++l) local_of[base + l] = -1;
+        for (int32_t g : touched) local_of[g] = -1;
+        T.e_off[t + 1] = T.e_off[t] + (int32_t)ne;
+        T.h_off[t + 1] = T.h_off[t] + (int32_t)touched.size();
+        T.max_local = std::max<int>(T.max_local, (int)nl);
+        T.max_elems = std::max<int>(T.max_elems, (int)ne);
+    }
+    return "";
+}
+
+}  // namespace fedfem

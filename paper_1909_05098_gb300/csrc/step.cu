@@ -72,16 +72,10 @@ __device__ __forceinline__ void flag_range(DevStatus* st, int64_t i, long long s
     atomicMin(&st->fail_node, (long long)i);
 }
 
-// returns false when the node left [T_lo, T_hi] (or became NaN)
+// Eq. 19 for free node i: T is its current (hi) value, F the summed element
+// loads; writes the new value to Tout[i] (and the compensation in place).
 template <typename R, bool KAHAN>
-__device__ __forceinline__ void node_phase(const StepArgs<R>& a, int64_t i, long long step) {
-    const int64_t s = i >> 5;
-    const int lane = (int)(i & 31);
-    const int32_t off = a.sell_off[s];
-    const int w = (a.sell_off[s + 1] - off) >> 5;
-    R F = R(0);
-    for (int k = 0; k < w; ++k) F = F + a.slots[a.sell_ids[off + 32 * k + lane]];
-    const R T = a.T[i];
+__device__ __forceinline__ void node_update(const StepArgs<R>& a, int64_t i, R T, R F, R* Tout, long long step) {
     const R u = T - a.T_ref;
     const R rho = a.rho0 + a.drho * u;
     const R c = a.c0 + a.dc * u;
@@ -99,8 +93,20 @@ __device__ __forceinline__ void node_phase(const StepArgs<R>& a, int64_t i, long
     } else {
         Tn = T + dT;
     }
-    a.T[i] = Tn;
+    Tout[i] = Tn;
     if (!(Tn >= a.T_lo && Tn <= a.T_hi)) flag_range(a.status, i, step);
+}
+
+// gather of node i's element loads from the global slots, in its fixed order
+template <typename R, bool KAHAN>
+__device__ __forceinline__ void node_phase(const StepArgs<R>& a, int64_t i, long long step) {
+    const int64_t s = i >> 5;
+    const int lane = (int)(i & 31);
+    const int32_t off = a.sell_off[s];
+    const int w = (a.sell_off[s + 1] - off) >> 5;
+    R F = R(0);
+    for (int k = 0; k < w; ++k) F = F + a.slots[a.sell_ids[off + 32 * k + lane]];
+    node_update<R, KAHAN>(a, i, a.T[i], F, a.T, step);
 }
 
 template <typename R, int NV>
@@ -174,6 +180,246 @@ __global__ void __launch_bounds__(256) k_persistent(StepArgs<R> a, long long n_s
     if (blockIdx.x == 0 && threadIdx.x == 0) a.status->steps_done = a.step0 + done;
 }
 
+// ---- tiled persistent kernel ------------------------------------------------
+// Tile t owns free nodes [t*B, t*B + own).  Its constant data (element
+// matrices, 16-bit local connectivity, 16-bit gather lists, halo ids, slice
+// offsets) is one packed block that a bulk (TMA) copy brings into a shared-
+// memory stage; two stages alternate, so the next tile's block (and, across
+// the grid barrier, the next step's first block) is in flight while the
+// current tile computes.  Per tile: stage owned + halo temperatures, compute
+// the loads of every element touching an owned node into shared memory, sum
+// each owned node's loads in its fixed order, update.  T is double-buffered
+// (tiles read their neighbours' nodes as halo), so one grid barrier per step.
+
+constexpr int kTiledThreads = 512;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait for a stage: false after spin_limit clock64 ticks
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long spin_limit) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > spin_limit) return false;
+    return true;
+}
+
+template <int NV>
+struct LConn;
+template <>
+struct LConn<8> {
+    static __device__ __forceinline__ void load(const uint16_t* p, int j, int c[8]) {
+        const uint4 v = reinterpret_cast<const uint4*>(p)[j];
+        c[0] = v.x & 0xffff; c[1] = v.x >> 16; c[2] = v.y & 0xffff; c[3] = v.y >> 16;
+        c[4] = v.z & 0xffff; c[5] = v.z >> 16; c[6] = v.w & 0xffff; c[7] = v.w >> 16;
+    }
+};
+template <>
+struct LConn<4> {
+    static __device__ __forceinline__ void load(const uint16_t* p, int j, int c[4]) {
+        const uint2 v = reinterpret_cast<const uint2*>(p)[j];
+        c[0] = v.x & 0xffff; c[1] = v.x >> 16; c[2] = v.y & 0xffff; c[3] = v.y >> 16;
+    }
+};
+
+template <typename R, int NV, bool KAHAN>
+__device__ __forceinline__ void tile_compute(const StepArgs<R>& a, const TileArgs<R>& ta, int64_t t,
+                                             const unsigned char* blk, const R* Tin, R* Tout, long long step, R* Ts,
+                                             R* Fs) {
+    const int4 hdr = *reinterpret_cast<const int4*>(blk);
+    const int ne = hdr.x, ne_pad = hdr.y, nh = hdr.z, G = hdr.w;
+    const R* M = reinterpret_cast<const R*>(blk + 16);
+    const uint16_t* lc = reinterpret_cast<const uint16_t*>(blk + 16 + 6 * (size_t)ne_pad * sizeof(R));
+    const uint16_t* gat = lc + NV * ne_pad;
+    const int32_t* halo = reinterpret_cast<const int32_t*>(gat + G);
+    const int32_t* so = halo + ((nh + 3) & ~3);
+    const int64_t base = t * ta.B;
+    const int own = (int)min((int64_t)ta.B, a.N_free - base);
+    for (int l = threadIdx.x; l < own; l += blockDim.x) Ts[l] = Tin[base + l];
+    for (int h = threadIdx.x; h < nh; h += blockDim.x) Ts[own + h] = Tin[halo[h]];
+    if (threadIdx.x == 0) Fs[NV * ne_pad] = R(0);
+    __syncthreads();
+    const Law<R> k{a.T_ref, a.k0, a.dk};
+    for (int j = threadIdx.x; j < ne; j += blockDim.x) {
+        int c[NV];
+        LConn<NV>::load(lc, j, c);
+        R tt[NV];
+#pragma unroll
+        for (int n = 0; n < NV; ++n) tt[n] = Ts[c[n]];
+        R m[6];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) m[q] = M[q * ne_pad + j];
+        const R ke = element_k<R, NV>(tt, k);
+        R F[NV];
+        if (NV == 8) hex8_loads<R>(tt, m, ke, F);
+        else tet4_loads<R>(tt, m, ke, F);
+#pragma unroll
+        for (int n = 0; n < NV; ++n) Fs[n * ne_pad + j] = F[n];
+    }
+    __syncthreads();
+    for (int l = threadIdx.x; l < own; l += blockDim.x) {
+        const int sl = l >> 5, lane = l & 31;
+        const int32_t off = so[sl];
+        const int w = (so[sl + 1] - off) >> 5;
+        const uint16_t* g = gat + off + lane;
+        R F = R(0);
+        for (int q = 0; q < w; ++q) F = F + Fs[g[32 * q]];
+        node_update<R, KAHAN>(a, base + l, Ts[l], F, Tout, step);
+    }
+}
+
+// Direct variant: the same per-tile blocks read straight from global memory
+// (coalesced within a tile), shared memory only for T and the element loads,
+// so more blocks fit on an SM.
+template <typename R, int NV, bool KAHAN>
+__global__ void __launch_bounds__(256) k_tiled_direct(StepArgs<R> a, TileArgs<R> ta, long long n_steps,
+                                                      long long spin_limit) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    R* Ts = reinterpret_cast<R*>(smem);
+    R* Fs = Ts + ta.max_local;
+    unsigned long long target = 0;
+    long long done = 0;
+    if (!grid_barrier(a.status, target, spin_limit)) return;
+    for (long long s = 0; s < n_steps; ++s) {
+        const R* Tin = (s & 1) ? a.T2 : a.T;
+        R* Tout = (s & 1) ? a.T : a.T2;
+        for (int64_t t = blockIdx.x; t < ta.n_tiles; t += gridDim.x) {
+            tile_compute<R, NV, KAHAN>(a, ta, t, ta.blocks + ta.block_off[t], Tin, Tout, a.step0 + s, Ts, Fs);
+            __syncthreads();
+        }
+        const bool ok = grid_barrier(a.status, target, spin_limit);
+        done = s + 1;
+        if (!ok) break;
+    }
+    if (done & 1) {
+        const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.N_free; i += stride) a.T[i] = a.T2[i];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.status->steps_done = a.step0 + done;
+}
+
+template <typename R, int NV, bool KAHAN>
+__global__ void __launch_bounds__(kTiledThreads) k_tiled(StepArgs<R> a, TileArgs<R> ta, long long n_steps,
+                                                         long long spin_limit) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
+    unsigned char* const stage0 = smem + 128;
+    unsigned char* const stage1 = smem + 128 + ta.max_block;
+    R* Ts = reinterpret_cast<R*>(smem + 128 + 2 * (size_t)ta.max_block);
+    R* Fs = Ts + ta.max_local;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    unsigned long long target = 0;
+    long long done = 0;
+    if (!grid_barrier(a.status, target, spin_limit)) return;
+    const int64_t first = blockIdx.x;
+    const int64_t n_my = first < ta.n_tiles ? (ta.n_tiles - 1 - first) / gridDim.x + 1 : 0;
+    const bool single = n_my == 1;   // one tile per block: its block stays resident across steps
+    uint32_t ph0 = 0u, ph1 = 0u;
+    bool pending = false;
+    int pbuf = 0;
+    auto issue = [&](int64_t t, int buf) {
+        const int64_t o = ta.block_off[t];
+        const uint32_t bytes = (uint32_t)(ta.block_off[t + 1] - o);
+        mbar_expect_tx(&bar[buf], bytes);
+        bulk_g2s(buf ? stage1 : stage0, ta.blocks + o, bytes, &bar[buf]);
+    };
+    if (n_my > 0) {
+        if (threadIdx.x == 0) issue(first, 0);
+        pending = true;
+        pbuf = 0;
+    }
+    long long kk = 0;
+    bool stop = false;
+    for (long long s = 0; s < n_steps && !stop; ++s) {
+        const R* Tin = (s & 1) ? a.T2 : a.T;
+        R* Tout = (s & 1) ? a.T : a.T2;
+        for (int64_t i = 0; i < n_my; ++i, ++kk) {
+            const int64_t t = first + i * gridDim.x;
+            const int buf = single ? 0 : (int)(kk & 1);
+            if (pending && pbuf == buf) {
+                const uint32_t ph = buf ? ph1 : ph0;
+                if (!mbar_wait(&bar[buf], ph, spin_limit)) {
+                    if (threadIdx.x == 0) atomicOr(&a.status->flags, STATUS_TIMEOUT);
+                    mbar_wait(&bar[buf], ph, spin_limit);   // the copy is from global memory: let it land
+                    return;
+                }
+                if (buf) ph1 ^= 1u; else ph0 ^= 1u;
+                pending = false;
+            }
+            __syncthreads();   // every thread is done with the other stage
+            if (!single && (i + 1 < n_my || s + 1 < n_steps)) {
+                const int64_t tn = (i + 1 < n_my) ? t + gridDim.x : first;
+                if (threadIdx.x == 0) {
+                    fence_proxy_async();
+                    issue(tn, buf ^ 1);
+                }
+                pending = true;
+                pbuf = buf ^ 1;
+            }
+            tile_compute<R, NV, KAHAN>(a, ta, t, buf ? stage1 : stage0, Tin, Tout, a.step0 + s, Ts, Fs);
+        }
+        const bool ok = grid_barrier(a.status, target, spin_limit);
+        done = s + 1;
+        if (!ok) stop = true;
+    }
+    if (pending) mbar_wait(&bar[pbuf], pbuf ? ph1 : ph0, spin_limit);   // a prefetch nobody consumed
+    if (done & 1) {   // the newest values are in T2: copy them back so that T is current
+        const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.N_free; i += stride) a.T[i] = a.T2[i];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.status->steps_done = a.step0 + done;
+}
+
+template <typename R, int NV, bool KAHAN>
+cudaError_t launch_tiled_impl(const StepArgs<R>& a, const TileArgs<R>& ta, int64_t n_steps, LaunchCfg& cfg,
+                              cudaStream_t s) {
+    auto kern = ta.staged ? k_tiled<R, NV, KAHAN> : k_tiled_direct<R, NV, KAHAN>;
+    const int b = ta.staged ? kTiledThreads : 256;
+    cudaError_t err = cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)ta.smem_bytes);
+    if (err != cudaSuccess) return err;
+    int per_sm = 0;
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, b, ta.smem_bytes);
+    if (err != cudaSuccess) return err;
+    if (cfg.blocks_per_sm > 0) per_sm = std::min(per_sm, cfg.blocks_per_sm);
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * cfg.sm_count, ta.n_tiles));
+    cfg.grid_used = grid;
+    StepArgs<R> args = a;
+    TileArgs<R> targs = ta;
+    long long n = n_steps, lim = cfg.spin_limit;
+    void* params[] = {&args, &targs, &n, &lim};
+    err = cudaMemsetAsync(&a.status->barrier, 0, sizeof(unsigned long long), s);
+    if (err != cudaSuccess) return err;
+    return cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(b), params, ta.smem_bytes, s);
+}
+
 inline int blocks_for(int64_t n, int t) {
     return (int)std::max<int64_t>(1, std::min<int64_t>((n + t - 1) / t, INT_MAX));
 }
@@ -208,6 +454,41 @@ cudaError_t launch_impl(const StepArgs<R>& a, int64_t n_steps, LaunchCfg& cfg, c
 }
 
 }  // namespace
+
+cudaError_t launch_tiled_f64(const StepArgs<double>& a, const TileArgs<double>& t, int64_t n_steps, LaunchCfg& cfg,
+                             cudaStream_t s) {
+    return t.nv == 8 ? launch_tiled_impl<double, 8, false>(a, t, n_steps, cfg, s)
+                     : launch_tiled_impl<double, 4, false>(a, t, n_steps, cfg, s);
+}
+
+cudaError_t launch_tiled_f32(const StepArgs<float>& a, const TileArgs<float>& t, bool kahan, int64_t n_steps,
+                             LaunchCfg& cfg, cudaStream_t s) {
+    if (t.nv == 8)
+        return kahan ? launch_tiled_impl<float, 8, true>(a, t, n_steps, cfg, s)
+                     : launch_tiled_impl<float, 8, false>(a, t, n_steps, cfg, s);
+    return kahan ? launch_tiled_impl<float, 4, true>(a, t, n_steps, cfg, s)
+                 : launch_tiled_impl<float, 4, false>(a, t, n_steps, cfg, s);
+}
+
+int tiled_blocks_per_sm(int precision, int nv, int staged, size_t smem) {
+    const int block = staged ? kTiledThreads : 256;
+    const void* k = nullptr;
+    if (staged) {
+        if (precision == FEDFEM_FP64) k = nv == 8 ? (const void*)k_tiled<double, 8, false> : (const void*)k_tiled<double, 4, false>;
+        else if (precision == FEDFEM_FP32_KAHAN) k = nv == 8 ? (const void*)k_tiled<float, 8, true> : (const void*)k_tiled<float, 4, true>;
+        else k = nv == 8 ? (const void*)k_tiled<float, 8, false> : (const void*)k_tiled<float, 4, false>;
+    } else {
+        if (precision == FEDFEM_FP64) k = nv == 8 ? (const void*)k_tiled_direct<double, 8, false> : (const void*)k_tiled_direct<double, 4, false>;
+        else if (precision == FEDFEM_FP32_KAHAN) k = nv == 8 ? (const void*)k_tiled_direct<float, 8, true> : (const void*)k_tiled_direct<float, 4, true>;
+        else k = nv == 8 ? (const void*)k_tiled_direct<float, 8, false> : (const void*)k_tiled_direct<float, 4, false>;
+    }
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, smem) != cudaSuccess) return 0;
+    return per_sm;
+}
+
+int tiled_threads() { return kTiledThreads; }
 
 cudaError_t launch_steps_f64(const StepArgs<double>& a, int nv, int64_t n_steps, LaunchCfg& cfg, cudaStream_t s) {
     return nv == 8 ? launch_impl<double, 8, false>(a, n_steps, cfg, s) : launch_impl<double, 4, false>(a, n_steps, cfg, s);

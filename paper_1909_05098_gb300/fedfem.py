@@ -23,7 +23,7 @@ OK, E_ARG, E_MESH, E_STATE, E_UNSTABLE_DT, E_RANGE, E_TIMEOUT, E_CUDA, E_OOM, E_
 TET4, HEX8 = 4, 8
 FP64, FP32_KAHAN, FP32_PLAIN = 0, 1, 2
 ORDER_INPUT, ORDER_MORTON, ORDER_RCM = 0, 1, 2
-KERNEL_TWO_PHASE, KERNEL_PERSISTENT, KERNEL_TILED = 0, 1, 2
+KERNEL_TWO_PHASE, KERNEL_PERSISTENT, KERNEL_TILED, KERNEL_TILED_STAGED = 0, 1, 2, 3
 
 STATUS_NAMES = {0: "OK", -1: "E_ARG", -2: "E_MESH", -3: "E_STATE", -4: "E_UNSTABLE_DT", -5: "E_RANGE",
                 -6: "E_TIMEOUT", -7: "E_CUDA", -8: "E_OOM", -9: "E_UNSUPPORTED"}
@@ -45,6 +45,17 @@ class fedfem_perfusion(C.Structure):
 
 class fedfem_tile(C.Structure):
     _fields_ = [("kernel", C.c_int), ("block", C.c_int), ("tile_nodes", C.c_int), ("blocks_per_sm", C.c_int)]
+
+
+class fedfem_layout_info(C.Structure):
+    _fields_ = [("n_nodes", C.c_int64), ("n_elems", C.c_int64), ("n_plain", C.c_int64), ("n_free", C.c_int64),
+                ("n_slices", C.c_int64), ("n_gather", C.c_int64), ("max_degree", C.c_int),
+                ("tile_nodes", C.c_int), ("n_tiles", C.c_int64), ("n_tile_elems", C.c_int64),
+                ("n_halo", C.c_int64), ("n_tile_gather", C.c_int64), ("n_tile_slice_off", C.c_int64),
+                ("max_tile_local", C.c_int), ("max_tile_elems", C.c_int)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
 
 
 class fedfem_info(C.Structure):
@@ -93,6 +104,8 @@ _SIGS = {
     "fedfem_destroy": ([_ctx_p], None),
     "fedfem_version": ([], C.c_char_p),
     "fedfem_debug_set": ([_ctx_p, C.c_int, _i64], C.c_int),
+    "fedfem_plan_layout": ([C.c_int, _i64, _dp, _i64, _ip, C.c_int, _i64, _ip, _i64, C.c_int, _ip, C.c_int,
+                            C.POINTER(fedfem_layout_info)] + [C.c_void_p] * 12, C.c_int),
     "fedfem_step_static": ([C.c_int, _i64, _i64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                             C.POINTER(fedfem_material), C.POINTER(fedfem_perfusion), C.c_void_p, C.c_void_p,
                             C.c_double, _i64, C.c_void_p, C.c_void_p], C.c_int),
@@ -273,6 +286,46 @@ def fedfem_last_error(ctx) -> str:
 
 def fedfem_debug_set(ctx, key: int, value: int):
     _check(ctx, _lib.fedfem_debug_set(ctx, key, value))
+
+
+def fedfem_plan_layout(elem_type, xyz, conn, order=ORDER_MORTON, dirichlet_nodes=(), faces=None,
+                       tile_nodes=0) -> dict:
+    """Host-only layout planning (no GPU needed); returns the info dict and arrays."""
+    x, px = _d(xyz)
+    c, pc = _i(conn)
+    dn, pdn = _i(np.asarray(dirichlet_nodes, dtype=np.int32).reshape(-1))
+    if faces is None or len(faces) == 0:
+        fc, pfc, nf, nvf = None, None, 0, 3
+    else:
+        fc, pfc = _i(faces)
+        nf, nvf = fc.shape[0], fc.shape[1]
+    info = fedfem_layout_info()
+    args = [elem_type, x.shape[0], px, c.shape[0], pc, order, dn.shape[0], pdn, nf, nvf, pfc, tile_nodes,
+            C.byref(info)]
+    rc = _lib.fedfem_plan_layout(*args, *([None] * 12))
+    if rc != OK:
+        raise FedfemError(rc, "fedfem_plan_layout")
+    d = info.as_dict()
+    arrs = {
+        "node_of": np.empty(d["n_nodes"], np.int32), "elem_of": np.empty(d["n_elems"], np.int32),
+        "slice_off": np.empty(d["n_slices"] + 1, np.int32), "gather": np.empty(d["n_gather"], np.int32),
+        "tile_elem_off": np.empty(d["n_tiles"] + 1, np.int32), "tile_elems": np.empty(d["n_tile_elems"], np.int32),
+        "tile_lconn": np.empty(d["n_tile_elems"] * elem_type, np.uint16),
+        "tile_halo_off": np.empty(d["n_tiles"] + 1, np.int32), "tile_halo": np.empty(d["n_halo"], np.int32),
+        "tile_gather_base": np.empty(d["n_tiles"], np.int32),
+        "tile_slice_off": np.empty(d["n_tile_slice_off"], np.int32),
+        "tile_gather": np.empty(d["n_tile_gather"], np.uint16),
+    }
+    ptrs = [a.ctypes.data_as(C.c_void_p) for a in arrs.values()]
+    rc = _lib.fedfem_plan_layout(*args, *ptrs)
+    if rc != OK:
+        raise FedfemError(rc, "fedfem_plan_layout")
+    if d["n_tiles"] == 0:
+        for k in list(arrs):
+            if k.startswith("tile_"):
+                arrs[k] = arrs[k][:0]
+    d.update(arrs)
+    return d
 
 
 def fedfem_step_static(elem_type, n_nodes, n_elems, xyz_dev, conn_dev, row_ptr_dev, slot_dev, material,

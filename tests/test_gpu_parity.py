@@ -54,9 +54,32 @@ def test_every_kernel_and_order_is_bit_identical(cube):
     for prec in (f.FP64, f.FP32_KAHAN):
         base, _ = run_gpu(w.problem, dt, 300, prec, order=f.ORDER_MORTON, kernel=f.KERNEL_PERSISTENT)
         for order in (f.ORDER_INPUT, f.ORDER_MORTON, f.ORDER_RCM):
-            for kernel in (f.KERNEL_TWO_PHASE, f.KERNEL_PERSISTENT):
+            for kernel in (f.KERNEL_TWO_PHASE, f.KERNEL_PERSISTENT, f.KERNEL_TILED, f.KERNEL_TILED_STAGED):
                 T, _ = run_gpu(w.problem, dt, 300, prec, order=order, kernel=kernel)
                 assert np.array_equal(T, base), (prec, order, kernel)
+
+
+@pytest.mark.parametrize("n_steps", [1, 2, 7])
+def test_tiled_kernel_odd_even_steps_and_tets(n_steps):
+    """The tiled kernel double-buffers T; any step count must leave the same
+    state as the other kernels, for hex and tet meshes and several tile sizes."""
+    f = ff()
+    for w in (cube_hex_td_convective(n=14), ellipsoid_tet_td(h=2e-3, axes=(0.024, 0.018, 0.014))):
+        p = w.problem
+        dt = 0.5 * critical_dt(Oracle(p))
+        base, _ = run_gpu(p, dt, n_steps, f.FP32_KAHAN, kernel=f.KERNEL_PERSISTENT)
+        for kern, B in ((f.KERNEL_TILED, 0), (f.KERNEL_TILED, 64), (f.KERNEL_TILED, 160),
+                        (f.KERNEL_TILED_STAGED, 0), (f.KERNEL_TILED_STAGED, 96)):
+            s = f.Solver(p, precision=f.FP32_KAHAN)
+            try:
+                f.fedfem_set_tile(s.ctx, kern, 0, B, 0)
+                s.step(dt, n_steps)
+                assert s.sync() == n_steps
+                assert np.array_equal(s.temperature(), base), (p.elem_type, kern, B, n_steps)
+                s.step(dt, 3)        # continue after an odd/even count
+                s.sync()
+            finally:
+                s.close()
 
 
 @pytest.mark.parametrize("prec_name", ["FP64", "FP32_KAHAN"])
@@ -95,6 +118,6 @@ def test_uniform_field_bit_unchanged_on_gpu():
     p.conv_T_inf = 37.0
     f = ff()
     for prec in (f.FP64, f.FP32_KAHAN, f.FP32_PLAIN):
-        for kernel in (f.KERNEL_TWO_PHASE, f.KERNEL_PERSISTENT):
+        for kernel in (f.KERNEL_TWO_PHASE, f.KERNEL_PERSISTENT, f.KERNEL_TILED, f.KERNEL_TILED_STAGED):
             T, _ = run_gpu(p, 1.0, 200, prec, kernel=kernel)
             assert np.all(T == 37.0), (prec, kernel)
