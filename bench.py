@@ -45,7 +45,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--steps-per-launch", type=int, default=STEPS_PER_LAUNCH)
     ap.add_argument("--n", type=int, default=WORKLOAD_N, help="cube edge in elements")
-    ap.add_argument("--kernel", default="persistent", choices=["two_phase", "persistent", "tiled"])
+    ap.add_argument("--kernel", default="auto", choices=["auto", "two_phase", "persistent", "tiled", "tiled_staged"])
+    ap.add_argument("--tile-nodes", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -275,15 +276,27 @@ def run_ours(args):
     from paper_1909_05098_gb300 import fedfem as ff
     from synth.scenarios import cube_hex_td_convective
 
-    kernel = {"two_phase": ff.KERNEL_TWO_PHASE, "persistent": ff.KERNEL_PERSISTENT,
-              "tiled": ff.KERNEL_TILED}[args.kernel]
+    names = {ff.KERNEL_TWO_PHASE: "two_phase", ff.KERNEL_PERSISTENT: "persistent", ff.KERNEL_TILED: "tiled",
+             ff.KERNEL_TILED_STAGED: "tiled_staged"}
     S = args.steps_per_launch
     w = cube_hex_td_convective(n=args.n)
     p = w.problem
     stream = torch.cuda.Stream(device=dev)
-    solver = ff.Solver(p, precision=ff.FP32_KAHAN, device=local, stream=stream.cuda_stream, kernel=kernel)
-    info = solver.info()
+    solver = ff.Solver(p, precision=ff.FP32_KAHAN, device=local, stream=stream.cuda_stream,
+                       kernel=ff.KERNEL_PERSISTENT)
     dt = 0.5 * solver.dt_cr
+    tuned = None
+    if args.kernel == "auto":
+        from paper_1909_05098_gb300.autotune import tune
+        tuned = tune(solver, dt, use_cache=False, stream=stream)
+        kernel = tuned["kernel"]
+    else:
+        kernel = {v: k for k, v in names.items()}[args.kernel]
+        ff.fedfem_set_tile(solver.ctx, kernel, 0, args.tile_nodes, 0)
+    solver.step(dt, 1)      # plans tiles if needed
+    solver.sync()
+    solver.init()
+    info = solver.info()
     N = info["n_nodes"]
 
     def timed(K):
@@ -322,7 +335,7 @@ def run_ours(args):
     # error of this FP32+Kahan run against an FP64 GPU run of the same steps
     # (the FP64 path is pinned to the oracle by the parity tests)
     T32 = solver.temperature()
-    ref64 = ff.Solver(p, precision=ff.FP64, device=local, stream=stream.cuda_stream, kernel=kernel)
+    ref64 = ff.Solver(p, precision=ff.FP64, device=local, stream=stream.cuda_stream, kernel=ff.KERNEL_PERSISTENT)
     ref64.step(dt, steps_done)
     ref64.sync()
     max_err = float(np.max(np.abs(T32 - ref64.temperature())))
@@ -349,8 +362,7 @@ def run_ours(args):
     launch_s = float(np.mean(per_launch_ms)) / 1e3
     peak, peak_src = measured_peak()
     achieved = alg_bytes_launch / launch_s / 1e9
-    traffic = ncu_traffic(f"persistent_fp32_kahan_hex8" if kernel == ff.KERNEL_PERSISTENT else args.kernel,
-                          args.n, S)
+    traffic = ncu_traffic(names[kernel] + "_fp32_kahan_hex8", args.n, S)
     solver.close()
     if rank != 0:
         return
@@ -359,7 +371,12 @@ def run_ours(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": workload_name(args.n), "nodes": N, "elements": info["n_elems"],
-                   "time_steps_per_bench_step": S, "kernel": args.kernel, "precision": "FP32+Kahan",
+                   "time_steps_per_bench_step": S, "kernel": names[kernel],
+                   "tile_nodes": info["tile_nodes"], "grid_blocks": info["grid_blocks"],
+                   "autotune": None if tuned is None else
+                   {names[t["kernel"]] + (f"/{t['tile_nodes']}" if t["tile_nodes"] else ""):
+                    round(t.get("us_per_step", -1), 1) for t in tuned["trials"]},
+                   "precision": "FP32+Kahan",
                    "dt_s": dt, "dt_cr_s": solver.dt_cr,
                    "l2": f"inputs larger than L2: {info['bytes_per_step'] / 1e6:.0f} MB moved per time step",
                    "parallelism": f"replicas x{world}"},

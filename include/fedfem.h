@@ -113,6 +113,8 @@ typedef struct {
     int64_t bytes_per_step;    /* bytes the chosen kernel reads and writes per time step (model) */
     int64_t algorithmic_bytes_per_step; /* minimum bytes any step must move (fused model) */
     int sm_count, grid_blocks, block_threads;
+    int kernel;                /* FEDFEM_KERNEL_* in use */
+    int tile_nodes;            /* owned nodes per tile of the tiled kernels (0 if none built) */
 } fedfem_info;
 
 /* Create a context on CUDA device `device`.  `precision` is a FEDFEM_FP*

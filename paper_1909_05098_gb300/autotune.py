@@ -1,0 +1,99 @@
+"""Autotuner for the time-loop launch knobs.
+
+Every kernel family and tile size gives bit-identical temperatures (the
+per-node summation order is fixed by the input mesh), so the choice is purely
+one of speed.  ``tune`` times each candidate on the live context with CUDA
+events, restores the context's state afterwards (checkpoint API), applies the
+fastest candidate and caches it under a signature of the mesh, precision and
+device.
+"""
+from __future__ import annotations
+
+import json
+import os
+import time
+
+from . import fedfem as ff
+
+CACHE = os.environ.get("FEDFEM_TUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "fedfem_tune.json"))
+
+
+def candidates(elem_type: int, precision: int):
+    """(kernel, tile_nodes, blocks_per_sm) triples; tile_nodes 0 = the library's default."""
+    out = [(ff.KERNEL_PERSISTENT, 0, 0)]
+    sizes = (0, 128, 256, 384) if elem_type == ff.HEX8 else (0, 64, 96, 128, 192)
+    staged = (0, 256, 384, 512) if elem_type == ff.HEX8 else (0, 128, 192)
+    if precision == ff.FP64:
+        sizes = tuple(s // 2 for s in sizes if s)[:2] + (0,)
+        staged = (0,)
+    out += [(ff.KERNEL_TILED, b, 0) for b in sizes]
+    out += [(ff.KERNEL_TILED_STAGED, b, 0) for b in staged]
+    return out
+
+
+def signature(info: dict, device_name: str) -> str:
+    return (f"{device_name}|nv{info['elem_type']}|p{info['precision']}|N{info['n_nodes']}|E{info['n_elems']}|"
+            f"F{info['n_free']}|C{info['n_convective']}|o{info['order']}")
+
+
+def _load_cache():
+    try:
+        return json.load(open(CACHE))
+    except Exception:
+        return {}
+
+
+def _save_cache(d):
+    try:
+        os.makedirs(os.path.dirname(CACHE), exist_ok=True)
+        json.dump(d, open(CACHE, "w"), indent=1)
+    except Exception:
+        pass
+
+
+def tune(solver, dt: float, steps: int = 30, use_cache: bool = True, stream=None, verbose: bool = False) -> dict:
+    """Pick the fastest launch configuration for ``solver`` (a fedfem.Solver)
+    and apply it.  Returns {"kernel", "tile_nodes", "blocks_per_sm", "us_per_step", "trials"}."""
+    import torch
+    ctx = solver.ctx
+    info = ff.fedfem_get_info(ctx)
+    sig = signature(info, torch.cuda.get_device_name())
+    cache = _load_cache() if use_cache else {}
+    if sig in cache:
+        best = cache[sig]
+        ff.fedfem_set_tile(ctx, best["kernel"], 0, best["tile_nodes"], best["blocks_per_sm"])
+        best = dict(best, cached=True)
+        return best
+    saved = ff.fedfem_get_state(ctx)
+    s = stream if stream is not None else torch.cuda.current_stream()
+    trials = []
+    for kern, B, bps in candidates(info["elem_type"], info["precision"]):
+        try:
+            t0 = time.perf_counter()
+            ff.fedfem_set_tile(ctx, kern, 0, B, bps)
+            ff.fedfem_step(ctx, dt, 3)            # builds tiles on first use, warms up
+            ff.fedfem_sync(ctx)
+            setup = time.perf_counter() - t0
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            ff.fedfem_step(ctx, dt, steps)
+            e1.record(s)
+            ff.fedfem_sync(ctx)
+            torch.cuda.synchronize()
+            us = e0.elapsed_time(e1) * 1e3 / steps
+            trials.append({"kernel": kern, "tile_nodes": B, "blocks_per_sm": bps, "us_per_step": us,
+                           "setup_s": setup})
+            if verbose:
+                print(f"tune: kernel {kern} tile {B} bps {bps}: {us:.1f} us/step (setup {setup:.2f} s)")
+        except ff.FedfemError as ex:
+            trials.append({"kernel": kern, "tile_nodes": B, "blocks_per_sm": bps, "error": str(ex)})
+        finally:
+            ff.fedfem_set_state(ctx, saved)
+    ok = [t for t in trials if "us_per_step" in t]
+    best = min(ok, key=lambda t: t["us_per_step"])
+    ff.fedfem_set_tile(ctx, best["kernel"], 0, best["tile_nodes"], best["blocks_per_sm"])
+    result = {k: best[k] for k in ("kernel", "tile_nodes", "blocks_per_sm", "us_per_step")}
+    if use_cache:
+        cache[sig] = result
+        _save_cache(cache)
+    return dict(result, trials=trials, cached=False)

@@ -936,7 +936,9 @@ int fedfem_get_info(fedfem_ctx* c, fedfem_info* info) {
     }
     info->sm_count = c->sm_count;
     info->grid_blocks = c->last.grid_used;
-    info->block_threads = 256;
+    info->block_threads = c->tile.kernel == FEDFEM_KERNEL_TILED_STAGED ? tiled_threads() : 256;
+    info->kernel = c->tile.kernel;
+    info->tile_nodes = c->tiles_ok ? c->tiles_B : 0;
     return FEDFEM_OK;
 }
 

@@ -49,7 +49,7 @@ struct Tiles {
     std::vector<int32_t> halo;             // global node ids
     std::vector<int32_t> g_base;           // n_tiles: first gather entry of the tile
     std::vector<int32_t> s_off;            // n_tiles * (spt + 1): slice offsets relative to g_base
-    std::vector<uint16_t> gat;             // corner * ne_pad + j, pad = nv * ne_pad (a zero cell); ne_pad = ne rounded up to 8
+    std::vector<uint16_t> gat;             // corner * ne_pad + j (ne_pad = ne rounded up to 8); pads = nv * (max ne_pad)
     int max_local = 0, max_elems = 0;
 };
 

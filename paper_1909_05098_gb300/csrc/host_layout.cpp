@@ -352,6 +352,15 @@ std::string build_tiles(const Layout& L, int B, Tiles& T) {
         T.max_local = std::max<int>(T.max_local, (int)nl);
         T.max_elems = std::max<int>(T.max_elems, (int)ne);
     }
+    // one zero cell for every tile: pads point at nv * (largest padded element count)
+    const int64_t max_pad = (int64_t)(T.max_elems + 7) / 8 * 8;
+    if (max_pad * nv + 1 > 65535) return "tile has too many elements for 16-bit gather entries; use smaller tiles";
+    for (int64_t t = 0; t < T.n_tiles; ++t) {
+        const int64_t ne = T.e_off[t + 1] - T.e_off[t], ne_pad = (ne + 7) / 8 * 8;
+        const int64_t g0 = T.g_base[t], g1 = t + 1 < T.n_tiles ? T.g_base[t + 1] : (int64_t)T.gat.size();
+        for (int64_t g = g0; g < g1; ++g)
+            if (T.gat[g] >= nv * ne_pad) T.gat[g] = (uint16_t)(nv * max_pad);
+    }
     return "";
 }
 

@@ -74,20 +74,35 @@ __device__ __forceinline__ void flag_range(DevStatus* st, int64_t i, long long s
 
 // Eq. 19 for free node i: T is its current (hi) value, F the summed element
 // loads; writes the new value to Tout[i] (and the compensation in place).
+// The node's constant data (and its compensation) as loaded values.
+template <typename R>
+struct NodeVals {
+    R V, Q, hA, lo;
+};
+
 template <typename R, bool KAHAN>
-__device__ __forceinline__ void node_update(const StepArgs<R>& a, int64_t i, R T, R F, R* Tout, long long step) {
+__device__ __forceinline__ NodeVals<R> node_load(const StepArgs<R>& a, int64_t i) {
+    NodeVals<R> v;
+    v.V = a.V[i];
+    v.Q = a.Q[i];
+    v.hA = i >= a.N_plain ? a.hA[i - a.N_plain] : R(0);
+    v.lo = KAHAN ? a.Tlo[i] : R(0);
+    return v;
+}
+
+template <typename R, bool KAHAN>
+__device__ __forceinline__ void node_update_v(const StepArgs<R>& a, int64_t i, R T, R F, const NodeVals<R>& v,
+                                              R* Tout, long long step) {
     const R u = T - a.T_ref;
     const R rho = a.rho0 + a.drho * u;
     const R c = a.c0 + a.dc * u;
-    const R V = a.V[i];
-    const R C = (V * rho) * c;
-    R r = (a.Q[i] + (a.wbcb * V) * (a.T_a - T)) - F;
-    if (i >= a.N_plain) r = r + a.hA[i - a.N_plain] * (a.T_inf - T);
+    const R C = (v.V * rho) * c;
+    R r = (v.Q + (a.wbcb * v.V) * (a.T_a - T)) - F;
+    if (i >= a.N_plain) r = r + v.hA * (a.T_inf - T);
     const R dT = (a.dt * r) / C;
     R Tn;
     if (KAHAN) {
-        const R lo = a.Tlo[i];
-        const R y = dT + lo;
+        const R y = dT + v.lo;
         Tn = T + y;
         a.Tlo[i] = y - (Tn - T);
     } else {
@@ -95,6 +110,11 @@ __device__ __forceinline__ void node_update(const StepArgs<R>& a, int64_t i, R T
     }
     Tout[i] = Tn;
     if (!(Tn >= a.T_lo && Tn <= a.T_hi)) flag_range(a.status, i, step);
+}
+
+template <typename R, bool KAHAN>
+__device__ __forceinline__ void node_update(const StepArgs<R>& a, int64_t i, R T, R F, R* Tout, long long step) {
+    node_update_v<R, KAHAN>(a, i, T, F, node_load<R, KAHAN>(a, i), Tout, step);
 }
 
 // gather of node i's element loads from the global slots, in its fixed order
@@ -256,9 +276,19 @@ __device__ __forceinline__ void tile_compute(const StepArgs<R>& a, const TileArg
     const int32_t* so = halo + ((nh + 3) & ~3);
     const int64_t base = t * ta.B;
     const int own = (int)min((int64_t)ta.B, a.N_free - base);
-    for (int l = threadIdx.x; l < own; l += blockDim.x) Ts[l] = Tin[base + l];
+    // this thread's first owned node: its data and temperature are fetched now,
+    // so the loads overlap the staging and element phases
+    const int l0 = threadIdx.x;
+    const bool has0 = l0 < own;
+    NodeVals<R> v0{};
+    R T0 = R(0);
+    if (has0) {
+        v0 = node_load<R, KAHAN>(a, base + l0);
+        T0 = Tin[base + l0];
+        Ts[l0] = T0;
+    }
+    for (int l = l0 + blockDim.x; l < own; l += blockDim.x) Ts[l] = Tin[base + l];
     for (int h = threadIdx.x; h < nh; h += blockDim.x) Ts[own + h] = Tin[halo[h]];
-    if (threadIdx.x == 0) Fs[NV * ne_pad] = R(0);
     __syncthreads();
     const Law<R> k{a.T_ref, a.k0, a.dk};
     for (int j = threadIdx.x; j < ne; j += blockDim.x) {
@@ -278,14 +308,17 @@ __device__ __forceinline__ void tile_compute(const StepArgs<R>& a, const TileArg
         for (int n = 0; n < NV; ++n) Fs[n * ne_pad + j] = F[n];
     }
     __syncthreads();
-    for (int l = threadIdx.x; l < own; l += blockDim.x) {
+    // Ts is not read below this point (own temperatures come from registers or
+    // are re-read from Tin), so the next tile may overwrite it without a barrier
+    for (int l = l0; l < own; l += blockDim.x) {
         const int sl = l >> 5, lane = l & 31;
         const int32_t off = so[sl];
         const int w = (so[sl + 1] - off) >> 5;
         const uint16_t* g = gat + off + lane;
         R F = R(0);
         for (int q = 0; q < w; ++q) F = F + Fs[g[32 * q]];
-        node_update<R, KAHAN>(a, base + l, Ts[l], F, Tout, step);
+        if (l == l0) node_update_v<R, KAHAN>(a, base + l, T0, F, v0, Tout, step);
+        else node_update<R, KAHAN>(a, base + l, Tin[base + l], F, Tout, step);
     }
 }
 
@@ -293,21 +326,20 @@ __device__ __forceinline__ void tile_compute(const StepArgs<R>& a, const TileArg
 // (coalesced within a tile), shared memory only for T and the element loads,
 // so more blocks fit on an SM.
 template <typename R, int NV, bool KAHAN>
-__global__ void __launch_bounds__(256) k_tiled_direct(StepArgs<R> a, TileArgs<R> ta, long long n_steps,
+__global__ void __launch_bounds__(256, 6) k_tiled_direct(StepArgs<R> a, TileArgs<R> ta, long long n_steps,
                                                       long long spin_limit) {
     extern __shared__ __align__(128) unsigned char smem[];
     R* Ts = reinterpret_cast<R*>(smem);
     R* Fs = Ts + ta.max_local;
+    if (threadIdx.x == 0) Fs[ta.fs_words - 1] = R(0);   // the zero cell every gather pad points at
     unsigned long long target = 0;
     long long done = 0;
     if (!grid_barrier(a.status, target, spin_limit)) return;
     for (long long s = 0; s < n_steps; ++s) {
         const R* Tin = (s & 1) ? a.T2 : a.T;
         R* Tout = (s & 1) ? a.T : a.T2;
-        for (int64_t t = blockIdx.x; t < ta.n_tiles; t += gridDim.x) {
+        for (int64_t t = blockIdx.x; t < ta.n_tiles; t += gridDim.x)
             tile_compute<R, NV, KAHAN>(a, ta, t, ta.blocks + ta.block_off[t], Tin, Tout, a.step0 + s, Ts, Fs);
-            __syncthreads();
-        }
         const bool ok = grid_barrier(a.status, target, spin_limit);
         done = s + 1;
         if (!ok) break;
@@ -332,6 +364,7 @@ __global__ void __launch_bounds__(kTiledThreads) k_tiled(StepArgs<R> a, TileArgs
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
         fence_mbar_init();
+        Fs[ta.fs_words - 1] = R(0);   // the zero cell every gather pad points at
     }
     __syncthreads();
     unsigned long long target = 0;

@@ -66,7 +66,8 @@ class fedfem_info(C.Structure):
                 ("dt_element_bound", C.c_double), ("lanczos_iterations", C.c_int),
                 ("steps_done", C.c_int64), ("sim_time", C.c_double), ("device_bytes", C.c_int64),
                 ("bytes_per_step", C.c_int64), ("algorithmic_bytes_per_step", C.c_int64),
-                ("sm_count", C.c_int), ("grid_blocks", C.c_int), ("block_threads", C.c_int)]
+                ("sm_count", C.c_int), ("grid_blocks", C.c_int), ("block_threads", C.c_int),
+                ("kernel", C.c_int), ("tile_nodes", C.c_int)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}

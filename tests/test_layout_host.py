@@ -114,7 +114,9 @@ def test_tiles_cover_and_emulated_gather_matches_oracle(ff, kind, B):
         ne_pad = (ne + 7) // 8 * 8
         Fpad = np.zeros((nv, ne_pad))
         Fpad[:, :ne] = Fe[elem_of[elems]].T
-        Fs = np.concatenate([Fpad.ravel(), [0.0]])                        # corner-major, stride ne_pad, zero cell
+        max_pad = (d["max_tile_elems"] + 7) // 8 * 8
+        Fs = np.zeros(nv * max_pad + 1)                                   # corner-major, stride ne_pad
+        Fs[: nv * ne_pad] = Fpad.ravel()                                  # ... and the shared zero cell at the end
         so = d["tile_slice_off"][t * (spt + 1): (t + 1) * (spt + 1)]
         gb = d["tile_gather_base"][t]
         for l in range(own):
@@ -124,6 +126,7 @@ def test_tiles_cover_and_emulated_gather_matches_oracle(ff, kind, B):
             # same (element, corner) sequence as the global gather
             ents = _decode_gather(d, nv, base + l)
             real = g[g < nv * ne_pad]
+            assert np.all((g < nv * ne_pad) | (g == nv * max_pad))           # pads hit the one zero cell
             assert np.all(real % ne_pad < ne)
             assert np.array_equal(elems[real % ne_pad] * nv + real // ne_pad, ents)
             acc = 0.0
