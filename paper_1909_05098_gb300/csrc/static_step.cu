@@ -144,7 +144,7 @@ __global__ void k_static_node(StaticArgs a) {
     const double T = a.T[i];
     const double V = a.s[kOffV + i];
     const double C = (V * a.rho(T)) * a.c(T);
-    const double r = (a.s[kOffQ + i] + (a.wbcb * V) * (a.T_a - T)) - F;
+    const double r = fmadd(a.wbcb * V, a.T_a - T, a.s[kOffQ + i]) - F;
     a.T[i] = T + (a.dt * r) / C;
 }
 

@@ -94,11 +94,11 @@ template <typename R, bool KAHAN>
 __device__ __forceinline__ void node_update_v(const StepArgs<R>& a, int64_t i, R T, R F, const NodeVals<R>& v,
                                               R* Tout, long long step) {
     const R u = T - a.T_ref;
-    const R rho = a.rho0 + a.drho * u;
-    const R c = a.c0 + a.dc * u;
+    const R rho = fmadd(a.drho, u, a.rho0);
+    const R c = fmadd(a.dc, u, a.c0);
     const R C = (v.V * rho) * c;
-    R r = (v.Q + (a.wbcb * v.V) * (a.T_a - T)) - F;
-    if (i >= a.N_plain) r = r + v.hA * (a.T_inf - T);
+    R r = fmadd(a.wbcb * v.V, a.T_a - T, v.Q) - F;
+    if (i >= a.N_plain) r = fmadd(v.hA, a.T_inf - T, r);
     const R dT = (a.dt * r) / C;
     R Tn;
     if (KAHAN) {
