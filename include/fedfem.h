@@ -115,6 +115,7 @@ typedef struct {
     int sm_count, grid_blocks, block_threads;
     int kernel;                /* FEDFEM_KERNEL_* in use */
     int tile_nodes;            /* owned nodes per tile of the tiled kernels (0 if none built) */
+    int lanes;                 /* scenario lanes (1 or 4) */
 } fedfem_info;
 
 /* Create a context on CUDA device `device`.  `precision` is a FEDFEM_FP*
@@ -207,6 +208,41 @@ int fedfem_read_temperature_device(fedfem_ctx* ctx, double* out_dev);
 int fedfem_get_state(fedfem_ctx* ctx, void* buf, size_t* bytes);
 int fedfem_set_state(fedfem_ctx* ctx, const void* buf, size_t bytes);
 
+/* ---- Batched planning: many independent problems in one launch ----------
+ * The paper's future work (Section 5) is treatment planning, i.e. many runs of
+ * the same method.  Two mechanisms let one context step many runs at once:
+ *
+ * Scenario lanes: up to 4 problems that share the mesh, materials, perfusion
+ * and boundary conditions but differ in their regional sources.  Their
+ * temperatures are stored interleaved (4 floats per node), so each element
+ * matrix and connectivity entry is read once for all lanes.  Each lane's
+ * arithmetic is exactly that of a single run (bit-identical results).  FP32
+ * precisions and the tiled kernels only; all lanes start from the same T0.
+ * Sources added with fedfem_add_gaussian_source / fedfem_set_source apply to
+ * every lane; the *_lane calls add to one lane.  Call before precompute. */
+int fedfem_set_lanes(fedfem_ctx* ctx, int n_lanes);   /* 1 (default) or 4 */
+/* group >= 0 restricts the source to the nodes of that element group (see
+ * fedfem_set_element_groups); -1: every node. */
+int fedfem_add_gaussian_source_lane(fedfem_ctx* ctx, int lane, int group, const double x0[3], double sigma,
+                                    double peak);
+int fedfem_set_source_lane(fedfem_ctx* ctx, int lane, const double* q_r);
+/* Temperatures of one lane (n_nodes doubles, input order). */
+int fedfem_read_temperature_lane(fedfem_ctx* ctx, int lane, double* out);
+
+/* Element groups: several independent meshes given as one mesh (their node
+ * sets disjoint); group[e] (n_elems values) keeps each mesh's elements
+ * together in the internal order, so tiles never mix meshes.  NULL clears.
+ * The critical step is then the smallest over the meshes. */
+int fedfem_set_element_groups(fedfem_ctx* ctx, const int32_t* group);
+
+/* Record one fedfem_step(dt, n_steps) as a CUDA graph on the context's
+ * stream, then launch it with fedfem_replay_graph (asynchronous, as
+ * fedfem_step).  Tiles are planned before the capture.  Step indices in range
+ * errors count from the capture.  A new capture replaces the old graph; any
+ * set_* call drops it. */
+int fedfem_capture_graph(fedfem_ctx* ctx, double dt, int64_t n_steps);
+int fedfem_replay_graph(fedfem_ctx* ctx);
+
 /* Launch knobs; see fedfem_tile.  May be called after precompute. */
 int fedfem_set_tile(fedfem_ctx* ctx, const fedfem_tile* tile);
 
@@ -248,11 +284,13 @@ typedef struct {
  *       first, then tile_halo), tile_halo_off[n_tiles+1], tile_halo[n_halo],
  *   tile_gather_base[n_tiles], tile_slice_off[n_tile_slice_off],
  *   tile_gather[n_tile_gather] (corner * tile_elements + j; pad = elem_type * tile_elements).
- * tile_nodes <= 0 requests no tiles.  Mesh / Dirichlet / face arguments as in
+ * tile_nodes <= 0 requests no tiles.  groups: element groups as in
+ * fedfem_set_element_groups, or NULL.  Mesh / Dirichlet / face arguments as in
  * the set_* calls.  Returns FEDFEM_E_MESH / FEDFEM_E_ARG on bad input. */
 int fedfem_plan_layout(int elem_type, int64_t n_nodes, const double* xyz, int64_t n_elems, const int32_t* conn,
-                       int order, int64_t n_dirichlet, const int32_t* dirichlet_nodes, int64_t n_faces, int nverts,
-                       const int32_t* faces, int tile_nodes, fedfem_layout_info* info, int32_t* node_of,
+                       const int32_t* groups, int order, int64_t n_dirichlet, const int32_t* dirichlet_nodes,
+                       int64_t n_faces, int nverts, const int32_t* faces, int tile_nodes,
+                       fedfem_layout_info* info, int32_t* node_of,
                        int32_t* elem_of, int32_t* slice_off, int32_t* gather, int32_t* tile_elem_off,
                        int32_t* tile_elems, uint16_t* tile_lconn, int32_t* tile_halo_off, int32_t* tile_halo,
                        int32_t* tile_gather_base, int32_t* tile_slice_off, uint16_t* tile_gather);

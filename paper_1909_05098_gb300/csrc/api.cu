@@ -28,8 +28,14 @@ struct fedfem_ctx {
     int order = FEDFEM_ORDER_MORTON;
     fedfem_material mat{};
     fedfem_perfusion perf{0.0, 0.0, 37.0, 0.0};
-    std::vector<double> qr;                       // empty: none
-    std::vector<std::array<double, 5>> sources;   // x0 y0 z0 sigma peak
+    std::vector<double> qr;                       // empty: none (applies to every lane)
+    std::vector<double> qr_lane[4];               // lane-specific densities (empty: none)
+    std::vector<std::array<double, 7>> sources;   // x0 y0 z0 sigma peak lane group (-1: every lane / group)
+    int n_lanes = 1;
+    std::vector<int32_t> groups;                  // element groups (empty: one group)
+    cudaGraphExec_t graph = nullptr;
+    int64_t graph_steps = 0;
+    double graph_dt = 0.0;
     std::vector<char> is_dir;
     std::vector<double> dir_T;
     std::vector<int32_t> conv_faces;
@@ -103,7 +109,14 @@ void free_tiles(fedfem_ctx* c) {
     c->tiles_host = Tiles();
 }
 
+void free_graph(fedfem_ctx* c) {
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+    c->graph_steps = 0;
+}
+
 void free_device(fedfem_ctx* c) {
+    free_graph(c);
     free_tiles(c);
     for (void* p : c->allocs) cudaFree(p);
     c->allocs.clear();
@@ -134,6 +147,7 @@ void release(fedfem_ctx* c, void* p, size_t bytes) {
 }
 
 void invalidate(fedfem_ctx* c) {
+    free_graph(c);
     c->pre = false;
     c->inited = false;
 }
@@ -172,14 +186,14 @@ int reset_status(fedfem_ctx* c) {
     return FEDFEM_OK;
 }
 
-template <typename R>
-StepArgs<R> make_args(fedfem_ctx* c, const R* M, const R* V, const R* Q, const R* hA, double dt) {
-    StepArgs<R> a{};
+template <typename R, typename L = R>
+StepArgs<R, L> make_args(fedfem_ctx* c, const R* M, const R* V, const R* Q, const R* hA, double dt) {
+    StepArgs<R, L> a{};
     a.E = c->E; a.N = c->N; a.N_plain = c->L.N_plain; a.N_free = c->L.N_free;
     a.conn4 = c->conn4; a.M = M; a.slots = (R*)c->slots;
     a.sell_off = c->sell_off; a.sell_ids = c->sell_ids;
-    a.V = V; a.Q = Q; a.hA = hA;
-    a.T = (R*)c->T; a.T2 = (R*)c->T2; a.Tlo = (R*)c->Tlo;
+    a.V = V; a.Q = (const L*)Q; a.hA = hA;
+    a.T = (L*)c->T; a.T2 = (L*)c->T2; a.Tlo = (L*)c->Tlo;
     a.T_ref = (R)c->mat.T_ref; a.rho0 = (R)c->mat.rho0; a.drho = (R)c->mat.drho;
     a.c0 = (R)c->mat.c0; a.dc = (R)c->mat.dc; a.k0 = (R)c->mat.k0; a.dk = (R)c->mat.dk;
     a.wbcb = (R)(c->perf.w_b * c->perf.c_b); a.T_a = (R)c->perf.T_a; a.T_inf = (R)c->conv_Tinf;
@@ -209,7 +223,7 @@ int64_t tile_block_bytes(const Tiles& t, int64_t i, size_t rs) {
     return (b + 15) / 16 * 16;
 }
 
-size_t tile_smem(const Tiles& t, size_t rs, int* max_block, int* fs_words, bool staged) {
+size_t tile_smem(const Tiles& t, size_t rs, size_t ls, int* max_block, int* fs_words, bool staged) {
     int64_t mb = 0, max_ne_pad = 0;
     for (int64_t i = 0; i < t.n_tiles; ++i) {
         mb = std::max(mb, tile_block_bytes(t, i, rs));
@@ -217,7 +231,7 @@ size_t tile_smem(const Tiles& t, size_t rs, int* max_block, int* fs_words, bool 
     }
     *max_block = (int)mb;
     *fs_words = (int)(t.nv * max_ne_pad + 1);
-    const size_t b = (staged ? 128 + 2 * (size_t)mb : 0) + rs * ((size_t)t.max_local + *fs_words);
+    const size_t b = (staged ? 128 + 2 * (size_t)mb : 0) + ls * ((size_t)t.max_local + *fs_words);
     return (b + 15) / 16 * 16;
 }
 
@@ -229,6 +243,7 @@ int plan_tiles(fedfem_ctx* c) {
     if (c->tiles_ok) return FEDFEM_OK;
     const bool staged = c->tile.kernel == FEDFEM_KERNEL_TILED_STAGED;
     const size_t rs = c->precision == FEDFEM_FP64 ? sizeof(double) : sizeof(float);
+    const size_t ls = rs * c->n_lanes;
     const int64_t NF = c->L.N_free;
     if (NF == 0) return fail(c, FEDFEM_E_ARG, "no free nodes");
     int B = c->tile.tile_nodes;
@@ -238,11 +253,12 @@ int plan_tiles(fedfem_ctx* c) {
     if (B <= 0) {
         int B0 = c->nv == 8 ? 256 : 128;
         if (c->precision == FEDFEM_FP64) B0 /= 2;
+        if (c->n_lanes > 1) B0 /= 2;
         B0 = (int)std::max<int64_t>(32, std::min<int64_t>(B0, ((NF + 31) / 32) * 32));
         m = build_tiles(c->L, B0, t);
         if (!m.empty()) return fail(c, FEDFEM_E_ARG, m);
-        size_t smem = tile_smem(t, rs, &mb, &fw, staged);
-        int per_sm = tiled_blocks_per_sm(c->precision, c->nv, staged, smem);
+        size_t smem = tile_smem(t, rs, ls, &mb, &fw, staged);
+        int per_sm = tiled_blocks_per_sm(c->precision, c->nv, staged, c->n_lanes, smem);
         if (c->tile.blocks_per_sm > 0) per_sm = std::min(per_sm, c->tile.blocks_per_sm);
         if (per_sm < 1) return fail(c, FEDFEM_E_UNSUPPORTED, "tile does not fit in shared memory");
         const int64_t grid = (int64_t)per_sm * c->sm_count;
@@ -254,8 +270,8 @@ int plan_tiles(fedfem_ctx* c) {
         m = build_tiles(c->L, B, t);
         if (!m.empty()) return fail(c, FEDFEM_E_ARG, m);
     }
-    const size_t smem = tile_smem(t, rs, &mb, &fw, staged);
-    if (tiled_blocks_per_sm(c->precision, c->nv, staged, smem) < 1)
+    const size_t smem = tile_smem(t, rs, ls, &mb, &fw, staged);
+    if (tiled_blocks_per_sm(c->precision, c->nv, staged, c->n_lanes, smem) < 1)
         return fail(c, FEDFEM_E_UNSUPPORTED, "tile does not fit in shared memory; use smaller tile_nodes");
     free_tiles(c);
     cudaStream_t st = c->stream;
@@ -318,13 +334,52 @@ TileArgs<R> make_tile_args(fedfem_ctx* c) {
     return t;
 }
 
+// Launch knobs of the next time-loop launch; plans tiles when a tiled kernel
+// is selected (host work and allocation: never inside a graph capture).
+int prepare_launch(fedfem_ctx* c, LaunchCfg& cfg) {
+    cfg.kernel = c->tile.kernel;
+    cfg.block = c->tile.block;
+    cfg.blocks_per_sm = c->tile.blocks_per_sm;
+    cfg.sm_count = c->sm_count;
+    cfg.spin_limit = c->spin_limit;
+    const bool tiled = cfg.kernel == FEDFEM_KERNEL_TILED || cfg.kernel == FEDFEM_KERNEL_TILED_STAGED;
+    if (c->n_lanes > 1 && !tiled) return fail(c, FEDFEM_E_UNSUPPORTED, "scenario lanes need a tiled kernel");
+    if (tiled) return plan_tiles(c);
+    return FEDFEM_OK;
+}
+
+// Enqueue n_steps of the selected kernel on the context's stream.
+cudaError_t launch_all(fedfem_ctx* c, double dt, int64_t n_steps, LaunchCfg& cfg) {
+    const bool tiled = cfg.kernel == FEDFEM_KERNEL_TILED || cfg.kernel == FEDFEM_KERNEL_TILED_STAGED;
+    if (tiled) {
+        if (c->precision == FEDFEM_FP64) {
+            StepArgs<double> a = make_args<double>(c, c->M64, c->V64, c->Q64, c->hA64, dt);
+            return launch_tiled_f64(a, make_tile_args<double>(c), n_steps, cfg, c->stream);
+        }
+        const bool kahan = c->precision == FEDFEM_FP32_KAHAN;
+        if (c->n_lanes == 4) {
+            StepArgs<float, F4> a = make_args<float, F4>(c, c->M32, c->V32, c->Q32, c->hA32, dt);
+            return launch_tiled_f32x4(a, make_tile_args<float>(c), kahan, n_steps, cfg, c->stream);
+        }
+        StepArgs<float> a = make_args<float>(c, c->M32, c->V32, c->Q32, c->hA32, dt);
+        return launch_tiled_f32(a, make_tile_args<float>(c), kahan, n_steps, cfg, c->stream);
+    }
+    if (c->precision == FEDFEM_FP64) {
+        StepArgs<double> a = make_args<double>(c, c->M64, c->V64, c->Q64, c->hA64, dt);
+        return launch_steps_f64(a, c->nv, n_steps, cfg, c->stream);
+    }
+    StepArgs<float> a = make_args<float>(c, c->M32, c->V32, c->Q32, c->hA32, dt);
+    return launch_steps_f32(a, c->nv, c->precision == FEDFEM_FP32_KAHAN, n_steps, cfg, c->stream);
+}
+
 }  // namespace
 
 extern "C" {
 
 int fedfem_plan_layout(int elem_type, int64_t n_nodes, const double* xyz, int64_t n_elems, const int32_t* conn,
-                       int order, int64_t n_dirichlet, const int32_t* dirichlet_nodes, int64_t n_faces, int nverts,
-                       const int32_t* faces, int tile_nodes, fedfem_layout_info* info, int32_t* node_of,
+                       const int32_t* groups, int order, int64_t n_dirichlet, const int32_t* dirichlet_nodes,
+                       int64_t n_faces, int nverts, const int32_t* faces, int tile_nodes,
+                       fedfem_layout_info* info, int32_t* node_of,
                        int32_t* elem_of, int32_t* slice_off, int32_t* gather, int32_t* tile_elem_off,
                        int32_t* tile_elems, uint16_t* tile_lconn, int32_t* tile_halo_off, int32_t* tile_halo,
                        int32_t* tile_gather_base, int32_t* tile_slice_off, uint16_t* tile_gather) {
@@ -348,6 +403,8 @@ int fedfem_plan_layout(int elem_type, int64_t n_nodes, const double* xyz, int64_
     in.nv = elem_type; in.N = n_nodes; in.E = n_elems; in.xyz = xyz; in.conn = conn;
     in.is_dirichlet = &dir; in.conv_faces = n_faces > 0 ? &fv : nullptr; in.conv_nverts = n_faces > 0 ? nverts : 0;
     in.order = order;
+    std::vector<int32_t> grp;
+    if (groups) { grp.assign(groups, groups + n_elems); in.groups = &grp; }
     Layout L;
     bool mesh_err = false;
     std::string m = build_layout(in, L, &mesh_err);
@@ -430,7 +487,8 @@ int fedfem_set_mesh(fedfem_ctx* c, int elem_type, int64_t n_nodes, const double*
     c->is_dir.assign(n_nodes, 0);
     c->dir_T.assign(n_nodes, 0.0);
     c->conv_faces.clear(); c->conv_nv = 0; c->conv_h = 0; c->conv_Tinf = 0;
-    c->flux.clear(); c->qr.clear(); c->sources.clear();
+    c->flux.clear(); c->qr.clear(); c->sources.clear(); c->groups.clear();
+    for (auto& q : c->qr_lane) q.clear();
     c->has_mesh = true;
     free_device(c);
     c->err.clear();
@@ -481,7 +539,55 @@ int fedfem_add_gaussian_source(fedfem_ctx* c, const double x0[3], double sigma, 
     if (!c || !x0) return fail(c, FEDFEM_E_ARG, "null source centre");
     if (!(is_finite(x0[0]) && is_finite(x0[1]) && is_finite(x0[2]) && is_finite(peak)) || !(sigma > 0) || !is_finite(sigma))
         return fail(c, FEDFEM_E_ARG, "source needs a finite centre and peak and sigma > 0");
-    c->sources.push_back({x0[0], x0[1], x0[2], sigma, peak});
+    c->sources.push_back({x0[0], x0[1], x0[2], sigma, peak, -1.0, -1.0});
+    invalidate(c);
+    return FEDFEM_OK;
+}
+
+int fedfem_add_gaussian_source_lane(fedfem_ctx* c, int lane, int group, const double x0[3], double sigma,
+                                    double peak) {
+    if (!c) return FEDFEM_E_ARG;
+    if (lane < 0 || lane >= c->n_lanes) return fail(c, FEDFEM_E_ARG, "lane out of range (set_lanes first)");
+    if (group < -1) return fail(c, FEDFEM_E_ARG, "group must be -1 or a group id");
+    int r = fedfem_add_gaussian_source(c, x0, sigma, peak);
+    if (r) return r;
+    c->sources.back()[5] = (double)lane;
+    c->sources.back()[6] = (double)group;
+    return FEDFEM_OK;
+}
+
+int fedfem_set_source_lane(fedfem_ctx* c, int lane, const double* q_r) {
+    if (!c) return FEDFEM_E_ARG;
+    if (!c->has_mesh) return fail(c, FEDFEM_E_STATE, "set_mesh first");
+    if (lane < 0 || lane >= c->n_lanes) return fail(c, FEDFEM_E_ARG, "lane out of range (set_lanes first)");
+    if (!q_r) { c->qr_lane[lane].clear(); invalidate(c); return FEDFEM_OK; }
+    for (int64_t i = 0; i < c->N; ++i)
+        if (!is_finite(q_r[i])) return fail(c, FEDFEM_E_ARG, "non-finite source density");
+    c->qr_lane[lane].assign(q_r, q_r + c->N);
+    invalidate(c);
+    return FEDFEM_OK;
+}
+
+int fedfem_set_lanes(fedfem_ctx* c, int n_lanes) {
+    if (!c) return FEDFEM_E_ARG;
+    if (n_lanes != 1 && n_lanes != 4) return fail(c, FEDFEM_E_ARG, "n_lanes must be 1 or 4");
+    if (n_lanes == 4 && c->precision == FEDFEM_FP64) return fail(c, FEDFEM_E_UNSUPPORTED, "lanes need an FP32 precision");
+    c->n_lanes = n_lanes;
+    for (auto& s : c->sources)
+        if (s[5] >= n_lanes) s[5] = -1.0;
+    for (int l = n_lanes; l < 4; ++l) c->qr_lane[l].clear();
+    if (n_lanes == 4 && (c->tile.kernel == FEDFEM_KERNEL_PERSISTENT || c->tile.kernel == FEDFEM_KERNEL_TWO_PHASE))
+        c->tile.kernel = FEDFEM_KERNEL_TILED;
+    free_tiles(c);
+    invalidate(c);
+    return FEDFEM_OK;
+}
+
+int fedfem_set_element_groups(fedfem_ctx* c, const int32_t* group) {
+    if (!c) return FEDFEM_E_ARG;
+    if (!c->has_mesh) return fail(c, FEDFEM_E_STATE, "set_mesh first");
+    if (!group) c->groups.clear();
+    else c->groups.assign(group, group + c->E);
     invalidate(c);
     return FEDFEM_OK;
 }
@@ -572,6 +678,7 @@ int fedfem_precompute(fedfem_ctx* c, double T_lo, double T_hi, double* dt_cr_out
     in.conv_faces = c->conv_nv ? &c->conv_faces : nullptr;
     in.conv_nverts = c->conv_nv;
     in.order = c->order;
+    in.groups = c->groups.empty() ? nullptr : &c->groups;
     bool mesh_err = false;
     std::string m = build_layout(in, c->L, &mesh_err);
     if (!m.empty()) return fail(c, mesh_err ? FEDFEM_E_MESH : FEDFEM_E_ARG, m);
@@ -602,12 +709,13 @@ int fedfem_precompute(fedfem_ctx* c, double T_lo, double T_hi, double* dt_cr_out
     CU(dalloc(c, &bad, sizeof(int)), "alloc");
     CU(dalloc(c, &c->sell_off, sizeof(int32_t) * L.sell_off.size()), "alloc");
     CU(dalloc(c, &c->sell_ids, sizeof(int32_t) * L.sell_ids.size()), "alloc");
+    const int NL = c->n_lanes;
     CU(dalloc(c, &c->V64, sizeof(double) * NF), "alloc");
-    CU(dalloc(c, &c->Q64, sizeof(double) * NF), "alloc");
+    CU(dalloc(c, &c->Q64, sizeof(double) * NF * NL), "alloc");
     CU(dalloc(c, &c->hA64, sizeof(double) * NC), "alloc");
     CU(dalloc(c, &c->node_of, sizeof(int32_t) * N), "alloc");
     CU(dalloc(c, &c->T_dir, sizeof(double) * (N - NF)), "alloc");
-    CU(dalloc(c, &c->io, sizeof(double) * N), "alloc");
+    CU(dalloc(c, &c->io, sizeof(double) * N * NL), "alloc");
     CU(dalloc(c, &c->st, sizeof(DevStatus)), "alloc");
     CU(cudaMemcpyAsync(c->conn4, c4.data(), sizeof(int32_t) * E * nv, cudaMemcpyHostToDevice, st), "copy");
     CU(cudaMemcpyAsync(x, xs.data(), sizeof(double) * N, cudaMemcpyHostToDevice, st), "copy");
@@ -638,11 +746,18 @@ int fedfem_precompute(fedfem_ctx* c, double T_lo, double T_hi, double* dt_cr_out
     if (!L.conv_face.empty())
         CU(cudaMemcpyAsync(conv_face, L.conv_face.data(), sizeof(int32_t) * L.conv_face.size(), cudaMemcpyHostToDevice, st), "copy");
     std::vector<double> qr_int, flux_int, src_h;
-    if (!c->qr.empty()) {
-        qr_int.resize(NF);
-        for (int64_t i = 0; i < NF; ++i) qr_int[i] = c->qr[L.node_of[i]];
-        CU(dalloc(c, &qr, sizeof(double) * NF), "alloc");
-        CU(cudaMemcpyAsync(qr, qr_int.data(), sizeof(double) * NF, cudaMemcpyHostToDevice, st), "copy");
+    bool any_qr = !c->qr.empty();
+    for (int l = 0; l < NL; ++l) any_qr = any_qr || !c->qr_lane[l].empty();
+    if (any_qr) {
+        qr_int.assign(NF * NL, 0.0);
+        for (int l = 0; l < NL; ++l)
+            for (int64_t i = 0; i < NF; ++i) {
+                const int64_t o = L.node_of[i];
+                qr_int[l * NF + i] = (c->qr.empty() ? 0.0 : c->qr[o]) + (c->qr_lane[l].empty() ? 0.0 : c->qr_lane[l][o]);
+            }
+        CU(dalloc(c, &qr, sizeof(double) * NF * NL), "alloc");
+        CU(cudaMemcpyAsync(qr, qr_int.data(), sizeof(double) * NF * NL, cudaMemcpyHostToDevice, st), "copy");
+        CU(cudaStreamSynchronize(st), "copy");
     }
     if (!c->flux.empty()) {
         flux_int.resize(NF);
@@ -650,7 +765,19 @@ int fedfem_precompute(fedfem_ctx* c, double T_lo, double T_hi, double* dt_cr_out
         CU(dalloc(c, &flux, sizeof(double) * NF), "alloc");
         CU(cudaMemcpyAsync(flux, flux_int.data(), sizeof(double) * NF, cudaMemcpyHostToDevice, st), "copy");
     }
-    for (auto& sgm : c->sources) src_h.insert(src_h.end(), sgm.begin(), sgm.end());
+    for (auto& sgm : c->sources) src_h.insert(src_h.end(), sgm.begin(), sgm.end());   // 7 per source
+    int32_t* node_group = nullptr;
+    if (!c->groups.empty()) {
+        std::vector<int32_t> ng(NF, -1);
+        for (int64_t e = 0; e < E; ++e)
+            for (int k = 0; k < nv; ++k) {
+                const int32_t n = L.conn[e * nv + k];
+                if (n < NF && ng[n] < 0) ng[n] = c->groups[L.elem_of[e]];
+            }
+        CU(dalloc(c, &node_group, sizeof(int32_t) * std::max<int64_t>(1, NF)), "alloc");
+        CU(cudaMemcpyAsync(node_group, ng.data(), sizeof(int32_t) * NF, cudaMemcpyHostToDevice, st), "copy");
+        CU(cudaStreamSynchronize(st), "copy");
+    }
     CU(dalloc(c, &src, sizeof(double) * std::max<size_t>(1, src_h.size())), "alloc");
     if (!src_h.empty())
         CU(cudaMemcpyAsync(src, src_h.data(), sizeof(double) * src_h.size(), cudaMemcpyHostToDevice, st), "copy");
@@ -661,7 +788,8 @@ int fedfem_precompute(fedfem_ctx* c, double T_lo, double T_hi, double* dt_cr_out
     pa.M64 = c->M64; pa.Vshare = Vshare; pa.bad_elem = bad;
     pa.sell_off = c->sell_off; pa.sell_ids = c->sell_ids;
     pa.V = c->V64; pa.Q = c->Q64; pa.hA = c->hA64;
-    pa.qr_node = qr; pa.flux_node = flux; pa.src = src; pa.n_src = (int)c->sources.size();
+    pa.qr_node = qr; pa.flux_node = flux; pa.src = src; pa.n_src = (int)c->sources.size(); pa.n_lanes = NL;
+    pa.node_group = node_group;
     pa.Q_m = c->perf.Q_m;
     pa.n_faces = c->conv_nv ? (int64_t)fint.size() / c->conv_nv : 0;
     pa.face_nv = c->conv_nv; pa.faces = faces; pa.face_share = face_share;
@@ -695,15 +823,15 @@ int fedfem_precompute(fedfem_ctx* c, double T_lo, double T_hi, double* dt_cr_out
     } else {
         CU(dalloc(c, &c->M32, sizeof(float) * 6 * E), "alloc");
         CU(dalloc(c, &c->V32, sizeof(float) * NF), "alloc");
-        CU(dalloc(c, &c->Q32, sizeof(float) * NF), "alloc");
+        CU(dalloc(c, &c->Q32, sizeof(float) * NF * NL), "alloc");
         CU(dalloc(c, &c->hA32, sizeof(float) * NC), "alloc");
         CU(launch_to_f32(c->M64, c->M32, 6 * E, st), "convert");
         CU(launch_to_f32(c->V64, c->V32, NF, st), "convert");
-        CU(launch_to_f32(c->Q64, c->Q32, NF, st), "convert");
+        CU(launch_pack_lanes(c->Q64, c->Q32, NL, NF, st), "convert");
         CU(launch_to_f32(c->hA64, c->hA32, NC, st), "convert");
-        CU(dalloc(c, (float**)&c->T, sizeof(float) * N), "alloc");
-        CU(dalloc(c, (float**)&c->T2, sizeof(float) * N), "alloc");
-        CU(dalloc(c, &c->Tlo, sizeof(float) * N), "alloc");
+        CU(dalloc(c, (float**)&c->T, sizeof(float) * N * NL), "alloc");
+        CU(dalloc(c, (float**)&c->T2, sizeof(float) * N * NL), "alloc");
+        CU(dalloc(c, &c->Tlo, sizeof(float) * N * NL), "alloc");
         CU(dalloc(c, (float**)&c->slots, sizeof(float) * (E * nv + 1)), "alloc");
         CU(cudaMemsetAsync(c->slots, 0, sizeof(float) * (E * nv + 1), st), "memset");
     }
@@ -715,12 +843,13 @@ int fedfem_precompute(fedfem_ctx* c, double T_lo, double T_hi, double* dt_cr_out
     release(c, face_share, sizeof(double) * (fint.size() / std::max(1, c->conv_nv)));
     release(c, conv_off, sizeof(int32_t) * L.conv_off.size());
     release(c, conv_face, sizeof(int32_t) * std::max<size_t>(1, L.conv_face.size()));
-    release(c, qr, sizeof(double) * NF); release(c, flux, sizeof(double) * NF);
+    release(c, qr, sizeof(double) * NF * NL); release(c, flux, sizeof(double) * NF);
     release(c, src, sizeof(double) * std::max<size_t>(1, src_h.size()));
+    release(c, node_group, sizeof(int32_t) * std::max<int64_t>(1, NF));
     if (c->precision != FEDFEM_FP64) {
         release(c, c->M64, sizeof(double) * 6 * E); c->M64 = nullptr;
         release(c, c->V64, sizeof(double) * NF); c->V64 = nullptr;
-        release(c, c->Q64, sizeof(double) * NF); c->Q64 = nullptr;
+        release(c, c->Q64, sizeof(double) * NF * NL); c->Q64 = nullptr;
         release(c, c->hA64, sizeof(double) * NC); c->hA64 = nullptr;
     }
     c->pre = true;
@@ -732,12 +861,16 @@ int fedfem_precompute(fedfem_ctx* c, double T_lo, double T_hi, double* dt_cr_out
 
 static int mirror_T(fedfem_ctx* c) {
     const size_t rs = c->precision == FEDFEM_FP64 ? sizeof(double) : sizeof(float);
-    CU(cudaMemcpyAsync(c->T2, c->T, rs * c->N, cudaMemcpyDeviceToDevice, c->stream), "mirror");
+    CU(cudaMemcpyAsync(c->T2, c->T, rs * c->N * c->n_lanes, cudaMemcpyDeviceToDevice, c->stream), "mirror");
     return FEDFEM_OK;
 }
 
 static int init_common(fedfem_ctx* c) {
-    CU(launch_init_state(c->precision, c->N, c->L.N_free, c->node_of, c->io, c->T_dir, c->T, c->Tlo, c->stream),
+    for (int l = 1; l < c->n_lanes; ++l)   // every lane starts from the same field
+        CU(cudaMemcpyAsync(c->io + l * c->N, c->io, sizeof(double) * c->N, cudaMemcpyDeviceToDevice, c->stream),
+           "init copy");
+    CU(launch_init_state(c->precision, c->n_lanes, c->N, c->L.N_free, c->node_of, c->io, c->T_dir, c->T, c->Tlo,
+                         c->stream),
        "init kernel");
     if (int r = mirror_T(c)) return r;
     int r = reset_status(c);
@@ -782,33 +915,50 @@ int fedfem_step(fedfem_ctx* c, double dt, int64_t n_steps) {
     if (n_steps == 0) return FEDFEM_OK;
     CU(cudaSetDevice(c->device), "set device");
     LaunchCfg cfg;
-    cfg.kernel = c->tile.kernel;
-    cfg.block = c->tile.block;
-    cfg.blocks_per_sm = c->tile.blocks_per_sm;
-    cfg.sm_count = c->sm_count;
-    cfg.spin_limit = c->spin_limit;
-    cudaError_t e;
-    if (cfg.kernel == FEDFEM_KERNEL_TILED || cfg.kernel == FEDFEM_KERNEL_TILED_STAGED) {
-        if (int r = plan_tiles(c)) return r;
-        if (c->precision == FEDFEM_FP64) {
-            StepArgs<double> a = make_args<double>(c, c->M64, c->V64, c->Q64, c->hA64, dt);
-            e = launch_tiled_f64(a, make_tile_args<double>(c), n_steps, cfg, c->stream);
-        } else {
-            StepArgs<float> a = make_args<float>(c, c->M32, c->V32, c->Q32, c->hA32, dt);
-            e = launch_tiled_f32(a, make_tile_args<float>(c), c->precision == FEDFEM_FP32_KAHAN, n_steps, cfg,
-                                 c->stream);
-        }
-    } else if (c->precision == FEDFEM_FP64) {
-        StepArgs<double> a = make_args<double>(c, c->M64, c->V64, c->Q64, c->hA64, dt);
-        e = launch_steps_f64(a, c->nv, n_steps, cfg, c->stream);
-    } else {
-        StepArgs<float> a = make_args<float>(c, c->M32, c->V32, c->Q32, c->hA32, dt);
-        e = launch_steps_f32(a, c->nv, c->precision == FEDFEM_FP32_KAHAN, n_steps, cfg, c->stream);
-    }
+    if (int r = prepare_launch(c, cfg)) return r;
+    cudaError_t e = launch_all(c, dt, n_steps, cfg);
     if (e != cudaSuccess) return cuda_fail(c, e, "step launch");
     c->last = cfg;
     c->steps_issued += n_steps;
     c->sim_time += dt * (double)n_steps;
+    return FEDFEM_OK;
+}
+
+int fedfem_capture_graph(fedfem_ctx* c, double dt, int64_t n_steps) {
+    if (!c) return FEDFEM_E_ARG;
+    if (!c->inited) return fail(c, FEDFEM_E_STATE, "init first");
+    if (!(dt > 0) || !is_finite(dt) || n_steps <= 0) return fail(c, FEDFEM_E_ARG, "need dt > 0 and n_steps > 0");
+    if (!(dt < c->dt_cr)) return fail(c, FEDFEM_E_UNSTABLE_DT, "dt >= critical step " + std::to_string(c->dt_cr));
+    CU(cudaSetDevice(c->device), "set device");
+    LaunchCfg cfg;
+    if (int r = prepare_launch(c, cfg)) return r;   // tiles are planned outside the capture
+    free_graph(c);
+    CU(cudaStreamSynchronize(c->stream), "capture");
+    CU(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+    cudaError_t e = launch_all(c, dt, n_steps, cfg);
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return cuda_fail(c, e != cudaSuccess ? e : e2, "graph capture");
+    }
+    e = cudaGraphInstantiate(&c->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { c->graph = nullptr; return cuda_fail(c, e, "graph instantiate"); }
+    c->graph_steps = n_steps;
+    c->graph_dt = dt;
+    c->last = cfg;
+    return FEDFEM_OK;
+}
+
+int fedfem_replay_graph(fedfem_ctx* c) {
+    if (!c) return FEDFEM_E_ARG;
+    if (!c->graph || !c->inited) return fail(c, FEDFEM_E_STATE, "capture a graph (after init) first");
+    CU(cudaSetDevice(c->device), "set device");
+    CU(cudaGraphLaunch(c->graph, c->stream), "graph launch");
+    c->steps_issued += c->graph_steps;
+    c->sim_time += c->graph_dt * (double)c->graph_steps;
     return FEDFEM_OK;
 }
 
@@ -838,7 +988,20 @@ int fedfem_read_temperature_device(fedfem_ctx* c, double* out_dev) {
     if (!c || !out_dev) return fail(c, FEDFEM_E_ARG, "null output");
     if (!c->inited) return fail(c, FEDFEM_E_STATE, "init first");
     CU(cudaSetDevice(c->device), "set device");
-    CU(launch_read_state(c->precision, c->N, c->node_of, c->T, c->Tlo, out_dev, c->stream), "read kernel");
+    CU(launch_read_state(c->precision, c->n_lanes, 0, c->N, c->node_of, c->T, c->Tlo, out_dev, c->stream),
+       "read kernel");
+    CU(cudaStreamSynchronize(c->stream), "read");
+    return FEDFEM_OK;
+}
+
+int fedfem_read_temperature_lane(fedfem_ctx* c, int lane, double* out) {
+    if (!c || !out) return fail(c, FEDFEM_E_ARG, "null output");
+    if (!c->inited) return fail(c, FEDFEM_E_STATE, "init first");
+    if (lane < 0 || lane >= c->n_lanes) return fail(c, FEDFEM_E_ARG, "lane out of range");
+    CU(cudaSetDevice(c->device), "set device");
+    CU(launch_read_state(c->precision, c->n_lanes, lane, c->N, c->node_of, c->T, c->Tlo, c->io, c->stream),
+       "read kernel");
+    CU(cudaMemcpyAsync(out, c->io, sizeof(double) * c->N, cudaMemcpyDeviceToHost, c->stream), "copy out");
     CU(cudaStreamSynchronize(c->stream), "read");
     return FEDFEM_OK;
 }
@@ -847,7 +1010,8 @@ int fedfem_read_temperature(fedfem_ctx* c, double* out) {
     if (!c || !out) return fail(c, FEDFEM_E_ARG, "null output");
     if (!c->inited) return fail(c, FEDFEM_E_STATE, "init first");
     CU(cudaSetDevice(c->device), "set device");
-    CU(launch_read_state(c->precision, c->N, c->node_of, c->T, c->Tlo, c->io, c->stream), "read kernel");
+    CU(launch_read_state(c->precision, c->n_lanes, 0, c->N, c->node_of, c->T, c->Tlo, c->io, c->stream),
+       "read kernel");
     CU(cudaMemcpyAsync(out, c->io, sizeof(double) * c->N, cudaMemcpyDeviceToHost, c->stream), "copy out");
     CU(cudaStreamSynchronize(c->stream), "read");
     return FEDFEM_OK;
@@ -867,8 +1031,8 @@ static const uint64_t kMagic = 0x5453464d45464546ULL;   // "FEFEMFST"
 int fedfem_get_state(fedfem_ctx* c, void* buf, size_t* bytes) {
     if (!c || !bytes) return fail(c, FEDFEM_E_ARG, "null size pointer");
     if (!c->inited) return fail(c, FEDFEM_E_STATE, "init first");
-    const size_t tb = (c->precision == FEDFEM_FP64 ? sizeof(double) : sizeof(float)) * c->N;
-    const size_t lb = (c->precision == FEDFEM_FP64 ? 0 : sizeof(float) * c->N);
+    const size_t tb = (c->precision == FEDFEM_FP64 ? sizeof(double) : sizeof(float)) * c->N * c->n_lanes;
+    const size_t lb = (c->precision == FEDFEM_FP64 ? 0 : sizeof(float) * c->N * c->n_lanes);
     const size_t need = sizeof(StateHeader) + tb + lb;
     if (!buf) { *bytes = need; return FEDFEM_OK; }
     if (*bytes < need) return fail(c, FEDFEM_E_ARG, "state buffer too small");
@@ -890,8 +1054,8 @@ int fedfem_set_state(fedfem_ctx* c, const void* buf, size_t bytes) {
     if (bytes < sizeof(StateHeader)) return fail(c, FEDFEM_E_ARG, "state too short");
     StateHeader h;
     std::memcpy(&h, buf, sizeof(h));
-    const size_t tb = (c->precision == FEDFEM_FP64 ? sizeof(double) : sizeof(float)) * c->N;
-    const size_t lb = (c->precision == FEDFEM_FP64 ? 0 : sizeof(float) * c->N);
+    const size_t tb = (c->precision == FEDFEM_FP64 ? sizeof(double) : sizeof(float)) * c->N * c->n_lanes;
+    const size_t lb = (c->precision == FEDFEM_FP64 ? 0 : sizeof(float) * c->N * c->n_lanes);
     if (h.magic != kMagic || h.version != 1 || h.precision != c->precision || h.N != c->N || h.E != c->E ||
         h.order != c->order || h.nv != c->nv || h.payload != tb + lb || bytes < sizeof(h) + tb + lb)
         return fail(c, FEDFEM_E_ARG, "state does not match this context");
@@ -924,21 +1088,23 @@ int fedfem_get_info(fedfem_ctx* c, fedfem_info* info) {
     const int64_t R = c->precision == FEDFEM_FP64 ? 8 : 4;
     const int64_t node_state = c->precision == FEDFEM_FP32_KAHAN ? 4 * R : 2 * R;   // T (+lo) read+write
     const int64_t E = c->E, NF = L.N_free, NC = L.N_free - L.N_plain;
-    info->algorithmic_bytes_per_step = E * (4 * c->nv + 6 * R) + NF * (node_state + 2 * R) + NC * R;
+    const int64_t NL = c->n_lanes;   // lanes share V, hA and the element data
+    info->algorithmic_bytes_per_step = E * (4 * c->nv + 6 * R) + NF * (NL * (node_state + R) + R) + NC * R;
     // two-phase / persistent model: + slot write and read, gather ids, slice offsets, T gather read once
     info->bytes_per_step = info->algorithmic_bytes_per_step + E * c->nv * 2 * R + (int64_t)L.sell_ids.size() * 4 +
                            (int64_t)L.sell_off.size() * 4;
     if ((c->tile.kernel == FEDFEM_KERNEL_TILED || c->tile.kernel == FEDFEM_KERNEL_TILED_STAGED) && c->tiles_ok) {
         const Tiles& t = c->tiles_host;
         // every packed block once, halo values, owned T read; then T written, lo read+write, V, Q, hA
-        const int64_t node_rest = NF * (node_state - R + 2 * R) + NC * R;
-        info->bytes_per_step = c->t_block_bytes + (int64_t)t.halo.size() * R + NF * R + node_rest;
+        const int64_t node_rest = NF * (NL * (node_state - R + R) + R) + NC * R;
+        info->bytes_per_step = c->t_block_bytes + (int64_t)t.halo.size() * R * NL + NF * R * NL + node_rest;
     }
     info->sm_count = c->sm_count;
     info->grid_blocks = c->last.grid_used;
     info->block_threads = c->tile.kernel == FEDFEM_KERNEL_TILED_STAGED ? tiled_threads() : 256;
     info->kernel = c->tile.kernel;
     info->tile_nodes = c->tiles_ok ? c->tiles_B : 0;
+    info->lanes = c->n_lanes;
     return FEDFEM_OK;
 }
 

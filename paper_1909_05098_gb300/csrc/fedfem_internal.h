@@ -64,6 +64,7 @@ struct MeshInput {
     const std::vector<int32_t>* conv_faces = nullptr;  // n_faces x conv_nverts
     int conv_nverts = 0;
     int order = FEDFEM_ORDER_MORTON;
+    const std::vector<int32_t>* groups = nullptr;      // element groups kept apart in the internal order
 };
 
 // Returns "" on success, else an error message.  Sets *mesh_error when the
@@ -88,7 +89,9 @@ struct DevStatus {
 // ---------------------------------------------------------------------------
 // Kernel parameter block of the time loop
 // ---------------------------------------------------------------------------
-template <typename R>
+// R: type of the element matrices and node constants; L: type of one node's
+// temperature state -- R itself, or F4 for four scenario lanes.
+template <typename R, typename L = R>
 struct StepArgs {
     int64_t E, N, N_plain, N_free;
     const int4* conn4;               // nv/4 planes of E int4
@@ -97,11 +100,11 @@ struct StepArgs {
     const int32_t* sell_off;
     const int32_t* sell_ids;
     const R* V;                      // lumped volume, free nodes
-    const R* Q;                      // constant nodal heat flow (W), free nodes
+    const L* Q;                      // constant nodal heat flow (W), free nodes (per lane)
     const R* hA;                     // film h * lumped area, nodes [N_plain, N_free)
-    R* T;                            // temperature (FP64) or its hi part (FP32), all N nodes
-    R* T2;                           // second buffer of the tiled kernel (same layout as T)
-    R* Tlo;                          // FP32 compensation, all N nodes (unused in FP64)
+    L* T;                            // temperature (FP64) or its hi part (FP32), all N nodes
+    L* T2;                           // second buffer of the tiled kernel (same layout as T)
+    L* Tlo;                          // FP32 compensation, all N nodes (unused in FP64)
     R T_ref, rho0, drho, c0, dc, k0, dk;
     R wbcb, T_a, T_inf;
     R dt, T_lo, T_hi;
@@ -137,12 +140,15 @@ struct TileArgs {
     size_t smem_bytes;
 };
 
+struct F4;
 cudaError_t launch_tiled_f64(const StepArgs<double>& a, const TileArgs<double>& t, int64_t n_steps,
                              LaunchCfg& cfg, cudaStream_t s);
 cudaError_t launch_tiled_f32(const StepArgs<float>& a, const TileArgs<float>& t, bool kahan, int64_t n_steps,
                              LaunchCfg& cfg, cudaStream_t s);
-// occupancy (blocks per SM) of the tiled kernel for a shared-memory size
-int tiled_blocks_per_sm(int precision, int nv, int staged, size_t smem_bytes);
+cudaError_t launch_tiled_f32x4(const StepArgs<float, F4>& a, const TileArgs<float>& t, bool kahan, int64_t n_steps,
+                               LaunchCfg& cfg, cudaStream_t s);
+// occupancy (blocks per SM) of the tiled kernel for a shared-memory size (lanes: 1 or 4)
+int tiled_blocks_per_sm(int precision, int nv, int staged, int lanes, size_t smem_bytes);
 int tiled_threads();
 
 cudaError_t launch_steps_f64(const StepArgs<double>& a, int nv, int64_t n_steps, LaunchCfg& cfg,
@@ -163,12 +169,14 @@ struct PreArgs {
     int* bad_elem;               // smallest internal element with det <= 0 (init INT_MAX)
     const int32_t* sell_off; const int32_t* sell_ids;
     double* V;                   // free nodes
-    double* Q;                   // free nodes
+    double* Q;                   // n_lanes x free nodes
     double* hA;                  // convective nodes
-    const double* qr_node;       // free nodes, W/m^3 (nullable)
+    const double* qr_node;       // n_lanes x free nodes, W/m^3 (nullable)
     const double* flux_node;     // free nodes, W (nullable)
-    const double* src;           // n_src x 5: x0 y0 z0 sigma peak
+    const double* src;           // n_src x 7: x0 y0 z0 sigma peak lane group (-1: every lane / group)
     int n_src;
+    int n_lanes;
+    const int32_t* node_group;   // free nodes: element group of the node (nullable)
     double Q_m;
     // film faces
     int64_t n_faces; int face_nv;
@@ -189,10 +197,13 @@ std::string lanczos_lambda_max(const PreArgs& a, double k0, double rho0c0, doubl
                                int max_iter, double rel_tol, LanczosResult& out, cudaStream_t s);
 
 // Init / output helpers (precompute.cu)
-cudaError_t launch_init_state(int precision, int64_t N, int64_t N_free, const int32_t* node_of,
+// T_in: input order, n_lanes x N; T / Tlo interleaved by lane
+cudaError_t launch_init_state(int precision, int n_lanes, int64_t N, int64_t N_free, const int32_t* node_of,
                               const double* T_in, const double* T_dir, void* T, float* Tlo,
                               cudaStream_t s);
-cudaError_t launch_read_state(int precision, int64_t N, const int32_t* node_of, const void* T,
-                              const float* Tlo, double* out, cudaStream_t s);
+cudaError_t launch_read_state(int precision, int n_lanes, int lane, int64_t N, const int32_t* node_of,
+                              const void* T, const float* Tlo, double* out, cudaStream_t s);
+// lane-major [lane][n] doubles -> interleaved floats [n][lane]
+cudaError_t launch_pack_lanes(const double* src, float* dst, int n_lanes, int64_t n, cudaStream_t s);
 
 }  // namespace fedfem

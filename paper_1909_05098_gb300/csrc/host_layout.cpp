@@ -29,6 +29,13 @@ uint64_t spread3(uint64_t v) {   // 21 bits -> every third of 63 bits
     return v;
 }
 
+// Keep element groups (independent meshes) apart: stable sort by group.
+void group_sort(const MeshInput& in, std::vector<int32_t>& elem_of) {
+    if (!in.groups) return;
+    const std::vector<int32_t>& g = *in.groups;
+    std::stable_sort(elem_of.begin(), elem_of.end(), [&](int32_t a, int32_t b) { return g[a] < g[b]; });
+}
+
 void morton_order(const MeshInput& in, std::vector<int32_t>& elem_of) {
     const int nv = in.nv;
     std::vector<double> c(3 * in.E);
@@ -163,6 +170,7 @@ std::string build_layout(const MeshInput& in, Layout& L, bool* mesh_error) {
     if (in.order == FEDFEM_ORDER_MORTON) morton_order(in, L.elem_of);
     else if (in.order == FEDFEM_ORDER_RCM) rcm_order(in, L.elem_of);
     else std::iota(L.elem_of.begin(), L.elem_of.end(), 0);
+    group_sort(in, L.elem_of);
     std::vector<int32_t> elem_at(E);
     for (int64_t e = 0; e < E; ++e) elem_at[L.elem_of[e]] = (int32_t)e;
 

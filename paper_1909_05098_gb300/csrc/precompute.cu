@@ -128,16 +128,21 @@ __global__ void k_nodal(PreArgs a) {
     for (int k = 0; k < w; ++k) V += a.Vshare[a.sell_ids[off + 32 * k + lane] / a.nv];
     a.V[i] = V;
     const double X = a.x[i], Y = a.y[i], Z = a.z[i];
-    double q = 0.0;
-    for (int j = 0; j < a.n_src; ++j) {
-        const double* S = a.src + 5 * j;
-        const double r2 = (X - S[0]) * (X - S[0]) + (Y - S[1]) * (Y - S[1]) + (Z - S[2]) * (Z - S[2]);
-        q += S[4] * exp(-r2 / (2.0 * S[3] * S[3]));
+    for (int l = 0; l < a.n_lanes; ++l) {      // scenario lanes share V, differ in sources
+        double q = 0.0;
+        const int grp = a.node_group ? a.node_group[i] : -1;
+        for (int j = 0; j < a.n_src; ++j) {
+            const double* S = a.src + 7 * j;
+            if (S[5] >= 0.0 && (int)S[5] != l) continue;
+            if (S[6] >= 0.0 && (int)S[6] != grp) continue;
+            const double r2 = (X - S[0]) * (X - S[0]) + (Y - S[1]) * (Y - S[1]) + (Z - S[2]) * (Z - S[2]);
+            q += S[4] * exp(-r2 / (2.0 * S[3] * S[3]));
+        }
+        if (a.qr_node) q += a.qr_node[l * a.N_free + i];
+        double Q = V * (a.Q_m + q);
+        if (a.flux_node) Q += a.flux_node[i];
+        a.Q[l * a.N_free + i] = Q;
     }
-    if (a.qr_node) q += a.qr_node[i];
-    double Q = V * (a.Q_m + q);
-    if (a.flux_node) Q += a.flux_node[i];
-    a.Q[i] = Q;
     if (i >= a.N_plain) {
         const int64_t c = i - a.N_plain;
         double hA = 0.0;
@@ -149,6 +154,12 @@ __global__ void k_nodal(PreArgs a) {
 __global__ void k_to_f32(const double* src, float* dst, int64_t n) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) dst[i] = (float)src[i];
+}
+
+__global__ void k_pack_lanes(const double* src, float* dst, int n_lanes, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int l = 0; l < n_lanes; ++l) dst[i * n_lanes + l] = (float)src[l * n + i];
 }
 
 // ---- Lanczos pieces (FP64) --------------------------------------------------
@@ -307,6 +318,11 @@ cudaError_t launch_to_f32(const double* src, float* dst, int64_t n, cudaStream_t
     return cudaGetLastError();
 }
 
+cudaError_t launch_pack_lanes(const double* src, float* dst, int n_lanes, int64_t n, cudaStream_t s) {
+    if (n > 0) k_pack_lanes<<<blocks_for(n), kThreads, 0, s>>>(src, dst, n_lanes, n);
+    return cudaGetLastError();
+}
+
 std::string lanczos_lambda_max(const PreArgs& p, double k0, double rho0c0, double wbcb, int max_iter,
                                double rel_tol, LanczosResult& out, cudaStream_t s) {
     const int64_t n = p.N_free;
@@ -387,41 +403,45 @@ __global__ void k_init64(int64_t N, int64_t N_free, const int32_t* node_of, cons
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < N) T[i] = (i >= N_free) ? T_dir[i - N_free] : T_in[node_of[i]];
 }
-__global__ void k_init32(int64_t N, int64_t N_free, const int32_t* node_of, const double* T_in,
+// FP32 state interleaved by lane: T[i * n_lanes + lane]
+__global__ void k_init32(int n_lanes, int64_t N, int64_t N_free, const int32_t* node_of, const double* T_in,
                          const double* T_dir, float* T, float* Tlo, bool kahan) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    const double v = (i >= N_free) ? T_dir[i - N_free] : T_in[node_of[i]];
-    const float hi = (float)v;
-    T[i] = hi;
-    Tlo[i] = kahan ? (float)(v - (double)hi) : 0.0f;
+    for (int l = 0; l < n_lanes; ++l) {
+        const double v = (i >= N_free) ? T_dir[i - N_free] : T_in[l * N + node_of[i]];
+        const float hi = (float)v;
+        T[i * n_lanes + l] = hi;
+        Tlo[i * n_lanes + l] = kahan ? (float)(v - (double)hi) : 0.0f;
+    }
 }
 __global__ void k_read64(int64_t N, const int32_t* node_of, const double* T, double* out) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < N) out[node_of[i]] = T[i];
 }
-__global__ void k_read32(int64_t N, const int32_t* node_of, const float* T, const float* Tlo, double* out) {
+__global__ void k_read32(int n_lanes, int lane, int64_t N, const int32_t* node_of, const float* T, const float* Tlo,
+                         double* out) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < N) out[node_of[i]] = (double)T[i] + (double)Tlo[i];
+    if (i < N) out[node_of[i]] = (double)T[i * n_lanes + lane] + (double)Tlo[i * n_lanes + lane];
 }
 }  // namespace
 
-cudaError_t launch_init_state(int precision, int64_t N, int64_t N_free, const int32_t* node_of,
+cudaError_t launch_init_state(int precision, int n_lanes, int64_t N, int64_t N_free, const int32_t* node_of,
                               const double* T_in, const double* T_dir, void* T, float* Tlo, cudaStream_t s) {
     if (precision == FEDFEM_FP64)
         k_init64<<<blocks_for(N), kThreads, 0, s>>>(N, N_free, node_of, T_in, T_dir, (double*)T);
     else
-        k_init32<<<blocks_for(N), kThreads, 0, s>>>(N, N_free, node_of, T_in, T_dir, (float*)T, Tlo,
+        k_init32<<<blocks_for(N), kThreads, 0, s>>>(n_lanes, N, N_free, node_of, T_in, T_dir, (float*)T, Tlo,
                                                     precision == FEDFEM_FP32_KAHAN);
     return cudaGetLastError();
 }
 
-cudaError_t launch_read_state(int precision, int64_t N, const int32_t* node_of, const void* T, const float* Tlo,
-                              double* out, cudaStream_t s) {
+cudaError_t launch_read_state(int precision, int n_lanes, int lane, int64_t N, const int32_t* node_of,
+                              const void* T, const float* Tlo, double* out, cudaStream_t s) {
     if (precision == FEDFEM_FP64)
         k_read64<<<blocks_for(N), kThreads, 0, s>>>(N, node_of, (const double*)T, out);
     else
-        k_read32<<<blocks_for(N), kThreads, 0, s>>>(N, node_of, (const float*)T, Tlo, out);
+        k_read32<<<blocks_for(N), kThreads, 0, s>>>(n_lanes, lane, N, node_of, (const float*)T, Tlo, out);
     return cudaGetLastError();
 }
 

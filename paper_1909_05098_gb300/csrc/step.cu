@@ -75,46 +75,50 @@ __device__ __forceinline__ void flag_range(DevStatus* st, int64_t i, long long s
 // Eq. 19 for free node i: T is its current (hi) value, F the summed element
 // loads; writes the new value to Tout[i] (and the compensation in place).
 // The node's constant data (and its compensation) as loaded values.
-template <typename R>
+template <typename R, typename L>
 struct NodeVals {
-    R V, Q, hA, lo;
+    R V, hA;
+    L Q, lo;
 };
 
-template <typename R, bool KAHAN>
-__device__ __forceinline__ NodeVals<R> node_load(const StepArgs<R>& a, int64_t i) {
-    NodeVals<R> v;
+template <typename L>
+__device__ __forceinline__ L lzero() { return L{}; }
+
+template <typename R, typename L, bool KAHAN>
+__device__ __forceinline__ NodeVals<R, L> node_load(const StepArgs<R, L>& a, int64_t i) {
+    NodeVals<R, L> v;
     v.V = a.V[i];
     v.Q = a.Q[i];
     v.hA = i >= a.N_plain ? a.hA[i - a.N_plain] : R(0);
-    v.lo = KAHAN ? a.Tlo[i] : R(0);
+    v.lo = KAHAN ? a.Tlo[i] : lzero<L>();
     return v;
 }
 
-template <typename R, bool KAHAN>
-__device__ __forceinline__ void node_update_v(const StepArgs<R>& a, int64_t i, R T, R F, const NodeVals<R>& v,
-                                              R* Tout, long long step) {
-    const R u = T - a.T_ref;
-    const R rho = fmadd(a.drho, u, a.rho0);
-    const R c = fmadd(a.dc, u, a.c0);
-    const R C = (v.V * rho) * c;
-    R r = fmadd(a.wbcb * v.V, a.T_a - T, v.Q) - F;
+template <typename R, typename L, bool KAHAN>
+__device__ __forceinline__ void node_update_v(const StepArgs<R, L>& a, int64_t i, L T, L F,
+                                              const NodeVals<R, L>& v, L* Tout, long long step) {
+    const L u = T - a.T_ref;
+    const L rho = fmadd(a.drho, u, a.rho0);
+    const L c = fmadd(a.dc, u, a.c0);
+    const L C = (v.V * rho) * c;
+    L r = fmadd(a.wbcb * v.V, a.T_a - T, v.Q) - F;
     if (i >= a.N_plain) r = fmadd(v.hA, a.T_inf - T, r);
-    const R dT = (a.dt * r) / C;
-    R Tn;
+    const L dT = (a.dt * r) / C;
+    L Tn;
     if (KAHAN) {
-        const R y = dT + v.lo;
+        const L y = dT + v.lo;
         Tn = T + y;
         a.Tlo[i] = y - (Tn - T);
     } else {
         Tn = T + dT;
     }
     Tout[i] = Tn;
-    if (!(Tn >= a.T_lo && Tn <= a.T_hi)) flag_range(a.status, i, step);
+    if (!all_in(Tn, a.T_lo, a.T_hi)) flag_range(a.status, i, step);
 }
 
-template <typename R, bool KAHAN>
-__device__ __forceinline__ void node_update(const StepArgs<R>& a, int64_t i, R T, R F, R* Tout, long long step) {
-    node_update_v<R, KAHAN>(a, i, T, F, node_load<R, KAHAN>(a, i), Tout, step);
+template <typename R, typename L, bool KAHAN>
+__device__ __forceinline__ void node_update(const StepArgs<R, L>& a, int64_t i, L T, L F, L* Tout, long long step) {
+    node_update_v<R, L, KAHAN>(a, i, T, F, node_load<R, L, KAHAN>(a, i), Tout, step);
 }
 
 // gather of node i's element loads from the global slots, in its fixed order
@@ -126,7 +130,7 @@ __device__ __forceinline__ void node_phase(const StepArgs<R>& a, int64_t i, long
     const int w = (a.sell_off[s + 1] - off) >> 5;
     R F = R(0);
     for (int k = 0; k < w; ++k) F = F + a.slots[a.sell_ids[off + 32 * k + lane]];
-    node_update<R, KAHAN>(a, i, a.T[i], F, a.T, step);
+    node_update<R, R, KAHAN>(a, i, a.T[i], F, a.T, step);
 }
 
 template <typename R, int NV>
@@ -263,10 +267,10 @@ struct LConn<4> {
     }
 };
 
-template <typename R, int NV, bool KAHAN>
-__device__ __forceinline__ void tile_compute(const StepArgs<R>& a, const TileArgs<R>& ta, int64_t t,
-                                             const unsigned char* blk, const R* Tin, R* Tout, long long step, R* Ts,
-                                             R* Fs) {
+template <typename R, typename L, int NV, bool KAHAN>
+__device__ __forceinline__ void tile_compute(const StepArgs<R, L>& a, const TileArgs<R>& ta, int64_t t,
+                                             const unsigned char* blk, const L* Tin, L* Tout, long long step, L* Ts,
+                                             L* Fs) {
     const int4 hdr = *reinterpret_cast<const int4*>(blk);
     const int ne = hdr.x, ne_pad = hdr.y, nh = hdr.z, G = hdr.w;
     const R* M = reinterpret_cast<const R*>(blk + 16);
@@ -280,10 +284,10 @@ __device__ __forceinline__ void tile_compute(const StepArgs<R>& a, const TileArg
     // so the loads overlap the staging and element phases
     const int l0 = threadIdx.x;
     const bool has0 = l0 < own;
-    NodeVals<R> v0{};
-    R T0 = R(0);
+    NodeVals<R, L> v0{};
+    L T0 = lzero<L>();
     if (has0) {
-        v0 = node_load<R, KAHAN>(a, base + l0);
+        v0 = node_load<R, L, KAHAN>(a, base + l0);
         T0 = Tin[base + l0];
         Ts[l0] = T0;
     }
@@ -294,16 +298,16 @@ __device__ __forceinline__ void tile_compute(const StepArgs<R>& a, const TileArg
     for (int j = threadIdx.x; j < ne; j += blockDim.x) {
         int c[NV];
         LConn<NV>::load(lc, j, c);
-        R tt[NV];
+        L tt[NV];
 #pragma unroll
         for (int n = 0; n < NV; ++n) tt[n] = Ts[c[n]];
         R m[6];
 #pragma unroll
         for (int q = 0; q < 6; ++q) m[q] = M[q * ne_pad + j];
-        const R ke = element_k<R, NV>(tt, k);
-        R F[NV];
-        if (NV == 8) hex8_loads<R>(tt, m, ke, F);
-        else tet4_loads<R>(tt, m, ke, F);
+        const L ke = element_k<R, NV, L>(tt, k);
+        L F[NV];
+        if (NV == 8) hex8_loads<R, L>(tt, m, ke, F);
+        else tet4_loads<R, L>(tt, m, ke, F);
 #pragma unroll
         for (int n = 0; n < NV; ++n) Fs[n * ne_pad + j] = F[n];
     }
@@ -315,31 +319,39 @@ __device__ __forceinline__ void tile_compute(const StepArgs<R>& a, const TileArg
         const int32_t off = so[sl];
         const int w = (so[sl + 1] - off) >> 5;
         const uint16_t* g = gat + off + lane;
-        R F = R(0);
+        L F = lzero<L>();
         for (int q = 0; q < w; ++q) F = F + Fs[g[32 * q]];
-        if (l == l0) node_update_v<R, KAHAN>(a, base + l, T0, F, v0, Tout, step);
-        else node_update<R, KAHAN>(a, base + l, Tin[base + l], F, Tout, step);
+        if (l == l0) node_update_v<R, L, KAHAN>(a, base + l, T0, F, v0, Tout, step);
+        else node_update<R, L, KAHAN>(a, base + l, Tin[base + l], F, Tout, step);
     }
 }
 
 // Direct variant: the same per-tile blocks read straight from global memory
 // (coalesced within a tile), shared memory only for T and the element loads,
 // so more blocks fit on an SM.
-template <typename R, int NV, bool KAHAN>
-__global__ void __launch_bounds__(256, 6) k_tiled_direct(StepArgs<R> a, TileArgs<R> ta, long long n_steps,
+// resident blocks per SM the direct tiled kernel is compiled for: one FP32
+// lane fits 6 blocks of 256 threads, FP64 or four-lane state needs about twice
+// the registers
+template <typename L>
+struct DirectOccupancy {
+    static constexpr int min_blocks = sizeof(L) >= 8 ? 3 : 6;
+};
+
+template <typename R, typename L, int NV, bool KAHAN>
+__global__ void __launch_bounds__(256, DirectOccupancy<L>::min_blocks) k_tiled_direct(StepArgs<R, L> a, TileArgs<R> ta, long long n_steps,
                                                       long long spin_limit) {
     extern __shared__ __align__(128) unsigned char smem[];
-    R* Ts = reinterpret_cast<R*>(smem);
-    R* Fs = Ts + ta.max_local;
-    if (threadIdx.x == 0) Fs[ta.fs_words - 1] = R(0);   // the zero cell every gather pad points at
+    L* Ts = reinterpret_cast<L*>(smem);
+    L* Fs = Ts + ta.max_local;
+    if (threadIdx.x == 0) Fs[ta.fs_words - 1] = lzero<L>();   // the zero cell every gather pad points at
     unsigned long long target = 0;
     long long done = 0;
     if (!grid_barrier(a.status, target, spin_limit)) return;
     for (long long s = 0; s < n_steps; ++s) {
-        const R* Tin = (s & 1) ? a.T2 : a.T;
-        R* Tout = (s & 1) ? a.T : a.T2;
+        const L* Tin = (s & 1) ? a.T2 : a.T;
+        L* Tout = (s & 1) ? a.T : a.T2;
         for (int64_t t = blockIdx.x; t < ta.n_tiles; t += gridDim.x)
-            tile_compute<R, NV, KAHAN>(a, ta, t, ta.blocks + ta.block_off[t], Tin, Tout, a.step0 + s, Ts, Fs);
+            tile_compute<R, L, NV, KAHAN>(a, ta, t, ta.blocks + ta.block_off[t], Tin, Tout, a.step0 + s, Ts, Fs);
         const bool ok = grid_barrier(a.status, target, spin_limit);
         done = s + 1;
         if (!ok) break;
@@ -351,20 +363,20 @@ __global__ void __launch_bounds__(256, 6) k_tiled_direct(StepArgs<R> a, TileArgs
     if (blockIdx.x == 0 && threadIdx.x == 0) a.status->steps_done = a.step0 + done;
 }
 
-template <typename R, int NV, bool KAHAN>
-__global__ void __launch_bounds__(kTiledThreads) k_tiled(StepArgs<R> a, TileArgs<R> ta, long long n_steps,
+template <typename R, typename L, int NV, bool KAHAN>
+__global__ void __launch_bounds__(kTiledThreads) k_tiled(StepArgs<R, L> a, TileArgs<R> ta, long long n_steps,
                                                          long long spin_limit) {
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
     unsigned char* const stage0 = smem + 128;
     unsigned char* const stage1 = smem + 128 + ta.max_block;
-    R* Ts = reinterpret_cast<R*>(smem + 128 + 2 * (size_t)ta.max_block);
-    R* Fs = Ts + ta.max_local;
+    L* Ts = reinterpret_cast<L*>(smem + 128 + 2 * (size_t)ta.max_block);
+    L* Fs = Ts + ta.max_local;
     if (threadIdx.x == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
         fence_mbar_init();
-        Fs[ta.fs_words - 1] = R(0);   // the zero cell every gather pad points at
+        Fs[ta.fs_words - 1] = lzero<L>();   // the zero cell every gather pad points at
     }
     __syncthreads();
     unsigned long long target = 0;
@@ -390,8 +402,8 @@ __global__ void __launch_bounds__(kTiledThreads) k_tiled(StepArgs<R> a, TileArgs
     long long kk = 0;
     bool stop = false;
     for (long long s = 0; s < n_steps && !stop; ++s) {
-        const R* Tin = (s & 1) ? a.T2 : a.T;
-        R* Tout = (s & 1) ? a.T : a.T2;
+        const L* Tin = (s & 1) ? a.T2 : a.T;
+        L* Tout = (s & 1) ? a.T : a.T2;
         for (int64_t i = 0; i < n_my; ++i, ++kk) {
             const int64_t t = first + i * gridDim.x;
             const int buf = single ? 0 : (int)(kk & 1);
@@ -415,7 +427,7 @@ __global__ void __launch_bounds__(kTiledThreads) k_tiled(StepArgs<R> a, TileArgs
                 pending = true;
                 pbuf = buf ^ 1;
             }
-            tile_compute<R, NV, KAHAN>(a, ta, t, buf ? stage1 : stage0, Tin, Tout, a.step0 + s, Ts, Fs);
+            tile_compute<R, L, NV, KAHAN>(a, ta, t, buf ? stage1 : stage0, Tin, Tout, a.step0 + s, Ts, Fs);
         }
         const bool ok = grid_barrier(a.status, target, spin_limit);
         done = s + 1;
@@ -429,10 +441,10 @@ __global__ void __launch_bounds__(kTiledThreads) k_tiled(StepArgs<R> a, TileArgs
     if (blockIdx.x == 0 && threadIdx.x == 0) a.status->steps_done = a.step0 + done;
 }
 
-template <typename R, int NV, bool KAHAN>
-cudaError_t launch_tiled_impl(const StepArgs<R>& a, const TileArgs<R>& ta, int64_t n_steps, LaunchCfg& cfg,
+template <typename R, typename L, int NV, bool KAHAN>
+cudaError_t launch_tiled_impl(const StepArgs<R, L>& a, const TileArgs<R>& ta, int64_t n_steps, LaunchCfg& cfg,
                               cudaStream_t s) {
-    auto kern = ta.staged ? k_tiled<R, NV, KAHAN> : k_tiled_direct<R, NV, KAHAN>;
+    auto kern = ta.staged ? k_tiled<R, L, NV, KAHAN> : k_tiled_direct<R, L, NV, KAHAN>;
     const int b = ta.staged ? kTiledThreads : 256;
     cudaError_t err = cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)ta.smem_bytes);
@@ -444,7 +456,7 @@ cudaError_t launch_tiled_impl(const StepArgs<R>& a, const TileArgs<R>& ta, int64
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * cfg.sm_count, ta.n_tiles));
     cfg.grid_used = grid;
-    StepArgs<R> args = a;
+    StepArgs<R, L> args = a;
     TileArgs<R> targs = ta;
     long long n = n_steps, lim = cfg.spin_limit;
     void* params[] = {&args, &targs, &n, &lim};
@@ -490,31 +502,44 @@ cudaError_t launch_impl(const StepArgs<R>& a, int64_t n_steps, LaunchCfg& cfg, c
 
 cudaError_t launch_tiled_f64(const StepArgs<double>& a, const TileArgs<double>& t, int64_t n_steps, LaunchCfg& cfg,
                              cudaStream_t s) {
-    return t.nv == 8 ? launch_tiled_impl<double, 8, false>(a, t, n_steps, cfg, s)
-                     : launch_tiled_impl<double, 4, false>(a, t, n_steps, cfg, s);
+    return t.nv == 8 ? launch_tiled_impl<double, double, 8, false>(a, t, n_steps, cfg, s)
+                     : launch_tiled_impl<double, double, 4, false>(a, t, n_steps, cfg, s);
 }
 
 cudaError_t launch_tiled_f32(const StepArgs<float>& a, const TileArgs<float>& t, bool kahan, int64_t n_steps,
                              LaunchCfg& cfg, cudaStream_t s) {
     if (t.nv == 8)
-        return kahan ? launch_tiled_impl<float, 8, true>(a, t, n_steps, cfg, s)
-                     : launch_tiled_impl<float, 8, false>(a, t, n_steps, cfg, s);
-    return kahan ? launch_tiled_impl<float, 4, true>(a, t, n_steps, cfg, s)
-                 : launch_tiled_impl<float, 4, false>(a, t, n_steps, cfg, s);
+        return kahan ? launch_tiled_impl<float, float, 8, true>(a, t, n_steps, cfg, s)
+                     : launch_tiled_impl<float, float, 8, false>(a, t, n_steps, cfg, s);
+    return kahan ? launch_tiled_impl<float, float, 4, true>(a, t, n_steps, cfg, s)
+                 : launch_tiled_impl<float, float, 4, false>(a, t, n_steps, cfg, s);
 }
 
-int tiled_blocks_per_sm(int precision, int nv, int staged, size_t smem) {
-    const int block = staged ? kTiledThreads : 256;
-    const void* k = nullptr;
+cudaError_t launch_tiled_f32x4(const StepArgs<float, F4>& a, const TileArgs<float>& t, bool kahan, int64_t n_steps,
+                               LaunchCfg& cfg, cudaStream_t s) {
+    if (t.nv == 8)
+        return kahan ? launch_tiled_impl<float, F4, 8, true>(a, t, n_steps, cfg, s)
+                     : launch_tiled_impl<float, F4, 8, false>(a, t, n_steps, cfg, s);
+    return kahan ? launch_tiled_impl<float, F4, 4, true>(a, t, n_steps, cfg, s)
+                 : launch_tiled_impl<float, F4, 4, false>(a, t, n_steps, cfg, s);
+}
+
+template <typename R, typename L>
+const void* pick_tiled(int staged, int nv, bool kahan) {
     if (staged) {
-        if (precision == FEDFEM_FP64) k = nv == 8 ? (const void*)k_tiled<double, 8, false> : (const void*)k_tiled<double, 4, false>;
-        else if (precision == FEDFEM_FP32_KAHAN) k = nv == 8 ? (const void*)k_tiled<float, 8, true> : (const void*)k_tiled<float, 4, true>;
-        else k = nv == 8 ? (const void*)k_tiled<float, 8, false> : (const void*)k_tiled<float, 4, false>;
-    } else {
-        if (precision == FEDFEM_FP64) k = nv == 8 ? (const void*)k_tiled_direct<double, 8, false> : (const void*)k_tiled_direct<double, 4, false>;
-        else if (precision == FEDFEM_FP32_KAHAN) k = nv == 8 ? (const void*)k_tiled_direct<float, 8, true> : (const void*)k_tiled_direct<float, 4, true>;
-        else k = nv == 8 ? (const void*)k_tiled_direct<float, 8, false> : (const void*)k_tiled_direct<float, 4, false>;
+        if (nv == 8) return kahan ? (const void*)k_tiled<R, L, 8, true> : (const void*)k_tiled<R, L, 8, false>;
+        return kahan ? (const void*)k_tiled<R, L, 4, true> : (const void*)k_tiled<R, L, 4, false>;
     }
+    if (nv == 8) return kahan ? (const void*)k_tiled_direct<R, L, 8, true> : (const void*)k_tiled_direct<R, L, 8, false>;
+    return kahan ? (const void*)k_tiled_direct<R, L, 4, true> : (const void*)k_tiled_direct<R, L, 4, false>;
+}
+
+int tiled_blocks_per_sm(int precision, int nv, int staged, int lanes, size_t smem) {
+    const int block = staged ? kTiledThreads : 256;
+    const bool kahan = precision == FEDFEM_FP32_KAHAN;
+    const void* k = precision == FEDFEM_FP64 ? pick_tiled<double, double>(staged, nv, false)
+                    : lanes == 4            ? pick_tiled<float, F4>(staged, nv, kahan)
+                                            : pick_tiled<float, float>(staged, nv, kahan);
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, smem) != cudaSuccess) return 0;

@@ -67,7 +67,7 @@ class fedfem_info(C.Structure):
                 ("steps_done", C.c_int64), ("sim_time", C.c_double), ("device_bytes", C.c_int64),
                 ("bytes_per_step", C.c_int64), ("algorithmic_bytes_per_step", C.c_int64),
                 ("sm_count", C.c_int), ("grid_blocks", C.c_int), ("block_threads", C.c_int),
-                ("kernel", C.c_int), ("tile_nodes", C.c_int)]
+                ("kernel", C.c_int), ("tile_nodes", C.c_int), ("lanes", C.c_int)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -105,8 +105,15 @@ _SIGS = {
     "fedfem_destroy": ([_ctx_p], None),
     "fedfem_version": ([], C.c_char_p),
     "fedfem_debug_set": ([_ctx_p, C.c_int, _i64], C.c_int),
-    "fedfem_plan_layout": ([C.c_int, _i64, _dp, _i64, _ip, C.c_int, _i64, _ip, _i64, C.c_int, _ip, C.c_int,
+    "fedfem_plan_layout": ([C.c_int, _i64, _dp, _i64, _ip, _ip, C.c_int, _i64, _ip, _i64, C.c_int, _ip, C.c_int,
                             C.POINTER(fedfem_layout_info)] + [C.c_void_p] * 12, C.c_int),
+    "fedfem_set_lanes": ([_ctx_p, C.c_int], C.c_int),
+    "fedfem_add_gaussian_source_lane": ([_ctx_p, C.c_int, C.c_int, _dp, C.c_double, C.c_double], C.c_int),
+    "fedfem_set_source_lane": ([_ctx_p, C.c_int, _dp], C.c_int),
+    "fedfem_read_temperature_lane": ([_ctx_p, C.c_int, _dp], C.c_int),
+    "fedfem_set_element_groups": ([_ctx_p, _ip], C.c_int),
+    "fedfem_capture_graph": ([_ctx_p, C.c_double, _i64], C.c_int),
+    "fedfem_replay_graph": ([_ctx_p], C.c_int),
     "fedfem_step_static": ([C.c_int, _i64, _i64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                             C.POINTER(fedfem_material), C.POINTER(fedfem_perfusion), C.c_void_p, C.c_void_p,
                             C.c_double, _i64, C.c_void_p, C.c_void_p], C.c_int),
@@ -290,10 +297,14 @@ def fedfem_debug_set(ctx, key: int, value: int):
 
 
 def fedfem_plan_layout(elem_type, xyz, conn, order=ORDER_MORTON, dirichlet_nodes=(), faces=None,
-                       tile_nodes=0) -> dict:
+                       tile_nodes=0, groups=None) -> dict:
     """Host-only layout planning (no GPU needed); returns the info dict and arrays."""
     x, px = _d(xyz)
     c, pc = _i(conn)
+    if groups is None:
+        g, pg = None, None
+    else:
+        g, pg = _i(groups)
     dn, pdn = _i(np.asarray(dirichlet_nodes, dtype=np.int32).reshape(-1))
     if faces is None or len(faces) == 0:
         fc, pfc, nf, nvf = None, None, 0, 3
@@ -301,7 +312,7 @@ def fedfem_plan_layout(elem_type, xyz, conn, order=ORDER_MORTON, dirichlet_nodes
         fc, pfc = _i(faces)
         nf, nvf = fc.shape[0], fc.shape[1]
     info = fedfem_layout_info()
-    args = [elem_type, x.shape[0], px, c.shape[0], pc, order, dn.shape[0], pdn, nf, nvf, pfc, tile_nodes,
+    args = [elem_type, x.shape[0], px, c.shape[0], pc, pg, order, dn.shape[0], pdn, nf, nvf, pfc, tile_nodes,
             C.byref(info)]
     rc = _lib.fedfem_plan_layout(*args, *([None] * 12))
     if rc != OK:
@@ -327,6 +338,47 @@ def fedfem_plan_layout(elem_type, xyz, conn, order=ORDER_MORTON, dirichlet_nodes
                 arrs[k] = arrs[k][:0]
     d.update(arrs)
     return d
+
+
+def fedfem_set_lanes(ctx, n_lanes: int):
+    _check(ctx, _lib.fedfem_set_lanes(ctx, n_lanes))
+
+
+def fedfem_add_gaussian_source_lane(ctx, lane, group, x0, sigma, peak):
+    x, px = _d(np.asarray(x0, dtype=np.float64).reshape(3))
+    _check(ctx, _lib.fedfem_add_gaussian_source_lane(ctx, lane, group, px, sigma, peak))
+
+
+def fedfem_set_source_lane(ctx, lane, q_r):
+    if q_r is None:
+        _check(ctx, _lib.fedfem_set_source_lane(ctx, lane, None))
+        return
+    q, pq = _d(q_r)
+    _check(ctx, _lib.fedfem_set_source_lane(ctx, lane, pq))
+
+
+def fedfem_read_temperature_lane(ctx, lane: int, out=None) -> np.ndarray:
+    info = fedfem_get_info(ctx)
+    if out is None:
+        out = np.empty(info["n_nodes"], dtype=np.float64)
+    _check(ctx, _lib.fedfem_read_temperature_lane(ctx, lane, out.ctypes.data_as(_dp)))
+    return out
+
+
+def fedfem_set_element_groups(ctx, groups):
+    if groups is None:
+        _check(ctx, _lib.fedfem_set_element_groups(ctx, None))
+        return
+    g, pg = _i(groups)
+    _check(ctx, _lib.fedfem_set_element_groups(ctx, pg))
+
+
+def fedfem_capture_graph(ctx, dt: float, n_steps: int):
+    _check(ctx, _lib.fedfem_capture_graph(ctx, dt, n_steps))
+
+
+def fedfem_replay_graph(ctx):
+    _check(ctx, _lib.fedfem_replay_graph(ctx))
 
 
 def fedfem_step_static(elem_type, n_nodes, n_elems, xyz_dev, conn_dev, row_ptr_dev, slot_dev, material,
@@ -404,6 +456,74 @@ class Solver:
 
     def info(self):
         return fedfem_get_info(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            fedfem_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Independent planning runs stepped together in ONE context and launch.
+
+    ``meshes`` is a list of lists: each inner list holds 1-4 problems that
+    share one mesh (same xyz, conn, material, perfusion, boundary conditions)
+    and differ only in their Gaussian sources.  The meshes are concatenated
+    (node ids offset), kept apart by element groups, and the scenarios of a
+    mesh become scenario lanes; a mesh with fewer than 4 scenarios repeats
+    its last one in the unused lanes.  All runs share one dt (the smallest
+    critical step) and all materials/perfusion/film parameters must agree."""
+
+    def __init__(self, meshes, precision=FP32_KAHAN, device=0, stream=None, kernel=KERNEL_TILED):
+        self.meshes = meshes
+        first = meshes[0][0]
+        xyz, conn, groups, dn, dT = [], [], [], [], []
+        self.node_off = [0]
+        for g, scen in enumerate(meshes):
+            p = scen[0]
+            if p.material != first.material or p.perfusion != first.perfusion:
+                raise ValueError("all runs of a batch must share material and perfusion")
+            off = self.node_off[-1]
+            xyz.append(p.xyz)
+            conn.append(np.asarray(p.conn, dtype=np.int64) + off)
+            groups.append(np.full(len(p.conn), g, dtype=np.int32))
+            dn.append(np.asarray(p.dirichlet_nodes, dtype=np.int64) + off)
+            dT.append(np.asarray(p.dirichlet_T, dtype=np.float64))
+            self.node_off.append(off + p.n_nodes)
+        self.n_nodes = self.node_off[-1]
+        self.ctx = fedfem_create(device, precision, stream)
+        try:
+            fedfem_set_mesh(self.ctx, first.elem_type, np.vstack(xyz), np.vstack(conn))
+            fedfem_set_element_groups(self.ctx, np.concatenate(groups))
+            fedfem_set_lanes(self.ctx, 4)
+            m = first.material
+            fedfem_set_material(self.ctx, m.T_ref, m.rho0, m.drho, m.c0, m.dc, m.k0, m.dk)
+            pf = first.perfusion
+            fedfem_set_perfusion(self.ctx, pf.w_b, pf.c_b, pf.T_a, pf.Q_m)
+            fedfem_set_dirichlet(self.ctx, np.concatenate(dn), np.concatenate(dT))
+            for g, scen in enumerate(meshes):
+                for lane in range(4):
+                    p = scen[min(lane, len(scen) - 1)]
+                    for s in p.sources:    # restricted to mesh g's nodes (group g)
+                        fedfem_add_gaussian_source_lane(self.ctx, lane, g, s.x0, s.sigma, s.peak)
+            fedfem_set_tile(self.ctx, kernel)
+            self.dt_cr = fedfem_precompute(self.ctx, min(p[0].T_lo for p in meshes),
+                                           max(p[0].T_hi for p in meshes))
+            fedfem_init(self.ctx, None, float(first.T0))
+        except Exception:
+            fedfem_destroy(self.ctx)
+            self.ctx = None
+            raise
+
+    def temperature(self, mesh: int, scenario: int) -> np.ndarray:
+        T = fedfem_read_temperature_lane(self.ctx, scenario)
+        return T[self.node_off[mesh]: self.node_off[mesh + 1]]
 
     def close(self):
         if self.ctx:

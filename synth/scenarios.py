@@ -63,13 +63,14 @@ def cube_hex_fp64(n: int = 10, h: float = 1e-3, n_steps: int = 2000) -> Workload
 
 def _sample_sources(rng, axes, count, sigma_range=(2e-3, 5e-3), peak_range=(1e6, 1e7)):
     """Sources with sigma ~ U[sigma_range], peak ~ U[peak_range] and a centre
-    uniform inside the ellipsoid shrunk by 2 sigma (rejection sampling)."""
+    uniform inside the ellipsoid shrunk by 2 sigma (rejection sampling); on
+    small ellipsoids each semi-axis keeps at least a quarter of its length."""
     out = []
     a = np.asarray(axes)
     while len(out) < count:
         sigma = rng.uniform(*sigma_range)
         peak = rng.uniform(*peak_range)
-        inner = a - 2 * sigma
+        inner = np.maximum(a - 2 * sigma, 0.25 * a)
         while True:
             x = rng.uniform(-inner, inner)
             if np.sum((x / inner) ** 2) <= 1.0:

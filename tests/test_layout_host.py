@@ -134,3 +134,20 @@ def test_tiles_cover_and_emulated_gather_matches_oracle(ff, kind, B):
                 acc = acc + Fs[v]
             out[base + l] = acc
     np.testing.assert_allclose(out, ref[node_of[:NF]], rtol=1e-11, atol=1e-11 * np.abs(ref).max())
+
+
+def test_element_groups_keep_meshes_apart(ff):
+    """Two meshes occupying the same space, given as one mesh with element
+    groups: the internal order must not interleave them."""
+    from synth.meshes import tet_ellipsoid
+    a = tet_ellipsoid((0.012, 0.01, 0.008), 2e-3, 4e-4, 1)
+    b = tet_ellipsoid((0.011, 0.01, 0.009), 2e-3, 4e-4, 2)
+    xyz = np.vstack([a.xyz, b.xyz])
+    conn = np.vstack([a.conn, b.conn + len(a.xyz)])
+    groups = np.concatenate([np.zeros(len(a.conn), np.int32), np.ones(len(b.conn), np.int32)])
+    for order in (0, 1, 2):
+        d = ff.fedfem_plan_layout(4, xyz, conn, order=order, groups=groups)
+        g = groups[d["elem_of"]]
+        assert np.all(np.diff(g) >= 0)
+        node_mesh = (d["node_of"] >= len(a.xyz)).astype(int)
+        assert np.all(np.diff(node_mesh) >= 0)
