@@ -335,6 +335,21 @@ int fedfem_step_static(int elem_type, int64_t n_nodes, int64_t n_elems, const do
                        const unsigned char* held_dev, double dt, int64_t n_steps, double* T_dev,
                        void* cuda_stream);
 
+/* ---- Learned surrogate building block ------------------------------------
+ * BF16 GEMM on the tensor cores (the paper has no counterpart; it only points
+ * to neural networks as future work, Section 4):
+ *   Z = A B^T + bias,  out = act(Z)  (act 0: identity, 1: SiLU)
+ * A: M x K bf16 (device, row-major, leading dimension lda), B: N x K bf16
+ * (ldb); lda, ldb multiples of 8; K a multiple of 64; N a multiple of 16, at
+ * most 256.  FP32 accumulation.  Outputs (any may be NULL): Z (fp32, ldz),
+ * Cf (fp32 out, ldc), Cb (bf16 out, ldc).  k_chunk < K splits K over blocks
+ * (multiples of 64); then `partial` must hold ceil(K/k_chunk) * M * N floats
+ * and the splits are summed in a fixed order.  `status` (device int): bit 0
+ * is set if a bounded wait gave up.  Asynchronous on `stream`. */
+int fedfem_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, int M, int N, int K, int k_chunk,
+                     const float* bias, int act, float* Z, int64_t ldz, float* Cf, void* Cb, int64_t ldc,
+                     float* partial, int* status, void* stream);
+
 /* Testing hooks (the paper has no counterpart).  key 1: barrier spin limit in
  * clock64 ticks for later fedfem_step calls (default 4e9, or the environment
  * variable FEDFEM_BARRIER_SPIN_LIMIT).  key 2: index of a block that never

@@ -157,6 +157,25 @@ cudaError_t launch_steps_f32(const StepArgs<float>& a, int nv, bool kahan, int64
                              LaunchCfg& cfg, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
+// BF16 tensor-core GEMM (gemm_tc.cu): C = A B^T (+ bias, SiLU)
+// ---------------------------------------------------------------------------
+struct GemmArgs {
+    const void* A; int64_t lda;      // bf16 M x K, row-major
+    const void* B; int64_t ldb;      // bf16 N x K, row-major
+    int M, N, K;
+    int k_chunk;                     // split-K chunk (multiple of 64; K = no split)
+    const float* bias;               // N or null
+    int act;                         // 0: none, 1: SiLU
+    float* Z; int64_t ldz;           // pre-activation out (fp32) or null
+    float* Cf; int64_t ldc;          // activation out fp32 or null
+    void* Cb;                        // activation out bf16 (leading dimension ldc) or null
+    float* partial;                  // splits x M x N scratch when split
+    int* status;                     // bit 0: an mbarrier wait gave up
+};
+cudaError_t launch_gemm_tc(GemmArgs g, cudaStream_t s);
+size_t gemm_partial_floats(int M, int N, int K, int k_chunk);
+
+// ---------------------------------------------------------------------------
 // Pre-computation (precompute.cu), FP64
 // ---------------------------------------------------------------------------
 struct PreArgs {
