@@ -350,6 +350,43 @@ int fedfem_gemm_bf16(const void* A, int64_t lda, const void* B, int64_t ldb, int
                      const float* bias, int act, float* Z, int64_t ldz, float* Cf, void* Cb, int64_t ldc,
                      float* partial, int* status, void* stream);
 
+/* Message-passing surrogate (the paper has no counterpart beyond pointing to
+ * neural networks as future work, Section 4).  An encode-process-decode graph
+ * network over the conduction sparsity graph (hidden 64, `layers` message-
+ * passing layers) that maps node inputs [(T-37)/10, q/1e7, k(T)/k0, c(T)/c0,
+ * Dirichlet flag] to y, the temperature change over a fixed number of
+ * explicit steps in degC.  GEMMs run on the tensor cores in BF16 with FP32
+ * accumulation; all sums have a fixed order (deterministic).  Flat parameter
+ * layout: W_ne[64][5] b_ne[64] W_ee[64][4] b_ee[64], per layer W_e[64][192]
+ * b_e[64] W_n[64][128] b_n[64], then w_d[64] b_d[1].  Batches of up to
+ * max_batch graphs share the graph; device arrays are batch-major.
+ *   src/dst: n_edges directed edges (host), sorted by dst then src;
+ *   xyz: n_nodes x 3 coordinates (host, m); edge inputs are
+ *   [(x_dst - x_src) / length_scale, |x_dst - x_src| / length_scale]. */
+typedef struct fedfem_mpnn fedfem_mpnn;
+int fedfem_mpnn_create(fedfem_mpnn** out, int device, int64_t n_nodes, int64_t n_edges, const int32_t* src,
+                       const int32_t* dst, const double* xyz, double length_scale, int layers, int max_batch,
+                       void* cuda_stream);
+void fedfem_mpnn_destroy(fedfem_mpnn* m);
+int64_t fedfem_mpnn_n_params(const fedfem_mpnn* m);
+const char* fedfem_mpnn_last_error(const fedfem_mpnn* m);
+/* Parameters as host floats (n_params); set_params also resets the optimiser. */
+int fedfem_mpnn_set_params(fedfem_mpnn* m, const float* params);
+int fedfem_mpnn_get_params(fedfem_mpnn* m, float* params);
+/* Node inputs (device): T and q are batch x n_nodes floats, dirichlet n_nodes
+ * bytes or NULL; x_out batch x n_nodes x 5. */
+int fedfem_mpnn_features(fedfem_mpnn* m, int batch, const float* T_dev, const float* q_dev,
+                         const unsigned char* dirichlet_dev, const fedfem_material* mat, float* x_out_dev);
+/* y_dev (batch x n_nodes) = network(x_dev). */
+int fedfem_mpnn_forward(fedfem_mpnn* m, int batch, const float* x_dev, float* y_dev);
+/* Mean squared error over nodes with mask 1 (mask_dev: n_nodes floats) and
+ * its gradient; *loss and grad (n_params host floats) may be NULL.  Keeps the
+ * gradient for fedfem_mpnn_adam. */
+int fedfem_mpnn_loss_grad(fedfem_mpnn* m, int batch, const float* x_dev, const float* target_dev,
+                          const float* mask_dev, float* loss, float* grad);
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8) with the last gradient. */
+int fedfem_mpnn_adam(fedfem_mpnn* m, float lr);
+
 /* Testing hooks (the paper has no counterpart).  key 1: barrier spin limit in
  * clock64 ticks for later fedfem_step calls (default 4e9, or the environment
  * variable FEDFEM_BARRIER_SPIN_LIMIT).  key 2: index of a block that never

@@ -114,6 +114,22 @@ _SIGS = {
     "fedfem_set_element_groups": ([_ctx_p, _ip], C.c_int),
     "fedfem_capture_graph": ([_ctx_p, C.c_double, _i64], C.c_int),
     "fedfem_replay_graph": ([_ctx_p], C.c_int),
+    "fedfem_mpnn_create": ([C.POINTER(C.c_void_p), C.c_int, _i64, _i64, _ip, _ip, _dp, C.c_double, C.c_int,
+                            C.c_int, C.c_void_p], C.c_int),
+    "fedfem_mpnn_destroy": ([C.c_void_p], None),
+    "fedfem_mpnn_n_params": ([C.c_void_p], _i64),
+    "fedfem_mpnn_last_error": ([C.c_void_p], C.c_char_p),
+    "fedfem_mpnn_set_params": ([C.c_void_p, C.POINTER(C.c_float)], C.c_int),
+    "fedfem_mpnn_get_params": ([C.c_void_p, C.POINTER(C.c_float)], C.c_int),
+    "fedfem_mpnn_features": ([C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(fedfem_material),
+                              C.c_void_p], C.c_int),
+    "fedfem_mpnn_forward": ([C.c_void_p, C.c_int, C.c_void_p, C.c_void_p], C.c_int),
+    "fedfem_mpnn_loss_grad": ([C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_float),
+                               C.POINTER(C.c_float)], C.c_int),
+    "fedfem_mpnn_adam": ([C.c_void_p, C.c_float], C.c_int),
+    "fedfem_gemm_bf16": ([C.c_void_p, _i64, C.c_void_p, _i64, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p,
+                          C.c_int, C.c_void_p, _i64, C.c_void_p, C.c_void_p, _i64, C.c_void_p, C.c_void_p,
+                          C.c_void_p], C.c_int),
     "fedfem_step_static": ([C.c_int, _i64, _i64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                             C.POINTER(fedfem_material), C.POINTER(fedfem_perfusion), C.c_void_p, C.c_void_p,
                             C.c_double, _i64, C.c_void_p, C.c_void_p], C.c_int),
@@ -535,3 +551,64 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+# ---- message-passing surrogate ---------------------------------------------------
+
+def _mcheck(m, rc):
+    if rc != OK:
+        msg = _lib.fedfem_mpnn_last_error(m).decode() if m else ""
+        raise FedfemError(rc, msg)
+
+
+def fedfem_mpnn_create(n_nodes, src, dst, xyz, length_scale, layers=4, max_batch=1, device=0, cuda_stream=None):
+    m = C.c_void_p()
+    s, ps = _i(src)
+    d, pd = _i(dst)
+    x, px = _d(xyz)
+    rc = _lib.fedfem_mpnn_create(C.byref(m), device, n_nodes, len(s), ps, pd, px, length_scale, layers, max_batch,
+                                 C.c_void_p(cuda_stream or 0))
+    _mcheck(None, rc)
+    return m
+
+
+def fedfem_mpnn_destroy(m):
+    _lib.fedfem_mpnn_destroy(m)
+
+
+def fedfem_mpnn_n_params(m) -> int:
+    return int(_lib.fedfem_mpnn_n_params(m))
+
+
+def fedfem_mpnn_set_params(m, params):
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    _mcheck(m, _lib.fedfem_mpnn_set_params(m, p.ctypes.data_as(C.POINTER(C.c_float))))
+
+
+def fedfem_mpnn_get_params(m) -> np.ndarray:
+    out = np.empty(fedfem_mpnn_n_params(m), dtype=np.float32)
+    _mcheck(m, _lib.fedfem_mpnn_get_params(m, out.ctypes.data_as(C.POINTER(C.c_float))))
+    return out
+
+
+def fedfem_mpnn_features(m, batch, T_dev, q_dev, dirichlet_dev, material, x_dev):
+    mat = fedfem_material(*material)
+    _mcheck(m, _lib.fedfem_mpnn_features(m, batch, C.c_void_p(T_dev), C.c_void_p(q_dev),
+                                         C.c_void_p(dirichlet_dev or 0), C.byref(mat), C.c_void_p(x_dev)))
+
+
+def fedfem_mpnn_forward(m, batch, x_dev, y_dev):
+    _mcheck(m, _lib.fedfem_mpnn_forward(m, batch, C.c_void_p(x_dev), C.c_void_p(y_dev)))
+
+
+def fedfem_mpnn_loss_grad(m, batch, x_dev, target_dev, mask_dev, want_grad=False):
+    loss = C.c_float()
+    g = np.empty(fedfem_mpnn_n_params(m), dtype=np.float32) if want_grad else None
+    _mcheck(m, _lib.fedfem_mpnn_loss_grad(m, batch, C.c_void_p(x_dev), C.c_void_p(target_dev), C.c_void_p(mask_dev),
+                                          C.byref(loss),
+                                          g.ctypes.data_as(C.POINTER(C.c_float)) if g is not None else None))
+    return loss.value, g
+
+
+def fedfem_mpnn_adam(m, lr):
+    _mcheck(m, _lib.fedfem_mpnn_adam(m, lr))
