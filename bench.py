@@ -48,10 +48,15 @@ def parse():
     ap.add_argument("--kernel", default="auto", choices=["auto", "two_phase", "persistent", "tiled", "tiled_staged"])
     ap.add_argument("--tile-nodes", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="cube", choices=["cube", "planning"],
+    ap.add_argument("--workload", default="cube", choices=["cube", "planning", "surrogate"],
                     help="cube: the 128^3 throughput cube (default); planning: 64 uneven tet meshes x 4 "
                          "scenarios in one batched launch, compared with the plain per-run GPU path")
     ap.add_argument("--meshes", type=int, default=64)
+    ap.add_argument("--train-scenarios", type=int, default=2000)
+    ap.add_argument("--eval-scenarios", type=int, default=500)
+    ap.add_argument("--epochs", type=int, default=2)
+    ap.add_argument("--budget", type=float, nargs="+", default=[0.005, 0.05],
+                    help="local error budgets (degC) of the surrogate's plain-path checks")
     return ap.parse_args()
 
 
@@ -499,12 +504,110 @@ def run_planning(args):
     print(json.dumps(line))
 
 
+# ---------------------------------------------------------------------------
+# learned surrogate workload (opt-in)
+# ---------------------------------------------------------------------------
+
+def run_surrogate(args):
+    """Train the message-passing surrogate on trajectories of the plain path
+    (10 mm hex cube, one seeded source per scenario), then advance held-out
+    scenarios with the surrogate + periodic plain-path checks + fallback, and
+    compare with the plain path alone."""
+    import torch
+    from paper_1909_05098_gb300.build import build
+    build()
+    from paper_1909_05098_gb300 import fedfem as ff
+    from paper_1909_05098_gb300.surrogate import PlainEnsemble, Surrogate, rollout
+    from synth.scenarios import cube_hex_fp64, source_density, surrogate_sources
+    torch.cuda.set_device(0)
+    log = lambda m: print(m, file=sys.stderr, flush=True)
+    p = cube_hex_fp64().problem
+    W, n_win = 50, 40                              # 50 explicit steps per surrogate step, 2000 steps
+    # --- training data from the plain path
+    t0 = time.perf_counter()
+    src_tr = surrogate_sources(args.train_scenarios, seed=20190905)
+    q_tr = source_density(p.xyz, src_tr)
+    ens = PlainEnsemble(p, q_tr)
+    dt = 0.5 * ens.dt_cr
+    T = torch.full((len(src_tr), p.n_nodes), 37.0, dtype=torch.float64, device="cuda")
+    T[:, torch.tensor(p.dirichlet_nodes, dtype=torch.int64)] = 37.0
+    ens.set_state(T)
+    states = [T.float()]
+    for _ in range(n_win):
+        ens.step(dt, W)
+        states.append(ens.state().float())
+    ens.close()
+    S = torch.stack(states, 1)                      # scenarios x (n_win + 1) x N
+    T_in = S[:, :-1].reshape(-1, p.n_nodes).contiguous()
+    T_out = S[:, 1:].reshape(-1, p.n_nodes).contiguous()
+    q32 = torch.tensor(q_tr, dtype=torch.float32, device="cuda")
+    q_in = q32[:, None, :].expand(-1, n_win, -1).reshape(-1, p.n_nodes).contiguous()
+    gen_s = time.perf_counter() - t0
+    log(f"training pairs {T_in.shape[0]} in {gen_s:.1f} s")
+    # --- training
+    sur = Surrogate(p, window=W, max_batch=64)
+    t0 = time.perf_counter()
+    losses = sur.train(T_in, q_in, T_out, epochs=args.epochs, batch=32, lr=1e-3, log=log)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    del T_in, T_out, q_in, S
+    # --- held-out scenarios
+    src_ev = surrogate_sources(args.eval_scenarios, seed=19090598)
+    q_ev = source_density(p.xyz, src_ev)
+    qe32 = torch.tensor(q_ev, dtype=torch.float32, device="cuda")
+    ens = PlainEnsemble(p, q_ev)
+    T0 = torch.full((len(src_ev), p.n_nodes), 37.0, dtype=torch.float64, device="cuda")
+    # plain path alone (the reference and the timing baseline)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ens.set_state(T0)
+    ens.step(dt, W * n_win)
+    T_plain = ens.state()
+    torch.cuda.synchronize()
+    plain_s = time.perf_counter() - t0
+    runs = {}
+    for budget in args.budget:
+        res = rollout(sur, ens, qe32, T0, dt, n_windows=n_win // 10, check_every=10, budget=budget)
+        runs[str(budget)] = {"sim_s_per_wall_s": dt * W * n_win * len(src_ev) / res.wall_s, "wall_s": res.wall_s,
+                             "checks": res.checks, "rejected": res.rejected,
+                             "surrogate_steps": res.surrogate_steps, "max_check_error_C": res.max_check_error,
+                             "max_err_vs_plain_C": float((res.T - T_plain).abs().max()),
+                             "gain_vs_plain": plain_s / res.wall_s}
+    # the surrogate alone (every check accepted): its raw cost per 50 explicit steps
+    res_free = rollout(sur, ens, qe32, T0, dt, n_windows=n_win // 10, check_every=10, budget=float("inf"))
+    sim = dt * W * n_win * len(src_ev)
+    best = runs[str(args.budget[-1])]
+    line = {
+        "metric": "simulated s / wall s (all held-out scenarios)", "value": best["sim_s_per_wall_s"],
+        "unit": "sim-s/s", "n_gpus": 1, "higher_is_better": True, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": f"10 mm hex cube (1331 nodes), surrogate = 4-layer message passing (hidden 64, "
+                               f"BF16 tcgen05 GEMMs) advancing {W} explicit steps; {len(src_tr)} training and "
+                               f"{len(src_ev)} held-out single-source scenarios, {W * n_win} steps each, check "
+                               f"every 10 surrogate steps; value at local budget {args.budget[-1]} degC",
+                   "dt_s": dt, "training_pairs": len(src_tr) * n_win, "epochs": args.epochs,
+                   "train_s": train_s, "data_s": gen_s, "params": sur.n_params},
+        "loss_first_last": [float(np.mean(losses[:100])), float(np.mean(losses[-100:]))],
+        "plain_gpu_path": {"sim_s_per_wall_s": sim / plain_s, "wall_s": plain_s},
+        "surrogate_with_fallback": runs,
+        "surrogate_unchecked": {"sim_s_per_wall_s": sim / res_free.wall_s, "wall_s": res_free.wall_s,
+                                "max_err_vs_plain_C": float((res_free.T - T_plain).abs().max()),
+                                "note": "includes the first plain check of each stretch"},
+        "gain_vs_plain": best["gain_vs_plain"],
+        "max_err_vs_plain_C": best["max_err_vs_plain_C"],
+    }
+    sur.close()
+    ens.close()
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "planning":
         run_planning(args)
+    elif args.workload == "surrogate":
+        run_surrogate(args)
     else:
         run_ours(args)
 

@@ -30,7 +30,9 @@
  *    in kg/(m^3 s) as in Eq. 1.
  *  - All device work is issued on the context's CUDA stream.  fedfem_step is
  *    asynchronous; every other call that touches the device returns after its
- *    work has completed.
+ *    work has completed.  Device buffers passed to the *_device calls must be
+ *    ready on that stream: when they were written on another stream, the
+ *    caller synchronizes first.
  *  - A context is used by one host thread at a time.
  *  - The library owns all device memory it allocates and frees it in
  *    fedfem_destroy.
@@ -228,6 +230,12 @@ int fedfem_add_gaussian_source_lane(fedfem_ctx* ctx, int lane, int group, const 
 int fedfem_set_source_lane(fedfem_ctx* ctx, int lane, const double* q_r);
 /* Temperatures of one lane (n_nodes doubles, input order). */
 int fedfem_read_temperature_lane(fedfem_ctx* ctx, int lane, double* out);
+/* Initial field per lane from device memory: n_lanes x n_nodes doubles
+ * (lane-major, input order); Dirichlet nodes take their values.  As
+ * fedfem_init otherwise. */
+int fedfem_init_lanes_device(fedfem_ctx* ctx, const double* T0_dev);
+/* All lanes' temperatures into device memory, n_lanes x n_nodes doubles. */
+int fedfem_read_lanes_device(fedfem_ctx* ctx, double* out_dev);
 
 /* Element groups: several independent meshes given as one mesh (their node
  * sets disjoint); group[e] (n_elems values) keeps each mesh's elements

@@ -865,8 +865,8 @@ static int mirror_T(fedfem_ctx* c) {
     return FEDFEM_OK;
 }
 
-static int init_common(fedfem_ctx* c) {
-    for (int l = 1; l < c->n_lanes; ++l)   // every lane starts from the same field
+static int init_common(fedfem_ctx* c, bool per_lane = false) {
+    for (int l = 1; l < c->n_lanes && !per_lane; ++l)   // every lane starts from the same field
         CU(cudaMemcpyAsync(c->io + l * c->N, c->io, sizeof(double) * c->N, cudaMemcpyDeviceToDevice, c->stream),
            "init copy");
     CU(launch_init_state(c->precision, c->n_lanes, c->N, c->L.N_free, c->node_of, c->io, c->T_dir, c->T, c->Tlo,
@@ -905,6 +905,27 @@ int fedfem_init_device(fedfem_ctx* c, const double* T0_dev) {
     CU(cudaSetDevice(c->device), "set device");
     CU(cudaMemcpyAsync(c->io, T0_dev, sizeof(double) * c->N, cudaMemcpyDeviceToDevice, c->stream), "copy T0");
     return init_common(c);
+}
+
+int fedfem_init_lanes_device(fedfem_ctx* c, const double* T0_dev) {
+    if (!c || !T0_dev) return fail(c, FEDFEM_E_ARG, "null T0");
+    if (!c->pre) return fail(c, FEDFEM_E_STATE, "precompute first");
+    CU(cudaSetDevice(c->device), "set device");
+    CU(cudaMemcpyAsync(c->io, T0_dev, sizeof(double) * c->N * c->n_lanes, cudaMemcpyDeviceToDevice, c->stream),
+       "copy T0");
+    return init_common(c, true);
+}
+
+int fedfem_read_lanes_device(fedfem_ctx* c, double* out_dev) {
+    if (!c || !out_dev) return fail(c, FEDFEM_E_ARG, "null output");
+    if (!c->inited) return fail(c, FEDFEM_E_STATE, "init first");
+    CU(cudaSetDevice(c->device), "set device");
+    for (int l = 0; l < c->n_lanes; ++l)
+        CU(launch_read_state(c->precision, c->n_lanes, l, c->N, c->node_of, c->T, c->Tlo, out_dev + l * c->N,
+                             c->stream),
+           "read kernel");
+    CU(cudaStreamSynchronize(c->stream), "read");
+    return FEDFEM_OK;
 }
 
 int fedfem_step(fedfem_ctx* c, double dt, int64_t n_steps) {

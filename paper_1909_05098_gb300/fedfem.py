@@ -112,6 +112,8 @@ _SIGS = {
     "fedfem_set_source_lane": ([_ctx_p, C.c_int, _dp], C.c_int),
     "fedfem_read_temperature_lane": ([_ctx_p, C.c_int, _dp], C.c_int),
     "fedfem_set_element_groups": ([_ctx_p, _ip], C.c_int),
+    "fedfem_init_lanes_device": ([_ctx_p, C.c_void_p], C.c_int),
+    "fedfem_read_lanes_device": ([_ctx_p, C.c_void_p], C.c_int),
     "fedfem_capture_graph": ([_ctx_p, C.c_double, _i64], C.c_int),
     "fedfem_replay_graph": ([_ctx_p], C.c_int),
     "fedfem_mpnn_create": ([C.POINTER(C.c_void_p), C.c_int, _i64, _i64, _ip, _ip, _dp, C.c_double, C.c_int,
@@ -379,6 +381,14 @@ def fedfem_read_temperature_lane(ctx, lane: int, out=None) -> np.ndarray:
         out = np.empty(info["n_nodes"], dtype=np.float64)
     _check(ctx, _lib.fedfem_read_temperature_lane(ctx, lane, out.ctypes.data_as(_dp)))
     return out
+
+
+def fedfem_init_lanes_device(ctx, T0_dev_ptr: int):
+    _check(ctx, _lib.fedfem_init_lanes_device(ctx, C.c_void_p(T0_dev_ptr)))
+
+
+def fedfem_read_lanes_device(ctx, out_dev_ptr: int):
+    _check(ctx, _lib.fedfem_read_lanes_device(ctx, C.c_void_p(out_dev_ptr)))
 
 
 def fedfem_set_element_groups(ctx, groups):

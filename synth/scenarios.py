@@ -148,3 +148,26 @@ def planning_batch(n_meshes: int = 64, n_scenarios: int = 4, n_range=(5_000, 200
                                  T0=37.0, T_lo=25.0, T_hi=400.0))
         out.append(PlanningMesh(seed, target, probs))
     return out
+
+
+def surrogate_sources(n: int, seed: int, cube_mm: float = 10.0, inner_mm: float = 6.0,
+                      sigma_range=(1e-3, 3e-3), peak_range=(1e6, 1e7)) -> List[GaussianSource]:
+    """Training / evaluation scenarios of the surrogate on the 10 mm cube: one
+    source per scenario, centre uniform in the central 6 mm cube, sigma
+    U[1, 3] mm, peak U[1e6, 1e7] W/m^3."""
+    rng = np.random.default_rng(seed)
+    lo = (cube_mm - inner_mm) / 2e3
+    out = []
+    for _ in range(n):
+        x0 = tuple(float(v) for v in rng.uniform(lo, lo + inner_mm / 1e3, 3))
+        out.append(GaussianSource(x0, float(rng.uniform(*sigma_range)), float(rng.uniform(*peak_range))))
+    return out
+
+
+def source_density(xyz: np.ndarray, sources: List[GaussianSource]) -> np.ndarray:
+    """Nodal source densities (W/m^3), one row per scenario -- the input field
+    the scenario prescribes."""
+    q = np.zeros((len(sources), len(xyz)))
+    for i, s in enumerate(sources):
+        q[i] = s.peak * np.exp(-np.sum((xyz - np.asarray(s.x0)) ** 2, axis=1) / (2.0 * s.sigma ** 2))
+    return q

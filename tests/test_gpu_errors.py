@@ -167,6 +167,7 @@ def test_device_pointer_init_and_read():
     try:
         dev = torch.device("cuda", 0)
         T0 = torch.linspace(36.0, 38.0, p.n_nodes, dtype=torch.float64, device=dev)
+        torch.cuda.synchronize()                   # the context has its own stream
         f.fedfem_init_device(s.ctx, T0.data_ptr())
         out = torch.empty(p.n_nodes, dtype=torch.float64, device=dev)
         f.fedfem_read_temperature_device(s.ctx, out.data_ptr())
