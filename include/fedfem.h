@@ -96,7 +96,9 @@ typedef struct { double w_b, c_b, T_a, Q_m; } fedfem_perfusion;
 typedef struct {
     int kernel;        /* FEDFEM_KERNEL_* */
     int block;         /* threads per block: 64..1024, multiple of 32 (0 = default) */
-    int tile_nodes;    /* TILED: owned nodes per tile, multiple of 32 (0 = default) */
+    int tile_nodes;    /* TILED: target owned nodes per tile, multiple of 8 (0 = default); the
+                          library moves it to the nearest size that gives every resident
+                          block the same number of tiles */
     int blocks_per_sm; /* PERSISTENT/TILED: resident blocks per SM (0 = occupancy maximum) */
 } fedfem_tile;
 
@@ -273,8 +275,10 @@ typedef struct {
     int64_t n_slices, n_gather;   /* sliced-ELL gather over the free nodes */
     int max_degree;
     int tile_nodes;               /* owned nodes per tile (0: no tiles requested) */
-    int64_t n_tiles, n_tile_elems, n_halo, n_tile_gather, n_tile_slice_off;
+    int64_t n_tiles, n_tile_elems, n_halo;
     int max_tile_local, max_tile_elems;
+    int max_tile_degree;          /* most elements at one owned node of a tile */
+    int tile_rank_shift;          /* tile_lconn entry = local id | rank << tile_rank_shift */
 } fedfem_layout_info;
 
 /* Host-only planning (no device work): the internal order and the gather
@@ -287,11 +291,13 @@ typedef struct {
  *       the element loads gather[slice_off[i/32] + 32k + i%32], k = 0.., each
  *       entry internal_element * elem_type + corner, pads = n_elems * elem_type,
  *       in input element order (the summation order of every kernel)
- *   tile_elem_off[n_tiles+1], tile_elems[n_tile_elems] (internal elements),
- *   tile_lconn[n_tile_elems * elem_type] (tile-local node ids: owned nodes
- *       first, then tile_halo), tile_halo_off[n_tiles+1], tile_halo[n_halo],
- *   tile_gather_base[n_tiles], tile_slice_off[n_tile_slice_off],
- *   tile_gather[n_tile_gather] (corner * tile_elements + j; pad = elem_type * tile_elements).
+ *   tile_elem_off[n_tiles+1], tile_elems[n_tile_elems] (internal elements,
+ *       ascending), tile_lconn[n_tile_elems * elem_type]: the local id of each
+ *       corner (owned nodes first, then tile_halo) in the low tile_rank_shift
+ *       bits and, for an owned corner, above them the element's rank in that
+ *       node's gather list (its position in the node's fixed-order sum),
+ *   tile_halo_off[n_tiles+1], tile_halo[n_halo] (internal node ids),
+ *   tile_degree[n_tiles] (most elements at one owned node of the tile).
  * tile_nodes <= 0 requests no tiles.  groups: element groups as in
  * fedfem_set_element_groups, or NULL.  Mesh / Dirichlet / face arguments as in
  * the set_* calls.  Returns FEDFEM_E_MESH / FEDFEM_E_ARG on bad input. */
@@ -301,7 +307,7 @@ int fedfem_plan_layout(int elem_type, int64_t n_nodes, const double* xyz, int64_
                        fedfem_layout_info* info, int32_t* node_of,
                        int32_t* elem_of, int32_t* slice_off, int32_t* gather, int32_t* tile_elem_off,
                        int32_t* tile_elems, uint16_t* tile_lconn, int32_t* tile_halo_off, int32_t* tile_halo,
-                       int32_t* tile_gather_base, int32_t* tile_slice_off, uint16_t* tile_gather);
+                       int32_t* tile_degree);
 
 /* Explicit steps that allocate nothing (the paper has no counterpart).
  *

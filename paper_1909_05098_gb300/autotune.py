@@ -22,7 +22,7 @@ def candidates(elem_type: int, precision: int):
     """(kernel, tile_nodes, blocks_per_sm) triples; tile_nodes 0 = the library's default."""
     out = [(ff.KERNEL_PERSISTENT, 0, 0)]
     sizes = (0, 128, 256, 384) if elem_type == ff.HEX8 else (0, 64, 96, 128, 192)
-    staged = (0, 256, 384, 512) if elem_type == ff.HEX8 else (0, 128, 192)
+    staged = (0, 384, 448, 576, 640) if elem_type == ff.HEX8 else (0, 128, 192, 320)
     if precision == ff.FP64:
         sizes = tuple(s // 2 for s in sizes if s)[:2] + (0,)
         staged = (0,)

@@ -68,7 +68,7 @@ struct fedfem_ctx {
     unsigned char* t_blocks = nullptr;
     int64_t* t_block_off = nullptr;
     int64_t t_block_bytes = 0;
-    int t_max_block = 0, t_max_local = 0, t_fs_words = 0;
+    int t_max_block = 0, t_max_local = 0;
     size_t t_smem = 0;
     void* slots = nullptr;
     int32_t* node_of = nullptr;
@@ -213,25 +213,25 @@ cudaError_t talloc(fedfem_ctx* c, P** p, size_t bytes) {
     return cudaSuccess;
 }
 
-// bytes of tile t's packed block (see TileArgs)
+// bytes of tile t's packed block: int4 header {elements, padded elements,
+// halo nodes, most elements at one owned node}, the 6 element-matrix rows
+// (padded element count each), the 16-bit local connectivity (nv per padded
+// element), the halo node ids; 16-byte multiple
 int64_t tile_block_bytes(const Tiles& t, int64_t i, size_t rs) {
     const int64_t ne = t.e_off[i + 1] - t.e_off[i], ne_pad = (ne + 7) / 8 * 8;
     const int64_t nh = t.h_off[i + 1] - t.h_off[i];
-    const int64_t G = (i + 1 < t.n_tiles ? t.g_base[i + 1] : (int64_t)t.gat.size()) - t.g_base[i];
-    int64_t b = 16 + 6 * ne_pad * (int64_t)rs + ne_pad * t.nv * 2 + G * 2 + (nh + 3) / 4 * 4 * 4 +
-                (t.spt + 1 + 3) / 4 * 4 * 4;
+    const int64_t b = 16 + 6 * ne_pad * (int64_t)rs + ne_pad * t.nv * 2 + nh * 4;
     return (b + 15) / 16 * 16;
 }
 
-size_t tile_smem(const Tiles& t, size_t rs, size_t ls, int* max_block, int* fs_words, bool staged) {
-    int64_t mb = 0, max_ne_pad = 0;
-    for (int64_t i = 0; i < t.n_tiles; ++i) {
-        mb = std::max(mb, tile_block_bytes(t, i, rs));
-        max_ne_pad = std::max<int64_t>(max_ne_pad, (t.e_off[i + 1] - t.e_off[i] + 7) / 8 * 8);
-    }
+// dynamic shared memory of the tiled kernels: (staged) two block stages, the
+// tile temperatures and the per-node load table (max_deg rows of B)
+size_t tile_smem(const Tiles& t, size_t rs, size_t ls, int* max_block, bool staged) {
+    int64_t mb = 0;
+    for (int64_t i = 0; i < t.n_tiles; ++i) mb = std::max(mb, tile_block_bytes(t, i, rs));
     *max_block = (int)mb;
-    *fs_words = (int)(t.nv * max_ne_pad + 1);
-    const size_t b = (staged ? 128 + 2 * (size_t)mb : 0) + ls * ((size_t)t.max_local + *fs_words);
+    const size_t ts = ((size_t)t.max_local * ls + 15) / 16 * 16;
+    const size_t b = (staged ? 128 + 2 * (size_t)mb : 0) + ts + ls * (size_t)std::max(1, t.max_deg) * t.B;
     return (b + 15) / 16 * 16;
 }
 
@@ -249,28 +249,45 @@ int plan_tiles(fedfem_ctx* c) {
     int B = c->tile.tile_nodes;
     Tiles t;
     std::string m;
-    int mb = 0, fw = 0;
-    if (B <= 0) {
-        int B0 = c->nv == 8 ? 256 : 128;
-        if (c->precision == FEDFEM_FP64) B0 /= 2;
-        if (c->n_lanes > 1) B0 /= 2;
-        B0 = (int)std::max<int64_t>(32, std::min<int64_t>(B0, ((NF + 31) / 32) * 32));
+    int mb = 0;
+    {
+        // target size, then the nearest size that gives every resident block the
+        // same number of tiles at the same occupancy
+        int B0 = B;
+        if (B0 <= 0) {
+            B0 = c->nv == 8 ? (staged ? 512 : 256) : (staged ? 256 : 128);
+            if (c->precision == FEDFEM_FP64) B0 /= 2;
+            if (c->n_lanes > 1) B0 /= 2;
+        }
+        B0 = (int)std::max<int64_t>(8, std::min<int64_t>(B0, (NF + 7) / 8 * 8));
         m = build_tiles(c->L, B0, t);
         if (!m.empty()) return fail(c, FEDFEM_E_ARG, m);
-        size_t smem = tile_smem(t, rs, ls, &mb, &fw, staged);
+        size_t smem = tile_smem(t, rs, ls, &mb, staged);
         int per_sm = tiled_blocks_per_sm(c->precision, c->nv, staged, c->n_lanes, smem);
         if (c->tile.blocks_per_sm > 0) per_sm = std::min(per_sm, c->tile.blocks_per_sm);
-        if (per_sm < 1) return fail(c, FEDFEM_E_UNSUPPORTED, "tile does not fit in shared memory");
+        if (per_sm < 1) return fail(c, FEDFEM_E_UNSUPPORTED, "tile does not fit in shared memory; use smaller tile_nodes");
+        B = B0;
         const int64_t grid = (int64_t)per_sm * c->sm_count;
-        const int64_t waves = std::max<int64_t>(1, (int64_t)std::llround((double)NF / ((double)B0 * grid)));
-        B = (int)(((NF + waves * grid - 1) / (waves * grid) + 31) / 32 * 32);
-        if (B > 2 * B0 || waves * grid * 32 > NF * 4) B = B0;   // small meshes: keep the default size
+        const int64_t w0 = std::max<int64_t>(1, (int64_t)std::llround((double)NF / ((double)B0 * grid)));
+        for (int64_t waves = w0; waves <= w0 + 1; ++waves) {
+            const int64_t Bw = ((NF + waves * grid - 1) / (waves * grid) + 7) / 8 * 8;
+            if (Bw < 32 || Bw > 2 * (int64_t)B0) continue;                 // small meshes: keep the target
+            Tiles tw;
+            if (!build_tiles(c->L, (int)Bw, tw).empty()) continue;
+            int mbw = 0;
+            int pw = tiled_blocks_per_sm(c->precision, c->nv, staged, c->n_lanes, tile_smem(tw, rs, ls, &mbw, staged));
+            if (c->tile.blocks_per_sm > 0) pw = std::min(pw, c->tile.blocks_per_sm);
+            if (pw != per_sm) continue;
+            B = (int)Bw;
+            t = std::move(tw);
+            break;
+        }
     }
     if (t.B != B) {
         m = build_tiles(c->L, B, t);
         if (!m.empty()) return fail(c, FEDFEM_E_ARG, m);
     }
-    const size_t smem = tile_smem(t, rs, ls, &mb, &fw, staged);
+    const size_t smem = tile_smem(t, rs, ls, &mb, staged);
     if (tiled_blocks_per_sm(c->precision, c->nv, staged, c->n_lanes, smem) < 1)
         return fail(c, FEDFEM_E_UNSUPPORTED, "tile does not fit in shared memory; use smaller tile_nodes");
     free_tiles(c);
@@ -288,9 +305,7 @@ int plan_tiles(fedfem_ctx* c) {
         unsigned char* b = blob.data() + off[i];
         const int64_t e0 = t.e_off[i], ne = t.e_off[i + 1] - e0, ne_pad = (ne + 7) / 8 * 8;
         const int64_t h0 = t.h_off[i], nh = t.h_off[i + 1] - h0;
-        const int64_t g0 = t.g_base[i];
-        const int64_t G = (i + 1 < t.n_tiles ? t.g_base[i + 1] : (int64_t)t.gat.size()) - g0;
-        const int32_t hdr[4] = {(int32_t)ne, (int32_t)ne_pad, (int32_t)nh, (int32_t)G};
+        const int32_t hdr[4] = {(int32_t)ne, (int32_t)ne_pad, (int32_t)nh, t.deg[i]};
         std::memcpy(b, hdr, 16);
         unsigned char* Mb = b + 16;
         for (int q = 0; q < 6; ++q)
@@ -298,12 +313,8 @@ int plan_tiles(fedfem_ctx* c) {
                 std::memcpy(Mb + rs * (q * ne_pad + j), Mh.data() + rs * (q * E + t.e_glob[e0 + j]), rs);
         uint16_t* lc = (uint16_t*)(Mb + rs * 6 * ne_pad);
         std::memcpy(lc, t.lconn.data() + e0 * t.nv, sizeof(uint16_t) * ne * t.nv);
-        uint16_t* g = lc + t.nv * ne_pad;
-        std::memcpy(g, t.gat.data() + g0, sizeof(uint16_t) * G);
-        int32_t* h = (int32_t*)(g + G);
+        int32_t* h = (int32_t*)(lc + t.nv * ne_pad);
         std::memcpy(h, t.halo.data() + h0, sizeof(int32_t) * nh);
-        int32_t* so = h + (nh + 3) / 4 * 4;
-        std::memcpy(so, t.s_off.data() + i * (t.spt + 1), sizeof(int32_t) * (t.spt + 1));
     }
     CU(talloc(c, &c->t_blocks, blob.size()), "tile alloc");
     CU(talloc(c, &c->t_block_off, sizeof(int64_t) * off.size()), "tile alloc");
@@ -314,7 +325,6 @@ int plan_tiles(fedfem_ctx* c) {
     c->t_block_bytes = (int64_t)blob.size();
     c->t_max_block = mb;
     c->t_max_local = t.max_local;
-    c->t_fs_words = fw;
     c->t_smem = smem;
     c->tiles_B = t.B;
     c->tiles_host = std::move(t);
@@ -326,9 +336,10 @@ template <typename R>
 TileArgs<R> make_tile_args(fedfem_ctx* c) {
     TileArgs<R> t{};
     const Tiles& h = c->tiles_host;
-    t.n_tiles = h.n_tiles; t.B = h.B; t.spt = h.spt; t.nv = h.nv;
+    t.n_tiles = h.n_tiles; t.B = h.B; t.nv = h.nv;
+    t.rank_shift = h.rank_shift; t.max_deg = std::max(1, h.max_deg);
     t.blocks = c->t_blocks; t.block_off = c->t_block_off;
-    t.max_block = c->t_max_block; t.max_local = c->t_max_local; t.fs_words = c->t_fs_words;
+    t.max_block = c->t_max_block; t.max_local = c->t_max_local;
     t.smem_bytes = c->t_smem;
     t.staged = c->tile.kernel == FEDFEM_KERNEL_TILED_STAGED;
     return t;
@@ -382,7 +393,7 @@ int fedfem_plan_layout(int elem_type, int64_t n_nodes, const double* xyz, int64_
                        fedfem_layout_info* info, int32_t* node_of,
                        int32_t* elem_of, int32_t* slice_off, int32_t* gather, int32_t* tile_elem_off,
                        int32_t* tile_elems, uint16_t* tile_lconn, int32_t* tile_halo_off, int32_t* tile_halo,
-                       int32_t* tile_gather_base, int32_t* tile_slice_off, uint16_t* tile_gather) {
+                       int32_t* tile_degree) {
     if (!info || !xyz || !conn || n_nodes <= 0 || n_elems <= 0) return FEDFEM_E_ARG;
     if (elem_type != FEDFEM_HEX8 && elem_type != FEDFEM_TET4) return FEDFEM_E_ARG;
     if (order < FEDFEM_ORDER_INPUT || order > FEDFEM_ORDER_RCM) return FEDFEM_E_ARG;
@@ -420,12 +431,12 @@ int fedfem_plan_layout(int elem_type, int64_t n_nodes, const double* xyz, int64_
     info->max_degree = L.max_degree;
     info->tile_nodes = tile_nodes > 0 ? tile_nodes : 0;
     info->n_tiles = t.n_tiles; info->n_tile_elems = (int64_t)t.e_glob.size(); info->n_halo = (int64_t)t.halo.size();
-    info->n_tile_gather = (int64_t)t.gat.size(); info->n_tile_slice_off = (int64_t)t.s_off.size();
     info->max_tile_local = t.max_local; info->max_tile_elems = t.max_elems;
+    info->max_tile_degree = t.max_deg; info->tile_rank_shift = tile_nodes > 0 ? t.rank_shift : 0;
     auto put = [](auto* dst, const auto& v) { if (dst && !v.empty()) std::memcpy(dst, v.data(), v.size() * sizeof(v[0])); };
     put(node_of, L.node_of); put(elem_of, L.elem_of); put(slice_off, L.sell_off); put(gather, L.sell_ids);
     put(tile_elem_off, t.e_off); put(tile_elems, t.e_glob); put(tile_lconn, t.lconn); put(tile_halo_off, t.h_off);
-    put(tile_halo, t.halo); put(tile_gather_base, t.g_base); put(tile_slice_off, t.s_off); put(tile_gather, t.gat);
+    put(tile_halo, t.halo); put(tile_degree, t.deg);
     return FEDFEM_OK;
 }
 
@@ -647,7 +658,7 @@ int fedfem_set_tile(fedfem_ctx* c, const fedfem_tile* t) {
     if (!c || !t) return fail(c, FEDFEM_E_ARG, "null tile");
     if (t->kernel < FEDFEM_KERNEL_TWO_PHASE || t->kernel > FEDFEM_KERNEL_TILED_STAGED) return fail(c, FEDFEM_E_ARG, "unknown kernel");
     if (t->block != 0 && (t->block < 64 || t->block > 1024 || t->block % 32)) return fail(c, FEDFEM_E_ARG, "block must be 64..1024, multiple of 32");
-    if (t->blocks_per_sm < 0 || t->tile_nodes < 0 || t->tile_nodes % 32) return fail(c, FEDFEM_E_ARG, "bad tile knobs");
+    if (t->blocks_per_sm < 0 || t->tile_nodes < 0 || t->tile_nodes % 8) return fail(c, FEDFEM_E_ARG, "bad tile knobs");
     if (t->tile_nodes != c->tile.tile_nodes || t->blocks_per_sm != c->tile.blocks_per_sm ||
         (t->kernel == FEDFEM_KERNEL_TILED_STAGED) != (c->tile.kernel == FEDFEM_KERNEL_TILED_STAGED))
         free_tiles(c);

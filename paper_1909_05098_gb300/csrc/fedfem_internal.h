@@ -38,19 +38,21 @@ struct Layout {
 // Tiles of the tiled time loop: tile t owns free nodes [t*B, min((t+1)*B, N_free))
 // and holds every element touching one of them (elements on a tile edge are
 // computed by each tile that touches them).  Local node ids: owned nodes
-// first (l = i - t*B), then the halo nodes in global order.
+// first (l = i - t*B), then the halo nodes in global order.  Each 16-bit
+// local connectivity entry is  local id | rank << rank_shift : for an owned
+// corner, rank is the element's position in that node's slot list (input
+// element order), i.e. where its load goes in the node's fixed-order sum.
 struct Tiles {
-    int B = 0, nv = 0, spt = 0;            // owned nodes per tile, corners, slices per tile (B/32)
+    int B = 0, nv = 0;                     // owned nodes per tile, corners
     int64_t n_tiles = 0;
     std::vector<int32_t> e_off;            // n_tiles + 1, into the tile-element arrays
     std::vector<int32_t> e_glob;           // internal element id of each tile element
-    std::vector<uint16_t> lconn;           // nv local node ids per tile element
+    std::vector<uint16_t> lconn;           // nv entries per tile element (id | rank << rank_shift)
     std::vector<int32_t> h_off;            // n_tiles + 1
     std::vector<int32_t> halo;             // global node ids
-    std::vector<int32_t> g_base;           // n_tiles: first gather entry of the tile
-    std::vector<int32_t> s_off;            // n_tiles * (spt + 1): slice offsets relative to g_base
-    std::vector<uint16_t> gat;             // corner * ne_pad + j (ne_pad = ne rounded up to 8); pads = nv * (max ne_pad)
-    int max_local = 0, max_elems = 0;
+    std::vector<int32_t> deg;              // n_tiles: most elements at one owned node
+    int rank_shift = 16;
+    int max_local = 0, max_elems = 0, max_deg = 0;
 };
 
 std::string build_tiles(const Layout& L, int B, Tiles& out);
@@ -122,20 +124,21 @@ struct LaunchCfg {
     int grid_used = 0;                     // out: grid of the last persistent launch
 };
 
-// Packed per-tile blocks of the tiled kernel, each 16-byte aligned and copied
-// whole into shared memory by one bulk (TMA) copy:
-//   int32 header {ne, ne_pad, nh, G}; M: 6 planes of ne_pad R;
-//   local connectivity: ne_pad x nv uint16; gather: G uint16 (G multiple of 32);
-//   halo ids: nh int32 (padded to 4); slice offsets: spt + 1 int32 (padded to 4).
+// Packed per-tile blocks of the tiled kernels, each 16-byte aligned (copied
+// whole into shared memory by one bulk (TMA) copy in the staged kernel):
+//   int32 header {ne, ne_pad, nh, deg}; M: 6 planes of ne_pad R;
+//   local connectivity: ne_pad x nv uint16 (id | rank << rank_shift);
+//   halo ids: nh int32.
 template <typename R>
 struct TileArgs {
     int64_t n_tiles;
-    int B, spt, nv;
+    int B, nv;
+    int rank_shift;                  // lconn entry = local id | rank << rank_shift
+    int max_deg;                     // rows of the per-node load table
     const unsigned char* blocks;
     const int64_t* block_off;        // n_tiles + 1 byte offsets
     int max_block;                   // bytes, multiple of 16
     int max_local;                   // R words of staged temperatures
-    int fs_words;                    // R words of element loads (nv * max ne_pad + 1)
     int staged;                      // 1: blocks bulk-copied into shared-memory stages; 0: read from global
     size_t smem_bytes;
 };

@@ -278,15 +278,16 @@ std::string build_tiles(const Layout& L, int B, Tiles& T) {
     T = Tiles();
     const int nv = L.nv;
     const int64_t NF = L.N_free;
-    if (B <= 0 || B % 32) return "tile size must be a positive multiple of 32";
-    T.B = B; T.nv = nv; T.spt = B / 32;
+    if (B <= 0 || B % 8) return "tile size must be a positive multiple of 8";
+    T.B = B; T.nv = nv;
     T.n_tiles = (NF + B - 1) / B;
     T.e_off.assign(T.n_tiles + 1, 0);
     T.h_off.assign(T.n_tiles + 1, 0);
-    T.g_base.assign(std::max<int64_t>(T.n_tiles, 1), 0);
-    T.s_off.assign(T.n_tiles * (T.spt + 1), 0);
-    std::vector<int32_t> elems, local_of(L.N, -1), halo;
+    T.deg.assign(T.n_tiles, 0);
+    std::vector<int32_t> elems, local_of(L.N, -1), rank_of;
     std::vector<int32_t> touched;
+    std::vector<int32_t> lid;                      // local ids, combined with the ranks at the end
+    std::vector<uint8_t> rank;
     for (int64_t t = 0; t < T.n_tiles; ++t) {
         const int64_t base = t * B, own = std::min<int64_t>(B, NF - base);
         // elements touching the owned nodes, from the nodes' slot lists
@@ -302,7 +303,6 @@ std::string build_tiles(const Layout& L, int B, Tiles& T) {
         std::sort(elems.begin(), elems.end());
         elems.erase(std::unique(elems.begin(), elems.end()), elems.end());
         const int64_t ne = (int64_t)elems.size();
-        if (ne * nv + 1 > 65535) return "tile has too many elements for 16-bit gather entries; use smaller tiles";
         // local numbering: owned first, then halo in global order
         touched.clear();
         for (int32_t e : elems)
@@ -316,59 +316,50 @@ std::string build_tiles(const Layout& L, int B, Tiles& T) {
         if (nl > 65535) return "tile has too many local nodes for 16-bit ids; use smaller tiles";
         for (int64_t l = 0; l < own; ++l) local_of[base + l] = (int32_t)l;
         for (size_t h = 0; h < touched.size(); ++h) local_of[touched[h]] = (int32_t)(own + h);
-        for (int32_t e : elems) {
-            T.e_glob.push_back(e);
-            for (int k = 0; k < nv; ++k) T.lconn.push_back((uint16_t)local_of[L.conn[(int64_t)e * nv + k]]);
+        // rank of each (element, owned corner) in the corner node's slot list,
+        // which is in input element order: the position its load takes in the sum
+        rank_of.assign(ne * nv, 0);
+        int dmax = 0;
+        for (int64_t i = base; i < base + own; ++i) {
+            const int64_t s = i / 32, lane = i % 32;
+            const int w = (L.sell_off[s + 1] - L.sell_off[s]) / 32;
+            int k = 0;
+            for (; k < w; ++k) {
+                const int32_t slot = L.sell_ids[L.sell_off[s] + 32 * k + lane];
+                if (slot >= L.E * nv) break;                 // pads come last
+                const int64_t j = std::lower_bound(elems.begin(), elems.end(), slot / nv) - elems.begin();
+                rank_of[j * nv + slot % nv] = k;
+            }
+            dmax = std::max(dmax, k);
+        }
+        if (dmax > 255) return "a node has more than 255 elements";
+        T.deg[t] = dmax;
+        for (int64_t j = 0; j < ne; ++j) {
+            T.e_glob.push_back(elems[j]);
+            for (int k = 0; k < nv; ++k) {
+                const int32_t l = local_of[L.conn[(int64_t)elems[j] * nv + k]];
+                lid.push_back(l);
+                rank.push_back((uint8_t)(l < own ? rank_of[j * nv + k] : 0));
+            }
         }
         T.halo.insert(T.halo.end(), touched.begin(), touched.end());
-        // gather lists of the owned nodes, in the global (input element) order
-        const int64_t gb = (int64_t)T.gat.size();
-        if (gb > INT32_MAX) return "gather lists too large";
-        T.g_base[t] = (int32_t)gb;
-        int32_t* so = &T.s_off[t * (T.spt + 1)];
-        const int64_t ne_pad = (ne + 7) / 8 * 8;
-        if (ne_pad * nv + 1 > 65535) return "tile has too many elements for 16-bit gather entries; use smaller tiles";
-        const uint16_t pad = (uint16_t)(nv * ne_pad);
-        int32_t cur = 0;
-        for (int s = 0; s < T.spt; ++s) {
-            so[s] = cur;
-            const int64_t i0 = base + 32 * s;
-            if (i0 >= base + own) continue;
-            const int64_t gs = i0 / 32;      // global slice (B is a multiple of 32)
-            const int w = (L.sell_off[gs + 1] - L.sell_off[gs]) / 32;
-            for (int k = 0; k < w; ++k)
-                for (int lane = 0; lane < 32; ++lane) {
-                    const int64_t i = i0 + lane;
-                    uint16_t v = pad;
-                    if (i < base + own) {
-                        const int32_t slot = L.sell_ids[L.sell_off[gs] + 32 * k + lane];
-                        if (slot < L.E * nv) {
-                            const int32_t e = slot / nv, corner = slot % nv;
-                            const int64_t j = std::lower_bound(elems.begin(), elems.end(), e) - elems.begin();
-                            v = (uint16_t)(corner * ne_pad + j);
-                        }
-                    }
-                    T.gat.push_back(v);
-                }
-            cur += 32 * w;
-        }
-        so[T.spt] = cur;
         for (int64_t l = 0; l < own; ++l) local_of[base + l] = -1;
         for (int32_t g : touched) local_of[g] = -1;
         T.e_off[t + 1] = T.e_off[t] + (int32_t)ne;
         T.h_off[t + 1] = T.h_off[t] + (int32_t)touched.size();
         T.max_local = std::max<int>(T.max_local, (int)nl);
         T.max_elems = std::max<int>(T.max_elems, (int)ne);
+        T.max_deg = std::max<int>(T.max_deg, dmax);
     }
-    // one zero cell for every tile: pads point at nv * (largest padded element count)
-    const int64_t max_pad = (int64_t)(T.max_elems + 7) / 8 * 8;
-    if (max_pad * nv + 1 > 65535) return "tile has too many elements for 16-bit gather entries; use smaller tiles";
-    for (int64_t t = 0; t < T.n_tiles; ++t) {
-        const int64_t ne = T.e_off[t + 1] - T.e_off[t], ne_pad = (ne + 7) / 8 * 8;
-        const int64_t g0 = T.g_base[t], g1 = t + 1 < T.n_tiles ? T.g_base[t + 1] : (int64_t)T.gat.size();
-        for (int64_t g = g0; g < g1; ++g)
-            if (T.gat[g] >= nv * ne_pad) T.gat[g] = (uint16_t)(nv * max_pad);
-    }
+    // 16-bit entries: local id in the low bits, rank above it
+    int rank_bits = 0;
+    while ((1 << rank_bits) < T.max_deg) ++rank_bits;
+    T.rank_shift = 16 - rank_bits;
+    if (T.max_local > (1 << T.rank_shift))
+        return "tile has too many local nodes for its 16-bit ids and ranks; use smaller tiles";
+    T.lconn.resize(lid.size());
+    for (size_t q = 0; q < lid.size(); ++q)
+        T.lconn[q] = (uint16_t)(lid[q] | (rank_bits ? (int)rank[q] << T.rank_shift : 0));
     return "";
 }
 

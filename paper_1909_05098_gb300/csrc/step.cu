@@ -204,16 +204,21 @@ __global__ void __launch_bounds__(256) k_persistent(StepArgs<R> a, long long n_s
     if (blockIdx.x == 0 && threadIdx.x == 0) a.status->steps_done = a.step0 + done;
 }
 
-// ---- tiled persistent kernel ------------------------------------------------
+// ---- tiled persistent kernels ------------------------------------------------
 // Tile t owns free nodes [t*B, t*B + own).  Its constant data (element
-// matrices, 16-bit local connectivity, 16-bit gather lists, halo ids, slice
-// offsets) is one packed block that a bulk (TMA) copy brings into a shared-
-// memory stage; two stages alternate, so the next tile's block (and, across
-// the grid barrier, the next step's first block) is in flight while the
-// current tile computes.  Per tile: stage owned + halo temperatures, compute
-// the loads of every element touching an owned node into shared memory, sum
-// each owned node's loads in its fixed order, update.  T is double-buffered
-// (tiles read their neighbours' nodes as halo), so one grid barrier per step.
+// matrices, 16-bit local connectivity with each owned corner's rank in its
+// node's sum, halo ids) is one packed block.  Per tile: the owned and halo
+// temperatures sit in shared memory; every element touching an owned node
+// computes its loads (Eq. 17) and writes each owned corner's load into row
+// `rank` of that node's column of a load table; each owned node then sums its
+// column in rank order (= input element order, the order of every other
+// kernel), zeroing it for the next tile, and applies Eq. 19.  T is double-
+// buffered (tiles read their neighbours' nodes as halo), so one grid barrier
+// per step.
+//
+// Staged variant: a bulk (TMA) copy brings each block into one of two shared-
+// memory stages, two tiles ahead; the next tile's temperatures are fetched
+// with asynchronous copies while the current tile's node phase runs.
 
 constexpr int kTiledThreads = 512;
 
@@ -226,11 +231,19 @@ __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_u32(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
-                 : "memory");
+// L2 policy for data read once per step and streamed: evicted before the
+// node arrays, which every step reads again
+__device__ __forceinline__ uint64_t policy_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar, uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::
+            "r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
+        : "memory");
 }
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
@@ -249,92 +262,170 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long l
     return true;
 }
 
+// asynchronous global -> shared copy of one temperature (4, 8 or 16 bytes)
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* dst, const void* src) {
+    if (BYTES == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_u32(dst)), "l"(src), "n"(BYTES)
+                     : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// the parts of a packed tile block
+template <typename R>
+struct TileView {
+    int ne, ne_pad, nh, deg;
+    const R* M;                 // 6 rows of ne_pad
+    const uint16_t* lc;         // nv entries per element
+    const int32_t* halo;        // nh global node ids
+};
+template <typename R, int NV>
+__device__ __forceinline__ TileView<R> tile_view(const unsigned char* blk) {
+    const int4 hdr = *reinterpret_cast<const int4*>(blk);
+    TileView<R> v;
+    v.ne = hdr.x; v.ne_pad = hdr.y; v.nh = hdr.z; v.deg = hdr.w;
+    v.M = reinterpret_cast<const R*>(blk + 16);
+    v.lc = reinterpret_cast<const uint16_t*>(blk + 16 + 6 * (size_t)v.ne_pad * sizeof(R));
+    v.halo = reinterpret_cast<const int32_t*>(v.lc + NV * v.ne_pad);
+    return v;
+}
+
 template <int NV>
 struct LConn;
+// (reload: a fresh load, so the entries need not stay in registers across the
+// element math; the block may sit in shared or global memory)
 template <>
 struct LConn<8> {
-    static __device__ __forceinline__ void load(const uint16_t* p, int j, int c[8]) {
-        const uint4 v = reinterpret_cast<const uint4*>(p)[j];
+    static __device__ __forceinline__ void split(uint4 v, int c[8]) {
         c[0] = v.x & 0xffff; c[1] = v.x >> 16; c[2] = v.y & 0xffff; c[3] = v.y >> 16;
         c[4] = v.z & 0xffff; c[5] = v.z >> 16; c[6] = v.w & 0xffff; c[7] = v.w >> 16;
+    }
+    static __device__ __forceinline__ void load(const uint16_t* p, int j, int c[8]) {
+        split(reinterpret_cast<const uint4*>(p)[j], c);
+    }
+    template <bool SHARED>
+    static __device__ __forceinline__ void reload(const uint16_t* p, int j, int c[8]) {
+        uint4 v;
+        if (SHARED)
+            asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                         : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                         : "r"(smem_u32(reinterpret_cast<const uint4*>(p) + j)));
+        else
+            asm volatile("ld.global.v4.u32 {%0, %1, %2, %3}, [%4];"
+                         : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                         : "l"(reinterpret_cast<const uint4*>(p) + j));
+        split(v, c);
     }
 };
 template <>
 struct LConn<4> {
-    static __device__ __forceinline__ void load(const uint16_t* p, int j, int c[4]) {
-        const uint2 v = reinterpret_cast<const uint2*>(p)[j];
+    static __device__ __forceinline__ void split(uint2 v, int c[4]) {
         c[0] = v.x & 0xffff; c[1] = v.x >> 16; c[2] = v.y & 0xffff; c[3] = v.y >> 16;
+    }
+    static __device__ __forceinline__ void load(const uint16_t* p, int j, int c[4]) {
+        split(reinterpret_cast<const uint2*>(p)[j], c);
+    }
+    template <bool SHARED>
+    static __device__ __forceinline__ void reload(const uint16_t* p, int j, int c[4]) {
+        uint2 v;
+        if (SHARED)
+            asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];"
+                         : "=r"(v.x), "=r"(v.y)
+                         : "r"(smem_u32(reinterpret_cast<const uint2*>(p) + j)));
+        else
+            asm volatile("ld.global.v2.u32 {%0, %1}, [%2];"
+                         : "=r"(v.x), "=r"(v.y)
+                         : "l"(reinterpret_cast<const uint2*>(p) + j));
+        split(v, c);
     }
 };
 
-template <typename R, typename L, int NV, bool KAHAN>
-__device__ __forceinline__ void tile_compute(const StepArgs<R, L>& a, const TileArgs<R>& ta, int64_t t,
-                                             const unsigned char* blk, const L* Tin, L* Tout, long long step, L* Ts,
-                                             L* Fs) {
-    const int4 hdr = *reinterpret_cast<const int4*>(blk);
-    const int ne = hdr.x, ne_pad = hdr.y, nh = hdr.z, G = hdr.w;
-    const R* M = reinterpret_cast<const R*>(blk + 16);
-    const uint16_t* lc = reinterpret_cast<const uint16_t*>(blk + 16 + 6 * (size_t)ne_pad * sizeof(R));
-    const uint16_t* gat = lc + NV * ne_pad;
-    const int32_t* halo = reinterpret_cast<const int32_t*>(gat + G);
-    const int32_t* so = halo + ((nh + 3) & ~3);
-    const int64_t base = t * ta.B;
-    const int own = (int)min((int64_t)ta.B, a.N_free - base);
-    // this thread's first owned node: its data and temperature are fetched now,
-    // so the loads overlap the staging and element phases
-    const int l0 = threadIdx.x;
-    const bool has0 = l0 < own;
-    NodeVals<R, L> v0{};
-    L T0 = lzero<L>();
-    if (has0) {
-        v0 = node_load<R, L, KAHAN>(a, base + l0);
-        T0 = Tin[base + l0];
-        Ts[l0] = T0;
+// owned and halo temperatures of a tile into Ts (asynchronous copies when ASYNC;
+// the caller commits, waits and synchronises)
+template <typename L, bool ASYNC>
+__device__ __forceinline__ void tile_fetch(const int32_t* halo, int nh, int64_t base, int own, const L* Tin, L* Ts) {
+    for (int l = threadIdx.x; l < own; l += blockDim.x) {
+        if (ASYNC) cp_async<sizeof(L)>(Ts + l, Tin + base + l);
+        else Ts[l] = Tin[base + l];
     }
-    for (int l = l0 + blockDim.x; l < own; l += blockDim.x) Ts[l] = Tin[base + l];
-    for (int h = threadIdx.x; h < nh; h += blockDim.x) Ts[own + h] = Tin[halo[h]];
-    __syncthreads();
-    const Law<R> k{a.T_ref, a.k0, a.dk};
-    for (int j = threadIdx.x; j < ne; j += blockDim.x) {
+    for (int h = threadIdx.x; h < nh; h += blockDim.x) {
+        if (ASYNC) cp_async<sizeof(L)>(Ts + own + h, Tin + halo[h]);
+        else Ts[own + h] = Tin[halo[h]];
+    }
+}
+
+// element phase of one tile: loads of every tile element; each owned corner's
+// load goes to Fn[rank * B + local id]
+template <typename R, typename L, int NV, bool SHARED>
+__device__ __forceinline__ void tile_elements(const TileView<R>& v, const Law<R>& k, int own, int B, int rank_shift,
+                                              const L* Ts, L* Fn) {
+    const int id_mask = (1 << rank_shift) - 1;
+    for (int j = threadIdx.x; j < v.ne; j += blockDim.x) {
         int c[NV];
-        LConn<NV>::load(lc, j, c);
+        LConn<NV>::load(v.lc, j, c);
         L tt[NV];
 #pragma unroll
-        for (int n = 0; n < NV; ++n) tt[n] = Ts[c[n]];
+        for (int n = 0; n < NV; ++n) tt[n] = Ts[c[n] & id_mask];
         R m[6];
 #pragma unroll
-        for (int q = 0; q < 6; ++q) m[q] = M[q * ne_pad + j];
+        for (int q = 0; q < 6; ++q) m[q] = v.M[q * v.ne_pad + j];
         const L ke = element_k<R, NV, L>(tt, k);
         L F[NV];
         if (NV == 8) hex8_loads<R, L>(tt, m, ke, F);
         else tet4_loads<R, L>(tt, m, ke, F);
+        LConn<NV>::template reload<SHARED>(v.lc, j, c);
 #pragma unroll
-        for (int n = 0; n < NV; ++n) Fs[n * ne_pad + j] = F[n];
+        for (int n = 0; n < NV; ++n) {
+            const int id = c[n] & id_mask;
+            if (id < own) Fn[(c[n] >> rank_shift) * B + id] = F[n];
+        }
     }
-    __syncthreads();
-    // Ts is not read below this point (own temperatures come from registers or
-    // are re-read from Tin), so the next tile may overwrite it without a barrier
-    for (int l = l0; l < own; l += blockDim.x) {
-        const int sl = l >> 5, lane = l & 31;
-        const int32_t off = so[sl];
-        const int w = (so[sl + 1] - off) >> 5;
-        const uint16_t* g = gat + off + lane;
+}
+
+// node phase: sum each owned node's column (rank order), clear it, Eq. 19.
+// The first owned node of each thread (l0 = threadIdx.x) comes with its
+// temperature T0 and constant data v0 already loaded; further nodes (tiles
+// larger than the block) read theirs from Tin.
+template <typename R, typename L, bool KAHAN>
+__device__ __forceinline__ void tile_nodes(const StepArgs<R, L>& a, int64_t base, int own, int deg, int B, L* Fn,
+                                           L T0, const NodeVals<R, L>& v0, const L* Tin, L* Tout, long long step) {
+    for (int l = threadIdx.x; l < own; l += blockDim.x) {
         L F = lzero<L>();
-        for (int q = 0; q < w; ++q) F = F + Fs[g[32 * q]];
-        if (l == l0) node_update_v<R, L, KAHAN>(a, base + l, T0, F, v0, Tout, step);
+        for (int r = 0; r < deg; ++r) {
+            F = F + Fn[r * B + l];
+            Fn[r * B + l] = lzero<L>();
+        }
+        if (l == (int)threadIdx.x) node_update_v<R, L, KAHAN>(a, base + l, T0, F, v0, Tout, step);
         else node_update<R, L, KAHAN>(a, base + l, Tin[base + l], F, Tout, step);
     }
 }
 
+template <typename R, typename L, bool KAHAN>
+__device__ __forceinline__ void first_node(const StepArgs<R, L>& a, int64_t base, int own, const L* Ts, L& T0,
+                                           NodeVals<R, L>& v0) {
+    if ((int)threadIdx.x < own) {
+        v0 = node_load<R, L, KAHAN>(a, base + threadIdx.x);
+        T0 = Ts[threadIdx.x];
+    }
+}
+
+template <typename L>
+__device__ __forceinline__ void zero_table(L* Fn, int n) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) Fn[i] = lzero<L>();
+}
+
 // Direct variant: the same per-tile blocks read straight from global memory
-// (coalesced within a tile), shared memory only for T and the element loads,
-// so more blocks fit on an SM.
+// (coalesced within a tile), shared memory only for T and the load table, so
+// more blocks fit on an SM.
 // resident blocks per SM the direct tiled kernel is compiled for: one FP32
-// lane fits 6 blocks of 256 threads, FP64 or four-lane state needs about twice
-// the registers
+// lane fits 5 blocks of 256 threads without spills, FP64 or four-lane state
+// needs about twice the registers
 template <typename L>
 struct DirectOccupancy {
-    static constexpr int min_blocks = sizeof(L) >= 8 ? 3 : 6;
+    static constexpr int min_blocks = sizeof(L) >= 8 ? 3 : 5;
 };
 
 template <typename R, typename L, int NV, bool KAHAN>
@@ -342,16 +433,29 @@ __global__ void __launch_bounds__(256, DirectOccupancy<L>::min_blocks) k_tiled_d
                                                       long long spin_limit) {
     extern __shared__ __align__(128) unsigned char smem[];
     L* Ts = reinterpret_cast<L*>(smem);
-    L* Fs = Ts + ta.max_local;
-    if (threadIdx.x == 0) Fs[ta.fs_words - 1] = lzero<L>();   // the zero cell every gather pad points at
+    L* Fn = reinterpret_cast<L*>(smem + ((size_t)ta.max_local * sizeof(L) + 15) / 16 * 16);
+    zero_table(Fn, ta.max_deg * ta.B);
     unsigned long long target = 0;
     long long done = 0;
-    if (!grid_barrier(a.status, target, spin_limit)) return;
+    if (!grid_barrier(a.status, target, spin_limit)) return;   // also orders the zeroing before first use
+    const Law<R> k{a.T_ref, a.k0, a.dk};
     for (long long s = 0; s < n_steps; ++s) {
         const L* Tin = (s & 1) ? a.T2 : a.T;
         L* Tout = (s & 1) ? a.T : a.T2;
-        for (int64_t t = blockIdx.x; t < ta.n_tiles; t += gridDim.x)
-            tile_compute<R, L, NV, KAHAN>(a, ta, t, ta.blocks + ta.block_off[t], Tin, Tout, a.step0 + s, Ts, Fs);
+        for (int64_t t = blockIdx.x; t < ta.n_tiles; t += gridDim.x) {
+            const TileView<R> v = tile_view<R, NV>(ta.blocks + ta.block_off[t]);
+            const int64_t base = t * ta.B;
+            const int own = (int)min((int64_t)ta.B, a.N_free - base);
+            tile_fetch<L, false>(v.halo, v.nh, base, own, Tin, Ts);
+            __syncthreads();
+            L T0 = lzero<L>();
+            NodeVals<R, L> v0{};
+            first_node<R, L, KAHAN>(a, base, own, Ts, T0, v0);
+            tile_elements<R, L, NV, false>(v, k, own, ta.B, ta.rank_shift, Ts, Fn);
+            __syncthreads();   // loads complete; Ts is free for the next tile
+            tile_nodes<R, L, KAHAN>(a, base, own, v.deg, ta.B, Fn, T0, v0, Tin, Tout, a.step0 + s);
+            __syncthreads();   // table cleared before the next tile writes it
+        }
         const bool ok = grid_barrier(a.status, target, spin_limit);
         done = s + 1;
         if (!ok) break;
@@ -363,77 +467,127 @@ __global__ void __launch_bounds__(256, DirectOccupancy<L>::min_blocks) k_tiled_d
     if (blockIdx.x == 0 && threadIdx.x == 0) a.status->steps_done = a.step0 + done;
 }
 
+// resident blocks per SM the staged kernel is compiled for: two for one FP32
+// lane (64 registers), one for FP64 or four-lane state
+template <typename L>
+struct StagedOccupancy {
+    static constexpr int min_blocks = sizeof(L) == 4 ? 2 : 1;
+};
+
 template <typename R, typename L, int NV, bool KAHAN>
-__global__ void __launch_bounds__(kTiledThreads) k_tiled(StepArgs<R, L> a, TileArgs<R> ta, long long n_steps,
-                                                         long long spin_limit) {
+__global__ void __launch_bounds__(kTiledThreads, StagedOccupancy<L>::min_blocks)
+    k_tiled(StepArgs<R, L> a, TileArgs<R> ta, long long n_steps, long long spin_limit) {
+    // shared memory: 2 mbarriers | 2 block stages | temperatures | load table
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
+    const size_t stage_bytes = (size_t)ta.max_block;
     unsigned char* const stage0 = smem + 128;
-    unsigned char* const stage1 = smem + 128 + ta.max_block;
-    L* Ts = reinterpret_cast<L*>(smem + 128 + 2 * (size_t)ta.max_block);
-    L* Fs = Ts + ta.max_local;
+    unsigned char* const stage1 = smem + 128 + stage_bytes;
+    L* const Ts = reinterpret_cast<L*>(smem + 128 + 2 * stage_bytes);
+    L* const Fn = reinterpret_cast<L*>(smem + 128 + 2 * stage_bytes + ((size_t)ta.max_local * sizeof(L) + 15) / 16 * 16);
     if (threadIdx.x == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
         fence_mbar_init();
-        Fs[ta.fs_words - 1] = lzero<L>();   // the zero cell every gather pad points at
     }
+    zero_table(Fn, ta.max_deg * ta.B);
     __syncthreads();
     unsigned long long target = 0;
     long long done = 0;
     if (!grid_barrier(a.status, target, spin_limit)) return;
     const int64_t first = blockIdx.x;
     const int64_t n_my = first < ta.n_tiles ? (ta.n_tiles - 1 - first) / gridDim.x + 1 : 0;
-    const bool single = n_my == 1;   // one tile per block: its block stays resident across steps
-    uint32_t ph0 = 0u, ph1 = 0u;
-    bool pending = false;
-    int pbuf = 0;
-    auto issue = [&](int64_t t, int buf) {
-        const int64_t o = ta.block_off[t];
-        const uint32_t bytes = (uint32_t)(ta.block_off[t + 1] - o);
-        mbar_expect_tx(&bar[buf], bytes);
-        bulk_g2s(buf ? stage1 : stage0, ta.blocks + o, bytes, &bar[buf]);
+    // Tiles in launch order: kk = s * n_my + i is tile first + i * gridDim.x of step s.  With at
+    // most two tiles per block both stay in their stages for the whole launch; otherwise tile kk
+    // uses stage kk & 1 and its copy is issued two tiles ahead.
+    const bool resident = n_my <= 2;
+    const long long total = (long long)n_steps * n_my;
+    const uint64_t policy = policy_evict_first();
+    uint32_t ph0 = 0u, ph1 = 0u;      // per stage: parity of the next completion
+    bool pend0 = false, pend1 = false;   // per stage: copy issued and not yet waited for
+    auto tile_of = [&](long long kk) { return first + (kk % n_my) * (int64_t)gridDim.x; };
+    auto buf_of = [&](long long kk) { return resident ? (int)(kk % n_my) : (int)(kk & 1); };
+    // tile kk's block into its stage (thread 0 copies; every thread records it)
+    auto issue = [&](long long kk) {
+        const int buf = buf_of(kk);
+        if (threadIdx.x == 0) {
+            const int64_t t = tile_of(kk);
+            const int64_t o0 = ta.block_off[t], o1 = ta.block_off[t + 1];
+            fence_proxy_async();
+            mbar_expect_tx(&bar[buf], (uint32_t)(o1 - o0));
+            bulk_g2s(buf ? stage1 : stage0, ta.blocks + o0, (uint32_t)(o1 - o0), &bar[buf], policy);
+        }
+        if (buf) pend1 = true; else pend0 = true;
     };
-    if (n_my > 0) {
-        if (threadIdx.x == 0) issue(first, 0);
-        pending = true;
-        pbuf = 0;
-    }
-    long long kk = 0;
+    // wait for stage buf's outstanding copy: one thread polls, the block
+    // synchronises on it; false (in every thread alike) when the wait gave up
+    auto land = [&](int buf) -> bool {
+        bool ok = true;
+        if (buf ? pend1 : pend0) {
+            if (threadIdx.x == 0) ok = mbar_wait(&bar[buf], buf ? ph1 : ph0, spin_limit);
+            if (buf) { ph1 ^= 1u; pend1 = false; }
+            else { ph0 ^= 1u; pend0 = false; }
+        }
+        return !__syncthreads_or(!ok);
+    };
+    auto fail_timeout = [&]() {
+        if (threadIdx.x == 0) atomicOr(&a.status->flags, STATUS_TIMEOUT);
+    };
+    auto view_of = [&](long long kk) { return tile_view<R, NV>(buf_of(kk) ? stage1 : stage0); };
+    // temperatures of tile kk (its stage has landed) into Ts, asynchronously
+    auto fetch = [&](long long kk, const L* Tin) {
+        const TileView<R> v = view_of(kk);
+        const int64_t base = tile_of(kk) * ta.B;
+        tile_fetch<L, true>(v.halo, v.nh, base, (int)min((int64_t)ta.B, a.N_free - base), Tin, Ts);
+        cp_async_commit();
+    };
     bool stop = false;
+    if (total > 0) {
+        for (long long kk = 0; kk < 2 && kk < n_my; ++kk) issue(kk);
+        if (!land(0)) { fail_timeout(); stop = true; }
+        else fetch(0, a.T);
+    }
+    const Law<R> k{a.T_ref, a.k0, a.dk};
+    long long kk = 0;
     for (long long s = 0; s < n_steps && !stop; ++s) {
         const L* Tin = (s & 1) ? a.T2 : a.T;
         L* Tout = (s & 1) ? a.T : a.T2;
         for (int64_t i = 0; i < n_my; ++i, ++kk) {
-            const int64_t t = first + i * gridDim.x;
-            const int buf = single ? 0 : (int)(kk & 1);
-            if (pending && pbuf == buf) {
-                const uint32_t ph = buf ? ph1 : ph0;
-                if (!mbar_wait(&bar[buf], ph, spin_limit)) {
-                    if (threadIdx.x == 0) atomicOr(&a.status->flags, STATUS_TIMEOUT);
-                    mbar_wait(&bar[buf], ph, spin_limit);   // the copy is from global memory: let it land
-                    return;
-                }
-                if (buf) ph1 ^= 1u; else ph0 ^= 1u;
-                pending = false;
+            const int buf = buf_of(kk);
+            cp_async_wait_all();
+            __syncthreads();   // Ts of this tile complete; the table is clear
+            const TileView<R> v = view_of(kk);
+            const int64_t base = tile_of(kk) * ta.B;
+            const int own = (int)min((int64_t)ta.B, a.N_free - base);
+            const int deg = v.deg;
+            L T0 = lzero<L>();
+            NodeVals<R, L> v0{};
+            first_node<R, L, KAHAN>(a, base, own, Ts, T0, v0);
+            tile_elements<R, L, NV, true>(v, k, own, ta.B, ta.rank_shift, Ts, Fn);
+            __syncthreads();   // loads complete; this stage and Ts are free
+            if (i + 1 < n_my) {   // the next tile of this step: its stage, then its temperatures
+                if (!land(buf_of(kk + 1))) { fail_timeout(); stop = true; break; }
+                fetch(kk + 1, Tin);
             }
-            __syncthreads();   // every thread is done with the other stage
-            if (!single && (i + 1 < n_my || s + 1 < n_steps)) {
-                const int64_t tn = (i + 1 < n_my) ? t + gridDim.x : first;
-                if (threadIdx.x == 0) {
-                    fence_proxy_async();
-                    issue(tn, buf ^ 1);
-                }
-                pending = true;
-                pbuf = buf ^ 1;
-            }
-            tile_compute<R, L, NV, KAHAN>(a, ta, t, buf ? stage1 : stage0, Tin, Tout, a.step0 + s, Ts, Fs);
+            if (!resident && kk + 2 < total) issue(kk + 2);
+            tile_nodes<R, L, KAHAN>(a, base, own, deg, ta.B, Fn, T0, v0, Tin, Tout, a.step0 + s);
         }
+        if (stop) break;
+        cp_async_wait_all();
         const bool ok = grid_barrier(a.status, target, spin_limit);
         done = s + 1;
-        if (!ok) stop = true;
+        if (!ok) break;
+        if (s + 1 < n_steps && n_my > 0) {   // the first tile of the next step reads this step's result
+            if (!land(buf_of(kk))) { fail_timeout(); break; }
+            fetch(kk, Tout);
+        }
     }
-    if (pending) mbar_wait(&bar[pbuf], pbuf ? ph1 : ph0, spin_limit);   // a prefetch nobody consumed
+    cp_async_wait_all();
+    // copies nobody consumed (early stop): let them land before the block exits
+    if (threadIdx.x == 0) {
+        if (pend0) mbar_wait(&bar[0], ph0, spin_limit);
+        if (pend1) mbar_wait(&bar[1], ph1, spin_limit);
+    }
     if (done & 1) {   // the newest values are in T2: copy them back so that T is current
         const int64_t stride = (int64_t)gridDim.x * blockDim.x;
         for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.N_free; i += stride) a.T[i] = a.T2[i];

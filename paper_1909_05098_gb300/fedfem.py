@@ -51,8 +51,8 @@ class fedfem_layout_info(C.Structure):
     _fields_ = [("n_nodes", C.c_int64), ("n_elems", C.c_int64), ("n_plain", C.c_int64), ("n_free", C.c_int64),
                 ("n_slices", C.c_int64), ("n_gather", C.c_int64), ("max_degree", C.c_int),
                 ("tile_nodes", C.c_int), ("n_tiles", C.c_int64), ("n_tile_elems", C.c_int64),
-                ("n_halo", C.c_int64), ("n_tile_gather", C.c_int64), ("n_tile_slice_off", C.c_int64),
-                ("max_tile_local", C.c_int), ("max_tile_elems", C.c_int)]
+                ("n_halo", C.c_int64), ("max_tile_local", C.c_int), ("max_tile_elems", C.c_int),
+                ("max_tile_degree", C.c_int), ("tile_rank_shift", C.c_int)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -106,7 +106,7 @@ _SIGS = {
     "fedfem_version": ([], C.c_char_p),
     "fedfem_debug_set": ([_ctx_p, C.c_int, _i64], C.c_int),
     "fedfem_plan_layout": ([C.c_int, _i64, _dp, _i64, _ip, _ip, C.c_int, _i64, _ip, _i64, C.c_int, _ip, C.c_int,
-                            C.POINTER(fedfem_layout_info)] + [C.c_void_p] * 12, C.c_int),
+                            C.POINTER(fedfem_layout_info)] + [C.c_void_p] * 10, C.c_int),
     "fedfem_set_lanes": ([_ctx_p, C.c_int], C.c_int),
     "fedfem_add_gaussian_source_lane": ([_ctx_p, C.c_int, C.c_int, _dp, C.c_double, C.c_double], C.c_int),
     "fedfem_set_source_lane": ([_ctx_p, C.c_int, _dp], C.c_int),
@@ -332,7 +332,7 @@ def fedfem_plan_layout(elem_type, xyz, conn, order=ORDER_MORTON, dirichlet_nodes
     info = fedfem_layout_info()
     args = [elem_type, x.shape[0], px, c.shape[0], pc, pg, order, dn.shape[0], pdn, nf, nvf, pfc, tile_nodes,
             C.byref(info)]
-    rc = _lib.fedfem_plan_layout(*args, *([None] * 12))
+    rc = _lib.fedfem_plan_layout(*args, *([None] * 10))
     if rc != OK:
         raise FedfemError(rc, "fedfem_plan_layout")
     d = info.as_dict()
@@ -342,9 +342,7 @@ def fedfem_plan_layout(elem_type, xyz, conn, order=ORDER_MORTON, dirichlet_nodes
         "tile_elem_off": np.empty(d["n_tiles"] + 1, np.int32), "tile_elems": np.empty(d["n_tile_elems"], np.int32),
         "tile_lconn": np.empty(d["n_tile_elems"] * elem_type, np.uint16),
         "tile_halo_off": np.empty(d["n_tiles"] + 1, np.int32), "tile_halo": np.empty(d["n_halo"], np.int32),
-        "tile_gather_base": np.empty(d["n_tiles"], np.int32),
-        "tile_slice_off": np.empty(d["n_tile_slice_off"], np.int32),
-        "tile_gather": np.empty(d["n_tile_gather"], np.uint16),
+        "tile_degree": np.empty(d["n_tiles"], np.int32),
     }
     ptrs = [a.ctypes.data_as(C.c_void_p) for a in arrs.values()]
     rc = _lib.fedfem_plan_layout(*args, *ptrs)

@@ -94,7 +94,6 @@ def test_tiles_cover_and_emulated_gather_matches_oracle(ff, kind, B):
     T_int = T_in[node_of]
     # internal connectivity
     conn_int = np.argsort(node_of)[p.conn[elem_of]]
-    spt = B // 32
     out = np.full(NF, np.nan)
     for t in range(d["n_tiles"]):
         base, own = t * B, min(B, NF - t * B)
@@ -105,33 +104,40 @@ def test_tiles_cover_and_emulated_gather_matches_oracle(ff, kind, B):
         ne = len(elems)
         local_nodes = np.concatenate([np.arange(base, base + own), halo])
         lconn = d["tile_lconn"][e0 * nv: e1 * nv].reshape(-1, nv).astype(np.int64)
-        assert np.array_equal(local_nodes[lconn], conn_int[elems])        # local ids resolve correctly
+        shift = d["tile_rank_shift"]
+        lconn_id, lconn_rank = lconn & ((1 << shift) - 1), lconn >> shift
+        assert np.array_equal(local_nodes[lconn_id], conn_int[elems])     # local ids resolve correctly
         # every element touching an owned node is in the tile
         touching = np.nonzero(np.any((conn_int >= base) & (conn_int < base + own), axis=1))[0]
         assert np.array_equal(np.sort(elems), touching)
         Ts = T_int[local_nodes]
-        assert np.allclose(Ts[lconn], T_int[conn_int[elems]])
-        ne_pad = (ne + 7) // 8 * 8
-        Fpad = np.zeros((nv, ne_pad))
-        Fpad[:, :ne] = Fe[elem_of[elems]].T
-        max_pad = (d["max_tile_elems"] + 7) // 8 * 8
-        Fs = np.zeros(nv * max_pad + 1)                                   # corner-major, stride ne_pad
-        Fs[: nv * ne_pad] = Fpad.ravel()                                  # ... and the shared zero cell at the end
-        so = d["tile_slice_off"][t * (spt + 1): (t + 1) * (spt + 1)]
-        gb = d["tile_gather_base"][t]
+        assert np.allclose(Ts[lconn_id], T_int[conn_int[elems]])
+        # the kernel's load table: each owned corner's load goes to row `rank`
+        # of its node's column; a node sums its column in row order
+        D = d["tile_degree"][t]
+        table = np.zeros((max(D, 1), own))
+        filled = np.zeros((max(D, 1), own), bool)
+        Fe_t = Fe[elem_of[elems]]
+        for j in range(ne):
+            for n in range(nv):
+                l, r = lconn_id[j, n], lconn_rank[j, n]
+                if l < own:
+                    assert r < D and not filled[r, l]                   # one load per cell
+                    table[r, l] = Fe_t[j, n]
+                    filled[r, l] = True
+                else:
+                    assert r == 0
         for l in range(own):
-            s, lane = l // 32, l % 32
-            w = (so[s + 1] - so[s]) // 32
-            g = d["tile_gather"][gb + so[s] + 32 * np.arange(w) + lane].astype(np.int64)
-            # same (element, corner) sequence as the global gather
             ents = _decode_gather(d, nv, base + l)
-            real = g[g < nv * ne_pad]
-            assert np.all((g < nv * ne_pad) | (g == nv * max_pad))           # pads hit the one zero cell
-            assert np.all(real % ne_pad < ne)
-            assert np.array_equal(elems[real % ne_pad] * nv + real // ne_pad, ents)
+            deg = len(ents)
+            assert filled[:deg, l].all() and not filled[deg:, l].any()  # rows 0..deg-1, then zeros
+            # row r holds the load of the node's r-th slot, in input element order
+            by_rank = sorted((lconn_rank[j, n], elems[j] * nv + n) for j in range(ne) for n in range(nv)
+                             if lconn_id[j, n] == l)
+            assert [e for _, e in by_rank] == list(ents)
             acc = 0.0
-            for v in g:
-                acc = acc + Fs[v]
+            for r in range(D):
+                acc = acc + table[r, l]
             out[base + l] = acc
     np.testing.assert_allclose(out, ref[node_of[:NF]], rtol=1e-11, atol=1e-11 * np.abs(ref).max())
 
