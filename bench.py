@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--n", type=int, default=WORKLOAD_N, help="cube edge in elements")
     ap.add_argument("--kernel", default="auto", choices=["auto", "two_phase", "persistent", "tiled", "tiled_staged"])
     ap.add_argument("--tile-nodes", type=int, default=0)
+    ap.add_argument("--block", type=int, default=0, help="threads per block (0 = the kernel's default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="cube", choices=["cube", "planning", "surrogate"],
                     help="cube: the 128^3 throughput cube (default); planning: 64 uneven tet meshes x 4 "
@@ -301,7 +302,7 @@ def run_ours(args):
         kernel = tuned["kernel"]
     else:
         kernel = {v: k for k, v in names.items()}[args.kernel]
-        ff.fedfem_set_tile(solver.ctx, kernel, 0, args.tile_nodes, 0)
+        ff.fedfem_set_tile(solver.ctx, kernel, args.block, args.tile_nodes, 0)
     solver.step(dt, 1)      # plans tiles if needed
     solver.sync()
     solver.init()
@@ -383,8 +384,10 @@ def run_ours(args):
                    "time_steps_per_bench_step": S, "kernel": names[kernel],
                    "tile_nodes": info["tile_nodes"], "grid_blocks": info["grid_blocks"],
                    "autotune": None if tuned is None else
-                   {names[t["kernel"]] + (f"/{t['tile_nodes']}" if t["tile_nodes"] else ""):
+                   {names[t["kernel"]] + (f"/{t['tile_nodes']}" if t["tile_nodes"] else "") +
+                    (f"x{t['block']}" if t.get("block") else ""):
                     round(t.get("us_per_step", -1), 1) for t in tuned["trials"]},
+                   "block_threads": info["block_threads"],
                    "precision": "FP32+Kahan",
                    "dt_s": dt, "dt_cr_s": solver.dt_cr,
                    "l2": f"inputs larger than L2: {info['bytes_per_step'] / 1e6:.0f} MB moved per time step",

@@ -95,7 +95,8 @@ typedef struct { double w_b, c_b, T_a, Q_m; } fedfem_perfusion;
 /* Launch knobs (chosen by the autotuner).  Results do not depend on them. */
 typedef struct {
     int kernel;        /* FEDFEM_KERNEL_* */
-    int block;         /* threads per block: 64..1024, multiple of 32 (0 = default) */
+    int block;         /* threads per block: 64..1024, multiple of 32 (0 = default); the
+                          staged tiled kernel is built for 256, 512 (default) and 1024 */
     int tile_nodes;    /* TILED: target owned nodes per tile, multiple of 8 (0 = default); the
                           library moves it to the nearest size that gives every resident
                           block the same number of tiles */

@@ -19,15 +19,17 @@ CACHE = os.environ.get("FEDFEM_TUNE_CACHE", os.path.join(os.path.expanduser("~")
 
 
 def candidates(elem_type: int, precision: int):
-    """(kernel, tile_nodes, blocks_per_sm) triples; tile_nodes 0 = the library's default."""
-    out = [(ff.KERNEL_PERSISTENT, 0, 0)]
+    """(kernel, block, tile_nodes, blocks_per_sm); 0 = the library's default."""
+    out = [(ff.KERNEL_PERSISTENT, 0, 0, 0)]
     sizes = (0, 128, 256, 384) if elem_type == ff.HEX8 else (0, 64, 96, 128, 192)
     staged = (0, 384, 448, 576, 640) if elem_type == ff.HEX8 else (0, 128, 192, 320)
+    staged1024 = (1024, 1280) if elem_type == ff.HEX8 else (512,)
     if precision == ff.FP64:
         sizes = tuple(s // 2 for s in sizes if s)[:2] + (0,)
-        staged = (0,)
-    out += [(ff.KERNEL_TILED, b, 0) for b in sizes]
-    out += [(ff.KERNEL_TILED_STAGED, b, 0) for b in staged]
+        staged, staged1024 = (0,), ()
+    out += [(ff.KERNEL_TILED, 0, b, 0) for b in sizes]
+    out += [(ff.KERNEL_TILED_STAGED, 0, b, 0) for b in staged]
+    out += [(ff.KERNEL_TILED_STAGED, 1024, b, 0) for b in staged1024]
     return out
 
 
@@ -53,7 +55,7 @@ def _save_cache(d):
 
 def tune(solver, dt: float, steps: int = 30, use_cache: bool = True, stream=None, verbose: bool = False) -> dict:
     """Pick the fastest launch configuration for ``solver`` (a fedfem.Solver)
-    and apply it.  Returns {"kernel", "tile_nodes", "blocks_per_sm", "us_per_step", "trials"}."""
+    and apply it.  Returns {"kernel", "block", "tile_nodes", "blocks_per_sm", "us_per_step", "trials"}."""
     import torch
     ctx = solver.ctx
     info = ff.fedfem_get_info(ctx)
@@ -61,16 +63,16 @@ def tune(solver, dt: float, steps: int = 30, use_cache: bool = True, stream=None
     cache = _load_cache() if use_cache else {}
     if sig in cache:
         best = cache[sig]
-        ff.fedfem_set_tile(ctx, best["kernel"], 0, best["tile_nodes"], best["blocks_per_sm"])
+        ff.fedfem_set_tile(ctx, best["kernel"], best.get("block", 0), best["tile_nodes"], best["blocks_per_sm"])
         best = dict(best, cached=True)
         return best
     saved = ff.fedfem_get_state(ctx)
     s = stream if stream is not None else torch.cuda.current_stream()
     trials = []
-    for kern, B, bps in candidates(info["elem_type"], info["precision"]):
+    for kern, blk, B, bps in candidates(info["elem_type"], info["precision"]):
         try:
             t0 = time.perf_counter()
-            ff.fedfem_set_tile(ctx, kern, 0, B, bps)
+            ff.fedfem_set_tile(ctx, kern, blk, B, bps)
             ff.fedfem_step(ctx, dt, 3)            # builds tiles on first use, warms up
             ff.fedfem_sync(ctx)
             setup = time.perf_counter() - t0
@@ -81,18 +83,18 @@ def tune(solver, dt: float, steps: int = 30, use_cache: bool = True, stream=None
             ff.fedfem_sync(ctx)
             torch.cuda.synchronize()
             us = e0.elapsed_time(e1) * 1e3 / steps
-            trials.append({"kernel": kern, "tile_nodes": B, "blocks_per_sm": bps, "us_per_step": us,
+            trials.append({"kernel": kern, "block": blk, "tile_nodes": B, "blocks_per_sm": bps, "us_per_step": us,
                            "setup_s": setup})
             if verbose:
-                print(f"tune: kernel {kern} tile {B} bps {bps}: {us:.1f} us/step (setup {setup:.2f} s)")
+                print(f"tune: kernel {kern} block {blk} tile {B} bps {bps}: {us:.1f} us/step (setup {setup:.2f} s)")
         except ff.FedfemError as ex:
-            trials.append({"kernel": kern, "tile_nodes": B, "blocks_per_sm": bps, "error": str(ex)})
+            trials.append({"kernel": kern, "block": blk, "tile_nodes": B, "blocks_per_sm": bps, "error": str(ex)})
         finally:
             ff.fedfem_set_state(ctx, saved)
     ok = [t for t in trials if "us_per_step" in t]
     best = min(ok, key=lambda t: t["us_per_step"])
-    ff.fedfem_set_tile(ctx, best["kernel"], 0, best["tile_nodes"], best["blocks_per_sm"])
-    result = {k: best[k] for k in ("kernel", "tile_nodes", "blocks_per_sm", "us_per_step")}
+    ff.fedfem_set_tile(ctx, best["kernel"], best["block"], best["tile_nodes"], best["blocks_per_sm"])
+    result = {k: best[k] for k in ("kernel", "block", "tile_nodes", "blocks_per_sm", "us_per_step")}
     if use_cache:
         cache[sig] = result
         _save_cache(cache)

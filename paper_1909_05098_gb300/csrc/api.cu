@@ -239,6 +239,11 @@ size_t tile_smem(const Tiles& t, size_t rs, size_t ls, int* max_block, bool stag
 // nodes; halved in FP64) per tile, then adjusted so the tile count is a whole
 // number of waves of the resident grid (every block gets the same number of
 // tiles).  Each tile's constant data is packed into one 16-byte-aligned block.
+// threads per block of the staged kernel: the block knob if it names a built size
+int staged_threads(const fedfem_ctx* c) {
+    return c->tile.block == 256 || c->tile.block == 1024 ? c->tile.block : tiled_threads();
+}
+
 int plan_tiles(fedfem_ctx* c) {
     if (c->tiles_ok) return FEDFEM_OK;
     const bool staged = c->tile.kernel == FEDFEM_KERNEL_TILED_STAGED;
@@ -263,7 +268,7 @@ int plan_tiles(fedfem_ctx* c) {
         m = build_tiles(c->L, B0, t);
         if (!m.empty()) return fail(c, FEDFEM_E_ARG, m);
         size_t smem = tile_smem(t, rs, ls, &mb, staged);
-        int per_sm = tiled_blocks_per_sm(c->precision, c->nv, staged, c->n_lanes, smem);
+        int per_sm = tiled_blocks_per_sm(c->precision, c->nv, staged, staged_threads(c), c->n_lanes, smem);
         if (c->tile.blocks_per_sm > 0) per_sm = std::min(per_sm, c->tile.blocks_per_sm);
         if (per_sm < 1) return fail(c, FEDFEM_E_UNSUPPORTED, "tile does not fit in shared memory; use smaller tile_nodes");
         B = B0;
@@ -275,7 +280,7 @@ int plan_tiles(fedfem_ctx* c) {
             Tiles tw;
             if (!build_tiles(c->L, (int)Bw, tw).empty()) continue;
             int mbw = 0;
-            int pw = tiled_blocks_per_sm(c->precision, c->nv, staged, c->n_lanes, tile_smem(tw, rs, ls, &mbw, staged));
+            int pw = tiled_blocks_per_sm(c->precision, c->nv, staged, staged_threads(c), c->n_lanes, tile_smem(tw, rs, ls, &mbw, staged));
             if (c->tile.blocks_per_sm > 0) pw = std::min(pw, c->tile.blocks_per_sm);
             if (pw != per_sm) continue;
             B = (int)Bw;
@@ -288,7 +293,7 @@ int plan_tiles(fedfem_ctx* c) {
         if (!m.empty()) return fail(c, FEDFEM_E_ARG, m);
     }
     const size_t smem = tile_smem(t, rs, ls, &mb, staged);
-    if (tiled_blocks_per_sm(c->precision, c->nv, staged, c->n_lanes, smem) < 1)
+    if (tiled_blocks_per_sm(c->precision, c->nv, staged, staged_threads(c), c->n_lanes, smem) < 1)
         return fail(c, FEDFEM_E_UNSUPPORTED, "tile does not fit in shared memory; use smaller tile_nodes");
     free_tiles(c);
     cudaStream_t st = c->stream;
@@ -342,6 +347,7 @@ TileArgs<R> make_tile_args(fedfem_ctx* c) {
     t.max_block = c->t_max_block; t.max_local = c->t_max_local;
     t.smem_bytes = c->t_smem;
     t.staged = c->tile.kernel == FEDFEM_KERNEL_TILED_STAGED;
+    t.threads = staged_threads(c);
     return t;
 }
 
@@ -660,6 +666,7 @@ int fedfem_set_tile(fedfem_ctx* c, const fedfem_tile* t) {
     if (t->block != 0 && (t->block < 64 || t->block > 1024 || t->block % 32)) return fail(c, FEDFEM_E_ARG, "block must be 64..1024, multiple of 32");
     if (t->blocks_per_sm < 0 || t->tile_nodes < 0 || t->tile_nodes % 8) return fail(c, FEDFEM_E_ARG, "bad tile knobs");
     if (t->tile_nodes != c->tile.tile_nodes || t->blocks_per_sm != c->tile.blocks_per_sm ||
+        t->block != c->tile.block ||
         (t->kernel == FEDFEM_KERNEL_TILED_STAGED) != (c->tile.kernel == FEDFEM_KERNEL_TILED_STAGED))
         free_tiles(c);
     c->tile = *t;
@@ -1133,7 +1140,7 @@ int fedfem_get_info(fedfem_ctx* c, fedfem_info* info) {
     }
     info->sm_count = c->sm_count;
     info->grid_blocks = c->last.grid_used;
-    info->block_threads = c->tile.kernel == FEDFEM_KERNEL_TILED_STAGED ? tiled_threads() : 256;
+    info->block_threads = c->tile.kernel == FEDFEM_KERNEL_TILED_STAGED ? staged_threads(c) : 256;
     info->kernel = c->tile.kernel;
     info->tile_nodes = c->tiles_ok ? c->tiles_B : 0;
     info->lanes = c->n_lanes;

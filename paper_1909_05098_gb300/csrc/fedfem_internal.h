@@ -140,6 +140,7 @@ struct TileArgs {
     int max_block;                   // bytes, multiple of 16
     int max_local;                   // R words of staged temperatures
     int staged;                      // 1: blocks bulk-copied into shared-memory stages; 0: read from global
+    int threads;                     // staged kernel: threads per block (256 or 512)
     size_t smem_bytes;
 };
 
@@ -151,8 +152,8 @@ cudaError_t launch_tiled_f32(const StepArgs<float>& a, const TileArgs<float>& t,
 cudaError_t launch_tiled_f32x4(const StepArgs<float, F4>& a, const TileArgs<float>& t, bool kahan, int64_t n_steps,
                                LaunchCfg& cfg, cudaStream_t s);
 // occupancy (blocks per SM) of the tiled kernel for a shared-memory size (lanes: 1 or 4)
-int tiled_blocks_per_sm(int precision, int nv, int staged, int lanes, size_t smem_bytes);
-int tiled_threads();
+int tiled_blocks_per_sm(int precision, int nv, int staged, int threads, int lanes, size_t smem_bytes);
+int tiled_threads();   // default threads per block of the staged kernel
 
 cudaError_t launch_steps_f64(const StepArgs<double>& a, int nv, int64_t n_steps, LaunchCfg& cfg,
                              cudaStream_t s);

@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(256) k_persistent(StepArgs<R> a, long long n_s
 // memory stages, two tiles ahead; the next tile's temperatures are fetched
 // with asynchronous copies while the current tile's node phase runs.
 
-constexpr int kTiledThreads = 512;
+constexpr int kTiledThreads = 512;        // default block of the staged kernel (256 and 1024 also built)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
@@ -467,15 +467,16 @@ __global__ void __launch_bounds__(256, DirectOccupancy<L>::min_blocks) k_tiled_d
     if (blockIdx.x == 0 && threadIdx.x == 0) a.status->steps_done = a.step0 + done;
 }
 
-// resident blocks per SM the staged kernel is compiled for: two for one FP32
-// lane (64 registers), one for FP64 or four-lane state
-template <typename L>
+// resident blocks per SM the staged kernel is compiled for (TPB threads per
+// block): 64 registers per thread for one FP32 lane, 128 for FP64 or
+// four-lane state
+template <typename L, int TPB>
 struct StagedOccupancy {
-    static constexpr int min_blocks = sizeof(L) == 4 ? 2 : 1;
+    static constexpr int min_blocks = (sizeof(L) == 4 ? 1024 : 512) / TPB > 0 ? (sizeof(L) == 4 ? 1024 : 512) / TPB : 1;
 };
 
-template <typename R, typename L, int NV, bool KAHAN>
-__global__ void __launch_bounds__(kTiledThreads, StagedOccupancy<L>::min_blocks)
+template <typename R, typename L, int NV, bool KAHAN, int TPB>
+__global__ void __launch_bounds__(TPB, StagedOccupancy<L, TPB>::min_blocks)
     k_tiled(StepArgs<R, L> a, TileArgs<R> ta, long long n_steps, long long spin_limit) {
     // shared memory: 2 mbarriers | 2 block stages | temperatures | load table
     extern __shared__ __align__(128) unsigned char smem[];
@@ -598,8 +599,11 @@ __global__ void __launch_bounds__(kTiledThreads, StagedOccupancy<L>::min_blocks)
 template <typename R, typename L, int NV, bool KAHAN>
 cudaError_t launch_tiled_impl(const StepArgs<R, L>& a, const TileArgs<R>& ta, int64_t n_steps, LaunchCfg& cfg,
                               cudaStream_t s) {
-    auto kern = ta.staged ? k_tiled<R, L, NV, KAHAN> : k_tiled_direct<R, L, NV, KAHAN>;
-    const int b = ta.staged ? kTiledThreads : 256;
+    auto kern = !ta.staged           ? k_tiled_direct<R, L, NV, KAHAN>
+                : ta.threads == 256  ? k_tiled<R, L, NV, KAHAN, 256>
+                : ta.threads == 1024 ? k_tiled<R, L, NV, KAHAN, 1024>
+                                     : k_tiled<R, L, NV, KAHAN, kTiledThreads>;
+    const int b = ta.staged ? ta.threads : 256;
     cudaError_t err = cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)ta.smem_bytes);
     if (err != cudaSuccess) return err;
@@ -678,22 +682,26 @@ cudaError_t launch_tiled_f32x4(const StepArgs<float, F4>& a, const TileArgs<floa
                  : launch_tiled_impl<float, F4, 4, false>(a, t, n_steps, cfg, s);
 }
 
-template <typename R, typename L>
-const void* pick_tiled(int staged, int nv, bool kahan) {
-    if (staged) {
-        if (nv == 8) return kahan ? (const void*)k_tiled<R, L, 8, true> : (const void*)k_tiled<R, L, 8, false>;
-        return kahan ? (const void*)k_tiled<R, L, 4, true> : (const void*)k_tiled<R, L, 4, false>;
-    }
-    if (nv == 8) return kahan ? (const void*)k_tiled_direct<R, L, 8, true> : (const void*)k_tiled_direct<R, L, 8, false>;
-    return kahan ? (const void*)k_tiled_direct<R, L, 4, true> : (const void*)k_tiled_direct<R, L, 4, false>;
+template <typename R, typename L, int NV, bool KAHAN>
+const void* pick_tiled_k(int staged, int threads) {
+    if (!staged) return (const void*)k_tiled_direct<R, L, NV, KAHAN>;
+    if (threads == 256) return (const void*)k_tiled<R, L, NV, KAHAN, 256>;
+    if (threads == 1024) return (const void*)k_tiled<R, L, NV, KAHAN, 1024>;
+    return (const void*)k_tiled<R, L, NV, KAHAN, kTiledThreads>;
 }
 
-int tiled_blocks_per_sm(int precision, int nv, int staged, int lanes, size_t smem) {
-    const int block = staged ? kTiledThreads : 256;
+template <typename R, typename L>
+const void* pick_tiled(int staged, int threads, int nv, bool kahan) {
+    if (nv == 8) return kahan ? pick_tiled_k<R, L, 8, true>(staged, threads) : pick_tiled_k<R, L, 8, false>(staged, threads);
+    return kahan ? pick_tiled_k<R, L, 4, true>(staged, threads) : pick_tiled_k<R, L, 4, false>(staged, threads);
+}
+
+int tiled_blocks_per_sm(int precision, int nv, int staged, int threads, int lanes, size_t smem) {
+    const int block = staged ? threads : 256;
     const bool kahan = precision == FEDFEM_FP32_KAHAN;
-    const void* k = precision == FEDFEM_FP64 ? pick_tiled<double, double>(staged, nv, false)
-                    : lanes == 4            ? pick_tiled<float, F4>(staged, nv, kahan)
-                                            : pick_tiled<float, float>(staged, nv, kahan);
+    const void* k = precision == FEDFEM_FP64 ? pick_tiled<double, double>(staged, threads, nv, false)
+                    : lanes == 4            ? pick_tiled<float, F4>(staged, threads, nv, kahan)
+                                            : pick_tiled<float, float>(staged, threads, nv, kahan);
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, smem) != cudaSuccess) return 0;
