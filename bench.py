@@ -183,28 +183,37 @@ def measured_peak():
     return FALLBACK_HBM_GBS, "fallback"
 
 
+# sources that decide what the time-loop kernels do and how tiles are packed
+KERNEL_SOURCES = ("step.cu", "elem_math.cuh", "fedfem_internal.h", "api.cu", "host_layout.cpp")
+
+
 def kernel_source_hash():
     csrc = os.path.join(ROOT, "paper_1909_05098_gb300", "csrc")
     h = hashlib.sha256()
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel_name, n, steps_per_launch):
-    """DRAM bytes per time step of `kernel_name` on the n^3 workload from the
-    committed ncu summary, scaled to one launch; None if the summary is absent
-    or was taken on different kernel sources."""
-    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
-    if not os.path.exists(p):
-        return None
-    d = json.load(open(p))
-    e = d.get(kernel_name)
-    if not e or e.get("source_hash") != kernel_source_hash():
-        return None
-    per_step = e["dram_bytes_per_step_full"] if e.get("n") != n else e["dram_bytes_per_step"]
-    return per_step * steps_per_launch
+def ncu_traffic(kernel, n, tile_nodes, steps_per_launch):
+    """DRAM bytes (read + write) per launch of the timed kernel, from the
+    committed ncu summary: a line
+        traffic: kernel=<name> n=<cube edge> tile_nodes=<B> source=<hash> dram_bytes_per_step=<bytes>
+    in profiles/*.md.  None unless kernel, workload, tile size and kernel
+    sources all match this run."""
+    pdir = os.path.join(ROOT, "profiles")
+    want = {"kernel": kernel, "n": str(n), "tile_nodes": str(tile_nodes), "source": kernel_source_hash()}
+    for f in sorted(os.listdir(pdir)) if os.path.isdir(pdir) else []:
+        if not f.endswith(".md"):
+            continue
+        for line in open(os.path.join(pdir, f)):
+            line = line.strip().strip("`")
+            if not line.startswith("traffic:"):
+                continue
+            kv = dict(x.split("=", 1) for x in line[len("traffic:"):].split())
+            if all(kv.get(k) == v for k, v in want.items()):
+                return float(kv["dram_bytes_per_step"]) * steps_per_launch
+    return None
 
 
 # ---------------------------------------------------------------------------
@@ -372,7 +381,7 @@ def run_ours(args):
     launch_s = float(np.mean(per_launch_ms)) / 1e3
     peak, peak_src = measured_peak()
     achieved = alg_bytes_launch / launch_s / 1e9
-    traffic = ncu_traffic(names[kernel] + "_fp32_kahan_hex8", args.n, S)
+    traffic = ncu_traffic(names[kernel] + "_fp32_kahan_hex8", args.n, info["tile_nodes"], S)
     solver.close()
     if rank != 0:
         return
