@@ -5,7 +5,7 @@ temperature-dependent k(T), c(T), perfusion, a Gaussian source, a film
 condition on one face and Dirichlet on the other five; FP32 state with Kahan
 compensation; the persistent multi-step kernel.  One bench step is one
 ``fedfem_step`` call that advances ``--steps-per-launch`` explicit time steps
-(Algorithm 1, lines 8-15) on the device.  Metric: node-steps/s (nodes x time
+(Algorithm 1's time loop) on the device.  Metric: node-steps/s (nodes x time
 steps / second), whole job.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]

@@ -128,7 +128,7 @@ typedef struct {
  * stream owned by the context.  *out receives the context (NULL on error). */
 int fedfem_create(fedfem_ctx** out, int device, int precision, void* cuda_stream);
 
-/* Mesh (Algorithm 1, pre-computation line 1).  xyz: n_nodes x 3 doubles,
+/* Mesh (the input of Algorithm 1).  xyz: n_nodes x 3 doubles,
  * metres, row-major.  conn: n_elems x elem_type 0-based node ids, row-major.
  * hex8 (Eq. 14): corners at natural coordinates (-1,-1,-1), (1,-1,-1),
  * (1,1,-1), (-1,1,-1), then the same four at zeta = +1, det J > 0.
@@ -172,7 +172,7 @@ int fedfem_set_convective(fedfem_ctx* ctx, int64_t n_faces, int nverts, const in
  * paper applies it).  Repeated nodes add. */
 int fedfem_set_nodal_flux(fedfem_ctx* ctx, int64_t n, const int32_t* nodes, const double* q_W);
 
-/* Pre-computation (Algorithm 1, lines 2-6) in FP64 on the GPU: element
+/* Pre-computation (the first stage of Algorithm 1) in FP64 on the GPU: element
  * geometry and A_e (Eq. 16), lumped volumes, perfusion and source loads, face
  * areas, and the critical step of Eq. 9 for properties anywhere in
  * [T_lo, T_hi].  Writes dt_cr to *dt_cr_out (may be NULL).  Returns
@@ -180,7 +180,7 @@ int fedfem_set_nodal_flux(fedfem_ctx* ctx, int64_t n, const int32_t* nodes, cons
  * is not positive on the range. */
 int fedfem_precompute(fedfem_ctx* ctx, double T_lo, double T_hi, double* dt_cr_out);
 
-/* Initial field (Algorithm 1, line 7): T0 has n_nodes values in input order,
+/* Initial field (the initialisation of Algorithm 1): T0 has n_nodes values in input order,
  * or is NULL for T0_uniform everywhere.  Dirichlet nodes take their values.
  * Clears the device status and the step counter. */
 int fedfem_init(fedfem_ctx* ctx, const double* T0, double T0_uniform);
@@ -188,7 +188,7 @@ int fedfem_init(fedfem_ctx* ctx, const double* T0, double T0_uniform);
 /* As fedfem_init, T0 a device pointer to n_nodes doubles (input order). */
 int fedfem_init_device(fedfem_ctx* ctx, const double* T0_dev);
 
-/* Advance n_steps explicit steps of size dt (Algorithm 1, lines 8-15),
+/* Advance n_steps explicit steps of size dt (Algorithm 1's time loop),
  * asynchronously.  FEDFEM_E_UNSTABLE_DT if dt >= dt_cr.  A range violation
  * or barrier timeout stops the loop on the device and is reported by
  * fedfem_sync. */

@@ -1,4 +1,4 @@
-// Pre-computation of Algorithm 1 (lines 2-6) in FP64 on the GPU:
+// Pre-computation stage of Algorithm 1 in FP64 on the GPU:
 //   * element geometry: J at the centre (hex8, Eq. 14) or the edge matrix
 //     (tet4, Eq. 15), det > 0 check, M_e of the factored A_e (Eq. 16), V_e;
 //   * lumped volumes V_i = sum_e V_e / nv (Section 2.3.4), gathered in the

@@ -1,4 +1,4 @@
-// The time loop of Algorithm 1 (lines 8-15): an element phase (Eq. 17 with
+// The time loop of Algorithm 1: an element phase (Eq. 17 with
 // k_e of Eq. 13) writing each element's nodal loads into its own slots, then
 // a node phase that gathers every free node's slots in a fixed order (the sum
 // of Eq. 11, no atomics), forms the lumped capacitance C_i(T) and applies the
