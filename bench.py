@@ -183,6 +183,18 @@ def measured_peak():
     return FALLBACK_HBM_GBS, "fallback"
 
 
+def bf16_peak(sustained=False):
+    """Dense BF16 tensor peak in TFLOP/s: the measured burst (or sustained)
+    figure, else the 1.9 PFLOP/s fallback."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    key = "bf16_tflops_sustained" if sustained else "bf16_tflops"
+    if os.path.exists(p):
+        d = json.load(open(p))
+        if d.get(key):
+            return float(d[key])
+    return 1900.0
+
+
 # sources that decide what the time-loop kernels do and how tiles are packed
 KERNEL_SOURCES = ("step.cu", "elem_math.cuh", "fedfem_internal.h", "api.cu", "host_layout.cpp")
 
@@ -520,6 +532,38 @@ def run_planning(args):
 # learned surrogate workload (opt-in)
 # ---------------------------------------------------------------------------
 
+def time_fused_forward(sur, q, reps=20):
+    """CUDA-event time of one fused inference forward on len(q) scenarios, and
+    its algorithmic bytes and tensor FLOPs: per layer the edge states are
+    read (not on the first layer, whose states come from the shared edge
+    encoder) and written (not on the last), the node states read, the message
+    sums written, node states read and written again; each edge row costs
+    2 x 192 x 64 and each node row 2 x 128 x 64 multiply-adds."""
+    import torch
+    from paper_1909_05098_gb300 import fedfem as ff
+    B, N, L, H = q.shape[0], sur.N, 4, 64
+    E = int(sur.n_edges)
+    T = torch.full((B, N), 40.0, device="cuda")
+    x = sur._features(T, q.contiguous())
+    y = torch.empty((B, N), device="cuda")
+    for _ in range(3):
+        ff.fedfem_mpnn_infer(sur.net, B, x.data_ptr(), y.data_ptr())
+    ff.fedfem_mpnn_sync(sur.net)
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(s)
+    for _ in range(reps):
+        ff.fedfem_mpnn_infer(sur.net, B, x.data_ptr(), y.data_ptr())
+    e1.record(s)
+    ff.fedfem_mpnn_sync(sur.net)
+    ms = e0.elapsed_time(e1) / reps
+    nbytes = 4 * H * (B * E * (2 * L - 2) + B * N * 5 * L) + 4 * B * N * 6
+    flops = 2.0 * B * L * (E * 3 * H * H + N * 2 * H * H)
+    return {"scenarios": B, "ms": ms, "algorithmic_bytes": nbytes, "flops": flops,
+            "achieved_gbs": nbytes / ms / 1e6, "achieved_tflops": flops / ms / 1e9}
+
+
 def run_surrogate(args):
     """Train the message-passing surrogate on trajectories of the plain path
     (10 mm hex cube, one seeded source per scenario), then advance held-out
@@ -563,6 +607,8 @@ def run_surrogate(args):
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
     del T_in, T_out, q_in, S
+    fwd = time_fused_forward(sur, q32[:sur.max_batch])
+    log(f"fused forward: {fwd}")
     # --- held-out scenarios
     src_ev = surrogate_sources(args.eval_scenarios, seed=19090598)
     q_ev = source_density(p.xyz, src_ev)
@@ -606,6 +652,12 @@ def run_surrogate(args):
                                 "note": "includes the first plain check of each stretch"},
         "gain_vs_plain": best["gain_vs_plain"],
         "max_err_vs_plain_C": best["max_err_vs_plain_C"],
+        "fused_forward": fwd,
+        "roofline": {"bound": "hbm", "kernel": "fused inference forward (encoders + 4 x edge/node layer kernels)",
+                     "achieved": fwd["achieved_gbs"], "peak": measured_peak()[0], "unit": "GB/s",
+                     "frac": fwd["achieved_gbs"] / measured_peak()[0], "traffic": None,
+                     "tensor_tflops": fwd["achieved_tflops"],
+                     "tensor_frac": fwd["achieved_tflops"] / bf16_peak()},
     }
     sur.close()
     ens.close()

@@ -392,8 +392,19 @@ int fedfem_mpnn_get_params(fedfem_mpnn* m, float* params);
  * bytes or NULL; x_out batch x n_nodes x 5. */
 int fedfem_mpnn_features(fedfem_mpnn* m, int batch, const float* T_dev, const float* q_dev,
                          const unsigned char* dirichlet_dev, const fedfem_material* mat, float* x_out_dev);
-/* y_dev (batch x n_nodes) = network(x_dev). */
+/* y_dev (batch x n_nodes) = network(x_dev); keeps what fedfem_mpnn_loss_grad
+ * needs (the training path). */
 int fedfem_mpnn_forward(fedfem_mpnn* m, int batch, const float* x_dev, float* y_dev);
+/* y_dev (batch x n_nodes) = network(x_dev) by the fused inference kernels:
+ * per layer one edge kernel (gather, tensor-core product, message, edge
+ * update and per-node message sums in its epilogue) and one node kernel; no
+ * training caches.  Same numbers as fedfem_mpnn_forward.  Asynchronous on the
+ * network's stream; fedfem_mpnn_sync reports a tensor-core wait that gave up
+ * (FEDFEM_E_TIMEOUT).  Needs every node's in-degree <= 128
+ * (FEDFEM_E_UNSUPPORTED at create otherwise). */
+int fedfem_mpnn_infer(fedfem_mpnn* m, int batch, const float* x_dev, float* y_dev);
+/* Wait for the network's stream; FEDFEM_E_TIMEOUT if a bounded wait gave up. */
+int fedfem_mpnn_sync(fedfem_mpnn* m);
 /* Mean squared error over nodes with mask 1 (mask_dev: n_nodes floats) and
  * its gradient; *loss and grad (n_params host floats) may be NULL.  Keeps the
  * gradient for fedfem_mpnn_adam. */

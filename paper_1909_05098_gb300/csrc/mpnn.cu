@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "fedfem_internal.h"
+#include "tcgen05.cuh"
 
 using bf16 = __nv_bfloat16;
 
@@ -283,6 +284,273 @@ __global__ void k_features(int64_t B, int64_t N, const float* T, const float* q,
     x[i * 5 + 4] = D ? (float)D[i % N] : 0.0f;
 }
 
+// ---- fused inference ---------------------------------------------------------
+// One layer of the network in two tensor-core kernels, without the training
+// caches: the edge kernel gathers [e; h_src; h_dst] for 128 edges straight into
+// shared memory (BF16, core-matrix layout), multiplies by W_e^T (tcgen05, FP32
+// accumulators in TMEM), and in its epilogue forms msg = SiLU(acc + b_e),
+// e += msg and the sum of msg over each destination node's in-edges (edge tiles
+// hold whole in-edge lists, summed in edge order); the node kernel gathers
+// [h; a], multiplies by W_n^T and adds SiLU(acc + b_n) to h in place (on the
+// last layer also the decoder).  Rounding points, the MMA sequence and every
+// summation order are those of the unfused forward, so both give the same
+// numbers.
+
+constexpr int kRows = 128;                      // rows (edges or nodes) per tile
+constexpr int kPad = 68;                        // floats per padded FP32 row in shared memory
+constexpr uint32_t kKBlock = kRows * 64 * 2;    // bytes of one 128 x 64 BF16 K-block
+constexpr uint32_t kWBlock = 64 * 64 * 2;       // bytes of one 64 x 64 BF16 weight K-block
+
+struct EdgeTile {
+    int32_t m0, count, n0, n1;   // edges [m0, m0 + count) are the in-edges of nodes [n0, n1)
+};
+
+__device__ __forceinline__ uint4 pack8(float4 a, float4 b) {
+    uint4 r;
+    __nv_bfloat162 p;
+    p = __floats2bfloat162_rn(a.x, a.y); r.x = *reinterpret_cast<uint32_t*>(&p);
+    p = __floats2bfloat162_rn(a.z, a.w); r.y = *reinterpret_cast<uint32_t*>(&p);
+    p = __floats2bfloat162_rn(b.x, b.y); r.z = *reinterpret_cast<uint32_t*>(&p);
+    p = __floats2bfloat162_rn(b.z, b.w); r.w = *reinterpret_cast<uint32_t*>(&p);
+    return r;
+}
+
+// W (64 x K, row-major BF16) into K/64 core-matrix blocks of 64 x 64
+__device__ __forceinline__ void stage_weights(unsigned char* sB, const bf16* W, int K) {
+    const int chunks = K / 8;
+    for (int c = threadIdx.x; c < 64 * chunks; c += blockDim.x) {
+        const int r = c / chunks, kc = c % chunks;
+        const uint4 v = *reinterpret_cast<const uint4*>(W + (int64_t)r * K + 8 * kc);
+        *reinterpret_cast<uint4*>(sB + (kc >> 3) * kWBlock + tc::core_offset(r, 8 * (kc & 7))) = v;
+    }
+}
+
+// one 64-wide FP32 row segment of row r into K-block kb (BF16), lane's two
+// 8-value chunks j = lane/8 and lane/8 + 4; optionally kept as FP32 in keep
+__device__ __forceinline__ void stage_row(unsigned char* sA, int kb, int r, const float* row, bool valid, float* keep) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const int j = (lane >> 3) + 4 * q;
+        float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0;
+        if (valid) {
+            v0 = reinterpret_cast<const float4*>(row)[2 * j];
+            v1 = reinterpret_cast<const float4*>(row)[2 * j + 1];
+        }
+        *reinterpret_cast<uint4*>(sA + kb * kKBlock + tc::core_offset(r, 8 * j)) = pack8(v0, v1);
+        if (keep) {
+            reinterpret_cast<float4*>(keep + r * kPad)[2 * j] = v0;
+            reinterpret_cast<float4*>(keep + r * kPad)[2 * j + 1] = v1;
+        }
+    }
+}
+
+// issue the K/16 MMAs of one tile (thread 0) and wait for them (every thread);
+// false when the bounded wait gave up (then the copies in flight are waited
+// for once more, so TMEM can be freed)
+__device__ __forceinline__ bool mma_tile(uint32_t tmem, const unsigned char* sA, const unsigned char* sB, int kblocks,
+                                         uint64_t* bar, uint32_t& phase, int* status, long long limit) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic writes -> tensor-core reads
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t idesc = tc::instr_desc(kRows, 64);
+        for (int kb = 0; kb < kblocks; ++kb)
+#pragma unroll
+            for (int st = 0; st < 4; ++st)
+                tc::mma_bf16(tmem, tc::smem_desc(tc::s_u32(sA + kb * kKBlock) + st * 256, 128, 1024),
+                             tc::smem_desc(tc::s_u32(sB + kb * kWBlock) + st * 256, 128, 1024), idesc,
+                             (kb > 0 || st > 0) ? 1u : 0u);
+        tc::mma_commit(bar);
+    }
+    const int timed_out = __syncthreads_or(!tc::mbar_wait(bar, phase, limit));
+    if (timed_out) {
+        if (threadIdx.x == 0) atomicOr(status, 1);
+        tc::mbar_wait(bar, phase, limit);
+    }
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    return !timed_out;
+}
+
+struct EdgeLayerArgs {
+    int B;
+    int64_t N, E;
+    const int32_t *src, *dst, *in_ptr;
+    const EdgeTile* tiles;
+    int n_tiles;
+    const float* e_in;        // B x E x H, or the shared E x H encoder output (e_in_stride 0)
+    int64_t e_in_stride;
+    float* e_out;             // B x E x H (may alias e_in); null on the last layer
+    const float* h;           // B x N x H
+    float* a;                 // B x N x H
+    const bf16* W;            // H x 3H
+    const float* bias;
+    int* status;
+    long long limit;
+};
+
+__global__ void __launch_bounds__(128) k_edge_layer(EdgeLayerArgs g) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char* sA = smem;                          // 3 K-blocks; after the MMAs: messages, 128 x kPad FP32
+    unsigned char* sB = smem + 3 * kKBlock;            // W_e, 3 K-blocks
+    float* eS = reinterpret_cast<float*>(smem + 3 * kKBlock + 3 * kWBlock);   // e rows, 128 x kPad FP32
+    float* msgS = reinterpret_cast<float*>(sA);
+    __shared__ uint64_t bar;
+    __shared__ uint32_t tmem_base;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(tc::s_u32(&tmem_base))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (threadIdx.x == 0) tc::mbar_init(&bar);
+    stage_weights(sB, g.W, 3 * H);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    uint32_t phase = 0;
+    const int64_t items = (int64_t)g.n_tiles * g.B;
+    for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
+        const int t = (int)(item % g.n_tiles);
+        const int64_t b = item / g.n_tiles;
+        const EdgeTile T = g.tiles[t];
+        for (int i = warp; i < kRows / 8; i += 4) {
+            const int r = 8 * i + (lane & 7);
+            const bool valid = r < T.count;
+            const int64_t m = T.m0 + (valid ? r : 0);   // read only for valid rows
+            const int32_t s = valid ? g.src[m] : 0, d = valid ? g.dst[m] : 0;
+            stage_row(sA, 0, r, g.e_in + b * g.e_in_stride + m * H, valid, eS);
+            stage_row(sA, 1, r, g.h + (b * g.N + s) * H, valid, nullptr);
+            stage_row(sA, 2, r, g.h + (b * g.N + d) * H, valid, nullptr);
+        }
+        if (!mma_tile(tmem, sA, sB, 3, &bar, phase, g.status, g.limit)) break;
+        // epilogue: this thread owns row r (TMEM lane r)
+        {
+            const int r = 32 * warp + lane;
+            float* er = eS + r * kPad;
+            float* mr = msgS + r * kPad;
+#pragma unroll
+            for (int c0 = 0; c0 < H; c0 += 32) {
+                float v[32];
+                tc::tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
+#pragma unroll
+                for (int c = 0; c < 32; c += 4) {
+                    float4 msg, ev = *reinterpret_cast<float4*>(er + c0 + c);
+                    msg.x = tc::silu(v[c] + g.bias[c0 + c]);
+                    msg.y = tc::silu(v[c + 1] + g.bias[c0 + c + 1]);
+                    msg.z = tc::silu(v[c + 2] + g.bias[c0 + c + 2]);
+                    msg.w = tc::silu(v[c + 3] + g.bias[c0 + c + 3]);
+                    ev.x = ev.x + msg.x; ev.y = ev.y + msg.y; ev.z = ev.z + msg.z; ev.w = ev.w + msg.w;
+                    *reinterpret_cast<float4*>(mr + c0 + c) = msg;
+                    *reinterpret_cast<float4*>(er + c0 + c) = ev;
+                }
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        if (g.e_out)   // e rows back, coalesced: a warp per row
+            for (int r = warp; r < T.count; r += 4)
+                reinterpret_cast<float2*>(g.e_out + (b * g.E + T.m0 + r) * H)[lane] =
+                    reinterpret_cast<const float2*>(eS + r * kPad)[lane];
+        // a_n = sum of the messages over n's in-edges, in edge order
+        {
+            const int c = threadIdx.x & 63;
+            for (int n = T.n0 + (threadIdx.x >> 6); n < T.n1; n += 2) {
+                float acc = 0.0f;
+                for (int32_t m = g.in_ptr[n]; m < g.in_ptr[n + 1]; ++m) acc += msgS[(m - T.m0) * kPad + c];
+                g.a[(b * g.N + n) * H + c] = acc;
+            }
+        }
+        __syncthreads();   // shared buffers are restaged by the next item
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem) : "memory");
+}
+
+struct NodeLayerArgs {
+    int64_t R;                // rows: batch x nodes
+    float* h;                 // R x H, updated in place
+    const float* a;           // R x H
+    const bf16* W;            // H x 2H
+    const float* bias;
+    const float* wd;          // decoder (last layer), else null
+    const float* bd;
+    float* y;                 // R decoder outputs (last layer)
+    int* status;
+    long long limit;
+};
+
+__global__ void __launch_bounds__(128) k_node_layer(NodeLayerArgs g) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char* sA = smem;                          // 2 K-blocks: [h | a]
+    unsigned char* sB = smem + 2 * kKBlock;            // W_n, 2 K-blocks
+    float* hS = reinterpret_cast<float*>(smem + 2 * kKBlock + 2 * kWBlock);   // h rows, 128 x kPad FP32
+    __shared__ uint64_t bar;
+    __shared__ uint32_t tmem_base;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;" ::"r"(tc::s_u32(&tmem_base))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (threadIdx.x == 0) tc::mbar_init(&bar);
+    stage_weights(sB, g.W, 2 * H);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    uint32_t phase = 0;
+    const int64_t tiles = (g.R + kRows - 1) / kRows;
+    for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const int64_t row0 = tile * kRows;
+        for (int i = warp; i < kRows / 8; i += 4) {
+            const int r = 8 * i + (lane & 7);
+            const bool valid = row0 + r < g.R;
+            const int64_t row = valid ? row0 + r : 0;
+            stage_row(sA, 0, r, g.h + row * H, valid, hS);
+            stage_row(sA, 1, r, g.a + row * H, valid, nullptr);
+        }
+        if (!mma_tile(tmem, sA, sB, 2, &bar, phase, g.status, g.limit)) break;
+        {
+            const int r = 32 * warp + lane;
+            float* hr = hS + r * kPad;
+#pragma unroll
+            for (int c0 = 0; c0 < H; c0 += 32) {
+                float v[32];
+                tc::tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
+#pragma unroll
+                for (int c = 0; c < 32; c += 4) {
+                    float4 hv = *reinterpret_cast<float4*>(hr + c0 + c);
+                    hv.x = hv.x + tc::silu(v[c] + g.bias[c0 + c]);
+                    hv.y = hv.y + tc::silu(v[c + 1] + g.bias[c0 + c + 1]);
+                    hv.z = hv.z + tc::silu(v[c + 2] + g.bias[c0 + c + 2]);
+                    hv.w = hv.w + tc::silu(v[c + 3] + g.bias[c0 + c + 3]);
+                    *reinterpret_cast<float4*>(hr + c0 + c) = hv;
+                }
+            }
+            if (g.y && row0 + r < g.R) {   // decoder, in the order of the unfused one
+                float acc = g.bd[0];
+                for (int k = 0; k < H; ++k) acc += g.wd[k] * hr[k];
+                g.y[row0 + r] = acc;
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        for (int r = warp; r < kRows && row0 + r < g.R; r += 4)
+            reinterpret_cast<float2*>(g.h + (row0 + r) * H)[lane] = reinterpret_cast<const float2*>(hS + r * kPad)[lane];
+        __syncthreads();
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem) : "memory");
+}
+
+constexpr size_t kEdgeSmem = 3 * kKBlock + 3 * kWBlock + (size_t)kRows * kPad * 4;
+constexpr size_t kNodeSmem = 2 * kKBlock + 2 * kWBlock + (size_t)kRows * kPad * 4;
+
 }  // namespace
 }  // namespace fedfem
 
@@ -311,6 +579,11 @@ struct fedfem_mpnn {
     bf16 *dzb_e = nullptr, *dzb_n = nullptr, *T1 = nullptr, *T2 = nullptr;
     float *part = nullptr, *colpart = nullptr, *lossp = nullptr;
     int* status = nullptr;
+    // fused inference: edge tiles (in-edges of consecutive destination nodes)
+    void* edge_tiles = nullptr;
+    int n_edge_tiles = 0;
+    int sm_count = 0;
+    long long spin_limit = 2000000000LL;
     int64_t part_floats = 0, colpart_floats = 0;
 };
 
@@ -463,6 +736,47 @@ int backward(fedfem_mpnn* m, int B, const float* x) {
     return FEDFEM_OK;
 }
 
+// fused inference forward: encoders, then per layer the edge and node kernels
+int infer(fedfem_mpnn* m, int B, const float* x, float* y) {
+    const int64_t N = m->N, E = m->E, RN = B * N;
+    const float* P = m->P;
+    cudaStream_t s = m->stream;
+    float* h = m->hL[0];
+    k_encode<<<grid(RN * H), kT, 0, s>>>(RN, NIN, x, P + m->off[P_WNE], P + m->off[P_BNE], m->zne, h);
+    k_encode<<<grid(E * H), kT, 0, s>>>(E, EIN, m->efeat, P + m->off[P_WEE], P + m->off[P_BEE], m->zee, m->e0);
+    MC(cudaGetLastError());
+    MC(cudaFuncSetAttribute(k_edge_layer, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEdgeSmem));
+    MC(cudaFuncSetAttribute(k_node_layer, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kNodeSmem));
+    const int64_t edge_items = (int64_t)m->n_edge_tiles * B;
+    const int64_t node_tiles = (RN + kRows - 1) / kRows;
+    const int resident = 2 * std::max(1, m->sm_count);
+    for (int l = 0; l < m->L; ++l) {
+        EdgeLayerArgs ea{};
+        ea.B = B; ea.N = N; ea.E = E;
+        ea.src = m->src; ea.dst = m->dst; ea.in_ptr = m->in_ptr;
+        ea.tiles = (const EdgeTile*)m->edge_tiles; ea.n_tiles = m->n_edge_tiles;
+        ea.e_in = l == 0 ? m->e0 : m->e;
+        ea.e_in_stride = l == 0 ? 0 : E * H;
+        ea.e_out = l + 1 < m->L ? m->e : nullptr;
+        ea.h = h; ea.a = m->a;
+        ea.W = m->We[l]; ea.bias = P + m->off[p_be(l)];
+        ea.status = m->status; ea.limit = m->spin_limit;
+        k_edge_layer<<<(unsigned)std::min<int64_t>(edge_items, resident), 128, kEdgeSmem, s>>>(ea);
+        MC(cudaGetLastError());
+        NodeLayerArgs na{};
+        na.R = RN; na.h = h; na.a = m->a;
+        na.W = m->Wn[l]; na.bias = P + m->off[p_bn(l)];
+        const bool last = l + 1 == m->L;
+        na.wd = last ? P + m->off[p_We(m->L)] : nullptr;
+        na.bd = last ? P + m->off[p_We(m->L) + 1] : nullptr;
+        na.y = last ? y : nullptr;
+        na.status = m->status; na.limit = m->spin_limit;
+        k_node_layer<<<(unsigned)std::min<int64_t>(node_tiles, resident), 128, kNodeSmem, s>>>(na);
+        MC(cudaGetLastError());
+    }
+    return FEDFEM_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -499,6 +813,21 @@ int fedfem_mpnn_create(fedfem_mpnn** out, int device, int64_t n_nodes, int64_t n
         std::vector<int32_t> pos(out_ptr.begin(), out_ptr.end() - 1);
         for (int64_t i = 0; i < n_edges; ++i) out_edge[pos[src[i]]++] = (int32_t)i;
     }
+    // edge tiles of the fused forward: whole in-edge lists of consecutive nodes, at most 128 edges
+    std::vector<EdgeTile> tiles;
+    for (int64_t n = 0; n < n_nodes;) {
+        EdgeTile t{in_ptr[n], 0, (int32_t)n, (int32_t)n};
+        while (n < n_nodes && in_ptr[n + 1] - t.m0 <= kRows) ++n;
+        if (n == t.n0) {   // one node with more than 128 in-edges
+            delete m;
+            return FEDFEM_E_UNSUPPORTED;
+        }
+        t.n1 = (int32_t)n;
+        t.count = in_ptr[n] - t.m0;
+        tiles.push_back(t);
+    }
+    m->n_edge_tiles = (int)tiles.size();
+    cudaDeviceGetAttribute(&m->sm_count, cudaDevAttrMultiProcessorCount, device);
     const int64_t Bm = max_batch, RN = Bm * n_nodes, RE = Bm * n_edges;
     double* xyz_d = nullptr;
     auto fail_alloc = [&](cudaError_t e) {
@@ -532,6 +861,11 @@ int fedfem_mpnn_create(fedfem_mpnn** out, int device, int64_t n_nodes, int64_t n
     MA(m->colpart, m->colpart_floats);
     MA(m->lossp, (RN + kT - 1) / kT + 1);
     MA(m->status, 1);
+    {
+        unsigned char* tp = nullptr;
+        MA(tp, sizeof(EdgeTile) * tiles.size());
+        m->edge_tiles = tp;
+    }
 #undef MA
     cudaStream_t s = m->stream;
     bool ok = cudaMemcpyAsync(m->src, src, sizeof(int32_t) * n_edges, cudaMemcpyHostToDevice, s) == cudaSuccess &&
@@ -540,6 +874,8 @@ int fedfem_mpnn_create(fedfem_mpnn** out, int device, int64_t n_nodes, int64_t n
               cudaMemcpyAsync(m->out_ptr, out_ptr.data(), sizeof(int32_t) * (n_nodes + 1), cudaMemcpyHostToDevice, s) == cudaSuccess &&
               cudaMemcpyAsync(m->out_edge, out_edge.data(), sizeof(int32_t) * n_edges, cudaMemcpyHostToDevice, s) == cudaSuccess &&
               cudaMemcpyAsync(xyz_d, xyz, sizeof(double) * 3 * n_nodes, cudaMemcpyHostToDevice, s) == cudaSuccess &&
+              cudaMemcpyAsync(m->edge_tiles, tiles.data(), sizeof(EdgeTile) * tiles.size(), cudaMemcpyHostToDevice,
+                              s) == cudaSuccess &&
               cudaMemsetAsync(m->P, 0, sizeof(float) * m->nP, s) == cudaSuccess &&
               cudaMemsetAsync(m->status, 0, sizeof(int), s) == cudaSuccess;
     if (ok) {
@@ -598,6 +934,22 @@ int fedfem_mpnn_forward(fedfem_mpnn* m, int batch, const float* x_dev, float* y_
     MC(cudaSetDevice(m->device));
     if (int r = forward(m, batch, x_dev)) return r;
     MC(cudaMemcpyAsync(y_dev, m->y, sizeof(float) * batch * m->N, cudaMemcpyDeviceToDevice, m->stream));
+    return FEDFEM_OK;
+}
+
+int fedfem_mpnn_infer(fedfem_mpnn* m, int batch, const float* x_dev, float* y_dev) {
+    if (!m || !x_dev || !y_dev || batch < 1 || batch > m->Bmax) return mfail(m, FEDFEM_E_ARG, "bad batch or pointer");
+    MC(cudaSetDevice(m->device));
+    return infer(m, batch, x_dev, y_dev);
+}
+
+int fedfem_mpnn_sync(fedfem_mpnn* m) {
+    if (!m) return FEDFEM_E_ARG;
+    MC(cudaSetDevice(m->device));
+    int st = 0;
+    MC(cudaMemcpyAsync(&st, m->status, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
+    MC(cudaStreamSynchronize(m->stream));
+    if (st) return mfail(m, FEDFEM_E_TIMEOUT, "a tensor-core wait gave up");
     return FEDFEM_OK;
 }
 

@@ -126,6 +126,8 @@ _SIGS = {
     "fedfem_mpnn_features": ([C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(fedfem_material),
                               C.c_void_p], C.c_int),
     "fedfem_mpnn_forward": ([C.c_void_p, C.c_int, C.c_void_p, C.c_void_p], C.c_int),
+    "fedfem_mpnn_infer": ([C.c_void_p, C.c_int, C.c_void_p, C.c_void_p], C.c_int),
+    "fedfem_mpnn_sync": ([C.c_void_p], C.c_int),
     "fedfem_mpnn_loss_grad": ([C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_float),
                                C.POINTER(C.c_float)], C.c_int),
     "fedfem_mpnn_adam": ([C.c_void_p, C.c_float], C.c_int),
@@ -607,6 +609,14 @@ def fedfem_mpnn_features(m, batch, T_dev, q_dev, dirichlet_dev, material, x_dev)
 
 def fedfem_mpnn_forward(m, batch, x_dev, y_dev):
     _mcheck(m, _lib.fedfem_mpnn_forward(m, batch, C.c_void_p(x_dev), C.c_void_p(y_dev)))
+
+
+def fedfem_mpnn_infer(m, batch, x_dev, y_dev):
+    _mcheck(m, _lib.fedfem_mpnn_infer(m, batch, C.c_void_p(x_dev), C.c_void_p(y_dev)))
+
+
+def fedfem_mpnn_sync(m):
+    _mcheck(m, _lib.fedfem_mpnn_sync(m))
 
 
 def fedfem_mpnn_loss_grad(m, batch, x_dev, target_dev, mask_dev, want_grad=False):

@@ -106,6 +106,7 @@ class Surrogate:
         self.p, self.window, self.max_batch = p, window, max_batch
         self.N = p.n_nodes
         src, dst = graph_edges(p.conn, self.N)
+        self.n_edges = len(src)
         if length_scale is None:
             length_scale = float(np.median(np.linalg.norm(p.xyz[dst] - p.xyz[src], axis=1)))
         self.net = ff.fedfem_mpnn_create(self.N, src, dst, p.xyz, length_scale, layers=layers, max_batch=max_batch,
@@ -146,7 +147,7 @@ class Surrogate:
             Tb, qb = T[b0:b0 + self.max_batch].contiguous(), q[b0:b0 + self.max_batch].contiguous()
             B = Tb.shape[0]
             x = self._features(Tb, qb)
-            ff.fedfem_mpnn_forward(self.net, B, x.data_ptr(), self._y.data_ptr())
+            ff.fedfem_mpnn_infer(self.net, B, x.data_ptr(), self._y.data_ptr())
             out[b0:b0 + B] = Tb + self._y[:B] * self.free
         return out
 
@@ -233,4 +234,5 @@ def rollout(sur: Surrogate, ens: PlainEnsemble, q32, T0, dt: float, n_windows: i
             sur_steps += int(good.sum()) * (check_every - 1)
         T = torch.where(bad[:, None], Rp, Ts) if nbad else Ts
     torch.cuda.synchronize()
+    ff.fedfem_mpnn_sync(sur.net)   # a tensor-core wait that gave up is an error
     return RolloutResult(T, time.perf_counter() - t0, checks, rejected, sur_steps, worst)

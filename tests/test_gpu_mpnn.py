@@ -90,3 +90,34 @@ def test_gradient_is_deterministic_and_adam_lowers_the_loss(setup):
         assert losses[-1] < 0.9 * losses[0]
     finally:
         f.fedfem_mpnn_destroy(net)
+
+
+@pytest.mark.parametrize("B", [1, 3])
+def test_fused_inference_equals_training_forward(setup, B):
+    """The fused inference kernels (gathered tensor-core tiles, message sums in
+    the epilogue) round at the same points and sum in the same order as the
+    unfused training forward, so the outputs agree exactly; both also match the
+    FP64 reference within the BF16 bound of the forward test."""
+    import torch
+    s = setup
+    f = ff()
+    net = _net(s)
+    try:
+        x = s["t"]["x"][:B].contiguous()
+        y_train = torch.empty((B, s["N"]), device="cuda")
+        y_fused = torch.full((B, s["N"]), float("nan"), device="cuda")
+        f.fedfem_mpnn_forward(net, B, x.data_ptr(), y_train.data_ptr())
+        f.fedfem_mpnn_infer(net, B, x.data_ptr(), y_fused.data_ptr())
+        f.fedfem_mpnn_sync(net)
+        # a second call must not depend on state left by the first
+        y_again = torch.full((B, s["N"]), float("nan"), device="cuda")
+        f.fedfem_mpnn_infer(net, B, x.data_ptr(), y_again.data_ptr())
+        f.fedfem_mpnn_sync(net)
+    finally:
+        f.fedfem_mpnn_destroy(net)
+    diff = (y_fused - y_train).abs().max().item()
+    print(f"fused vs training forward: max|dy| = {diff:.3e}")
+    assert torch.equal(y_fused, y_again)
+    assert torch.equal(y_fused, y_train), diff
+    yref, _ = ref.forward(s["params"].astype(np.float64), s["x"][:B].astype(np.float64), s["f"], s["src"], s["dst"])
+    assert np.abs(y_fused.cpu().numpy() - yref).max() <= 2e-2 * max(1.0, np.abs(yref).max())
