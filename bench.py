@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--tile-nodes", type=int, default=0)
     ap.add_argument("--block", type=int, default=0, help="threads per block (0 = the kernel's default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="cube", choices=["cube", "planning", "surrogate"],
+    ap.add_argument("--workload", default="cube", choices=["cube", "planning", "surrogate", "suite"],
                     help="cube: the 128^3 throughput cube (default); planning: 64 uneven tet meshes x 4 "
                          "scenarios in one batched launch, compared with the plain per-run GPU path")
     ap.add_argument("--meshes", type=int, default=64)
@@ -615,6 +615,9 @@ def run_surrogate(args):
     qe32 = torch.tensor(q_ev, dtype=torch.float32, device="cuda")
     ens = PlainEnsemble(p, q_ev)
     T0 = torch.full((len(src_ev), p.n_nodes), 37.0, dtype=torch.float64, device="cuda")
+    ens.set_state(T0)
+    ens.step(dt, 1)                                 # plans the tiles outside the timed region
+    ens.state()
     # plain path alone (the reference and the timing baseline)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -664,6 +667,92 @@ def run_surrogate(args):
     print(json.dumps(line))
 
 
+def run_suite(args):
+    """Each workload of the project brief on its own (device-resident, CUDA
+    events, autotuned kernel): time per step, node-steps/s, fraction of the
+    HBM roofline by algorithmic bytes, set-up time (layout + FP64
+    pre-computation + critical step), and the error against the FP64 oracle
+    (11^3 cube) or the FP64 GPU run (larger meshes)."""
+    import torch
+    from paper_1909_05098_gb300.build import build
+    build()
+    from paper_1909_05098_gb300 import fedfem as ff
+    from paper_1909_05098_gb300.autotune import tune
+    from synth.scenarios import cube_hex_fp64, cube_hex_td_convective, ellipsoid_tet_td
+    torch.cuda.set_device(0)
+    log = lambda m: print(m, file=sys.stderr, flush=True)
+    names = {ff.KERNEL_TWO_PHASE: "two_phase", ff.KERNEL_PERSISTENT: "persistent", ff.KERNEL_TILED: "tiled",
+             ff.KERNEL_TILED_STAGED: "tiled_staged"}
+    peak = measured_peak()[0]
+    stream = torch.cuda.Stream()
+    rows = []
+
+    def measure(label, p, prec, steps, reps=3, ref=None):
+        t0 = time.perf_counter()
+        s = ff.Solver(p, precision=prec, stream=stream.cuda_stream, kernel=ff.KERNEL_PERSISTENT)
+        setup_s = time.perf_counter() - t0
+        dt = 0.5 * s.dt_cr
+        tuned = tune(s, dt, use_cache=False, stream=stream, steps=min(steps, 50))
+        s.step(dt, 1)
+        s.sync()
+        s.init()
+        s.step(dt, steps)          # warm-up
+        s.sync()
+        s.init()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        torch.cuda.synchronize()
+        for a, b in ev:
+            s.init()
+            a.record(stream)
+            s.step(dt, steps)
+            b.record(stream)
+        s.sync()
+        torch.cuda.synchronize()
+        ms = min(a.elapsed_time(b) for a, b in ev)
+        info = s.info()
+        us = 1e3 * ms / steps
+        T = s.temperature()
+        err = None
+        if ref is not None:
+            err = float(np.max(np.abs(T - ref(dt, steps))))
+        row = {"workload": label, "precision": {ff.FP64: "FP64", ff.FP32_KAHAN: "FP32+Kahan"}[prec],
+               "nodes": info["n_nodes"], "elements": info["n_elems"], "steps": steps,
+               "kernel": names[tuned["kernel"]], "tile_nodes": info["tile_nodes"],
+               "us_per_step": us, "node_steps_per_s": info["n_nodes"] / (us * 1e-6),
+               "sim_s_per_wall_s": dt / (us * 1e-6),
+               "algorithmic_gbs": info["algorithmic_bytes_per_step"] / (us * 1e3),
+               "hbm_frac": info["algorithmic_bytes_per_step"] / (us * 1e3) / peak,
+               "setup_s": setup_s, "max_err_C": err}
+        log(json.dumps(row))
+        rows.append(row)
+        s.close()
+        return dt
+
+    # 11^3 hex cube, FP64, 2000 steps, against the oracle
+    from oracle import Oracle
+    w1 = cube_hex_fp64()
+    orc = Oracle(w1.problem)
+    measure("hex cube 10^3 elements (1331 nodes)", w1.problem, ff.FP64, 2000, ref=lambda dt, n: orc.run(dt, n))
+    # tet ellipsoid 60/45/35 mm at 1 mm, FP32+Kahan and FP64, against the FP64 GPU run
+    w2 = ellipsoid_tet_td()
+
+    def gpu64(p):
+        def f(dt, n):
+            r = ff.Solver(p, precision=ff.FP64, stream=stream.cuda_stream, kernel=ff.KERNEL_TILED)
+            r.step(dt, n)
+            r.sync()
+            T = r.temperature()
+            r.close()
+            return T
+        return f
+    measure("tet ellipsoid 60/45/35 mm, h = 1 mm", w2.problem, ff.FP32_KAHAN, 1000, ref=gpu64(w2.problem))
+    measure("tet ellipsoid 60/45/35 mm, h = 1 mm", w2.problem, ff.FP64, 1000)
+    # 128^3 hex cube, FP64 variant
+    w3 = cube_hex_td_convective(n=128)
+    measure("hex cube 128^3 elements", w3.problem, ff.FP64, 200)
+    print(json.dumps({"workload": "suite", "n_gpus": 1, "data": "synthetic", "hbm_peak_gbs": peak, "rows": rows}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -672,6 +761,8 @@ def main():
         run_planning(args)
     elif args.workload == "surrogate":
         run_surrogate(args)
+    elif args.workload == "suite":
+        run_suite(args)
     else:
         run_ours(args)
 
