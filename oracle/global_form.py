@@ -11,6 +11,15 @@ time-stepping block, taken in its global matrix form):
    (the pre-computed K_b and Q_b of Section 2.3.5 in difference form);
 5. T <- T + dt R / C on free nodes (Eq. 8, Eq. 19); Dirichlet nodes keep
    their initial value (Eq. 3).
+
+Time-varying loads (the boundary/load update at the end of each step of
+Algorithm 1; the two-stage heating and relaxation of Section 3.1.5): the
+regional source part of Q is scaled by the schedule factor of the step's start
+time, Q(t) = Q_const + f(t) Q_src.  Thermal dose (the treatment-planning use
+named in Section 5; the paper gives no formula): cumulative equivalent minutes
+at 43 degC (Sapareto and Dewey, 1984), CEM43 += (dt / 60) R^(43 - T), R = 1/2
+for T >= 43 degC and 1/4 below, with T the node's temperature at the start of
+the step.
 """
 from __future__ import annotations
 
@@ -75,6 +84,13 @@ class Oracle:
         self.Q = self.V * (p.perfusion.Q_m + qr)
         if len(p.flux_nodes):
             np.add.at(self.Q, np.asarray(p.flux_nodes, dtype=np.int64), np.asarray(p.flux_q, dtype=np.float64))
+        # split for time-varying sources: Q(t) = Q_const + f(t) Q_src
+        self.sched_end = np.asarray(p.schedule_end, dtype=np.float64)
+        self.sched_f = np.asarray(p.schedule_factor, dtype=np.float64)
+        self.Q_src = self.V * qr
+        self.Q_const = self.V * p.perfusion.Q_m
+        if len(p.flux_nodes):
+            np.add.at(self.Q_const, np.asarray(p.flux_nodes, dtype=np.int64), np.asarray(p.flux_q, dtype=np.float64))
         self.free = np.ones(N, dtype=bool)
         self.free[np.asarray(p.dirichlet_nodes, dtype=np.int64)] = False
         # sparsity pattern of K: one entry per (row, col) pair met in any element
@@ -120,24 +136,47 @@ class Oracle:
             T[np.asarray(self.p.dirichlet_nodes, dtype=np.int64)] = self.p.dirichlet_T
         return T
 
-    def rate(self, T) -> np.ndarray:
-        """R = -K(T) T + beta (T_a - T) + Q + hA (T_inf - T)  (W per node)."""
+    def schedule_factor(self, t: float) -> float:
+        """f(t): the factor of the segment that contains t (the last one after its end)."""
+        if len(self.sched_f) == 0:
+            return 1.0
+        k = int(np.searchsorted(self.sched_end, t, side="right"))
+        return float(self.sched_f[min(k, len(self.sched_f) - 1)])
+
+    def nodal_load(self, t: float) -> np.ndarray:
+        if len(self.sched_f) == 0:
+            return self.Q
+        return self.Q_const + self.schedule_factor(t) * self.Q_src
+
+    def rate(self, T, t: float = 0.0) -> np.ndarray:
+        """R = -K(T) T + beta (T_a - T) + Q(t) + hA (T_inf - T)  (W per node)."""
         K = self.assemble_K(self.element_conductivity(T))
         F = self.conduction_load(K, T)
         pf = self.p.perfusion
-        return -F + self.beta * (pf.T_a - T) + self.Q + self.hA * (self.p.conv_T_inf - T)
+        return -F + self.beta * (pf.T_a - T) + self.nodal_load(t) + self.hA * (self.p.conv_T_inf - T)
 
     def capacitance(self, T) -> np.ndarray:
         return self.V * self.rho_of(T) * self.c_of(T)
 
-    def step(self, T, dt: float) -> np.ndarray:
-        """One explicit Euler step (Eq. 6, Eq. 8) with lumped C."""
-        Tn = T + dt * self.rate(T) / self.capacitance(T)
+    def step(self, T, dt: float, t: float = 0.0) -> np.ndarray:
+        """One explicit Euler step (Eq. 6, Eq. 8) with lumped C, from time t."""
+        Tn = T + dt * self.rate(T, t) / self.capacitance(T)
         Tn[~self.free] = T[~self.free]
         return Tn
 
-    def run(self, dt: float, n_steps: int, T=None) -> np.ndarray:
+    def run(self, dt: float, n_steps: int, T=None, dose: bool = False):
+        """n_steps steps from t = 0; with dose=True also returns CEM43 (minutes)."""
         T = self.initial_field() if T is None else np.array(T, dtype=np.float64)
-        for _ in range(n_steps):
-            T = self.step(T, dt)
-        return T
+        D = np.zeros(self.N)
+        for k in range(n_steps):
+            if dose:
+                D = D + cem43_increment(T, dt)
+            T = self.step(T, dt, k * dt)
+        return (T, D) if dose else T
+
+
+def cem43_increment(T, dt: float) -> np.ndarray:
+    """(dt / 60) R^(43 - T) minutes, R = 1/2 at or above 43 degC, 1/4 below."""
+    T = np.asarray(T, dtype=np.float64)
+    R = np.where(T >= 43.0, 0.5, 0.25)
+    return (dt / 60.0) * R ** (43.0 - T)

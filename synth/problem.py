@@ -86,6 +86,12 @@ class Problem:
     T0: float | np.ndarray = 37.0
     T_lo: float = 0.0                    # declared admissible temperature range
     T_hi: float = 100.0
+    # time-varying regional sources (Algorithm 1 updates the loads every step):
+    # the regional source density is multiplied by schedule_factor[k] while the
+    # step's start time t lies in [schedule_end[k-1], schedule_end[k]); after the
+    # last end the last factor holds.  Empty: sources always on.
+    schedule_end: np.ndarray = field(default_factory=lambda: np.zeros(0, np.float64))
+    schedule_factor: np.ndarray = field(default_factory=lambda: np.zeros(0, np.float64))
 
     @property
     def n_nodes(self) -> int:

@@ -61,21 +61,28 @@ def test_every_kernel_and_order_is_bit_identical(cube):
 
 @pytest.mark.parametrize("n_steps", [1, 2, 7])
 def test_tiled_kernel_odd_even_steps_and_tets(n_steps):
-    """The tiled kernel double-buffers T; any step count must leave the same
-    state as the other kernels, for hex and tet meshes and several tile sizes."""
+    """The tiled kernels double-buffer T; any step count must leave the same
+    state as the other kernels, for hex and tet meshes, several tile sizes
+    (some larger than the block, so threads own more than one node) and every
+    block size the staged kernel is built for."""
     f = ff()
     for w in (cube_hex_td_convective(n=14), ellipsoid_tet_td(h=2e-3, axes=(0.024, 0.018, 0.014))):
         p = w.problem
         dt = 0.5 * critical_dt(Oracle(p))
         base, _ = run_gpu(p, dt, n_steps, f.FP32_KAHAN, kernel=f.KERNEL_PERSISTENT)
-        for kern, B in ((f.KERNEL_TILED, 0), (f.KERNEL_TILED, 64), (f.KERNEL_TILED, 160),
-                        (f.KERNEL_TILED_STAGED, 0), (f.KERNEL_TILED_STAGED, 96)):
+        # hex tiles larger than the block (threads own two nodes); tets (about 24
+        # elements per node) with smaller tiles so that the load table fits
+        big = ((f.KERNEL_TILED_STAGED, 0, 1000), (f.KERNEL_TILED_STAGED, 1024, 1280)) if p.elem_type == 8 else \
+              ((f.KERNEL_TILED_STAGED, 1024, 200),)
+        for kern, blk, B in ((f.KERNEL_TILED, 0, 0), (f.KERNEL_TILED, 0, 64), (f.KERNEL_TILED, 0, 160),
+                             (f.KERNEL_TILED_STAGED, 0, 0), (f.KERNEL_TILED_STAGED, 0, 96),
+                             (f.KERNEL_TILED_STAGED, 256, 72)) + big:
             s = f.Solver(p, precision=f.FP32_KAHAN)
             try:
-                f.fedfem_set_tile(s.ctx, kern, 0, B, 0)
+                f.fedfem_set_tile(s.ctx, kern, blk, B, 0)
                 s.step(dt, n_steps)
                 assert s.sync() == n_steps
-                assert np.array_equal(s.temperature(), base), (p.elem_type, kern, B, n_steps)
+                assert np.array_equal(s.temperature(), base), (p.elem_type, kern, blk, B, n_steps)
                 s.step(dt, 3)        # continue after an odd/even count
                 s.sync()
             finally:
