@@ -18,6 +18,7 @@ data-parallel split), value = all ranks' node-steps / max rank time.
 from __future__ import annotations
 
 import argparse
+import copy
 import hashlib
 import json
 import os
@@ -687,9 +688,9 @@ def run_suite(args):
     stream = torch.cuda.Stream()
     rows = []
 
-    def measure(label, p, prec, steps, reps=3, ref=None):
+    def measure(label, p, prec, steps, reps=3, ref=None, dose=False):
         t0 = time.perf_counter()
-        s = ff.Solver(p, precision=prec, stream=stream.cuda_stream, kernel=ff.KERNEL_PERSISTENT)
+        s = ff.Solver(p, precision=prec, stream=stream.cuda_stream, kernel=ff.KERNEL_PERSISTENT, dose=dose)
         setup_s = time.perf_counter() - t0
         dt = 0.5 * s.dt_cr
         tuned = tune(s, dt, use_cache=False, stream=stream, steps=min(steps, 50))
@@ -750,6 +751,10 @@ def run_suite(args):
     # 128^3 hex cube, FP64 variant
     w3 = cube_hex_td_convective(n=128)
     measure("hex cube 128^3 elements", w3.problem, ff.FP64, 200)
+    # the same cube, FP32+Kahan, with time-varying sources (heating, then off) and the CEM43 dose
+    p3 = copy.copy(w3.problem)
+    p3.schedule_end, p3.schedule_factor = np.array([150.0, 1e30]), np.array([1.0, 0.0])
+    measure("hex cube 128^3 elements, two-stage sources + CEM43 dose", p3, ff.FP32_KAHAN, 200, dose=True)
     print(json.dumps({"workload": "suite", "n_gpus": 1, "data": "synthetic", "hbm_peak_gbs": peak, "rows": rows}))
 
 

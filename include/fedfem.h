@@ -172,6 +172,35 @@ int fedfem_set_convective(fedfem_ctx* ctx, int64_t n_faces, int nverts, const in
  * paper applies it).  Repeated nodes add. */
 int fedfem_set_nodal_flux(fedfem_ctx* ctx, int64_t n, const int32_t* nodes, const double* q_W);
 
+/* Time-varying regional sources: Algorithm 1 updates the loads after every
+ * step; Section 3.1.5 heats for 3 s and then relaxes with the sources
+ * removed.  The regional source part of each node's load (Gaussian sources
+ * and fedfem_set_source densities, every lane) is multiplied by factor[k]
+ * for steps whose start time t lies in [t_end[k-1], t_end[k]) (t_end[-1] =
+ * -inf); after t_end[n-1] the last factor holds.  Metabolic heat and nodal
+ * flows stay constant.  t is the simulated time since fedfem_init.  n = 0
+ * removes the schedule.  At most 8 segments; t_end strictly increasing
+ * (E_ARG otherwise).  Host arrays, copied.  Takes effect at the next
+ * fedfem_precompute (call order: set_* -> precompute).  A context with a
+ * schedule cannot capture a CUDA graph (E_UNSUPPORTED): the start time of
+ * each call is a launch argument. */
+int fedfem_set_source_schedule(fedfem_ctx* ctx, int n, const double* t_end, const double* factor);
+
+/* Thermal dose (the treatment-planning use Section 5 names; the paper gives
+ * no formula): cumulative equivalent minutes at 43 degC of Sapareto and
+ * Dewey, CEM43 += (dt / 60) R^(43 - T) with R = 1/2 at or above 43 degC and
+ * 1/4 below, T the node's temperature at the start of each step (the hi part
+ * in FP32+Kahan), accumulated in FP64 inside the node update of every
+ * kernel.  on != 0 enables it from the next fedfem_precompute (single-lane
+ * contexts only: E_UNSUPPORTED there otherwise); fedfem_init resets it to 0;
+ * checkpoints carry it. */
+int fedfem_enable_dose(fedfem_ctx* ctx, int on);
+/* CEM43 in minutes, n_nodes doubles in input node order (caller-owned host
+ * buffer).  Dirichlet nodes report their fixed temperature held for the
+ * elapsed simulated time.  Waits for the context's stream.  E_STATE if the
+ * dose is not enabled or before fedfem_init. */
+int fedfem_read_dose(fedfem_ctx* ctx, double* out);
+
 /* Pre-computation (the first stage of Algorithm 1) in FP64 on the GPU: element
  * geometry and A_e (Eq. 16), lumped volumes, perfusion and source loads, face
  * areas, and the critical step of Eq. 9 for properties anywhere in

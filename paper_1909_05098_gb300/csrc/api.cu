@@ -42,6 +42,8 @@ struct fedfem_ctx {
     int conv_nv = 0;
     double conv_h = 0.0, conv_Tinf = 0.0;
     std::vector<double> flux;                     // empty: none
+    std::vector<double> sched_end, sched_f;       // source schedule (empty: sources always on)
+    bool dose_on = false;
     fedfem_tile tile{FEDFEM_KERNEL_PERSISTENT, 256, 0, 0};
     // ---- pre-computed ----
     bool pre = false, inited = false;
@@ -55,8 +57,9 @@ struct fedfem_ctx {
     double* M64 = nullptr;
     float* M32 = nullptr;
     int32_t *sell_off = nullptr, *sell_ids = nullptr;
-    double *V64 = nullptr, *Q64 = nullptr, *hA64 = nullptr;
-    float *V32 = nullptr, *Q32 = nullptr, *hA32 = nullptr;
+    double *V64 = nullptr, *Q64 = nullptr, *hA64 = nullptr, *Qs64 = nullptr;
+    float *V32 = nullptr, *Q32 = nullptr, *hA32 = nullptr, *Qs32 = nullptr;
+    double* dose = nullptr;                       // CEM43 minutes per free node
     void* T = nullptr;
     void* T2 = nullptr;
     float* Tlo = nullptr;
@@ -122,7 +125,8 @@ void free_device(fedfem_ctx* c) {
     c->allocs.clear();
     c->dev_bytes = 0;
     c->conn4 = nullptr; c->M64 = nullptr; c->M32 = nullptr; c->sell_off = c->sell_ids = nullptr;
-    c->V64 = c->Q64 = c->hA64 = nullptr; c->V32 = c->Q32 = c->hA32 = nullptr;
+    c->V64 = c->Q64 = c->hA64 = c->Qs64 = nullptr; c->V32 = c->Q32 = c->hA32 = c->Qs32 = nullptr;
+    c->dose = nullptr;
     c->T = nullptr; c->T2 = nullptr; c->Tlo = nullptr; c->slots = nullptr; c->node_of = nullptr; c->T_dir = nullptr;
     c->io = nullptr; c->st = nullptr;
     c->pre = false;
@@ -187,8 +191,19 @@ int reset_status(fedfem_ctx* c) {
 }
 
 template <typename R, typename L = R>
-StepArgs<R, L> make_args(fedfem_ctx* c, const R* M, const R* V, const R* Q, const R* hA, double dt) {
+StepArgs<R, L> make_args(fedfem_ctx* c, const R* M, const R* V, const R* Q, const R* hA, double dt,
+                         const R* Qs = nullptr) {
     StepArgs<R, L> a{};
+    a.Qs = c->sched_f.empty() ? nullptr : (const L*)Qs;
+    a.t0 = c->sim_time;
+    a.dtd = dt;
+    a.n_seg = (int)c->sched_f.size();
+    for (int k = 0; k < a.n_seg; ++k) {
+        a.seg_end[k] = c->sched_end[k];
+        a.seg_f[k] = (R)c->sched_f[k];
+    }
+    a.dose = c->dose;
+    a.dose_dt = dt / 60.0;
     a.E = c->E; a.N = c->N; a.N_plain = c->L.N_plain; a.N_free = c->L.N_free;
     a.conn4 = c->conn4; a.M = M; a.slots = (R*)c->slots;
     a.sell_off = c->sell_off; a.sell_ids = c->sell_ids;
@@ -370,22 +385,22 @@ cudaError_t launch_all(fedfem_ctx* c, double dt, int64_t n_steps, LaunchCfg& cfg
     const bool tiled = cfg.kernel == FEDFEM_KERNEL_TILED || cfg.kernel == FEDFEM_KERNEL_TILED_STAGED;
     if (tiled) {
         if (c->precision == FEDFEM_FP64) {
-            StepArgs<double> a = make_args<double>(c, c->M64, c->V64, c->Q64, c->hA64, dt);
+            StepArgs<double> a = make_args<double>(c, c->M64, c->V64, c->Q64, c->hA64, dt, c->Qs64);
             return launch_tiled_f64(a, make_tile_args<double>(c), n_steps, cfg, c->stream);
         }
         const bool kahan = c->precision == FEDFEM_FP32_KAHAN;
         if (c->n_lanes == 4) {
-            StepArgs<float, F4> a = make_args<float, F4>(c, c->M32, c->V32, c->Q32, c->hA32, dt);
+            StepArgs<float, F4> a = make_args<float, F4>(c, c->M32, c->V32, c->Q32, c->hA32, dt, c->Qs32);
             return launch_tiled_f32x4(a, make_tile_args<float>(c), kahan, n_steps, cfg, c->stream);
         }
-        StepArgs<float> a = make_args<float>(c, c->M32, c->V32, c->Q32, c->hA32, dt);
+        StepArgs<float> a = make_args<float>(c, c->M32, c->V32, c->Q32, c->hA32, dt, c->Qs32);
         return launch_tiled_f32(a, make_tile_args<float>(c), kahan, n_steps, cfg, c->stream);
     }
     if (c->precision == FEDFEM_FP64) {
-        StepArgs<double> a = make_args<double>(c, c->M64, c->V64, c->Q64, c->hA64, dt);
+        StepArgs<double> a = make_args<double>(c, c->M64, c->V64, c->Q64, c->hA64, dt, c->Qs64);
         return launch_steps_f64(a, c->nv, n_steps, cfg, c->stream);
     }
-    StepArgs<float> a = make_args<float>(c, c->M32, c->V32, c->Q32, c->hA32, dt);
+    StepArgs<float> a = make_args<float>(c, c->M32, c->V32, c->Q32, c->hA32, dt, c->Qs32);
     return launch_steps_f32(a, c->nv, c->precision == FEDFEM_FP32_KAHAN, n_steps, cfg, c->stream);
 }
 
@@ -660,6 +675,46 @@ int fedfem_set_nodal_flux(fedfem_ctx* c, int64_t n, const int32_t* nodes, const 
     return FEDFEM_OK;
 }
 
+int fedfem_set_source_schedule(fedfem_ctx* c, int n, const double* t_end, const double* factor) {
+    if (!c) return FEDFEM_E_ARG;
+    if (n < 0 || n > kMaxSegments || (n > 0 && (!t_end || !factor)))
+        return fail(c, FEDFEM_E_ARG, "schedule: 0.." + std::to_string(kMaxSegments) + " segments");
+    for (int k = 0; k < n; ++k) {
+        if (!is_finite(factor[k]) || std::isnan(t_end[k])) return fail(c, FEDFEM_E_ARG, "schedule: bad value");
+        if (k > 0 && !(t_end[k] > t_end[k - 1])) return fail(c, FEDFEM_E_ARG, "schedule: ends must increase");
+    }
+    c->sched_end.assign(t_end, t_end + n);
+    c->sched_f.assign(factor, factor + n);
+    invalidate(c);
+    return FEDFEM_OK;
+}
+
+int fedfem_enable_dose(fedfem_ctx* c, int on) {
+    if (!c) return FEDFEM_E_ARG;
+    c->dose_on = on != 0;
+    invalidate(c);
+    return FEDFEM_OK;
+}
+
+int fedfem_read_dose(fedfem_ctx* c, double* out) {
+    if (!c || !out) return fail(c, FEDFEM_E_ARG, "null output");
+    if (!c->dose) return fail(c, FEDFEM_E_STATE, "enable the dose before fedfem_precompute");
+    if (!c->inited) return fail(c, FEDFEM_E_STATE, "init first");
+    CU(cudaSetDevice(c->device), "set device");
+    const int64_t NF = c->L.N_free;
+    std::vector<double> d(std::max<int64_t>(1, NF));
+    CU(cudaStreamSynchronize(c->stream), "dose read");
+    CU(cudaMemcpy(d.data(), c->dose, sizeof(double) * NF, cudaMemcpyDeviceToHost), "dose read");
+    for (int64_t i = 0; i < NF; ++i) out[c->L.node_of[i]] = d[i];
+    // Dirichlet nodes sit at their fixed temperature for the whole elapsed time
+    for (int64_t i = NF; i < c->N; ++i) {
+        const int64_t o = c->L.node_of[i];
+        const double T = c->dir_T[o];
+        out[o] = c->sim_time / 60.0 * std::exp2(T >= 43.0 ? T - 43.0 : 2.0 * (T - 43.0));
+    }
+    return FEDFEM_OK;
+}
+
 int fedfem_set_tile(fedfem_ctx* c, const fedfem_tile* t) {
     if (!c || !t) return fail(c, FEDFEM_E_ARG, "null tile");
     if (t->kernel < FEDFEM_KERNEL_TWO_PHASE || t->kernel > FEDFEM_KERNEL_TILED_STAGED) return fail(c, FEDFEM_E_ARG, "unknown kernel");
@@ -822,6 +877,19 @@ int fedfem_precompute(fedfem_ctx* c, double T_lo, double T_hi, double* dt_cr_out
         return fail(c, FEDFEM_E_MESH, "element " + std::to_string(in_e) + " has det J <= 0 (inverted or degenerate)");
     }
     CU(launch_nodal(pa, st), "nodal kernel");
+    if (!c->sched_f.empty()) {   // time-varying sources: Q = constant part, Qs = source part
+        CU(dalloc(c, &c->Qs64, sizeof(double) * NF * NL), "alloc");
+        PreArgs ps = pa;
+        ps.Q = c->Qs64; ps.Q_m = 0.0; ps.flux_node = nullptr;
+        CU(launch_nodal(ps, st), "nodal kernel");
+        PreArgs pc = pa;
+        pc.qr_node = nullptr; pc.n_src = 0;
+        CU(launch_nodal(pc, st), "nodal kernel");
+    }
+    if (c->dose_on) {
+        if (NL != 1) return fail(c, FEDFEM_E_UNSUPPORTED, "thermal dose needs a single-lane context");
+        CU(dalloc(c, &c->dose, sizeof(double) * std::max<int64_t>(1, NF)), "alloc");
+    }
     CU(cudaStreamSynchronize(st), "nodal kernel");
     LanczosResult lr;
     std::string lm = lanczos_lambda_max(pa, c->mat.k0, c->mat.rho0 * c->mat.c0, c->perf.w_b * c->perf.c_b,
@@ -847,6 +915,10 @@ int fedfem_precompute(fedfem_ctx* c, double T_lo, double T_hi, double* dt_cr_out
         CU(launch_to_f32(c->V64, c->V32, NF, st), "convert");
         CU(launch_pack_lanes(c->Q64, c->Q32, NL, NF, st), "convert");
         CU(launch_to_f32(c->hA64, c->hA32, NC, st), "convert");
+        if (c->Qs64) {
+            CU(dalloc(c, &c->Qs32, sizeof(float) * NF * NL), "alloc");
+            CU(launch_pack_lanes(c->Qs64, c->Qs32, NL, NF, st), "convert");
+        }
         CU(dalloc(c, (float**)&c->T, sizeof(float) * N * NL), "alloc");
         CU(dalloc(c, (float**)&c->T2, sizeof(float) * N * NL), "alloc");
         CU(dalloc(c, &c->Tlo, sizeof(float) * N * NL), "alloc");
@@ -869,6 +941,7 @@ int fedfem_precompute(fedfem_ctx* c, double T_lo, double T_hi, double* dt_cr_out
         release(c, c->V64, sizeof(double) * NF); c->V64 = nullptr;
         release(c, c->Q64, sizeof(double) * NF * NL); c->Q64 = nullptr;
         release(c, c->hA64, sizeof(double) * NC); c->hA64 = nullptr;
+        if (c->Qs64) { release(c, c->Qs64, sizeof(double) * NF * NL); c->Qs64 = nullptr; }
     }
     c->pre = true;
     c->inited = false;
@@ -891,6 +964,8 @@ static int init_common(fedfem_ctx* c, bool per_lane = false) {
                          c->stream),
        "init kernel");
     if (int r = mirror_T(c)) return r;
+    if (c->dose)
+        CU(cudaMemsetAsync(c->dose, 0, sizeof(double) * std::max<int64_t>(1, c->L.N_free), c->stream), "dose reset");
     int r = reset_status(c);
     if (r) return r;
     c->inited = true;
@@ -968,6 +1043,8 @@ int fedfem_capture_graph(fedfem_ctx* c, double dt, int64_t n_steps) {
     if (!c->inited) return fail(c, FEDFEM_E_STATE, "init first");
     if (!(dt > 0) || !is_finite(dt) || n_steps <= 0) return fail(c, FEDFEM_E_ARG, "need dt > 0 and n_steps > 0");
     if (!(dt < c->dt_cr)) return fail(c, FEDFEM_E_UNSTABLE_DT, "dt >= critical step " + std::to_string(c->dt_cr));
+    if (!c->sched_f.empty())
+        return fail(c, FEDFEM_E_UNSUPPORTED, "a graph fixes the start time; step a source schedule with fedfem_step");
     CU(cudaSetDevice(c->device), "set device");
     LaunchCfg cfg;
     if (int r = prepare_launch(c, cfg)) return r;   // tiles are planned outside the capture
@@ -1072,17 +1149,19 @@ int fedfem_get_state(fedfem_ctx* c, void* buf, size_t* bytes) {
     if (!c->inited) return fail(c, FEDFEM_E_STATE, "init first");
     const size_t tb = (c->precision == FEDFEM_FP64 ? sizeof(double) : sizeof(float)) * c->N * c->n_lanes;
     const size_t lb = (c->precision == FEDFEM_FP64 ? 0 : sizeof(float) * c->N * c->n_lanes);
-    const size_t need = sizeof(StateHeader) + tb + lb;
+    const size_t db = c->dose ? sizeof(double) * c->L.N_free : 0;
+    const size_t need = sizeof(StateHeader) + tb + lb + db;
     if (!buf) { *bytes = need; return FEDFEM_OK; }
     if (*bytes < need) return fail(c, FEDFEM_E_ARG, "state buffer too small");
     int64_t done = 0;
     int rc = fedfem_sync(c, &done);
     if (rc) return rc;
-    StateHeader h{kMagic, 1, c->precision, c->N, c->E, c->order, c->nv, done, c->sim_time, tb + lb};
+    StateHeader h{kMagic, 1, c->precision, c->N, c->E, c->order, c->nv, done, c->sim_time, tb + lb + db};
     std::memcpy(buf, &h, sizeof(h));
     char* p = (char*)buf + sizeof(h);
     CU(cudaMemcpy(p, c->T, tb, cudaMemcpyDeviceToHost), "state copy");
     if (lb) CU(cudaMemcpy(p + tb, c->Tlo, lb, cudaMemcpyDeviceToHost), "state copy");
+    if (db) CU(cudaMemcpy(p + tb + lb, c->dose, db, cudaMemcpyDeviceToHost), "state copy");
     *bytes = need;
     return FEDFEM_OK;
 }
@@ -1095,13 +1174,15 @@ int fedfem_set_state(fedfem_ctx* c, const void* buf, size_t bytes) {
     std::memcpy(&h, buf, sizeof(h));
     const size_t tb = (c->precision == FEDFEM_FP64 ? sizeof(double) : sizeof(float)) * c->N * c->n_lanes;
     const size_t lb = (c->precision == FEDFEM_FP64 ? 0 : sizeof(float) * c->N * c->n_lanes);
+    const size_t db = c->dose ? sizeof(double) * c->L.N_free : 0;
     if (h.magic != kMagic || h.version != 1 || h.precision != c->precision || h.N != c->N || h.E != c->E ||
-        h.order != c->order || h.nv != c->nv || h.payload != tb + lb || bytes < sizeof(h) + tb + lb)
+        h.order != c->order || h.nv != c->nv || h.payload != tb + lb + db || bytes < sizeof(h) + tb + lb + db)
         return fail(c, FEDFEM_E_ARG, "state does not match this context");
     CU(cudaSetDevice(c->device), "set device");
     const char* p = (const char*)buf + sizeof(h);
     CU(cudaMemcpy(c->T, p, tb, cudaMemcpyHostToDevice), "state copy");
     if (lb) CU(cudaMemcpy(c->Tlo, p + tb, lb, cudaMemcpyHostToDevice), "state copy");
+    if (db) CU(cudaMemcpy(c->dose, p + tb + lb, db, cudaMemcpyHostToDevice), "state copy");
     if (int m = mirror_T(c)) return m;
     int r = reset_status(c);
     if (r) return r;
@@ -1129,6 +1210,9 @@ int fedfem_get_info(fedfem_ctx* c, fedfem_info* info) {
     const int64_t E = c->E, NF = L.N_free, NC = L.N_free - L.N_plain;
     const int64_t NL = c->n_lanes;   // lanes share V, hA and the element data
     info->algorithmic_bytes_per_step = E * (4 * c->nv + 6 * R) + NF * (NL * (node_state + R) + R) + NC * R;
+    // a source schedule reads the source part of Q too; the dose is read and written in FP64
+    const int64_t extra = (c->sched_f.empty() ? 0 : NF * NL * R) + (c->dose ? NF * 16 : 0);
+    info->algorithmic_bytes_per_step += extra;
     // two-phase / persistent model: + slot write and read, gather ids, slice offsets, T gather read once
     info->bytes_per_step = info->algorithmic_bytes_per_step + E * c->nv * 2 * R + (int64_t)L.sell_ids.size() * 4 +
                            (int64_t)L.sell_off.size() * 4;
@@ -1136,7 +1220,8 @@ int fedfem_get_info(fedfem_ctx* c, fedfem_info* info) {
         const Tiles& t = c->tiles_host;
         // every packed block once, halo values, owned T read; then T written, lo read+write, V, Q, hA
         const int64_t node_rest = NF * (NL * (node_state - R + R) + R) + NC * R;
-        info->bytes_per_step = c->t_block_bytes + (int64_t)t.halo.size() * R * NL + NF * R * NL + node_rest;
+        info->bytes_per_step =
+            c->t_block_bytes + (int64_t)t.halo.size() * R * NL + NF * R * NL + node_rest + extra;
     }
     info->sm_count = c->sm_count;
     info->grid_blocks = c->last.grid_used;

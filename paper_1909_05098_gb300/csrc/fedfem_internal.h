@@ -93,6 +93,8 @@ struct DevStatus {
 // ---------------------------------------------------------------------------
 // R: type of the element matrices and node constants; L: type of one node's
 // temperature state -- R itself, or F4 for four scenario lanes.
+constexpr int kMaxSegments = 8;   // pieces of a source schedule
+
 template <typename R, typename L = R>
 struct StepArgs {
     int64_t E, N, N_plain, N_free;
@@ -112,6 +114,17 @@ struct StepArgs {
     R dt, T_lo, T_hi;
     DevStatus* status;
     long long step0;                 // step index (since init) of the first step of this call
+    // time-varying regional sources: Q(t) = Q + f(t) Qs with Q the constant part;
+    // f(t) = seg_f[k] for the first k with t < seg_end[k] (the last one after the
+    // last end), t the step's start time t0 + (step - step0) dt.  Qs null: Q is total.
+    const L* Qs;
+    double t0, dtd;
+    int n_seg;
+    double seg_end[kMaxSegments];
+    R seg_f[kMaxSegments];
+    // CEM43 thermal dose (one lane): dose[i] += dose_dt R^(43 - T_i), minutes
+    double* dose;
+    double dose_dt;                  // dt / 60
 };
 
 // Launchers (step.cu).  mode: FEDFEM_FP64 / FEDFEM_FP32_KAHAN / FEDFEM_FP32_PLAIN.

@@ -94,6 +94,15 @@ __device__ __forceinline__ NodeVals<R, L> node_load(const StepArgs<R, L>& a, int
     return v;
 }
 
+// f(t) of the source schedule for the step with index `step`
+template <typename R, typename L>
+__device__ __forceinline__ R schedule_factor(const StepArgs<R, L>& a, long long step) {
+    const double t = a.t0 + (double)(step - a.step0) * a.dtd;
+    int k = 0;
+    while (k + 1 < a.n_seg && t >= a.seg_end[k]) ++k;
+    return a.seg_f[k];
+}
+
 template <typename R, typename L, bool KAHAN>
 __device__ __forceinline__ void node_update_v(const StepArgs<R, L>& a, int64_t i, L T, L F,
                                               const NodeVals<R, L>& v, L* Tout, long long step) {
@@ -101,7 +110,15 @@ __device__ __forceinline__ void node_update_v(const StepArgs<R, L>& a, int64_t i
     const L rho = fmadd(a.drho, u, a.rho0);
     const L c = fmadd(a.dc, u, a.c0);
     const L C = (v.V * rho) * c;
-    L r = fmadd(a.wbcb * v.V, a.T_a - T, v.Q) - F;
+    L q = v.Q;
+    if (a.Qs) q = fmadd(schedule_factor(a, step), a.Qs[i], q);
+    if constexpr (sizeof(L) == sizeof(R)) {   // CEM43 at the step's start temperature (one lane)
+        if (a.dose) {
+            const double Td = (double)T;
+            a.dose[i] += a.dose_dt * exp2(Td >= 43.0 ? Td - 43.0 : 2.0 * (Td - 43.0));
+        }
+    }
+    L r = fmadd(a.wbcb * v.V, a.T_a - T, q) - F;
     if (i >= a.N_plain) r = fmadd(v.hA, a.T_inf - T, r);
     const L dT = (a.dt * r) / C;
     L Tn;

@@ -108,6 +108,9 @@ _SIGS = {
     "fedfem_plan_layout": ([C.c_int, _i64, _dp, _i64, _ip, _ip, C.c_int, _i64, _ip, _i64, C.c_int, _ip, C.c_int,
                             C.POINTER(fedfem_layout_info)] + [C.c_void_p] * 10, C.c_int),
     "fedfem_set_lanes": ([_ctx_p, C.c_int], C.c_int),
+    "fedfem_set_source_schedule": ([_ctx_p, C.c_int, _dp, _dp], C.c_int),
+    "fedfem_enable_dose": ([_ctx_p, C.c_int], C.c_int),
+    "fedfem_read_dose": ([_ctx_p, _dp], C.c_int),
     "fedfem_add_gaussian_source_lane": ([_ctx_p, C.c_int, C.c_int, _dp, C.c_double, C.c_double], C.c_int),
     "fedfem_set_source_lane": ([_ctx_p, C.c_int, _dp], C.c_int),
     "fedfem_read_temperature_lane": ([_ctx_p, C.c_int, _dp], C.c_int),
@@ -424,6 +427,25 @@ def fedfem_step_static(elem_type, n_nodes, n_elems, xyz_dev, conn_dev, row_ptr_d
 
 # ---- convenience wrapper ------------------------------------------------------
 
+def fedfem_set_source_schedule(ctx, t_end, factor):
+    e, pe = _d(np.asarray(t_end, dtype=np.float64).reshape(-1))
+    f, pf = _d(np.asarray(factor, dtype=np.float64).reshape(-1))
+    if e.shape != f.shape:
+        raise ValueError("t_end and factor differ in length")
+    _check(ctx, _lib.fedfem_set_source_schedule(ctx, e.shape[0], pe, pf))
+
+
+def fedfem_enable_dose(ctx, on=True):
+    _check(ctx, _lib.fedfem_enable_dose(ctx, 1 if on else 0))
+
+
+def fedfem_read_dose(ctx) -> np.ndarray:
+    n = fedfem_get_info(ctx)["n_nodes"]
+    out = np.empty(n, dtype=np.float64)
+    _check(ctx, _lib.fedfem_read_dose(ctx, out.ctypes.data_as(C.POINTER(C.c_double))))
+    return out
+
+
 class Solver:
     """One problem on one GPU: set-up, pre-computation, initial field.
 
@@ -433,7 +455,7 @@ class Solver:
     _T_inf, flux_nodes/_q, T0, T_lo, T_hi."""
 
     def __init__(self, problem, precision=FP32_KAHAN, device=0, stream=None, order=ORDER_MORTON,
-                 kernel=KERNEL_PERSISTENT, T_lo=None, T_hi=None):
+                 kernel=KERNEL_PERSISTENT, T_lo=None, T_hi=None, dose=False):
         self.ctx = fedfem_create(device, precision, stream)
         self.problem = problem
         try:
@@ -454,6 +476,10 @@ class Solver:
                 fedfem_set_convective(self.ctx, p.conv_faces, p.conv_h, p.conv_T_inf)
             if len(p.flux_nodes):
                 fedfem_set_nodal_flux(self.ctx, p.flux_nodes, p.flux_q)
+            if len(getattr(p, "schedule_factor", ())):
+                fedfem_set_source_schedule(self.ctx, p.schedule_end, p.schedule_factor)
+            if dose:
+                fedfem_enable_dose(self.ctx, True)
             fedfem_set_tile(self.ctx, kernel)
             self.dt_cr = fedfem_precompute(self.ctx, p.T_lo if T_lo is None else T_lo,
                                            p.T_hi if T_hi is None else T_hi)
@@ -479,6 +505,10 @@ class Solver:
 
     def temperature(self):
         return fedfem_read_temperature(self.ctx)
+
+    def dose(self):
+        """CEM43 minutes per node (input order); needs dose=True."""
+        return fedfem_read_dose(self.ctx)
 
     def info(self):
         return fedfem_get_info(self.ctx)
@@ -506,7 +536,7 @@ class Batch:
     its last one in the unused lanes.  All runs share one dt (the smallest
     critical step) and all materials/perfusion/film parameters must agree."""
 
-    def __init__(self, meshes, precision=FP32_KAHAN, device=0, stream=None, kernel=KERNEL_TILED):
+    def __init__(self, meshes, precision=FP32_KAHAN, device=0, stream=None, kernel=KERNEL_TILED, schedule=None):
         self.meshes = meshes
         first = meshes[0][0]
         xyz, conn, groups, dn, dT = [], [], [], [], []
@@ -538,6 +568,8 @@ class Batch:
                     p = scen[min(lane, len(scen) - 1)]
                     for s in p.sources:    # restricted to mesh g's nodes (group g)
                         fedfem_add_gaussian_source_lane(self.ctx, lane, g, s.x0, s.sigma, s.peak)
+            if schedule is not None:       # (t_end, factor): every run's sources follow it
+                fedfem_set_source_schedule(self.ctx, *schedule)
             fedfem_set_tile(self.ctx, kernel)
             self.dt_cr = fedfem_precompute(self.ctx, min(p[0].T_lo for p in meshes),
                                            max(p[0].T_hi for p in meshes))
