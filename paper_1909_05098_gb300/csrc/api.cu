@@ -94,6 +94,7 @@ int fail(fedfem_ctx* c, int code, const std::string& msg) {
 }
 
 int cuda_fail(fedfem_ctx* c, cudaError_t e, const char* what) {
+    cudaGetLastError();   // a failed call must not surface again in a later, unrelated check
     return fail(c, e == cudaErrorMemoryAllocation ? FEDFEM_E_OOM : FEDFEM_E_CUDA,
                 std::string(what) + ": " + cudaGetErrorString(e));
 }

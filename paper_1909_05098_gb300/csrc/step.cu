@@ -84,13 +84,13 @@ struct NodeVals {
 template <typename L>
 __device__ __forceinline__ L lzero() { return L{}; }
 
-template <typename R, typename L, bool KAHAN>
+template <typename R, typename L, int MODE>
 __device__ __forceinline__ NodeVals<R, L> node_load(const StepArgs<R, L>& a, int64_t i) {
     NodeVals<R, L> v;
     v.V = a.V[i];
     v.Q = a.Q[i];
     v.hA = i >= a.N_plain ? a.hA[i - a.N_plain] : R(0);
-    v.lo = KAHAN ? a.Tlo[i] : lzero<L>();
+    v.lo = (MODE & 1) ? a.Tlo[i] : lzero<L>();
     return v;
 }
 
@@ -103,7 +103,12 @@ __device__ __forceinline__ R schedule_factor(const StepArgs<R, L>& a, long long 
     return a.seg_f[k];
 }
 
-template <typename R, typename L, bool KAHAN>
+// CEM43 increment of node i at the step's start temperature T
+__device__ __forceinline__ void dose_add(double* dose, int64_t i, double dose_dt, double T) {
+    dose[i] += dose_dt * exp2(T >= 43.0 ? T - 43.0 : 2.0 * (T - 43.0));
+}
+
+template <typename R, typename L, int MODE>
 __device__ __forceinline__ void node_update_v(const StepArgs<R, L>& a, int64_t i, L T, L F,
                                               const NodeVals<R, L>& v, L* Tout, long long step) {
     const L u = T - a.T_ref;
@@ -111,18 +116,17 @@ __device__ __forceinline__ void node_update_v(const StepArgs<R, L>& a, int64_t i
     const L c = fmadd(a.dc, u, a.c0);
     const L C = (v.V * rho) * c;
     L q = v.Q;
-    if (a.Qs) q = fmadd(schedule_factor(a, step), a.Qs[i], q);
-    if constexpr (sizeof(L) == sizeof(R)) {   // CEM43 at the step's start temperature (one lane)
-        if (a.dose) {
-            const double Td = (double)T;
-            a.dose[i] += a.dose_dt * exp2(Td >= 43.0 ? Td - 43.0 : 2.0 * (Td - 43.0));
+    if constexpr ((MODE & 2) != 0) {   // kernels built with the time-varying / dose extensions
+        if (a.Qs) q = fmadd(schedule_factor(a, step), a.Qs[i], q);
+        if constexpr (sizeof(L) == sizeof(R)) {   // CEM43 at the step's start temperature (one lane)
+            if (a.dose) dose_add(a.dose, i, a.dose_dt, (double)T);
         }
     }
     L r = fmadd(a.wbcb * v.V, a.T_a - T, q) - F;
     if (i >= a.N_plain) r = fmadd(v.hA, a.T_inf - T, r);
     const L dT = (a.dt * r) / C;
     L Tn;
-    if (KAHAN) {
+    if (MODE & 1) {
         const L y = dT + v.lo;
         Tn = T + y;
         a.Tlo[i] = y - (Tn - T);
@@ -133,13 +137,13 @@ __device__ __forceinline__ void node_update_v(const StepArgs<R, L>& a, int64_t i
     if (!all_in(Tn, a.T_lo, a.T_hi)) flag_range(a.status, i, step);
 }
 
-template <typename R, typename L, bool KAHAN>
+template <typename R, typename L, int MODE>
 __device__ __forceinline__ void node_update(const StepArgs<R, L>& a, int64_t i, L T, L F, L* Tout, long long step) {
-    node_update_v<R, L, KAHAN>(a, i, T, F, node_load<R, L, KAHAN>(a, i), Tout, step);
+    node_update_v<R, L, MODE>(a, i, T, F, node_load<R, L, MODE>(a, i), Tout, step);
 }
 
 // gather of node i's element loads from the global slots, in its fixed order
-template <typename R, bool KAHAN>
+template <typename R, int MODE>
 __device__ __forceinline__ void node_phase(const StepArgs<R>& a, int64_t i, long long step) {
     const int64_t s = i >> 5;
     const int lane = (int)(i & 31);
@@ -147,7 +151,7 @@ __device__ __forceinline__ void node_phase(const StepArgs<R>& a, int64_t i, long
     const int w = (a.sell_off[s + 1] - off) >> 5;
     R F = R(0);
     for (int k = 0; k < w; ++k) F = F + a.slots[a.sell_ids[off + 32 * k + lane]];
-    node_update<R, R, KAHAN>(a, i, a.T[i], F, a.T, step);
+    node_update<R, R, MODE>(a, i, a.T[i], F, a.T, step);
 }
 
 template <typename R, int NV>
@@ -157,11 +161,11 @@ __global__ void __launch_bounds__(256) k_elem(StepArgs<R> a) {
     if (e < a.E) element_phase<R, NV>(a, e);
 }
 
-template <typename R, bool KAHAN>
+template <typename R, int MODE>
 __global__ void __launch_bounds__(256) k_node(StepArgs<R> a, long long step) {
     if (*(volatile int*)&a.status->flags) return;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < a.N_free) node_phase<R, KAHAN>(a, i, step);
+    if (i < a.N_free) node_phase<R, MODE>(a, i, step);
 }
 
 // ---- bounded grid barrier --------------------------------------------------
@@ -203,7 +207,7 @@ __device__ __forceinline__ bool grid_barrier(DevStatus* st, unsigned long long& 
     return s_ok != 0;
 }
 
-template <typename R, int NV, bool KAHAN>
+template <typename R, int NV, int MODE>
 __global__ void __launch_bounds__(256) k_persistent(StepArgs<R> a, long long n_steps, long long spin_limit) {
     unsigned long long target = 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -213,7 +217,7 @@ __global__ void __launch_bounds__(256) k_persistent(StepArgs<R> a, long long n_s
     for (long long s = 0; s < n_steps; ++s) {
         for (int64_t e = tid; e < a.E; e += stride) element_phase<R, NV>(a, e);
         if (!grid_barrier(a.status, target, spin_limit)) break;
-        for (int64_t i = tid; i < a.N_free; i += stride) node_phase<R, KAHAN>(a, i, a.step0 + s);
+        for (int64_t i = tid; i < a.N_free; i += stride) node_phase<R, MODE>(a, i, a.step0 + s);
         const bool ok = grid_barrier(a.status, target, spin_limit);
         done = s + 1;
         if (!ok) break;
@@ -406,7 +410,7 @@ __device__ __forceinline__ void tile_elements(const TileView<R>& v, const Law<R>
 // The first owned node of each thread (l0 = threadIdx.x) comes with its
 // temperature T0 and constant data v0 already loaded; further nodes (tiles
 // larger than the block) read theirs from Tin.
-template <typename R, typename L, bool KAHAN>
+template <typename R, typename L, int MODE>
 __device__ __forceinline__ void tile_nodes(const StepArgs<R, L>& a, int64_t base, int own, int deg, int B, L* Fn,
                                            L T0, const NodeVals<R, L>& v0, const L* Tin, L* Tout, long long step) {
     for (int l = threadIdx.x; l < own; l += blockDim.x) {
@@ -415,16 +419,16 @@ __device__ __forceinline__ void tile_nodes(const StepArgs<R, L>& a, int64_t base
             F = F + Fn[r * B + l];
             Fn[r * B + l] = lzero<L>();
         }
-        if (l == (int)threadIdx.x) node_update_v<R, L, KAHAN>(a, base + l, T0, F, v0, Tout, step);
-        else node_update<R, L, KAHAN>(a, base + l, Tin[base + l], F, Tout, step);
+        if (l == (int)threadIdx.x) node_update_v<R, L, MODE>(a, base + l, T0, F, v0, Tout, step);
+        else node_update<R, L, MODE>(a, base + l, Tin[base + l], F, Tout, step);
     }
 }
 
-template <typename R, typename L, bool KAHAN>
+template <typename R, typename L, int MODE>
 __device__ __forceinline__ void first_node(const StepArgs<R, L>& a, int64_t base, int own, const L* Ts, L& T0,
                                            NodeVals<R, L>& v0) {
     if ((int)threadIdx.x < own) {
-        v0 = node_load<R, L, KAHAN>(a, base + threadIdx.x);
+        v0 = node_load<R, L, MODE>(a, base + threadIdx.x);
         T0 = Ts[threadIdx.x];
     }
 }
@@ -445,7 +449,7 @@ struct DirectOccupancy {
     static constexpr int min_blocks = sizeof(L) >= 8 ? 3 : 5;
 };
 
-template <typename R, typename L, int NV, bool KAHAN>
+template <typename R, typename L, int NV, int MODE>
 __global__ void __launch_bounds__(256, DirectOccupancy<L>::min_blocks) k_tiled_direct(StepArgs<R, L> a, TileArgs<R> ta, long long n_steps,
                                                       long long spin_limit) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -467,10 +471,10 @@ __global__ void __launch_bounds__(256, DirectOccupancy<L>::min_blocks) k_tiled_d
             __syncthreads();
             L T0 = lzero<L>();
             NodeVals<R, L> v0{};
-            first_node<R, L, KAHAN>(a, base, own, Ts, T0, v0);
+            first_node<R, L, MODE>(a, base, own, Ts, T0, v0);
             tile_elements<R, L, NV, false>(v, k, own, ta.B, ta.rank_shift, Ts, Fn);
             __syncthreads();   // loads complete; Ts is free for the next tile
-            tile_nodes<R, L, KAHAN>(a, base, own, v.deg, ta.B, Fn, T0, v0, Tin, Tout, a.step0 + s);
+            tile_nodes<R, L, MODE>(a, base, own, v.deg, ta.B, Fn, T0, v0, Tin, Tout, a.step0 + s);
             __syncthreads();   // table cleared before the next tile writes it
         }
         const bool ok = grid_barrier(a.status, target, spin_limit);
@@ -492,7 +496,7 @@ struct StagedOccupancy {
     static constexpr int min_blocks = (sizeof(L) == 4 ? 1024 : 512) / TPB > 0 ? (sizeof(L) == 4 ? 1024 : 512) / TPB : 1;
 };
 
-template <typename R, typename L, int NV, bool KAHAN, int TPB>
+template <typename R, typename L, int NV, int MODE, int TPB>
 __global__ void __launch_bounds__(TPB, StagedOccupancy<L, TPB>::min_blocks)
     k_tiled(StepArgs<R, L> a, TileArgs<R> ta, long long n_steps, long long spin_limit) {
     // shared memory: 2 mbarriers | 2 block stages | temperatures | load table
@@ -580,7 +584,7 @@ __global__ void __launch_bounds__(TPB, StagedOccupancy<L, TPB>::min_blocks)
             const int deg = v.deg;
             L T0 = lzero<L>();
             NodeVals<R, L> v0{};
-            first_node<R, L, KAHAN>(a, base, own, Ts, T0, v0);
+            first_node<R, L, MODE>(a, base, own, Ts, T0, v0);
             tile_elements<R, L, NV, true>(v, k, own, ta.B, ta.rank_shift, Ts, Fn);
             __syncthreads();   // loads complete; this stage and Ts are free
             if (i + 1 < n_my) {   // the next tile of this step: its stage, then its temperatures
@@ -588,7 +592,7 @@ __global__ void __launch_bounds__(TPB, StagedOccupancy<L, TPB>::min_blocks)
                 fetch(kk + 1, Tin);
             }
             if (!resident && kk + 2 < total) issue(kk + 2);
-            tile_nodes<R, L, KAHAN>(a, base, own, deg, ta.B, Fn, T0, v0, Tin, Tout, a.step0 + s);
+            tile_nodes<R, L, MODE>(a, base, own, deg, ta.B, Fn, T0, v0, Tin, Tout, a.step0 + s);
         }
         if (stop) break;
         cp_async_wait_all();
@@ -613,13 +617,21 @@ __global__ void __launch_bounds__(TPB, StagedOccupancy<L, TPB>::min_blocks)
     if (blockIdx.x == 0 && threadIdx.x == 0) a.status->steps_done = a.step0 + done;
 }
 
+// MODE bit 0: Kahan-compensated state; bit 1: built with the time-varying
+// source and thermal-dose paths (launched only when a context enables one)
+template <typename R, typename L, int NV, int MODE>
+auto tiled_kernel(const TileArgs<R>& ta) {
+    return !ta.staged           ? k_tiled_direct<R, L, NV, MODE>
+           : ta.threads == 256  ? k_tiled<R, L, NV, MODE, 256>
+           : ta.threads == 1024 ? k_tiled<R, L, NV, MODE, 1024>
+                                : k_tiled<R, L, NV, MODE, kTiledThreads>;
+}
+
 template <typename R, typename L, int NV, bool KAHAN>
 cudaError_t launch_tiled_impl(const StepArgs<R, L>& a, const TileArgs<R>& ta, int64_t n_steps, LaunchCfg& cfg,
                               cudaStream_t s) {
-    auto kern = !ta.staged           ? k_tiled_direct<R, L, NV, KAHAN>
-                : ta.threads == 256  ? k_tiled<R, L, NV, KAHAN, 256>
-                : ta.threads == 1024 ? k_tiled<R, L, NV, KAHAN, 1024>
-                                     : k_tiled<R, L, NV, KAHAN, kTiledThreads>;
+    constexpr int M = KAHAN ? 1 : 0;
+    auto kern = (a.Qs || a.dose) ? tiled_kernel<R, L, NV, M | 2>(ta) : tiled_kernel<R, L, NV, M>(ta);
     const int b = ta.staged ? ta.threads : 256;
     cudaError_t err = cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)ta.smem_bytes);
@@ -646,16 +658,19 @@ inline int blocks_for(int64_t n, int t) {
 
 template <typename R, int NV, bool KAHAN>
 cudaError_t launch_impl(const StepArgs<R>& a, int64_t n_steps, LaunchCfg& cfg, cudaStream_t s) {
+    constexpr int M = KAHAN ? 1 : 0;
+    const bool ext = a.Qs || a.dose;
     if (cfg.kernel == FEDFEM_KERNEL_TWO_PHASE) {
         const int b = cfg.block > 0 ? std::min(cfg.block, 256) : 256;
+        auto node = ext ? k_node<R, M | 2> : k_node<R, M>;
         for (int64_t k = 0; k < n_steps; ++k) {
             k_elem<R, NV><<<blocks_for(a.E, b), b, 0, s>>>(a);
-            k_node<R, KAHAN><<<blocks_for(a.N_free, b), b, 0, s>>>(a, a.step0 + k);
+            node<<<blocks_for(a.N_free, b), b, 0, s>>>(a, a.step0 + k);
         }
         return cudaGetLastError();
     }
     // persistent: one cooperative launch, grid = resident blocks
-    auto kern = k_persistent<R, NV, KAHAN>;
+    auto kern = ext ? k_persistent<R, NV, M | 2> : k_persistent<R, NV, M>;
     const int b = 256;
     int per_sm = 0;
     cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, b, 0);
@@ -701,10 +716,10 @@ cudaError_t launch_tiled_f32x4(const StepArgs<float, F4>& a, const TileArgs<floa
 
 template <typename R, typename L, int NV, bool KAHAN>
 const void* pick_tiled_k(int staged, int threads) {
-    if (!staged) return (const void*)k_tiled_direct<R, L, NV, KAHAN>;
-    if (threads == 256) return (const void*)k_tiled<R, L, NV, KAHAN, 256>;
-    if (threads == 1024) return (const void*)k_tiled<R, L, NV, KAHAN, 1024>;
-    return (const void*)k_tiled<R, L, NV, KAHAN, kTiledThreads>;
+    TileArgs<R> ta{};
+    ta.staged = staged;
+    ta.threads = threads;
+    return (const void*)tiled_kernel<R, L, NV, KAHAN ? 1 : 0>(ta);
 }
 
 template <typename R, typename L>
@@ -719,9 +734,16 @@ int tiled_blocks_per_sm(int precision, int nv, int staged, int threads, int lane
     const void* k = precision == FEDFEM_FP64 ? pick_tiled<double, double>(staged, threads, nv, false)
                     : lanes == 4            ? pick_tiled<float, F4>(staged, threads, nv, kahan)
                                             : pick_tiled<float, float>(staged, threads, nv, kahan);
-    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+    // a size the kernel cannot take is an answer (0 blocks), not an error: clear it
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, block, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
     return per_sm;
 }
 

@@ -177,3 +177,23 @@ def test_device_pointer_init_and_read():
         assert np.array_equal(s.temperature(), expect)
     finally:
         s.close()
+
+
+def test_refused_tile_size_leaves_the_context_usable():
+    """A tile whose shared memory no block can hold is refused with
+    E_UNSUPPORTED; the refusal must not surface as an error in later calls."""
+    f = ff()
+    p = cube_hex_td_convective(n=24).problem
+    s = _solver(p, kernel=f.KERNEL_PERSISTENT)
+    try:
+        dt = 0.5 * s.dt_cr
+        f.fedfem_set_tile(s.ctx, f.KERNEL_TILED_STAGED, 1024, 4096, 0)   # two stages of ~200 KB
+        with pytest.raises(f.FedfemError) as e:
+            s.step(dt, 5)
+        assert e.value.code == f.E_UNSUPPORTED
+        f.fedfem_set_tile(s.ctx, f.KERNEL_PERSISTENT)
+        s.init()
+        s.step(dt, 5)
+        assert s.sync() == 5
+    finally:
+        s.close()
