@@ -390,11 +390,16 @@ struct EdgeLayerArgs {
     long long limit;
 };
 
-__global__ void __launch_bounds__(128) k_edge_layer(EdgeLayerArgs g) {
+constexpr int kFusedThreads = 256;   // 8 warps: two per TMEM lane quadrant, one per 32-column half
+
+// epilogue coordinates of this thread: TMEM lane quadrant (rows 32q..32q+31) and column half
+__device__ __forceinline__ int epi_row() { return 32 * ((threadIdx.x >> 5) & 3) + (threadIdx.x & 31); }
+__device__ __forceinline__ int epi_col0() { return 32 * (threadIdx.x >> 7); }
+
+__global__ void __launch_bounds__(kFusedThreads, 3) k_edge_layer(EdgeLayerArgs g) {
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* sA = smem;                          // 3 K-blocks; after the MMAs: messages, 128 x kPad FP32
     unsigned char* sB = smem + 3 * kKBlock;            // W_e, 3 K-blocks
-    float* eS = reinterpret_cast<float*>(smem + 3 * kKBlock + 3 * kWBlock);   // e rows, 128 x kPad FP32
     float* msgS = reinterpret_cast<float*>(sA);
     __shared__ uint64_t bar;
     __shared__ uint32_t tmem_base;
@@ -411,53 +416,56 @@ __global__ void __launch_bounds__(128) k_edge_layer(EdgeLayerArgs g) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_base;
     uint32_t phase = 0;
+    const int nw = blockDim.x >> 5;
     const int64_t items = (int64_t)g.n_tiles * g.B;
     for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
         const int t = (int)(item % g.n_tiles);
         const int64_t b = item / g.n_tiles;
         const EdgeTile T = g.tiles[t];
-        for (int i = warp; i < kRows / 8; i += 4) {
+        for (int i = warp; i < kRows / 8; i += nw) {
             const int r = 8 * i + (lane & 7);
             const bool valid = r < T.count;
             const int64_t m = T.m0 + (valid ? r : 0);   // read only for valid rows
             const int32_t s = valid ? g.src[m] : 0, d = valid ? g.dst[m] : 0;
-            stage_row(sA, 0, r, g.e_in + b * g.e_in_stride + m * H, valid, eS);
+            stage_row(sA, 0, r, g.e_in + b * g.e_in_stride + m * H, valid, nullptr);
             stage_row(sA, 1, r, g.h + (b * g.N + s) * H, valid, nullptr);
             stage_row(sA, 2, r, g.h + (b * g.N + d) * H, valid, nullptr);
         }
         if (!mma_tile(tmem, sA, sB, 3, &bar, phase, g.status, g.limit)) break;
-        // epilogue: this thread owns row r (TMEM lane r)
+        // epilogue: row r (TMEM lane r), columns c0..c0+31; e is re-read (it was
+        // just staged, so it comes from L2) and written back, the messages go to
+        // shared memory (over the A operand, which the MMAs no longer read)
         {
-            const int r = 32 * warp + lane;
-            float* er = eS + r * kPad;
-            float* mr = msgS + r * kPad;
-#pragma unroll
-            for (int c0 = 0; c0 < H; c0 += 32) {
-                float v[32];
-                tc::tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
+            const int r = epi_row(), c0 = epi_col0();
+            float v[32];
+            tc::tmem_ld32(tmem + ((uint32_t)(r & ~31) << 16) + (uint32_t)c0, v);
+            if (r < T.count) {
+                const int64_t m = T.m0 + r;
+                const float* er = g.e_in + b * g.e_in_stride + m * H + c0;
+                float* mr = msgS + r * kPad + c0;
+                float* eo = g.e_out ? g.e_out + (b * g.E + m) * H + c0 : nullptr;
 #pragma unroll
                 for (int c = 0; c < 32; c += 4) {
-                    float4 msg, ev = *reinterpret_cast<float4*>(er + c0 + c);
+                    float4 msg;
                     msg.x = tc::silu(v[c] + g.bias[c0 + c]);
                     msg.y = tc::silu(v[c + 1] + g.bias[c0 + c + 1]);
                     msg.z = tc::silu(v[c + 2] + g.bias[c0 + c + 2]);
                     msg.w = tc::silu(v[c + 3] + g.bias[c0 + c + 3]);
-                    ev.x = ev.x + msg.x; ev.y = ev.y + msg.y; ev.z = ev.z + msg.z; ev.w = ev.w + msg.w;
-                    *reinterpret_cast<float4*>(mr + c0 + c) = msg;
-                    *reinterpret_cast<float4*>(er + c0 + c) = ev;
+                    *reinterpret_cast<float4*>(mr + c) = msg;
+                    if (eo) {
+                        float4 ev = *reinterpret_cast<const float4*>(er + c);
+                        ev.x = ev.x + msg.x; ev.y = ev.y + msg.y; ev.z = ev.z + msg.z; ev.w = ev.w + msg.w;
+                        *reinterpret_cast<float4*>(eo + c) = ev;
+                    }
                 }
             }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
-        if (g.e_out)   // e rows back, coalesced: a warp per row
-            for (int r = warp; r < T.count; r += 4)
-                reinterpret_cast<float2*>(g.e_out + (b * g.E + T.m0 + r) * H)[lane] =
-                    reinterpret_cast<const float2*>(eS + r * kPad)[lane];
         // a_n = sum of the messages over n's in-edges, in edge order
         {
             const int c = threadIdx.x & 63;
-            for (int n = T.n0 + (threadIdx.x >> 6); n < T.n1; n += 2) {
+            for (int n = T.n0 + (threadIdx.x >> 6); n < T.n1; n += blockDim.x >> 6) {
                 float acc = 0.0f;
                 for (int32_t m = g.in_ptr[n]; m < g.in_ptr[n + 1]; ++m) acc += msgS[(m - T.m0) * kPad + c];
                 g.a[(b * g.N + n) * H + c] = acc;
@@ -483,11 +491,10 @@ struct NodeLayerArgs {
     long long limit;
 };
 
-__global__ void __launch_bounds__(128) k_node_layer(NodeLayerArgs g) {
+__global__ void __launch_bounds__(kFusedThreads, 3) k_node_layer(NodeLayerArgs g) {
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* sA = smem;                          // 2 K-blocks: [h | a]
     unsigned char* sB = smem + 2 * kKBlock;            // W_n, 2 K-blocks
-    float* hS = reinterpret_cast<float*>(smem + 2 * kKBlock + 2 * kWBlock);   // h rows, 128 x kPad FP32
     __shared__ uint64_t bar;
     __shared__ uint32_t tmem_base;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -503,53 +510,52 @@ __global__ void __launch_bounds__(128) k_node_layer(NodeLayerArgs g) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_base;
     uint32_t phase = 0;
+    const int nw = blockDim.x >> 5;
     const int64_t tiles = (g.R + kRows - 1) / kRows;
     for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
         const int64_t row0 = tile * kRows;
-        for (int i = warp; i < kRows / 8; i += 4) {
+        for (int i = warp; i < kRows / 8; i += nw) {
             const int r = 8 * i + (lane & 7);
             const bool valid = row0 + r < g.R;
             const int64_t row = valid ? row0 + r : 0;
-            stage_row(sA, 0, r, g.h + row * H, valid, hS);
+            stage_row(sA, 0, r, g.h + row * H, valid, nullptr);
             stage_row(sA, 1, r, g.a + row * H, valid, nullptr);
         }
         if (!mma_tile(tmem, sA, sB, 2, &bar, phase, g.status, g.limit)) break;
-        {
-            const int r = 32 * warp + lane;
-            float* hr = hS + r * kPad;
-#pragma unroll
-            for (int c0 = 0; c0 < H; c0 += 32) {
-                float v[32];
-                tc::tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
+        {   // h += SiLU(acc + b_n), in place: each (row, column half) belongs to one thread
+            const int r = epi_row(), c0 = epi_col0();
+            float v[32];
+            tc::tmem_ld32(tmem + ((uint32_t)(r & ~31) << 16) + (uint32_t)c0, v);
+            if (row0 + r < g.R) {
+                float* hr = g.h + (row0 + r) * H + c0;
 #pragma unroll
                 for (int c = 0; c < 32; c += 4) {
-                    float4 hv = *reinterpret_cast<float4*>(hr + c0 + c);
+                    float4 hv = *reinterpret_cast<const float4*>(hr + c);
                     hv.x = hv.x + tc::silu(v[c] + g.bias[c0 + c]);
                     hv.y = hv.y + tc::silu(v[c + 1] + g.bias[c0 + c + 1]);
                     hv.z = hv.z + tc::silu(v[c + 2] + g.bias[c0 + c + 2]);
                     hv.w = hv.w + tc::silu(v[c + 3] + g.bias[c0 + c + 3]);
-                    *reinterpret_cast<float4*>(hr + c0 + c) = hv;
+                    *reinterpret_cast<float4*>(hr + c) = hv;
                 }
-            }
-            if (g.y && row0 + r < g.R) {   // decoder, in the order of the unfused one
-                float acc = g.bd[0];
-                for (int k = 0; k < H; ++k) acc += g.wd[k] * hr[k];
-                g.y[row0 + r] = acc;
             }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-        for (int r = warp; r < kRows && row0 + r < g.R; r += 4)
-            reinterpret_cast<float2*>(g.h + (row0 + r) * H)[lane] = reinterpret_cast<const float2*>(hS + r * kPad)[lane];
-        __syncthreads();
+        __syncthreads();   // the new rows are visible to the block; A is restaged next
+        if (g.y && threadIdx.x < kRows && row0 + threadIdx.x < g.R) {   // decoder, in the unfused order
+            const float* hr = g.h + (row0 + threadIdx.x) * H;
+            float acc = g.bd[0];
+            for (int k = 0; k < H; ++k) acc += g.wd[k] * hr[k];
+            g.y[row0 + threadIdx.x] = acc;
+        }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tmem) : "memory");
 }
 
-constexpr size_t kEdgeSmem = 3 * kKBlock + 3 * kWBlock + (size_t)kRows * kPad * 4;
-constexpr size_t kNodeSmem = 2 * kKBlock + 2 * kWBlock + (size_t)kRows * kPad * 4;
+constexpr size_t kEdgeSmem = 3 * kKBlock + 3 * kWBlock;   // the messages reuse the A operand
+constexpr size_t kNodeSmem = 2 * kKBlock + 2 * kWBlock;
+static_assert((size_t)kRows * kPad * 4 <= 3 * kKBlock, "messages fit over the edge A operand");
 
 }  // namespace
 }  // namespace fedfem
@@ -749,7 +755,7 @@ int infer(fedfem_mpnn* m, int B, const float* x, float* y) {
     MC(cudaFuncSetAttribute(k_node_layer, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kNodeSmem));
     const int64_t edge_items = (int64_t)m->n_edge_tiles * B;
     const int64_t node_tiles = (RN + kRows - 1) / kRows;
-    const int resident = 2 * std::max(1, m->sm_count);
+    const int resident = 3 * std::max(1, m->sm_count);
     for (int l = 0; l < m->L; ++l) {
         EdgeLayerArgs ea{};
         ea.B = B; ea.N = N; ea.E = E;
@@ -761,7 +767,7 @@ int infer(fedfem_mpnn* m, int B, const float* x, float* y) {
         ea.h = h; ea.a = m->a;
         ea.W = m->We[l]; ea.bias = P + m->off[p_be(l)];
         ea.status = m->status; ea.limit = m->spin_limit;
-        k_edge_layer<<<(unsigned)std::min<int64_t>(edge_items, resident), 128, kEdgeSmem, s>>>(ea);
+        k_edge_layer<<<(unsigned)std::min<int64_t>(edge_items, resident), kFusedThreads, kEdgeSmem, s>>>(ea);
         MC(cudaGetLastError());
         NodeLayerArgs na{};
         na.R = RN; na.h = h; na.a = m->a;
@@ -771,7 +777,7 @@ int infer(fedfem_mpnn* m, int B, const float* x, float* y) {
         na.bd = last ? P + m->off[p_We(m->L) + 1] : nullptr;
         na.y = last ? y : nullptr;
         na.status = m->status; na.limit = m->spin_limit;
-        k_node_layer<<<(unsigned)std::min<int64_t>(node_tiles, resident), 128, kNodeSmem, s>>>(na);
+        k_node_layer<<<(unsigned)std::min<int64_t>(node_tiles, resident), kFusedThreads, kNodeSmem, s>>>(na);
         MC(cudaGetLastError());
     }
     return FEDFEM_OK;
