@@ -325,24 +325,32 @@ __device__ __forceinline__ void stage_weights(unsigned char* sB, const bf16* W, 
     }
 }
 
-// one 64-wide FP32 row segment of row r into K-block kb (BF16), lane's two
-// 8-value chunks j = lane/8 and lane/8 + 4; optionally kept as FP32 in keep
-__device__ __forceinline__ void stage_row(unsigned char* sA, int kb, int r, const float* row, bool valid, float* keep) {
+// SEG 64-wide FP32 row segments of tile row r into K-blocks 0..SEG-1 (BF16):
+// all of the lane's loads are issued before any conversion, so a warp keeps
+// 4 x SEG loads in flight instead of a chain of dependent ones
+template <int SEG>
+__device__ __forceinline__ void stage_rows(unsigned char* sA, int r, const float* const (&row)[SEG], bool valid) {
     const int lane = threadIdx.x & 31;
+    float4 v[SEG][2][2];
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-        const int j = (lane >> 3) + 4 * q;
-        float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0;
-        if (valid) {
-            v0 = reinterpret_cast<const float4*>(row)[2 * j];
-            v1 = reinterpret_cast<const float4*>(row)[2 * j + 1];
+    for (int sg = 0; sg < SEG; ++sg)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int j = (lane >> 3) + 4 * q;
+            if (valid) {
+                v[sg][q][0] = reinterpret_cast<const float4*>(row[sg])[2 * j];
+                v[sg][q][1] = reinterpret_cast<const float4*>(row[sg])[2 * j + 1];
+            } else {
+                v[sg][q][0] = v[sg][q][1] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
         }
-        *reinterpret_cast<uint4*>(sA + kb * kKBlock + tc::core_offset(r, 8 * j)) = pack8(v0, v1);
-        if (keep) {
-            reinterpret_cast<float4*>(keep + r * kPad)[2 * j] = v0;
-            reinterpret_cast<float4*>(keep + r * kPad)[2 * j + 1] = v1;
+#pragma unroll
+    for (int sg = 0; sg < SEG; ++sg)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int j = (lane >> 3) + 4 * q;
+            *reinterpret_cast<uint4*>(sA + sg * kKBlock + tc::core_offset(r, 8 * j)) = pack8(v[sg][q][0], v[sg][q][1]);
         }
-    }
 }
 
 // issue the K/16 MMAs of one tile (thread 0) and wait for them (every thread);
@@ -427,9 +435,9 @@ __global__ void __launch_bounds__(kFusedThreads, 3) k_edge_layer(EdgeLayerArgs g
             const bool valid = r < T.count;
             const int64_t m = T.m0 + (valid ? r : 0);   // read only for valid rows
             const int32_t s = valid ? g.src[m] : 0, d = valid ? g.dst[m] : 0;
-            stage_row(sA, 0, r, g.e_in + b * g.e_in_stride + m * H, valid, nullptr);
-            stage_row(sA, 1, r, g.h + (b * g.N + s) * H, valid, nullptr);
-            stage_row(sA, 2, r, g.h + (b * g.N + d) * H, valid, nullptr);
+            const float* const rows[3] = {g.e_in + b * g.e_in_stride + m * H, g.h + (b * g.N + s) * H,
+                                          g.h + (b * g.N + d) * H};
+            stage_rows<3>(sA, r, rows, valid);
         }
         if (!mma_tile(tmem, sA, sB, 3, &bar, phase, g.status, g.limit)) break;
         // epilogue: row r (TMEM lane r), columns c0..c0+31; e is re-read (it was
@@ -518,8 +526,8 @@ __global__ void __launch_bounds__(kFusedThreads, 3) k_node_layer(NodeLayerArgs g
             const int r = 8 * i + (lane & 7);
             const bool valid = row0 + r < g.R;
             const int64_t row = valid ? row0 + r : 0;
-            stage_row(sA, 0, r, g.h + row * H, valid, nullptr);
-            stage_row(sA, 1, r, g.a + row * H, valid, nullptr);
+            const float* const rows[2] = {g.h + row * H, g.a + row * H};
+            stage_rows<2>(sA, r, rows, valid);
         }
         if (!mma_tile(tmem, sA, sB, 2, &bar, phase, g.status, g.limit)) break;
         {   // h += SiLU(acc + b_n), in place: each (row, column half) belongs to one thread
