@@ -627,6 +627,7 @@ def run_surrogate(args):
     T_plain = ens.state()
     torch.cuda.synchronize()
     plain_s = time.perf_counter() - t0
+    rollout(sur, ens, qe32, T0, dt, n_windows=1, check_every=2, budget=args.budget[0])   # warm-up, untimed
     runs = {}
     for budget in args.budget:
         res = rollout(sur, ens, qe32, T0, dt, n_windows=n_win // 10, check_every=10, budget=budget)

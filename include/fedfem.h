@@ -191,7 +191,7 @@ int fedfem_set_source_schedule(fedfem_ctx* ctx, int n, const double* t_end, cons
  * Dewey, CEM43 += (dt / 60) R^(43 - T) with R = 1/2 at or above 43 degC and
  * 1/4 below, T the node's temperature at the start of each step (the hi part
  * in FP32+Kahan), accumulated in FP64 inside the node update of every
- * kernel.  on != 0 enables it from the next fedfem_precompute (single-lane
+ * kernel; the power is evaluated in the state's precision.  on != 0 enables it from the next fedfem_precompute (single-lane
  * contexts only: E_UNSUPPORTED there otherwise); fedfem_init resets it to 0;
  * checkpoints carry it. */
 int fedfem_enable_dose(fedfem_ctx* ctx, int on);

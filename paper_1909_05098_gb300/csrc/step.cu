@@ -103,9 +103,14 @@ __device__ __forceinline__ R schedule_factor(const StepArgs<R, L>& a, long long 
     return a.seg_f[k];
 }
 
-// CEM43 increment of node i at the step's start temperature T
+// CEM43 increment of node i at the step's start temperature T, accumulated in
+// FP64; the power is taken in the state's precision (FP32 state: exp2f, whose
+// relative error is far below that of the FP32 temperature it is taken of)
 __device__ __forceinline__ void dose_add(double* dose, int64_t i, double dose_dt, double T) {
     dose[i] += dose_dt * exp2(T >= 43.0 ? T - 43.0 : 2.0 * (T - 43.0));
+}
+__device__ __forceinline__ void dose_add(double* dose, int64_t i, double dose_dt, float T) {
+    dose[i] += dose_dt * (double)exp2f(T >= 43.0f ? T - 43.0f : 2.0f * (T - 43.0f));
 }
 
 template <typename R, typename L, int MODE>
@@ -119,7 +124,7 @@ __device__ __forceinline__ void node_update_v(const StepArgs<R, L>& a, int64_t i
     if constexpr ((MODE & 2) != 0) {   // kernels built with the time-varying / dose extensions
         if (a.Qs) q = fmadd(schedule_factor(a, step), a.Qs[i], q);
         if constexpr (sizeof(L) == sizeof(R)) {   // CEM43 at the step's start temperature (one lane)
-            if (a.dose) dose_add(a.dose, i, a.dose_dt, (double)T);
+            if (a.dose) dose_add(a.dose, i, a.dose_dt, T);
         }
     }
     L r = fmadd(a.wbcb * v.V, a.T_a - T, q) - F;
