@@ -208,14 +208,15 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel, n, tile_nodes, steps_per_launch):
+def ncu_traffic(kernel, n, tile_nodes, block, steps_per_launch):
     """DRAM bytes (read + write) per launch of the timed kernel, from the
     committed ncu summary: a line
-        traffic: kernel=<name> n=<cube edge> tile_nodes=<B> source=<hash> dram_bytes_per_step=<bytes>
-    in profiles/*.md.  None unless kernel, workload, tile size and kernel
-    sources all match this run."""
+        traffic: kernel=<name> n=<cube edge> tile_nodes=<B> block=<threads> source=<hash> dram_bytes_per_step=<bytes>
+    in profiles/*.md.  None unless kernel, workload, tile size, block size and
+    kernel sources all match this run."""
     pdir = os.path.join(ROOT, "profiles")
-    want = {"kernel": kernel, "n": str(n), "tile_nodes": str(tile_nodes), "source": kernel_source_hash()}
+    want = {"kernel": kernel, "n": str(n), "tile_nodes": str(tile_nodes), "block": str(block),
+            "source": kernel_source_hash()}
     for f in sorted(os.listdir(pdir)) if os.path.isdir(pdir) else []:
         if not f.endswith(".md"):
             continue
@@ -394,7 +395,7 @@ def run_ours(args):
     launch_s = float(np.mean(per_launch_ms)) / 1e3
     peak, peak_src = measured_peak()
     achieved = alg_bytes_launch / launch_s / 1e9
-    traffic = ncu_traffic(names[kernel] + "_fp32_kahan_hex8", args.n, info["tile_nodes"], S)
+    traffic = ncu_traffic(names[kernel] + "_fp32_kahan_hex8", args.n, info["tile_nodes"], info["block_threads"], S)
     solver.close()
     if rank != 0:
         return

@@ -97,9 +97,9 @@ typedef struct {
     int kernel;        /* FEDFEM_KERNEL_* */
     int block;         /* threads per block: 64..1024, multiple of 32 (0 = default); the
                           staged tiled kernel is built for 256, 512 (default) and 1024 */
-    int tile_nodes;    /* TILED: target owned nodes per tile, multiple of 8 (0 = default); the
-                          library moves it to the nearest size that gives every resident
-                          block the same number of tiles */
+    int tile_nodes;    /* TILED: owned nodes per tile, multiple of 8 (0 = default: the library
+                          picks a size near 512 (hex) / 256 (tet) that gives every resident
+                          block the same number of tiles) */
     int blocks_per_sm; /* PERSISTENT/TILED: resident blocks per SM (0 = occupancy maximum) */
 } fedfem_tile;
 

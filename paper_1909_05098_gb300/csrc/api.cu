@@ -272,8 +272,9 @@ int plan_tiles(fedfem_ctx* c) {
     std::string m;
     int mb = 0;
     {
-        // target size, then the nearest size that gives every resident block the
-        // same number of tiles at the same occupancy
+        // the requested size exactly; the default size is moved to the nearest one
+        // that gives every resident block the same number of tiles at the same
+        // occupancy
         int B0 = B;
         if (B0 <= 0) {
             B0 = c->nv == 8 ? (staged ? 512 : 256) : (staged ? 256 : 128);
@@ -290,7 +291,7 @@ int plan_tiles(fedfem_ctx* c) {
         B = B0;
         const int64_t grid = (int64_t)per_sm * c->sm_count;
         const int64_t w0 = std::max<int64_t>(1, (int64_t)std::llround((double)NF / ((double)B0 * grid)));
-        for (int64_t waves = w0; waves <= w0 + 1; ++waves) {
+        for (int64_t waves = w0; waves <= w0 + 1 && c->tile.tile_nodes <= 0; ++waves) {
             const int64_t Bw = ((NF + waves * grid - 1) / (waves * grid) + 7) / 8 * 8;
             if (Bw < 32 || Bw > 2 * (int64_t)B0) continue;                 // small meshes: keep the target
             Tiles tw;
