@@ -191,15 +191,17 @@ int fedfem_set_source_schedule(fedfem_ctx* ctx, int n, const double* t_end, cons
  * Dewey, CEM43 += (dt / 60) R^(43 - T) with R = 1/2 at or above 43 degC and
  * 1/4 below, T the node's temperature at the start of each step (the hi part
  * in FP32+Kahan), accumulated in FP64 inside the node update of every
- * kernel; the power is evaluated in the state's precision.  on != 0 enables it from the next fedfem_precompute (single-lane
- * contexts only: E_UNSUPPORTED there otherwise); fedfem_init resets it to 0;
- * checkpoints carry it. */
+ * kernel (every scenario lane separately); the power is evaluated in the
+ * state's precision.  on != 0 enables it from the next fedfem_precompute;
+ * fedfem_init resets it to 0; checkpoints carry it. */
 int fedfem_enable_dose(fedfem_ctx* ctx, int on);
 /* CEM43 in minutes, n_nodes doubles in input node order (caller-owned host
  * buffer).  Dirichlet nodes report their fixed temperature held for the
  * elapsed simulated time.  Waits for the context's stream.  E_STATE if the
  * dose is not enabled or before fedfem_init. */
 int fedfem_read_dose(fedfem_ctx* ctx, double* out);
+/* The same for one scenario lane (0 .. lanes-1; E_ARG otherwise). */
+int fedfem_read_dose_lane(fedfem_ctx* ctx, int lane, double* out);
 
 /* Pre-computation (the first stage of Algorithm 1) in FP64 on the GPU: element
  * geometry and A_e (Eq. 16), lumped volumes, perfusion and source loads, face

@@ -698,16 +698,17 @@ int fedfem_enable_dose(fedfem_ctx* c, int on) {
     return FEDFEM_OK;
 }
 
-int fedfem_read_dose(fedfem_ctx* c, double* out) {
+int fedfem_read_dose_lane(fedfem_ctx* c, int lane, double* out) {
     if (!c || !out) return fail(c, FEDFEM_E_ARG, "null output");
     if (!c->dose) return fail(c, FEDFEM_E_STATE, "enable the dose before fedfem_precompute");
     if (!c->inited) return fail(c, FEDFEM_E_STATE, "init first");
+    if (lane < 0 || lane >= c->n_lanes) return fail(c, FEDFEM_E_ARG, "lane out of range");
     CU(cudaSetDevice(c->device), "set device");
-    const int64_t NF = c->L.N_free;
-    std::vector<double> d(std::max<int64_t>(1, NF));
+    const int64_t NF = c->L.N_free, NL = c->n_lanes;
+    std::vector<double> d(std::max<int64_t>(1, NF * NL));
     CU(cudaStreamSynchronize(c->stream), "dose read");
-    CU(cudaMemcpy(d.data(), c->dose, sizeof(double) * NF, cudaMemcpyDeviceToHost), "dose read");
-    for (int64_t i = 0; i < NF; ++i) out[c->L.node_of[i]] = d[i];
+    CU(cudaMemcpy(d.data(), c->dose, sizeof(double) * NF * NL, cudaMemcpyDeviceToHost), "dose read");
+    for (int64_t i = 0; i < NF; ++i) out[c->L.node_of[i]] = d[i * NL + lane];
     // Dirichlet nodes sit at their fixed temperature for the whole elapsed time
     for (int64_t i = NF; i < c->N; ++i) {
         const int64_t o = c->L.node_of[i];
@@ -716,6 +717,8 @@ int fedfem_read_dose(fedfem_ctx* c, double* out) {
     }
     return FEDFEM_OK;
 }
+
+int fedfem_read_dose(fedfem_ctx* c, double* out) { return fedfem_read_dose_lane(c, 0, out); }
 
 int fedfem_set_tile(fedfem_ctx* c, const fedfem_tile* t) {
     if (!c || !t) return fail(c, FEDFEM_E_ARG, "null tile");
@@ -888,10 +891,7 @@ int fedfem_precompute(fedfem_ctx* c, double T_lo, double T_hi, double* dt_cr_out
         pc.qr_node = nullptr; pc.n_src = 0;
         CU(launch_nodal(pc, st), "nodal kernel");
     }
-    if (c->dose_on) {
-        if (NL != 1) return fail(c, FEDFEM_E_UNSUPPORTED, "thermal dose needs a single-lane context");
-        CU(dalloc(c, &c->dose, sizeof(double) * std::max<int64_t>(1, NF)), "alloc");
-    }
+    if (c->dose_on) CU(dalloc(c, &c->dose, sizeof(double) * std::max<int64_t>(1, NF * NL)), "alloc");
     CU(cudaStreamSynchronize(st), "nodal kernel");
     LanczosResult lr;
     std::string lm = lanczos_lambda_max(pa, c->mat.k0, c->mat.rho0 * c->mat.c0, c->perf.w_b * c->perf.c_b,
@@ -967,7 +967,8 @@ static int init_common(fedfem_ctx* c, bool per_lane = false) {
        "init kernel");
     if (int r = mirror_T(c)) return r;
     if (c->dose)
-        CU(cudaMemsetAsync(c->dose, 0, sizeof(double) * std::max<int64_t>(1, c->L.N_free), c->stream), "dose reset");
+        CU(cudaMemsetAsync(c->dose, 0, sizeof(double) * std::max<int64_t>(1, c->L.N_free * c->n_lanes), c->stream),
+           "dose reset");
     int r = reset_status(c);
     if (r) return r;
     c->inited = true;
@@ -1151,7 +1152,7 @@ int fedfem_get_state(fedfem_ctx* c, void* buf, size_t* bytes) {
     if (!c->inited) return fail(c, FEDFEM_E_STATE, "init first");
     const size_t tb = (c->precision == FEDFEM_FP64 ? sizeof(double) : sizeof(float)) * c->N * c->n_lanes;
     const size_t lb = (c->precision == FEDFEM_FP64 ? 0 : sizeof(float) * c->N * c->n_lanes);
-    const size_t db = c->dose ? sizeof(double) * c->L.N_free : 0;
+    const size_t db = c->dose ? sizeof(double) * c->L.N_free * c->n_lanes : 0;
     const size_t need = sizeof(StateHeader) + tb + lb + db;
     if (!buf) { *bytes = need; return FEDFEM_OK; }
     if (*bytes < need) return fail(c, FEDFEM_E_ARG, "state buffer too small");
@@ -1176,7 +1177,7 @@ int fedfem_set_state(fedfem_ctx* c, const void* buf, size_t bytes) {
     std::memcpy(&h, buf, sizeof(h));
     const size_t tb = (c->precision == FEDFEM_FP64 ? sizeof(double) : sizeof(float)) * c->N * c->n_lanes;
     const size_t lb = (c->precision == FEDFEM_FP64 ? 0 : sizeof(float) * c->N * c->n_lanes);
-    const size_t db = c->dose ? sizeof(double) * c->L.N_free : 0;
+    const size_t db = c->dose ? sizeof(double) * c->L.N_free * c->n_lanes : 0;
     if (h.magic != kMagic || h.version != 1 || h.precision != c->precision || h.N != c->N || h.E != c->E ||
         h.order != c->order || h.nv != c->nv || h.payload != tb + lb + db || bytes < sizeof(h) + tb + lb + db)
         return fail(c, FEDFEM_E_ARG, "state does not match this context");

@@ -122,7 +122,7 @@ struct StepArgs {
     int n_seg;
     double seg_end[kMaxSegments];
     R seg_f[kMaxSegments];
-    // CEM43 thermal dose (one lane): dose[i] += dose_dt R^(43 - T_i), minutes
+    // CEM43 thermal dose: dose[i * lanes + l] += dose_dt R^(43 - T_il), minutes
     double* dose;
     double dose_dt;                  // dt / 60
 };

@@ -112,6 +112,17 @@ __device__ __forceinline__ void dose_add(double* dose, int64_t i, double dose_dt
 __device__ __forceinline__ void dose_add(double* dose, int64_t i, double dose_dt, float T) {
     dose[i] += dose_dt * (double)exp2f(T >= 43.0f ? T - 43.0f : 2.0f * (T - 43.0f));
 }
+// four scenario lanes: the node's four doses are contiguous
+__device__ __forceinline__ void dose_add(double* dose, int64_t i, double dose_dt, F4 T) {
+    double2* d = reinterpret_cast<double2*>(dose + 4 * i);
+    double2 a = d[0], b = d[1];
+    a.x += dose_dt * (double)exp2f(T.x >= 43.0f ? T.x - 43.0f : 2.0f * (T.x - 43.0f));
+    a.y += dose_dt * (double)exp2f(T.y >= 43.0f ? T.y - 43.0f : 2.0f * (T.y - 43.0f));
+    b.x += dose_dt * (double)exp2f(T.z >= 43.0f ? T.z - 43.0f : 2.0f * (T.z - 43.0f));
+    b.y += dose_dt * (double)exp2f(T.w >= 43.0f ? T.w - 43.0f : 2.0f * (T.w - 43.0f));
+    d[0] = a;
+    d[1] = b;
+}
 
 template <typename R, typename L, int MODE>
 __device__ __forceinline__ void node_update_v(const StepArgs<R, L>& a, int64_t i, L T, L F,
@@ -123,9 +134,7 @@ __device__ __forceinline__ void node_update_v(const StepArgs<R, L>& a, int64_t i
     L q = v.Q;
     if constexpr ((MODE & 2) != 0) {   // kernels built with the time-varying / dose extensions
         if (a.Qs) q = fmadd(schedule_factor(a, step), a.Qs[i], q);
-        if constexpr (sizeof(L) == sizeof(R)) {   // CEM43 at the step's start temperature (one lane)
-            if (a.dose) dose_add(a.dose, i, a.dose_dt, T);
-        }
+        if (a.dose) dose_add(a.dose, i, a.dose_dt, T);   // CEM43 at the step's start temperature
     }
     L r = fmadd(a.wbcb * v.V, a.T_a - T, q) - F;
     if (i >= a.N_plain) r = fmadd(v.hA, a.T_inf - T, r);

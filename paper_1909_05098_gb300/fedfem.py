@@ -111,6 +111,7 @@ _SIGS = {
     "fedfem_set_source_schedule": ([_ctx_p, C.c_int, _dp, _dp], C.c_int),
     "fedfem_enable_dose": ([_ctx_p, C.c_int], C.c_int),
     "fedfem_read_dose": ([_ctx_p, _dp], C.c_int),
+    "fedfem_read_dose_lane": ([_ctx_p, C.c_int, _dp], C.c_int),
     "fedfem_add_gaussian_source_lane": ([_ctx_p, C.c_int, C.c_int, _dp, C.c_double, C.c_double], C.c_int),
     "fedfem_set_source_lane": ([_ctx_p, C.c_int, _dp], C.c_int),
     "fedfem_read_temperature_lane": ([_ctx_p, C.c_int, _dp], C.c_int),
@@ -439,10 +440,10 @@ def fedfem_enable_dose(ctx, on=True):
     _check(ctx, _lib.fedfem_enable_dose(ctx, 1 if on else 0))
 
 
-def fedfem_read_dose(ctx) -> np.ndarray:
+def fedfem_read_dose(ctx, lane=0) -> np.ndarray:
     n = fedfem_get_info(ctx)["n_nodes"]
     out = np.empty(n, dtype=np.float64)
-    _check(ctx, _lib.fedfem_read_dose(ctx, out.ctypes.data_as(C.POINTER(C.c_double))))
+    _check(ctx, _lib.fedfem_read_dose_lane(ctx, lane, out.ctypes.data_as(C.POINTER(C.c_double))))
     return out
 
 
@@ -536,7 +537,8 @@ class Batch:
     its last one in the unused lanes.  All runs share one dt (the smallest
     critical step) and all materials/perfusion/film parameters must agree."""
 
-    def __init__(self, meshes, precision=FP32_KAHAN, device=0, stream=None, kernel=KERNEL_TILED, schedule=None):
+    def __init__(self, meshes, precision=FP32_KAHAN, device=0, stream=None, kernel=KERNEL_TILED, schedule=None,
+                 dose=False):
         self.meshes = meshes
         first = meshes[0][0]
         xyz, conn, groups, dn, dT = [], [], [], [], []
@@ -570,6 +572,8 @@ class Batch:
                         fedfem_add_gaussian_source_lane(self.ctx, lane, g, s.x0, s.sigma, s.peak)
             if schedule is not None:       # (t_end, factor): every run's sources follow it
                 fedfem_set_source_schedule(self.ctx, *schedule)
+            if dose:
+                fedfem_enable_dose(self.ctx, True)
             fedfem_set_tile(self.ctx, kernel)
             self.dt_cr = fedfem_precompute(self.ctx, min(p[0].T_lo for p in meshes),
                                            max(p[0].T_hi for p in meshes))
@@ -582,6 +586,11 @@ class Batch:
     def temperature(self, mesh: int, scenario: int) -> np.ndarray:
         T = fedfem_read_temperature_lane(self.ctx, scenario)
         return T[self.node_off[mesh]: self.node_off[mesh + 1]]
+
+    def dose(self, mesh: int, scenario: int) -> np.ndarray:
+        """CEM43 minutes of one run (needs dose=True)."""
+        D = fedfem_read_dose(self.ctx, scenario)
+        return D[self.node_off[mesh]: self.node_off[mesh + 1]]
 
     def close(self):
         if self.ctx:

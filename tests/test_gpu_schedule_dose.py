@@ -90,11 +90,12 @@ def test_checkpoint_carries_the_dose(two_stage):
         b.close()
 
 
-def test_schedule_with_scenario_lanes_equals_single_runs():
+@pytest.mark.parametrize("kernel_name", ["KERNEL_TILED", "KERNEL_TILED_STAGED"])
+def test_schedule_and_dose_with_scenario_lanes_equal_single_runs(kernel_name):
     f = ff()
     meshes = [pm.problems for pm in planning_batch(n_meshes=2, n_scenarios=4, n_range=(900, 3000), base_seed=7)]
     sched = (np.array([30.0, 1e30]), np.array([1.0, 0.25]))
-    b = f.Batch(meshes, kernel=f.KERNEL_TILED_STAGED, schedule=sched)
+    b = f.Batch(meshes, kernel=getattr(f, kernel_name), schedule=sched, dose=True)
     try:
         dt = 0.5 * b.dt_cr
         f.fedfem_step(b.ctx, dt, 120)
@@ -103,11 +104,12 @@ def test_schedule_with_scenario_lanes_equals_single_runs():
             for s_i in (0, 3):
                 p = copy.copy(scen[s_i])
                 p.schedule_end, p.schedule_factor = sched
-                s = f.Solver(p, precision=f.FP32_KAHAN, kernel=f.KERNEL_PERSISTENT)
+                s = f.Solver(p, precision=f.FP32_KAHAN, kernel=f.KERNEL_PERSISTENT, dose=True)
                 try:
                     s.step(dt, 120)
                     s.sync()
                     assert np.array_equal(b.temperature(g, s_i), s.temperature()), (g, s_i)
+                    assert np.array_equal(b.dose(g, s_i), s.dose()), (g, s_i)
                 finally:
                     s.close()
     finally:
@@ -131,11 +133,10 @@ def test_unsupported_combinations_are_refused(two_stage):
     finally:
         s.close()
     meshes = [pm.problems for pm in planning_batch(n_meshes=1, n_scenarios=2, n_range=(900, 1200), base_seed=3)]
-    b = f.Batch(meshes)
+    b = f.Batch(meshes, dose=True)
     try:
-        f.fedfem_enable_dose(b.ctx, True)
         with pytest.raises(f.FedfemError) as e:
-            f.fedfem_precompute(b.ctx, 20.0, 100.0)
-        assert e.value.code == f.E_UNSUPPORTED
+            f.fedfem_read_dose(b.ctx, 4)
+        assert e.value.code == f.E_ARG
     finally:
         b.close()
