@@ -508,6 +508,27 @@ def run_planning(args):
     ref.close()
     batched_sim = runs * dt_b * steps_b / t_b
     plain_sim = runs * dt_b / plain_wall_per_step
+    # the same batch as a treatment plan: sources on for the first half of the
+    # timed span, then off, and the CEM43 dose of every run (no graph: the
+    # schedule's start time is a launch argument)
+    b.close()
+    sched = (np.array([0.5 * dt_b * steps_b, 1e30]), np.array([1.0, 0.0]))
+    bd = ff.Batch(meshes, stream=stream.cuda_stream, kernel=tuned["kernel"], schedule=sched, dose=True)
+    ff.fedfem_set_tile(bd.ctx, tuned["kernel"], tuned.get("block", 0), tuned["tile_nodes"], tuned["blocks_per_sm"])
+    ff.fedfem_step(bd.ctx, dt_b, S)
+    ff.fedfem_sync(bd.ctx)
+    ff.fedfem_init(bd.ctx, None, float(meshes[0][0].T0))
+    e0.record(stream)
+    for _ in range(args.steps):
+        ff.fedfem_step(bd.ctx, dt_b, S)
+    e1.record(stream)
+    ff.fedfem_sync(bd.ctx)
+    torch.cuda.synchronize()
+    t_d = e0.elapsed_time(e1) / 1e3
+    dose_max = float(max(bd.dose(gi, si).max() for gi in range(len(meshes)) for si in range(4)))
+    bd.close()
+    plan = {"sim_s_per_wall_s": runs * dt_b * steps_b / t_d, "heating_s": float(sched[0][0]),
+            "max_cem43_min": dose_max}
     line = {
         "metric": "simulated s / wall s (all runs)", "value": batched_sim, "unit": "sim-s/s",
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_b / args.steps,
@@ -524,9 +545,9 @@ def run_planning(args):
                                   f"(one scenario), counted once per scenario"},
         "speedup_vs_plain": batched_sim / plain_sim,
         "max_err_vs_fp64_C": max_err,
+        "with_schedule_and_dose": plan,
         "clocks": clocks,
     }
-    b.close()
     print(json.dumps(line))
 
 
