@@ -35,6 +35,15 @@ __device__ __forceinline__ F4 operator+(F4 a, F4 b) { return F4{a.x + b.x, a.y +
 __device__ __forceinline__ F4 operator-(F4 a, F4 b) { return F4{a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w}; }
 __device__ __forceinline__ F4 operator*(F4 a, F4 b) { return F4{a.x * b.x, a.y * b.y, a.z * b.z, a.w * b.w}; }
 __device__ __forceinline__ F4 operator/(F4 a, F4 b) { return F4{a.x / b.x, a.y / b.y, a.z / b.z, a.w / b.w}; }
+
+// the explicit increment's quotient r / C: FP64 state divides exactly (IEEE);
+// FP32 state uses the fast quotient (a few ulp), far below the rounding of r
+// itself and carried into the compensated sum like any other increment
+__device__ __forceinline__ double increment_div(double a, double b) { return a / b; }
+__device__ __forceinline__ float increment_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ F4 increment_div(F4 a, F4 b) {
+    return F4{__fdividef(a.x, b.x), __fdividef(a.y, b.y), __fdividef(a.z, b.z), __fdividef(a.w, b.w)};
+}
 __device__ __forceinline__ F4 operator-(F4 a) { return F4{-a.x, -a.y, -a.z, -a.w}; }
 __device__ __forceinline__ F4 operator+(F4 a, float b) { return a + f4(b); }
 __device__ __forceinline__ F4 operator-(F4 a, float b) { return a - f4(b); }

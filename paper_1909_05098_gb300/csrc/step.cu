@@ -138,7 +138,7 @@ __device__ __forceinline__ void node_update_v(const StepArgs<R, L>& a, int64_t i
     }
     L r = fmadd(a.wbcb * v.V, a.T_a - T, q) - F;
     if (i >= a.N_plain) r = fmadd(v.hA, a.T_inf - T, r);
-    const L dT = (a.dt * r) / C;
+    const L dT = increment_div(a.dt * r, C);
     L Tn;
     if (MODE & 1) {
         const L y = dT + v.lo;
@@ -429,9 +429,19 @@ __device__ __forceinline__ void tile_nodes(const StepArgs<R, L>& a, int64_t base
                                            L T0, const NodeVals<R, L>& v0, const L* Tin, L* Tout, long long step) {
     for (int l = threadIdx.x; l < own; l += blockDim.x) {
         L F = lzero<L>();
-        for (int r = 0; r < deg; ++r) {
-            F = F + Fn[r * B + l];
-            Fn[r * B + l] = lzero<L>();
+        L* col = Fn + l;
+        int r = 0;
+        for (; r + 8 <= deg; r += 8) {   // hex interiors: one unrolled pass of 8 rows
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                F = F + col[u * B];
+                col[u * B] = lzero<L>();
+            }
+            col += 8 * B;
+        }
+        for (; r < deg; ++r, col += B) {
+            F = F + *col;
+            *col = lzero<L>();
         }
         if (l == (int)threadIdx.x) node_update_v<R, L, MODE>(a, base + l, T0, F, v0, Tout, step);
         else node_update<R, L, MODE>(a, base + l, Tin[base + l], F, Tout, step);
