@@ -332,7 +332,7 @@ int plan_tiles(fedfem_ctx* c) {
         unsigned char* Mb = b + 16;
         for (int q = 0; q < 6; ++q)
             for (int64_t j = 0; j < ne; ++j)
-                std::memcpy(Mb + rs * (q * ne_pad + j), Mh.data() + rs * (q * E + t.e_glob[e0 + j]), rs);
+                std::memcpy(Mb + rs * (6 * j + q), Mh.data() + rs * (q * E + t.e_glob[e0 + j]), rs);
         uint16_t* lc = (uint16_t*)(Mb + rs * 6 * ne_pad);
         std::memcpy(lc, t.lconn.data() + e0 * t.nv, sizeof(uint16_t) * ne * t.nv);
         int32_t* h = (int32_t*)(lc + t.nv * ne_pad);

@@ -139,7 +139,7 @@ struct LaunchCfg {
 
 // Packed per-tile blocks of the tiled kernels, each 16-byte aligned (copied
 // whole into shared memory by one bulk (TMA) copy in the staged kernel):
-//   int32 header {ne, ne_pad, nh, deg}; M: 6 planes of ne_pad R;
+//   int32 header {ne, ne_pad, nh, deg}; M: ne_pad x 6 R (one element's six values together);
 //   local connectivity: ne_pad x nv uint16 (id | rank << rank_shift);
 //   halo ids: nh int32.
 template <typename R>

@@ -25,6 +25,17 @@ namespace fedfem {
 namespace {
 
 template <typename R>
+struct Vec2;
+template <>
+struct Vec2<float> {
+    using type = float2;
+};
+template <>
+struct Vec2<double> {
+    using type = double2;
+};
+
+template <typename R>
 struct Vec;
 template <>
 struct Vec<float> {
@@ -313,7 +324,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 template <typename R>
 struct TileView {
     int ne, ne_pad, nh, deg;
-    const R* M;                 // 6 rows of ne_pad
+    const R* M;                 // ne_pad x 6: an element's six values together
     const uint16_t* lc;         // nv entries per element
     const int32_t* halo;        // nh global node ids
 };
@@ -406,7 +417,11 @@ __device__ __forceinline__ void tile_elements(const TileView<R>& v, const Law<R>
         for (int n = 0; n < NV; ++n) tt[n] = Ts[c[n] & id_mask];
         R m[6];
 #pragma unroll
-        for (int q = 0; q < 6; ++q) m[q] = v.M[q * v.ne_pad + j];
+        for (int q = 0; q < 6; q += 2) {   // three 2-wide loads (8- or 16-byte aligned)
+            const typename Vec2<R>::type p = reinterpret_cast<const typename Vec2<R>::type*>(v.M + 6 * j)[q / 2];
+            m[q] = p.x;
+            m[q + 1] = p.y;
+        }
         const L ke = element_k<R, NV, L>(tt, k);
         L F[NV];
         if (NV == 8) hex8_loads<R, L>(tt, m, ke, F);
