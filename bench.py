@@ -201,10 +201,15 @@ KERNEL_SOURCES = ("step.cu", "elem_math.cuh", "fedfem_internal.h", "api.cu", "ho
 
 
 def kernel_source_hash():
+    """Hash of the kernel sources with comments and blank lines removed (a
+    comment edit does not change the kernel)."""
     csrc = os.path.join(ROOT, "paper_1909_05098_gb300", "csrc")
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        h.update(open(os.path.join(csrc, f), "rb").read())
+        text = open(os.path.join(csrc, f), encoding="utf-8").read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        h.update("\n".join(line.rstrip() for line in text.splitlines() if line.strip()).encode())
     return h.hexdigest()[:16]
 
 

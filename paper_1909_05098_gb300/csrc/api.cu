@@ -251,15 +251,16 @@ size_t tile_smem(const Tiles& t, size_t rs, size_t ls, int* max_block, bool stag
     return (b + 15) / 16 * 16;
 }
 
-// Tiles for the tiled kernels.  Default size: 256 owned hex nodes (128 tet
-// nodes; halved in FP64) per tile, then adjusted so the tile count is a whole
-// number of waves of the resident grid (every block gets the same number of
-// tiles).  Each tile's constant data is packed into one 16-byte-aligned block.
 // threads per block of the staged kernel: the block knob if it names a built size
 int staged_threads(const fedfem_ctx* c) {
     return c->tile.block == 256 || c->tile.block == 1024 ? c->tile.block : tiled_threads();
 }
 
+// Tiles for the tiled kernels.  The requested size is used as given; the
+// default (512 owned hex nodes staged, 256 direct; 256 / 128 tet nodes; halved
+// in FP64 and with scenario lanes) is moved to the nearest size that gives
+// every resident block the same number of tiles.  Each tile's constant data
+// is packed into one 16-byte-aligned block (see tile_block_bytes).
 int plan_tiles(fedfem_ctx* c) {
     if (c->tiles_ok) return FEDFEM_OK;
     const bool staged = c->tile.kernel == FEDFEM_KERNEL_TILED_STAGED;
@@ -1216,7 +1217,7 @@ int fedfem_get_info(fedfem_ctx* c, fedfem_info* info) {
     // a source schedule reads the source part of Q too; the dose is read and written in FP64
     const int64_t extra = (c->sched_f.empty() ? 0 : NF * NL * R) + (c->dose ? NF * 16 : 0);
     info->algorithmic_bytes_per_step += extra;
-    // two-phase / persistent model: + slot write and read, gather ids, slice offsets, T gather read once
+    // two-phase / persistent model: + slot write and read, gather ids, their slice offsets, T gathered once
     info->bytes_per_step = info->algorithmic_bytes_per_step + E * c->nv * 2 * R + (int64_t)L.sell_ids.size() * 4 +
                            (int64_t)L.sell_off.size() * 4;
     if ((c->tile.kernel == FEDFEM_KERNEL_TILED || c->tile.kernel == FEDFEM_KERNEL_TILED_STAGED) && c->tiles_ok) {
