@@ -1,5 +1,6 @@
 """Pins of the surrogate's FP64 reference network (the gradient oracle):
-central finite differences and permutation equivariance."""
+central finite differences, permutation equivariance, L-hop locality and
+translation invariance."""
 import numpy as np
 import pytest
 
@@ -57,3 +58,73 @@ def test_permutation_equivariance():
     order = np.lexsort((s2, d2))
     y2, _ = mpnn.forward(flat, x[:, inv], f[order], s2[order], d2[order], H, L)
     np.testing.assert_allclose(y2[:, perm], y, rtol=1e-12, atol=1e-12)
+
+
+def _hops(src, dst, N, start):
+    """Graph distance from `start` along edges src -> dst (breadth-first)."""
+    dist = np.full(N, np.inf)
+    dist[start] = 0
+    frontier = [start]
+    adj = [[] for _ in range(N)]
+    for s, d in zip(src, dst):
+        adj[s].append(d)
+    k = 0
+    while frontier:
+        k += 1
+        nxt = []
+        for u in frontier:
+            for v in adj[u]:
+                if dist[v] == np.inf:
+                    dist[v] = k
+                    nxt.append(v)
+        frontier = nxt
+    return dist
+
+
+@pytest.mark.parametrize("L", [1, 2, 3])
+def test_l_layers_see_exactly_l_hops(L):
+    """Message passing over in-edges: after L layers a node's output depends on
+    the inputs within L hops and on none farther away.  Perturbing one node's
+    input must change every node within L hops (generic weights) and no other."""
+    H = 8
+    m = hex_box(8, 1, 1, 1e-3)                         # a chain of cubes: long graph distances
+    N = len(m.xyz)
+    src, dst = mesh_edges(m.conn, N)
+    d = (m.xyz[dst] - m.xyz[src]) / 1e-3
+    f = np.concatenate([d, np.linalg.norm(d, axis=1, keepdims=True)], axis=1)
+    rng = np.random.default_rng(7)
+    flat = rng.normal(size=mpnn.n_params(H, L)) * 0.5
+    x = rng.normal(size=(1, N, 5))
+    y0, _ = mpnn.forward(flat, x, f, src, dst, H, L)
+    start = 0
+    x1 = x.copy()
+    x1[0, start] += 0.3
+    y1, _ = mpnn.forward(flat, x1, f, src, dst, H, L)
+    changed = np.abs(y1[0] - y0[0]) > 1e-12
+    dist = _hops(src, dst, N, start)
+    assert np.all(changed[dist <= L]) and not np.any(changed[dist > L])
+    assert np.any(dist > L)
+
+
+def test_translation_and_rotation_of_the_mesh_change_nothing_that_they_should_not():
+    """Edge inputs are relative positions: a translation leaves the output
+    unchanged; a rotation by 90 degrees about z permutes the x/y edge inputs
+    and so (for generic weights) does change it."""
+    H, L = 8, 2
+    m = hex_box(2, 2, 1, 1e-3)
+    N = len(m.xyz)
+    src, dst = mesh_edges(m.conn, N)
+
+    def feats(xyz):
+        d = (xyz[dst] - xyz[src]) / 1e-3
+        return np.concatenate([d, np.linalg.norm(d, axis=1, keepdims=True)], axis=1)
+
+    rng = np.random.default_rng(11)
+    flat = rng.normal(size=mpnn.n_params(H, L)) * 0.5
+    x = rng.normal(size=(2, N, 5))
+    y, _ = mpnn.forward(flat, x, feats(m.xyz), src, dst, H, L)
+    yt, _ = mpnn.forward(flat, x, feats(m.xyz + np.array([0.3, -0.2, 0.7])), src, dst, H, L)
+    np.testing.assert_allclose(yt, y, rtol=1e-9, atol=1e-12)
+    rot = m.xyz[:, [1, 0, 2]] * np.array([-1.0, 1.0, 1.0])
+    yr, _ = mpnn.forward(flat, x, feats(rot), src, dst, H, L)
+    assert np.max(np.abs(yr - y)) > 1e-6
