@@ -128,3 +128,33 @@ def test_uniform_field_bit_unchanged_on_gpu():
         for kernel in (f.KERNEL_TWO_PHASE, f.KERNEL_PERSISTENT, f.KERNEL_TILED, f.KERNEL_TILED_STAGED):
             T, _ = run_gpu(p, 1.0, 200, prec, kernel=kernel)
             assert np.all(T == 37.0), (prec, kernel)
+
+
+@pytest.mark.parametrize("prec_name", ["FP64", "FP32_KAHAN"])
+@pytest.mark.parametrize("mesh", ["tet", "hex"])
+def test_section_3_1_6_laws_with_density_varying(prec_name, mesh):
+    """The temperature-dependent variant the paper verifies (Section 3.1.6,
+    Table 5): rho, c and k all linear in T through their 37 and 65 degC values
+    (rho falls from 1040 to 1000 kg/m^3), on a tet and a hex mesh."""
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
+    g = g["td_properties_sec_3_1_6"]
+    from synth.problem import Material
+    mat = Material.from_two_points(g["T1"], g["T2"], tuple(g["rho"]), tuple(g["c"]), tuple(g["k"]))
+    assert mat.drho != 0.0
+    if mesh == "tet":
+        w = ellipsoid_tet_td(h=1.5e-3, axes=(0.024, 0.018, 0.014), n_steps=1200)
+    else:
+        w = cube_hex_td_convective(n=12)
+    p = copy.copy(w.problem)
+    p.material = mat
+    orc = Oracle(p)
+    dt = 0.5 * critical_dt(orc)
+    ref = orc.run(dt, 800)
+    f = ff()
+    T, info = run_gpu(p, dt, 800, getattr(f, prec_name))
+    assert info["dt_cr"] == pytest.approx(critical_dt(orc), rel=1e-9)
+    err = max_abs(T, ref)
+    print(f"Section 3.1.6 laws, {mesh} {p.n_nodes} nodes {prec_name}: max|dT| = {err:.3e}, max T = {ref.max():.2f}")
+    assert err <= (TOL64 if prec_name == "FP64" else TOL32)
