@@ -25,9 +25,13 @@ from .global_form import Oracle
 
 
 def td_scale(material, T_lo: float, T_hi: float) -> float:
-    """The factor s above for linear laws.  rho(T) c(T) is a quadratic in T,
-    so its minimum over [T_lo, T_hi] is at an end point or at its vertex."""
+    """The factor s above.  For linear laws rho(T) c(T) is a quadratic in T,
+    so its minimum over [T_lo, T_hi] is at an end point or at its vertex; for
+    tabulated laws the same holds on every interval, and k is largest at an
+    end point or a table point."""
     m = material
+    if m.table is not None:
+        return _td_scale_table(m, T_lo, T_hi)
     k_max = max(m.k0 + m.dk * (T_lo - m.T_ref), m.k0 + m.dk * (T_hi - m.T_ref))
     cands = [T_lo, T_hi]
     a = m.drho * m.dc                       # rho c = (rho0 + drho u)(c0 + dc u), u = T - T_ref
@@ -38,6 +42,29 @@ def td_scale(material, T_lo: float, T_hi: float) -> float:
     rc_min = min((m.rho0 + m.drho * (T - m.T_ref)) * (m.c0 + m.dc * (T - m.T_ref)) for T in cands)
     if rc_min <= 0.0:
         raise ValueError("rho(T) c(T) is not positive on the declared range")
+    return max(1.0, k_max / m.k0) * max(1.0, m.rho0 * m.c0 / rc_min)
+
+
+def _td_scale_table(m, T_lo: float, T_hi: float) -> float:
+    from .global_form import piecewise_linear
+    Tj, rho, c, k = (np.asarray(a, dtype=np.float64) for a in m.table)
+    pts = [T_lo, T_hi] + [t for t in Tj if T_lo < t < T_hi]
+    k_max = float(np.max(piecewise_linear(Tj, k, np.array(pts))))
+    cands = list(pts)
+    n = len(Tj)
+    for i in range(n - 1):                  # vertex of rho c on interval i (also the extended end ones)
+        sr = (rho[i + 1] - rho[i]) / (Tj[i + 1] - Tj[i])
+        sc = (c[i + 1] - c[i]) / (Tj[i + 1] - Tj[i])
+        if sr * sc != 0.0:
+            tv = Tj[i] - (rho[i] * sc + c[i] * sr) / (2.0 * sr * sc)
+            lo = -np.inf if i == 0 else Tj[i]
+            hi = np.inf if i == n - 2 else Tj[i + 1]
+            if max(lo, T_lo) < tv < min(hi, T_hi):
+                cands.append(tv)
+    cands = np.array(cands)
+    rc_min = float(np.min(piecewise_linear(Tj, rho, cands) * piecewise_linear(Tj, c, cands)))
+    if rc_min <= 0.0 or np.min(piecewise_linear(Tj, k, np.array(pts))) <= 0.0:
+        raise ValueError("rho(T) c(T) or k(T) is not positive on the declared range")
     return max(1.0, k_max / m.k0) * max(1.0, m.rho0 * m.c0 / rc_min)
 
 

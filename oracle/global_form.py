@@ -12,6 +12,9 @@ time-stepping block, taken in its global matrix form):
 5. T <- T + dt R / C on free nodes (Eq. 8, Eq. 19); Dirichlet nodes keep
    their initial value (Eq. 3).
 
+Material laws are linear in T (Section 3.1.6) or, optionally, piecewise
+linear through tabulated points, extended linearly beyond the table.
+
 Time-varying loads (the boundary/load update at the end of each step of
 Algorithm 1; the two-stage heating and relaxation of Section 3.1.5): the
 regional source part of Q is scaled by the schedule factor of the step's start
@@ -106,14 +109,20 @@ class Oracle:
     # --- material laws (linear in T, Section 3.1.6) -------------------------
     def k_of(self, T):
         m = self.p.material
+        if m.table is not None:
+            return piecewise_linear(m.table[0], m.table[3], T)
         return m.k0 + m.dk * (T - m.T_ref)
 
     def rho_of(self, T):
         m = self.p.material
+        if m.table is not None:
+            return piecewise_linear(m.table[0], m.table[1], T)
         return m.rho0 + m.drho * (T - m.T_ref)
 
     def c_of(self, T):
         m = self.p.material
+        if m.table is not None:
+            return piecewise_linear(m.table[0], m.table[2], T)
         return m.c0 + m.dc * (T - m.T_ref)
 
     # --- Eq. 11 and Eq. 13: global conduction matrix at the current field ---
@@ -173,6 +182,18 @@ class Oracle:
                 D = D + cem43_increment(T, dt)
             T = self.step(T, dt, k * dt)
         return (T, D) if dose else T
+
+
+def piecewise_linear(Tj, pj, T):
+    """p(T) through the points (Tj, pj): on the interval [Tj[i], Tj[i+1]] that
+    holds T, and along the first / last interval outside the table,
+    p = pj[i] + slope_i (T - Tj[i]) with slope_i = (pj[i+1] - pj[i]) / (Tj[i+1] - Tj[i])."""
+    Tj = np.asarray(Tj, dtype=np.float64)
+    pj = np.asarray(pj, dtype=np.float64)
+    T = np.asarray(T, dtype=np.float64)
+    i = np.clip(np.searchsorted(Tj, T, side="right") - 1, 0, len(Tj) - 2)
+    slope = (pj[1:] - pj[:-1]) / (Tj[1:] - Tj[:-1])
+    return pj[i] + slope[i] * (T - Tj[i])
 
 
 def cem43_increment(T, dt: float) -> np.ndarray:

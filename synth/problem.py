@@ -35,9 +35,24 @@ class Material:
     k0: float
     dk: float
 
+    # Optional piecewise-linear tables (T_j, rho_j, c_j, k_j), T_j increasing,
+    # linear inside each interval and along the end intervals beyond the table.
+    # When set, T_ref/rho0/c0/k0 are the first point and the linear slopes unused.
+    table: Optional[tuple] = None
+
     @staticmethod
     def constant(rho: float, c: float, k: float, T_ref: float = 37.0) -> "Material":
         return Material(T_ref, rho, 0.0, c, 0.0, k, 0.0)
+
+    @staticmethod
+    def tabulated(T, rho, c, k) -> "Material":
+        """Piecewise-linear laws through the points (T_j, rho_j), (T_j, c_j), (T_j, k_j)."""
+        T, rho, c, k = (tuple(float(v) for v in a) for a in (T, rho, c, k))
+        if not (2 <= len(T) <= 8 and len(rho) == len(c) == len(k) == len(T)):
+            raise ValueError("2 to 8 points, one value of each property per point")
+        if any(b <= a for a, b in zip(T, T[1:])):
+            raise ValueError("table temperatures must increase")
+        return Material(T[0], rho[0], 0.0, c[0], 0.0, k[0], 0.0, table=(T, rho, c, k))
 
     @staticmethod
     def from_two_points(T1: float, T2: float, rho: tuple, c: tuple, k: tuple) -> "Material":
