@@ -141,8 +141,26 @@ int fedfem_set_mesh(fedfem_ctx* ctx, int elem_type, int64_t n_nodes, const doubl
 /* Element order used internally (FEDFEM_ORDER_*; default MORTON). */
 int fedfem_set_order(fedfem_ctx* ctx, int order);
 
-/* Homogeneous tissue laws (Eq. 2). */
+/* Homogeneous tissue laws (Eq. 2), linear in T.  Clears any table set by
+ * fedfem_set_material_table. */
 int fedfem_set_material(fedfem_ctx* ctx, const fedfem_material* m);
+
+/* Tabulated laws: Section 3.1.6 gives rho, c and k at two temperatures (a
+ * two-point table, the linear laws above); n points give piecewise-linear
+ * laws.  T: n strictly increasing temperatures (degC); rho, c, k: the values
+ * at each (kg/m^3, J/(kg K), W/(m K)), n in 2..8.  Inside [T[0], T[n-1]]
+ * each property is linear on the interval that holds T; below and above the
+ * table the first and last intervals extend linearly.  The first point is
+ * the reference state of the critical step (k0 = k[0], rho0 c0 = rho[0]
+ * c[0]), which fedfem_precompute bounds over [T_lo, T_hi] as for linear
+ * laws; E_RANGE there if rho c or k is not positive on that range.
+ * Replaces the material (a later fedfem_set_material replaces the table).
+ * Host arrays, copied; E_ARG for non-finite values, T not increasing, or
+ * rho[0], c[0], k[0] not positive.  Steps of a context with a table run the
+ * kernel builds that hold the source-schedule and dose paths.
+ * (fedfem_step_static, which has no context, takes linear laws only.) */
+int fedfem_set_material_table(fedfem_ctx* ctx, int n, const double* T, const double* rho, const double* c,
+                              const double* k);
 
 /* Perfusion and metabolism (Eq. 1); K_b and Q_b are lumped (Section 2.3.5). */
 int fedfem_set_perfusion(fedfem_ctx* ctx, const fedfem_perfusion* p);

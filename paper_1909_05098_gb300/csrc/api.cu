@@ -7,6 +7,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "fedfem_internal.h"
@@ -44,6 +45,8 @@ struct fedfem_ctx {
     std::vector<double> flux;                     // empty: none
     std::vector<double> sched_end, sched_f;       // source schedule (empty: sources always on)
     bool dose_on = false;
+    int tab_n = 0;                                // piecewise-linear laws (0: linear laws of mat)
+    double tab_T[kMaxTable] = {}, tab_p[3][kMaxTable] = {};   // points; P: 0 rho, 1 c, 2 k
     fedfem_tile tile{FEDFEM_KERNEL_PERSISTENT, 256, 0, 0};
     // ---- pre-computed ----
     bool pre = false, inited = false;
@@ -59,6 +62,8 @@ struct fedfem_ctx {
     int32_t *sell_off = nullptr, *sell_ids = nullptr;
     double *V64 = nullptr, *Q64 = nullptr, *hA64 = nullptr, *Qs64 = nullptr;
     float *V32 = nullptr, *Q32 = nullptr, *hA32 = nullptr, *Qs32 = nullptr;
+    double* tab64 = nullptr;   // device copy of the property table (7 x kMaxTable), state precision
+    float* tab32 = nullptr;
     double* dose = nullptr;                       // CEM43 minutes per free node
     void* T = nullptr;
     void* T2 = nullptr;
@@ -127,6 +132,7 @@ void free_device(fedfem_ctx* c) {
     c->dev_bytes = 0;
     c->conn4 = nullptr; c->M64 = nullptr; c->M32 = nullptr; c->sell_off = c->sell_ids = nullptr;
     c->V64 = c->Q64 = c->hA64 = c->Qs64 = nullptr; c->V32 = c->Q32 = c->hA32 = c->Qs32 = nullptr;
+    c->tab64 = nullptr; c->tab32 = nullptr;
     c->dose = nullptr;
     c->T = nullptr; c->T2 = nullptr; c->Tlo = nullptr; c->slots = nullptr; c->node_of = nullptr; c->T_dir = nullptr;
     c->io = nullptr; c->st = nullptr;
@@ -159,9 +165,51 @@ void invalidate(fedfem_ctx* c) {
 
 bool is_finite(double v) { return std::isfinite(v); }
 
+// slope of property P on table interval j
+double tab_slope(const fedfem_ctx* c, int P, int j) {
+    return (c->tab_p[P][j + 1] - c->tab_p[P][j]) / (c->tab_T[j + 1] - c->tab_T[j]);
+}
+
+// property P of the table at T (the interval that holds T, the end ones outside)
+double tab_eval(const fedfem_ctx* c, int P, double T) {
+    int j = 0;
+    while (j + 1 < c->tab_n - 1 && T >= c->tab_T[j + 1]) ++j;
+    return c->tab_p[P][j] + tab_slope(c, P, j) * (T - c->tab_T[j]);
+}
+
+// property_scale for tables: k is largest at an end point or a table point;
+// rho c is a quadratic on every interval, smallest at an end point, a table
+// point or the vertex of an interval's quadratic inside it.
+int property_scale_table(fedfem_ctx* c, double lo, double hi, double* s_out) {
+    std::vector<double> pts{lo, hi};
+    for (int j = 0; j < c->tab_n; ++j)
+        if (lo < c->tab_T[j] && c->tab_T[j] < hi) pts.push_back(c->tab_T[j]);
+    double kmax = -INFINITY, kmin = INFINITY;
+    for (double T : pts) {
+        kmax = std::max(kmax, tab_eval(c, 2, T));
+        kmin = std::min(kmin, tab_eval(c, 2, T));
+    }
+    std::vector<double> cand = pts;
+    for (int j = 0; j + 1 < c->tab_n; ++j) {
+        const double sr = tab_slope(c, 0, j), sc = tab_slope(c, 1, j);
+        if (sr * sc == 0.0) continue;
+        const double tv = c->tab_T[j] - (c->tab_p[0][j] * sc + c->tab_p[1][j] * sr) / (2.0 * sr * sc);
+        const double a = j == 0 ? -INFINITY : c->tab_T[j];
+        const double b = j + 2 == c->tab_n ? INFINITY : c->tab_T[j + 1];
+        if (std::max(a, lo) < tv && tv < std::min(b, hi)) cand.push_back(tv);
+    }
+    double rc_min = INFINITY;
+    for (double T : cand) rc_min = std::min(rc_min, tab_eval(c, 0, T) * tab_eval(c, 1, T));
+    if (!(rc_min > 0) || !(kmin > 0)) return fail(c, FEDFEM_E_RANGE, "rho(T) c(T) or k(T) is not positive on [T_lo, T_hi]");
+    const double rc0 = c->tab_p[0][0] * c->tab_p[1][0];
+    *s_out = std::max(1.0, kmax / c->tab_p[2][0]) * std::max(1.0, rc0 / rc_min);
+    return FEDFEM_OK;
+}
+
 // s = max(1, max k/k0) * max(1, max rho0 c0 / (rho c)) over [lo, hi]; rho c is
 // quadratic in T, so its minimum is at an end point or the vertex.
 int property_scale(fedfem_ctx* c, double lo, double hi, double* s_out) {
+    if (c->tab_n > 0) return property_scale_table(c, lo, hi, s_out);
     const fedfem_material& m = c->mat;
     auto k = [&](double T) { return m.k0 + m.dk * (T - m.T_ref); };
     auto rc = [&](double T) { return (m.rho0 + m.drho * (T - m.T_ref)) * (m.c0 + m.dc * (T - m.T_ref)); };
@@ -216,6 +264,9 @@ StepArgs<R, L> make_args(fedfem_ctx* c, const R* M, const R* V, const R* Q, cons
     a.dt = (R)dt; a.T_lo = (R)c->T_lo; a.T_hi = (R)c->T_hi;
     a.status = c->st;
     a.step0 = c->steps_issued;
+    a.n_tab = c->tab_n;
+    for (int j = 0; j < c->tab_n; ++j) a.tab_T[j] = (R)c->tab_T[j];
+    a.tab = std::is_same<R, double>::value ? (const R*)c->tab64 : (const R*)c->tab32;
     return a;
 }
 
@@ -545,6 +596,32 @@ int fedfem_set_material(fedfem_ctx* c, const fedfem_material* m) {
         if (!is_finite(x)) return fail(c, FEDFEM_E_ARG, "non-finite material value");
     if (!(m->rho0 > 0 && m->c0 > 0 && m->k0 > 0)) return fail(c, FEDFEM_E_ARG, "rho0, c0 and k0 must be positive");
     c->mat = *m;
+    c->has_mat = true;
+    c->tab_n = 0;
+    invalidate(c);
+    return FEDFEM_OK;
+}
+
+int fedfem_set_material_table(fedfem_ctx* c, int n, const double* T, const double* rho, const double* cp,
+                              const double* k) {
+    if (!c) return FEDFEM_E_ARG;
+    if (n < 2 || n > kMaxTable || !T || !rho || !cp || !k)
+        return fail(c, FEDFEM_E_ARG, "material table: 2.." + std::to_string(kMaxTable) + " points");
+    for (int j = 0; j < n; ++j) {
+        if (!(is_finite(T[j]) && is_finite(rho[j]) && is_finite(cp[j]) && is_finite(k[j])))
+            return fail(c, FEDFEM_E_ARG, "material table: non-finite value");
+        if (j > 0 && !(T[j] > T[j - 1])) return fail(c, FEDFEM_E_ARG, "material table: T must increase");
+    }
+    if (!(rho[0] > 0 && cp[0] > 0 && k[0] > 0))
+        return fail(c, FEDFEM_E_ARG, "material table: rho, c and k at the first point must be positive");
+    c->tab_n = n;
+    for (int j = 0; j < n; ++j) {
+        c->tab_T[j] = T[j];
+        c->tab_p[0][j] = rho[j];
+        c->tab_p[1][j] = cp[j];
+        c->tab_p[2][j] = k[j];
+    }
+    c->mat = fedfem_material{T[0], rho[0], 0.0, cp[0], 0.0, k[0], 0.0};
     c->has_mat = true;
     invalidate(c);
     return FEDFEM_OK;
@@ -893,6 +970,26 @@ int fedfem_precompute(fedfem_ctx* c, double T_lo, double T_hi, double* dt_cr_out
         CU(launch_nodal(pc, st), "nodal kernel");
     }
     if (c->dose_on) CU(dalloc(c, &c->dose, sizeof(double) * std::max<int64_t>(1, NF * NL)), "alloc");
+    if (c->tab_n > 0) {   // [T_j | rho_j | c_j | k_j | slopes of rho, c, k], kMaxTable each
+        double h[7 * kMaxTable] = {};
+        for (int j = 0; j < c->tab_n; ++j) {
+            h[j] = c->tab_T[j];
+            for (int P = 0; P < 3; ++P) {
+                h[(1 + P) * kMaxTable + j] = c->tab_p[P][j];
+                h[(4 + P) * kMaxTable + j] = j + 1 < c->tab_n ? tab_slope(c, P, j) : 0.0;
+            }
+        }
+        float f[7 * kMaxTable];
+        for (int q = 0; q < 7 * kMaxTable; ++q) f[q] = (float)h[q];
+        if (c->precision == FEDFEM_FP64) {
+            CU(dalloc(c, &c->tab64, sizeof(h)), "alloc");
+            CU(cudaMemcpyAsync(c->tab64, h, sizeof(h), cudaMemcpyHostToDevice, st), "copy");
+        } else {
+            CU(dalloc(c, &c->tab32, sizeof(f)), "alloc");
+            CU(cudaMemcpyAsync(c->tab32, f, sizeof(f), cudaMemcpyHostToDevice, st), "copy");
+        }
+        CU(cudaStreamSynchronize(st), "copy");   // h and f are on this stack frame
+    }
     CU(cudaStreamSynchronize(st), "nodal kernel");
     LanczosResult lr;
     std::string lm = lanczos_lambda_max(pa, c->mat.k0, c->mat.rho0 * c->mat.c0, c->perf.w_b * c->perf.c_b,

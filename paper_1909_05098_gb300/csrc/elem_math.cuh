@@ -97,9 +97,9 @@ __device__ __forceinline__ void tet4_loads(const L t[4], const R m[6], L ke, L F
     F[1] = q0; F[2] = q1; F[3] = q2;
 }
 
-// k_e of Eq. 13: mean over the element's nodes of k(T_n)
-template <typename R, int NV, typename L = R>
-__device__ __forceinline__ L element_k(const L t[NV], const Law<R>& k) {
+// k_e of Eq. 13: mean over the element's nodes of k(T_n)  (K: a law with at())
+template <typename R, int NV, typename L = R, typename K>
+__device__ __forceinline__ L element_k(const L t[NV], const K& k) {
     L s = k.at(t[0]);
 #pragma unroll
     for (int n = 1; n < NV; ++n) s = s + k.at(t[n]);

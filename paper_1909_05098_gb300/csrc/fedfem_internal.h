@@ -94,6 +94,7 @@ struct DevStatus {
 // R: type of the element matrices and node constants; L: type of one node's
 // temperature state -- R itself, or F4 for four scenario lanes.
 constexpr int kMaxSegments = 8;   // pieces of a source schedule
+constexpr int kMaxTable = 8;      // points of a piecewise-linear property table
 
 template <typename R, typename L = R>
 struct StepArgs {
@@ -125,6 +126,14 @@ struct StepArgs {
     // CEM43 thermal dose: dose[i * lanes + l] += dose_dt R^(43 - T_il), minutes
     double* dose;
     double dose_dt;                  // dt / 60
+    // piecewise-linear laws (n_tab > 0): property P (0 rho, 1 c, 2 k) is
+    // p_P[j] + s_P[j] (T - T_j) on the interval j that holds T (the first one
+    // below the table, the last one above it).  tab: device array of 7 rows of
+    // kMaxTable, [T_j | p_rho | p_c | p_k | s_rho | s_c | s_k]; tab_T: the T_j
+    // again, as launch arguments, for the interval search.
+    int n_tab;
+    R tab_T[kMaxTable];
+    const R* tab;
 };
 
 // Launchers (step.cu).  mode: FEDFEM_FP64 / FEDFEM_FP32_KAHAN / FEDFEM_FP32_PLAIN.

@@ -51,7 +51,42 @@ struct Vec<double> {
     }
 };
 
-template <typename R, int NV>
+// Property P (0 rho, 1 c, 2 k) of a piecewise-linear table at T.  The table
+// points increase, so the interval j is the number of interior points <= T
+// (compares against launch arguments); its start, value and slope are then
+// three cached loads.
+template <int P, typename R, typename L>
+__device__ __forceinline__ R tab_law(const StepArgs<R, L>& a, R T) {
+    int j = 0;
+#pragma unroll
+    for (int q = 1; q < kMaxTable - 1; ++q) j += (q < a.n_tab - 1 && T >= a.tab_T[q]) ? 1 : 0;
+    const R* t = a.tab + j;
+    return fmadd(__ldg(t + (4 + P) * kMaxTable), T - __ldg(t), __ldg(t + (1 + P) * kMaxTable));
+}
+template <int P, typename R, typename L>
+__device__ __forceinline__ F4 tab_law(const StepArgs<R, L>& a, F4 T) {
+    return F4{tab_law<P>(a, T.x), tab_law<P>(a, T.y), tab_law<P>(a, T.z), tab_law<P>(a, T.w)};
+}
+
+// k(T) of kernels built with the extensions: the table when one is set, else
+// the linear law
+template <typename R, typename L>
+struct ExtKLaw {
+    const StepArgs<R, L>& a;
+    template <typename X>
+    __device__ __forceinline__ X at(X T) const {
+        if (a.n_tab > 0) return tab_law<2>(a, T);
+        return fmadd(a.dk, T - a.T_ref, a.k0);
+    }
+};
+
+template <int MODE, typename R, typename L>
+__device__ __forceinline__ auto k_law(const StepArgs<R, L>& a) {
+    if constexpr ((MODE & 2) != 0) return ExtKLaw<R, L>{a};
+    else return Law<R>{a.T_ref, a.k0, a.dk};
+}
+
+template <typename R, int NV, int MODE>
 __device__ __forceinline__ void element_phase(const StepArgs<R>& a, int64_t e) {
     const int64_t E = a.E;
     int c[8];
@@ -67,7 +102,7 @@ __device__ __forceinline__ void element_phase(const StepArgs<R>& a, int64_t e) {
     R t[NV];
 #pragma unroll
     for (int n = 0; n < NV; ++n) t[n] = a.T[c[n]];
-    const Law<R> k{a.T_ref, a.k0, a.dk};
+    const auto k = k_law<MODE>(a);
     const R ke = element_k<R, NV>(t, k);
     R F[NV];
     if (NV == 8) hex8_loads<R>(t, m, ke, F);
@@ -139,8 +174,14 @@ template <typename R, typename L, int MODE>
 __device__ __forceinline__ void node_update_v(const StepArgs<R, L>& a, int64_t i, L T, L F,
                                               const NodeVals<R, L>& v, L* Tout, long long step) {
     const L u = T - a.T_ref;
-    const L rho = fmadd(a.drho, u, a.rho0);
-    const L c = fmadd(a.dc, u, a.c0);
+    L rho = fmadd(a.drho, u, a.rho0);
+    L c = fmadd(a.dc, u, a.c0);
+    if constexpr ((MODE & 2) != 0) {
+        if (a.n_tab > 0) {
+            rho = tab_law<0>(a, T);
+            c = tab_law<1>(a, T);
+        }
+    }
     const L C = (v.V * rho) * c;
     L q = v.Q;
     if constexpr ((MODE & 2) != 0) {   // kernels built with the time-varying / dose extensions
@@ -179,11 +220,11 @@ __device__ __forceinline__ void node_phase(const StepArgs<R>& a, int64_t i, long
     node_update<R, R, MODE>(a, i, a.T[i], F, a.T, step);
 }
 
-template <typename R, int NV>
+template <typename R, int NV, int MODE>
 __global__ void __launch_bounds__(256) k_elem(StepArgs<R> a) {
     if (*(volatile int*)&a.status->flags) return;
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e < a.E) element_phase<R, NV>(a, e);
+    if (e < a.E) element_phase<R, NV, MODE>(a, e);
 }
 
 template <typename R, int MODE>
@@ -240,7 +281,7 @@ __global__ void __launch_bounds__(256) k_persistent(StepArgs<R> a, long long n_s
     long long done = 0;
     if (!grid_barrier(a.status, target, spin_limit)) return;   // flags from an earlier call stop here
     for (long long s = 0; s < n_steps; ++s) {
-        for (int64_t e = tid; e < a.E; e += stride) element_phase<R, NV>(a, e);
+        for (int64_t e = tid; e < a.E; e += stride) element_phase<R, NV, MODE>(a, e);
         if (!grid_barrier(a.status, target, spin_limit)) break;
         for (int64_t i = tid; i < a.N_free; i += stride) node_phase<R, MODE>(a, i, a.step0 + s);
         const bool ok = grid_barrier(a.status, target, spin_limit);
@@ -405,8 +446,8 @@ __device__ __forceinline__ void tile_fetch(const int32_t* halo, int nh, int64_t 
 
 // element phase of one tile: loads of every tile element; each owned corner's
 // load goes to Fn[rank * B + local id]
-template <typename R, typename L, int NV, bool SHARED>
-__device__ __forceinline__ void tile_elements(const TileView<R>& v, const Law<R>& k, int own, int B, int rank_shift,
+template <typename R, typename L, int NV, bool SHARED, typename K>
+__device__ __forceinline__ void tile_elements(const TileView<R>& v, const K& k, int own, int B, int rank_shift,
                                               const L* Ts, L* Fn) {
     const int id_mask = (1 << rank_shift) - 1;
     for (int j = threadIdx.x; j < v.ne; j += blockDim.x) {
@@ -498,7 +539,7 @@ __global__ void __launch_bounds__(256, DirectOccupancy<L>::min_blocks) k_tiled_d
     unsigned long long target = 0;
     long long done = 0;
     if (!grid_barrier(a.status, target, spin_limit)) return;   // also orders the zeroing before first use
-    const Law<R> k{a.T_ref, a.k0, a.dk};
+    const auto k = k_law<MODE>(a);
     for (long long s = 0; s < n_steps; ++s) {
         const L* Tin = (s & 1) ? a.T2 : a.T;
         L* Tout = (s & 1) ? a.T : a.T2;
@@ -608,7 +649,7 @@ __global__ void __launch_bounds__(TPB, StagedOccupancy<L, TPB>::min_blocks)
         if (!land(0)) { fail_timeout(); stop = true; }
         else fetch(0, a.T);
     }
-    const Law<R> k{a.T_ref, a.k0, a.dk};
+    const auto k = k_law<MODE>(a);
     long long kk = 0;
     for (long long s = 0; s < n_steps && !stop; ++s) {
         const L* Tin = (s & 1) ? a.T2 : a.T;
@@ -657,7 +698,8 @@ __global__ void __launch_bounds__(TPB, StagedOccupancy<L, TPB>::min_blocks)
 }
 
 // MODE bit 0: Kahan-compensated state; bit 1: built with the time-varying
-// source and thermal-dose paths (launched only when a context enables one)
+// source, thermal-dose and tabulated-law paths (launched only when a context
+// enables one)
 template <typename R, typename L, int NV, int MODE>
 auto tiled_kernel(const TileArgs<R>& ta) {
     return !ta.staged           ? k_tiled_direct<R, L, NV, MODE>
@@ -670,7 +712,7 @@ template <typename R, typename L, int NV, bool KAHAN>
 cudaError_t launch_tiled_impl(const StepArgs<R, L>& a, const TileArgs<R>& ta, int64_t n_steps, LaunchCfg& cfg,
                               cudaStream_t s) {
     constexpr int M = KAHAN ? 1 : 0;
-    auto kern = (a.Qs || a.dose) ? tiled_kernel<R, L, NV, M | 2>(ta) : tiled_kernel<R, L, NV, M>(ta);
+    auto kern = (a.Qs || a.dose || a.n_tab > 0) ? tiled_kernel<R, L, NV, M | 2>(ta) : tiled_kernel<R, L, NV, M>(ta);
     const int b = ta.staged ? ta.threads : 256;
     cudaError_t err = cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)ta.smem_bytes);
@@ -698,12 +740,13 @@ inline int blocks_for(int64_t n, int t) {
 template <typename R, int NV, bool KAHAN>
 cudaError_t launch_impl(const StepArgs<R>& a, int64_t n_steps, LaunchCfg& cfg, cudaStream_t s) {
     constexpr int M = KAHAN ? 1 : 0;
-    const bool ext = a.Qs || a.dose;
+    const bool ext = a.Qs || a.dose || a.n_tab > 0;
     if (cfg.kernel == FEDFEM_KERNEL_TWO_PHASE) {
         const int b = cfg.block > 0 ? std::min(cfg.block, 256) : 256;
         auto node = ext ? k_node<R, M | 2> : k_node<R, M>;
+        auto elem = ext ? k_elem<R, NV, 2> : k_elem<R, NV, 0>;
         for (int64_t k = 0; k < n_steps; ++k) {
-            k_elem<R, NV><<<blocks_for(a.E, b), b, 0, s>>>(a);
+            elem<<<blocks_for(a.E, b), b, 0, s>>>(a);
             node<<<blocks_for(a.N_free, b), b, 0, s>>>(a, a.step0 + k);
         }
         return cudaGetLastError();

@@ -109,6 +109,7 @@ _SIGS = {
                             C.POINTER(fedfem_layout_info)] + [C.c_void_p] * 10, C.c_int),
     "fedfem_set_lanes": ([_ctx_p, C.c_int], C.c_int),
     "fedfem_set_source_schedule": ([_ctx_p, C.c_int, _dp, _dp], C.c_int),
+    "fedfem_set_material_table": ([_ctx_p, C.c_int, _dp, _dp, _dp, _dp], C.c_int),
     "fedfem_enable_dose": ([_ctx_p, C.c_int], C.c_int),
     "fedfem_read_dose": ([_ctx_p, _dp], C.c_int),
     "fedfem_read_dose_lane": ([_ctx_p, C.c_int, _dp], C.c_int),
@@ -199,6 +200,22 @@ def fedfem_set_order(ctx, order: int):
 def fedfem_set_material(ctx, T_ref, rho0, drho, c0, dc, k0, dk):
     m = fedfem_material(T_ref, rho0, drho, c0, dc, k0, dk)
     _check(ctx, _lib.fedfem_set_material(ctx, C.byref(m)))
+
+
+def fedfem_set_material_table(ctx, T, rho, c, k):
+    arrs = [np.asarray(a, dtype=np.float64).reshape(-1) for a in (T, rho, c, k)]
+    if len({a.shape for a in arrs}) != 1:
+        raise ValueError("T, rho, c and k differ in length")
+    ptrs = [_d(a)[1] for a in arrs]
+    _check(ctx, _lib.fedfem_set_material_table(ctx, arrs[0].shape[0], *ptrs))
+
+
+def apply_material(ctx, m):
+    """Linear laws, or the tabulated ones when the material carries a table."""
+    if getattr(m, "table", None) is not None:
+        fedfem_set_material_table(ctx, *m.table)
+    else:
+        fedfem_set_material(ctx, m.T_ref, m.rho0, m.drho, m.c0, m.dc, m.k0, m.dk)
 
 
 def fedfem_set_perfusion(ctx, w_b, c_b, T_a, Q_m=0.0):
@@ -463,8 +480,7 @@ class Solver:
             p = problem
             fedfem_set_mesh(self.ctx, p.elem_type, p.xyz, p.conn)
             fedfem_set_order(self.ctx, order)
-            m = p.material
-            fedfem_set_material(self.ctx, m.T_ref, m.rho0, m.drho, m.c0, m.dc, m.k0, m.dk)
+            apply_material(self.ctx, p.material)
             pf = p.perfusion
             fedfem_set_perfusion(self.ctx, pf.w_b, pf.c_b, pf.T_a, pf.Q_m)
             for s in p.sources:
@@ -560,8 +576,7 @@ class Batch:
             fedfem_set_mesh(self.ctx, first.elem_type, np.vstack(xyz), np.vstack(conn))
             fedfem_set_element_groups(self.ctx, np.concatenate(groups))
             fedfem_set_lanes(self.ctx, 4)
-            m = first.material
-            fedfem_set_material(self.ctx, m.T_ref, m.rho0, m.drho, m.c0, m.dc, m.k0, m.dk)
+            apply_material(self.ctx, first.material)
             pf = first.perfusion
             fedfem_set_perfusion(self.ctx, pf.w_b, pf.c_b, pf.T_a, pf.Q_m)
             fedfem_set_dirichlet(self.ctx, np.concatenate(dn), np.concatenate(dT))

@@ -58,8 +58,7 @@ class PlainEnsemble:
         ff.fedfem_set_mesh(self.ctx, p.elem_type, xyz, conn)
         ff.fedfem_set_element_groups(self.ctx, groups)
         ff.fedfem_set_lanes(self.ctx, 4)
-        m = p.material
-        ff.fedfem_set_material(self.ctx, m.T_ref, m.rho0, m.drho, m.c0, m.dc, m.k0, m.dk)
+        ff.apply_material(self.ctx, p.material)
         pf = p.perfusion
         ff.fedfem_set_perfusion(self.ctx, pf.w_b, pf.c_b, pf.T_a, pf.Q_m)
         ff.fedfem_set_dirichlet(self.ctx, dn, dT)
@@ -128,6 +127,8 @@ class Surrogate:
         self.D = torch.tensor(D, device="cuda")
         self.free = torch.tensor((1 - D).astype(np.float32), device="cuda")
         m = p.material
+        if m.table is not None:
+            raise ValueError("the surrogate's input features take linear laws, not a table")
         self.mat = (m.T_ref, m.rho0, m.drho, m.c0, m.dc, m.k0, m.dk)
         self._x = torch.empty((max_batch, self.N, 5), device="cuda")
         self._y = torch.empty((max_batch, self.N), device="cuda")
