@@ -98,8 +98,9 @@ typedef struct {
     int block;         /* threads per block: 64..1024, multiple of 32 (0 = default); the
                           staged tiled kernel is built for 256, 512 (default) and 1024 */
     int tile_nodes;    /* TILED: owned nodes per tile, multiple of 8 (0 = default: the library
-                          picks a size near 512 (hex) / 256 (tet) that gives every resident
-                          block the same number of tiles) */
+                          picks a size near 512 (hex) / 256 (tet), smaller when such tiles
+                          do not fit in shared memory, that gives every resident block the
+                          same number of tiles) */
     int blocks_per_sm; /* PERSISTENT/TILED: resident blocks per SM (0 = occupancy maximum) */
 } fedfem_tile;
 

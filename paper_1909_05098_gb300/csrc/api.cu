@@ -309,8 +309,9 @@ int staged_threads(const fedfem_ctx* c) {
 
 // Tiles for the tiled kernels.  The requested size is used as given; the
 // default (512 owned hex nodes staged, 256 direct; 256 / 128 tet nodes; halved
-// in FP64 and with scenario lanes) is moved to the nearest size that gives
-// every resident block the same number of tiles.  Each tile's constant data
+// in FP64 and with scenario lanes, and again while its tiles do not fit in
+// shared memory) is moved to the nearest size that gives every resident block
+// the same number of tiles.  Each tile's constant data
 // is packed into one 16-byte-aligned block (see tile_block_bytes).
 int plan_tiles(fedfem_ctx* c) {
     if (c->tiles_ok) return FEDFEM_OK;
@@ -334,11 +335,16 @@ int plan_tiles(fedfem_ctx* c) {
             if (c->n_lanes > 1) B0 /= 2;
         }
         B0 = (int)std::max<int64_t>(8, std::min<int64_t>(B0, (NF + 7) / 8 * 8));
-        m = build_tiles(c->L, B0, t);
-        if (!m.empty()) return fail(c, FEDFEM_E_ARG, m);
-        size_t smem = tile_smem(t, rs, ls, &mb, staged);
-        int per_sm = tiled_blocks_per_sm(c->precision, c->nv, staged, staged_threads(c), c->n_lanes, smem);
-        if (c->tile.blocks_per_sm > 0) per_sm = std::min(per_sm, c->tile.blocks_per_sm);
+        int per_sm = 0;
+        for (;;) {   // the default size halves while its tiles do not fit (meshes whose tiles hold many elements)
+            m = build_tiles(c->L, B0, t);
+            if (!m.empty()) return fail(c, FEDFEM_E_ARG, m);
+            size_t smem = tile_smem(t, rs, ls, &mb, staged);
+            per_sm = tiled_blocks_per_sm(c->precision, c->nv, staged, staged_threads(c), c->n_lanes, smem);
+            if (c->tile.blocks_per_sm > 0) per_sm = std::min(per_sm, c->tile.blocks_per_sm);
+            if (per_sm >= 1 || c->tile.tile_nodes > 0 || B0 <= 32) break;
+            B0 = std::max(32, B0 / 2 / 8 * 8);
+        }
         if (per_sm < 1) return fail(c, FEDFEM_E_UNSUPPORTED, "tile does not fit in shared memory; use smaller tile_nodes");
         B = B0;
         const int64_t grid = (int64_t)per_sm * c->sm_count;
