@@ -68,11 +68,46 @@ def _td_scale_table(m, T_lo: float, T_hi: float) -> float:
     return max(1.0, k_max / m.k0) * max(1.0, m.rho0 * m.c0 / rc_min)
 
 
+def region_scale(materials, T_lo: float, T_hi: float) -> float:
+    """The factor s for heterogeneous tissue (linear laws), against the
+    reference state of the first region's material (k0, rho0 c0):
+    s = max(1, max_r max_T k_r / k0) * max(1, rho0 c0 / min_r min_T rho_r c_r).
+    It bounds the step as td_scale does: every k_e is at most max k, and
+    C_i = sum_r W_ri rho_r c_r is at least min(rho c) V_i."""
+    ref = materials[0]
+    k_max = max(max(m.k0 + m.dk * (T_lo - m.T_ref), m.k0 + m.dk * (T_hi - m.T_ref)) for m in materials)
+    rc_min = min(_rc_min(m, T_lo, T_hi) for m in materials)
+    return max(1.0, k_max / ref.k0) * max(1.0, ref.rho0 * ref.c0 / rc_min)
+
+
+def _rc_min(m, T_lo: float, T_hi: float) -> float:
+    """min over [T_lo, T_hi] of rho(T) c(T) for linear laws (end points or the vertex)."""
+    if m.table is not None:
+        raise ValueError("heterogeneous tissue takes linear laws")
+    cands = [T_lo, T_hi]
+    a = m.drho * m.dc
+    if a != 0.0:
+        u_v = -(m.rho0 * m.dc + m.c0 * m.drho) / (2.0 * a)
+        if T_lo < m.T_ref + u_v < T_hi:
+            cands.append(m.T_ref + u_v)
+    rc = min((m.rho0 + m.drho * (T - m.T_ref)) * (m.c0 + m.dc * (T - m.T_ref)) for T in cands)
+    if rc <= 0.0:
+        raise ValueError("rho(T) c(T) is not positive on the declared range")
+    return rc
+
+
 def reference_operator(orc: Oracle) -> sp.csr_matrix:
-    """C0^-1/2 (K0 + K_b + H) C0^-1/2 restricted to free nodes (symmetric)."""
+    """C0^-1/2 (K0 + K_b + H) C0^-1/2 restricted to free nodes (symmetric).
+    Heterogeneous tissue: K0 and C0 at the first region's reference state
+    everywhere and K_b at the largest w_b c_b of any region -- an operator that
+    bounds every region's from above once scaled by region_scale."""
     m = orc.p.material
+    beta = orc.beta
+    if orc.regions is not None:
+        m = orc.p.region_materials[0]
+        beta = max(pf.w_b * pf.c_b for pf in orc.p.region_perfusion) * orc.V
     K0 = orc.assemble_K(np.full(len(orc.conn), m.k0))
-    D = sp.diags(orc.beta + orc.hA)
+    D = sp.diags(beta + orc.hA)
     C0 = orc.V * m.rho0 * m.c0
     f = np.nonzero(orc.free)[0]
     S = sp.diags(1.0 / np.sqrt(C0[f]))
@@ -97,7 +132,10 @@ def critical_dt(problem_or_oracle, T_lo: float | None = None, T_hi: float | None
     p = orc.p
     T_lo = p.T_lo if T_lo is None else T_lo
     T_hi = p.T_hi if T_hi is None else T_hi
-    s = td_scale(p.material, T_lo, T_hi)
+    if p.regions is None:
+        s = td_scale(p.material, T_lo, T_hi)
+    else:
+        s = region_scale(p.region_materials, T_lo, T_hi)
     return 2.0 / (s * lambda_max_reference(orc))
 
 

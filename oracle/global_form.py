@@ -15,6 +15,13 @@ time-stepping block, taken in its global matrix form):
 Material laws are linear in T (Section 3.1.6) or, optionally, piecewise
 linear through tabulated points, extended linearly beyond the table.
 
+Heterogeneous tissue (finite elements let the properties vary from element to
+element, as the introduction notes): each element belongs to a region with its
+own laws and perfusion.  Step 1 averages the element's own k law over its
+nodes; the lumped C_i, beta_i and metabolic heat of node i become sums over
+its elements of (V_e / nv) times the element's rho(T_i) c(T_i), w_b c_b and
+Q_m.
+
 Time-varying loads (the boundary/load update at the end of each step of
 Algorithm 1; the two-stage heating and relaxation of Section 3.1.5): the
 regional source part of Q is scaled by the schedule factor of the step's start
@@ -80,18 +87,29 @@ class Oracle:
         self.A_e, self.det_e, self.V_e = element_matrices(p.elem_type, p.xyz, self.conn)
         self.V = lumped_volumes(self.conn, self.V_e, N)
         self.hA = p.conv_h * lumped_face_areas(p.xyz, np.asarray(p.conv_faces, dtype=np.int64), N)
-        self.beta = p.perfusion.w_b * p.perfusion.c_b * self.V
+        if p.regions is None:
+            self.regions = None
+            self.beta = p.perfusion.w_b * p.perfusion.c_b * self.V
+            metabolic = self.V * p.perfusion.Q_m
+        else:
+            # W[r]: lumped volume of node i from the elements of region r
+            self.regions = np.asarray(p.regions, dtype=np.int64)
+            R = len(p.region_materials)
+            self.W = [lumped_volumes(self.conn[self.regions == r], self.V_e[self.regions == r], N) for r in range(R)]
+            pr = p.region_perfusion
+            self.beta = sum(self.W[r] * pr[r].w_b * pr[r].c_b for r in range(R))
+            metabolic = sum(self.W[r] * pr[r].Q_m for r in range(R))
         qr = gaussian_density(p.xyz, p.sources)
         if p.q_r is not None:
             qr = qr + np.asarray(p.q_r, dtype=np.float64)
-        self.Q = self.V * (p.perfusion.Q_m + qr)
+        self.Q = metabolic + self.V * qr
         if len(p.flux_nodes):
             np.add.at(self.Q, np.asarray(p.flux_nodes, dtype=np.int64), np.asarray(p.flux_q, dtype=np.float64))
         # split for time-varying sources: Q(t) = Q_const + f(t) Q_src
         self.sched_end = np.asarray(p.schedule_end, dtype=np.float64)
         self.sched_f = np.asarray(p.schedule_factor, dtype=np.float64)
         self.Q_src = self.V * qr
-        self.Q_const = self.V * p.perfusion.Q_m
+        self.Q_const = metabolic.copy()
         if len(p.flux_nodes):
             np.add.at(self.Q_const, np.asarray(p.flux_nodes, dtype=np.int64), np.asarray(p.flux_q, dtype=np.float64))
         self.free = np.ones(N, dtype=bool)
@@ -107,27 +125,33 @@ class Oracle:
         self.indptr = np.searchsorted(self._rows, np.arange(N + 1))
 
     # --- material laws (linear in T, Section 3.1.6) -------------------------
-    def k_of(self, T):
-        m = self.p.material
+    def k_of(self, T, m=None):
+        m = self.p.material if m is None else m
         if m.table is not None:
             return piecewise_linear(m.table[0], m.table[3], T)
         return m.k0 + m.dk * (T - m.T_ref)
 
-    def rho_of(self, T):
-        m = self.p.material
+    def rho_of(self, T, m=None):
+        m = self.p.material if m is None else m
         if m.table is not None:
             return piecewise_linear(m.table[0], m.table[1], T)
         return m.rho0 + m.drho * (T - m.T_ref)
 
-    def c_of(self, T):
-        m = self.p.material
+    def c_of(self, T, m=None):
+        m = self.p.material if m is None else m
         if m.table is not None:
             return piecewise_linear(m.table[0], m.table[2], T)
         return m.c0 + m.dc * (T - m.T_ref)
 
     # --- Eq. 11 and Eq. 13: global conduction matrix at the current field ---
     def element_conductivity(self, T):
-        return self.k_of(T)[self.conn].mean(axis=1)
+        if self.regions is None:
+            return self.k_of(T)[self.conn].mean(axis=1)
+        k_e = np.empty(len(self.conn))
+        for r, m in enumerate(self.p.region_materials):
+            sel = self.regions == r
+            k_e[sel] = self.k_of(T[self.conn[sel]], m).mean(axis=1)
+        return k_e
 
     def assemble_K(self, k_e) -> sp.csr_matrix:
         vals = (k_e[:, None, None] * self.A_e).ravel()
@@ -165,7 +189,9 @@ class Oracle:
         return -F + self.beta * (pf.T_a - T) + self.nodal_load(t) + self.hA * (self.p.conv_T_inf - T)
 
     def capacitance(self, T) -> np.ndarray:
-        return self.V * self.rho_of(T) * self.c_of(T)
+        if self.regions is None:
+            return self.V * self.rho_of(T) * self.c_of(T)
+        return sum(self.W[r] * self.rho_of(T, m) * self.c_of(T, m) for r, m in enumerate(self.p.region_materials))
 
     def step(self, T, dt: float, t: float = 0.0) -> np.ndarray:
         """One explicit Euler step (Eq. 6, Eq. 8) with lumped C, from time t."""

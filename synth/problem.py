@@ -107,6 +107,12 @@ class Problem:
     # last end the last factor holds.  Empty: sources always on.
     schedule_end: np.ndarray = field(default_factory=lambda: np.zeros(0, np.float64))
     schedule_factor: np.ndarray = field(default_factory=lambda: np.zeros(0, np.float64))
+    # heterogeneous tissue: element e takes region_materials[regions[e]] and the
+    # w_b, c_b, Q_m of region_perfusion[regions[e]] (T_a stays perfusion.T_a);
+    # None: material and perfusion everywhere
+    regions: Optional[np.ndarray] = None
+    region_materials: tuple = ()
+    region_perfusion: tuple = ()
 
     @property
     def n_nodes(self) -> int:
