@@ -163,6 +163,29 @@ int fedfem_set_material(fedfem_ctx* ctx, const fedfem_material* m);
 int fedfem_set_material_table(fedfem_ctx* ctx, int n, const double* T, const double* rho, const double* c,
                               const double* k);
 
+/* Heterogeneous tissue (the finite element form lets properties vary from
+ * element to element, Section 1): element e (input order) belongs to region
+ * region[e] in 0..n-1, n in 1..16, with region r's linear laws mats[r] (as in
+ * fedfem_set_material) and perfusion perf[r] (w_b, c_b and Q_m; T_a stays
+ * that of fedfem_set_perfusion).  k_e (Eq. 13) averages the element's own k
+ * law over its nodes; the lumped C_i, the perfusion beta_i and the metabolic
+ * heat of node i sum the shares V_e / nv of its elements times their
+ * region's rho(T_i) c(T_i), w_b c_b and Q_m.  The critical step
+ * (fedfem_precompute) is computed for the first region's k0 and rho0 c0
+ * everywhere with the largest w_b c_b of any region, then scaled by
+ * max(1, max k / k0) * max(1, rho0 c0 / min rho c) over every region and
+ * [T_lo, T_hi]: an upper bound of every region's eigenvalue, so the step is
+ * safe but may be smaller than that of the exact heterogeneous operator.
+ * Requires a mesh (E_STATE); E_ARG for n out of range, a region id out of
+ * range, or a material or perfusion value fedfem_set_material /
+ * fedfem_set_perfusion would refuse.  Replaces the material and any table;
+ * a later fedfem_set_material, fedfem_set_material_table or fedfem_set_mesh
+ * removes the regions.  Host arrays, copied.  Steps of a context with regions
+ * run the kernel builds that hold the source-schedule and dose paths.
+ * (fedfem_step_static takes one material.) */
+int fedfem_set_regions(fedfem_ctx* ctx, int n, const fedfem_material* mats, const fedfem_perfusion* perf,
+                       const int32_t* region);
+
 /* Perfusion and metabolism (Eq. 1); K_b and Q_b are lumped (Section 2.3.5). */
 int fedfem_set_perfusion(fedfem_ctx* ctx, const fedfem_perfusion* p);
 

@@ -45,6 +45,11 @@ struct fedfem_ctx {
     std::vector<double> flux;                     // empty: none
     std::vector<double> sched_end, sched_f;       // source schedule (empty: sources always on)
     bool dose_on = false;
+    int n_reg = 0;                                // heterogeneous tissue regions (0: mat everywhere)
+    std::vector<fedfem_material> reg_mat;
+    std::vector<fedfem_perfusion> reg_perf;       // w_b, c_b, Q_m per region (T_a from perf)
+    std::vector<int32_t> region;                  // per input element
+    std::vector<unsigned char> emat_host;         // per internal element (set by precompute)
     int tab_n = 0;                                // piecewise-linear laws (0: linear laws of mat)
     double tab_T[kMaxTable] = {}, tab_p[3][kMaxTable] = {};   // points; P: 0 rho, 1 c, 2 k
     fedfem_tile tile{FEDFEM_KERNEL_PERSISTENT, 256, 0, 0};
@@ -64,6 +69,9 @@ struct fedfem_ctx {
     float *V32 = nullptr, *Q32 = nullptr, *hA32 = nullptr, *Qs32 = nullptr;
     double* tab64 = nullptr;   // device copy of the property table (7 x kMaxTable), state precision
     float* tab32 = nullptr;
+    unsigned char* emat = nullptr;             // regions: per internal element
+    double *Cq64 = nullptr, *matk64 = nullptr;   // regions: node coefficients (4 x N_free), k laws (3 each)
+    float *Cq32 = nullptr, *matk32 = nullptr;
     double* dose = nullptr;                       // CEM43 minutes per free node
     void* T = nullptr;
     void* T2 = nullptr;
@@ -75,6 +83,8 @@ struct fedfem_ctx {
     std::vector<void*> tile_allocs;
     unsigned char* t_blocks = nullptr;
     int64_t* t_block_off = nullptr;
+    unsigned char* t_emat = nullptr;   // regions of the tile elements
+    int32_t* t_emat_off = nullptr;
     int64_t t_block_bytes = 0;
     int t_max_block = 0, t_max_local = 0;
     size_t t_smem = 0;
@@ -113,6 +123,8 @@ int cuda_fail(fedfem_ctx* c, cudaError_t e, const char* what) {
 void free_tiles(fedfem_ctx* c) {
     for (void* p : c->tile_allocs) cudaFree(p);
     c->tile_allocs.clear();
+    c->t_emat = nullptr;
+    c->t_emat_off = nullptr;
     c->tiles_ok = false;
     c->tiles_B = 0;
     c->tiles_host = Tiles();
@@ -133,6 +145,7 @@ void free_device(fedfem_ctx* c) {
     c->conn4 = nullptr; c->M64 = nullptr; c->M32 = nullptr; c->sell_off = c->sell_ids = nullptr;
     c->V64 = c->Q64 = c->hA64 = c->Qs64 = nullptr; c->V32 = c->Q32 = c->hA32 = c->Qs32 = nullptr;
     c->tab64 = nullptr; c->tab32 = nullptr;
+    c->emat = nullptr; c->Cq64 = c->matk64 = nullptr; c->Cq32 = c->matk32 = nullptr;
     c->dose = nullptr;
     c->T = nullptr; c->T2 = nullptr; c->Tlo = nullptr; c->slots = nullptr; c->node_of = nullptr; c->T_dir = nullptr;
     c->io = nullptr; c->st = nullptr;
@@ -208,8 +221,36 @@ int property_scale_table(fedfem_ctx* c, double lo, double hi, double* s_out) {
 
 // s = max(1, max k/k0) * max(1, max rho0 c0 / (rho c)) over [lo, hi]; rho c is
 // quadratic in T, so its minimum is at an end point or the vertex.
+int property_scale(fedfem_ctx* c, double lo, double hi, double* s_out);
+
+// property_scale for regions, against the first region's reference state:
+// the largest k of any region over [lo, hi] and the smallest rho c of any
+// region (each a linear law: k at an end point, rho c at an end point or its
+// vertex).  Every C_i is a positive combination of the regions' rho c and
+// every k_e a region's k, so the bound of the homogeneous case carries over.
+int property_scale_regions(fedfem_ctx* c, double lo, double hi, double* s_out) {
+    const fedfem_material ref = c->reg_mat[0];
+    double kmax = -INFINITY, rc_min = INFINITY;
+    for (const fedfem_material& m : c->reg_mat) {
+        auto k = [&](double T) { return m.k0 + m.dk * (T - m.T_ref); };
+        auto rc = [&](double T) { return (m.rho0 + m.drho * (T - m.T_ref)) * (m.c0 + m.dc * (T - m.T_ref)); };
+        if (!(k(lo) > 0 && k(hi) > 0)) return fail(c, FEDFEM_E_RANGE, "a region's k(T) is not positive on [T_lo, T_hi]");
+        kmax = std::max(kmax, std::max(k(lo), k(hi)));
+        rc_min = std::min(rc_min, std::min(rc(lo), rc(hi)));
+        const double qa = m.drho * m.dc;
+        if (qa != 0.0) {
+            const double u = -(m.rho0 * m.dc + m.c0 * m.drho) / (2.0 * qa);
+            if (lo < m.T_ref + u && m.T_ref + u < hi) rc_min = std::min(rc_min, rc(m.T_ref + u));
+        }
+    }
+    if (!(rc_min > 0)) return fail(c, FEDFEM_E_RANGE, "a region's rho(T) c(T) is not positive on [T_lo, T_hi]");
+    *s_out = std::max(1.0, kmax / ref.k0) * std::max(1.0, ref.rho0 * ref.c0 / rc_min);
+    return FEDFEM_OK;
+}
+
 int property_scale(fedfem_ctx* c, double lo, double hi, double* s_out) {
     if (c->tab_n > 0) return property_scale_table(c, lo, hi, s_out);
+    if (c->n_reg > 0) return property_scale_regions(c, lo, hi, s_out);
     const fedfem_material& m = c->mat;
     auto k = [&](double T) { return m.k0 + m.dk * (T - m.T_ref); };
     auto rc = [&](double T) { return (m.rho0 + m.drho * (T - m.T_ref)) * (m.c0 + m.dc * (T - m.T_ref)); };
@@ -267,6 +308,13 @@ StepArgs<R, L> make_args(fedfem_ctx* c, const R* M, const R* V, const R* Q, cons
     a.n_tab = c->tab_n;
     for (int j = 0; j < c->tab_n; ++j) a.tab_T[j] = (R)c->tab_T[j];
     a.tab = std::is_same<R, double>::value ? (const R*)c->tab64 : (const R*)c->tab32;
+    if (c->n_reg > 0 && c->emat) {
+        a.emat = c->emat;
+        a.emat_tile = c->t_emat;
+        a.emat_off = c->t_emat_off;
+        a.mat_k = std::is_same<R, double>::value ? (const R*)c->matk64 : (const R*)c->matk32;
+        a.Cq = std::is_same<R, double>::value ? (const R*)c->Cq64 : (const R*)c->Cq32;
+    }
     return a;
 }
 
@@ -401,6 +449,16 @@ int plan_tiles(fedfem_ctx* c) {
     CU(cudaMemcpyAsync(c->t_blocks, blob.data(), blob.size(), cudaMemcpyHostToDevice, st), "tile copy");
     CU(cudaMemcpyAsync(c->t_block_off, off.data(), sizeof(int64_t) * off.size(), cudaMemcpyHostToDevice, st),
        "tile copy");
+    if (c->n_reg > 0 && !c->emat_host.empty()) {   // regions of the tile elements, tile t's from e_off[t]
+        std::vector<unsigned char> te(std::max<size_t>(1, t.e_glob.size()));
+        for (size_t j = 0; j < t.e_glob.size(); ++j) te[j] = c->emat_host[t.e_glob[j]];
+        CU(talloc(c, &c->t_emat, te.size()), "tile alloc");
+        CU(talloc(c, &c->t_emat_off, sizeof(int32_t) * t.e_off.size()), "tile alloc");
+        CU(cudaMemcpyAsync(c->t_emat, te.data(), te.size(), cudaMemcpyHostToDevice, st), "tile copy");
+        CU(cudaMemcpyAsync(c->t_emat_off, t.e_off.data(), sizeof(int32_t) * t.e_off.size(), cudaMemcpyHostToDevice,
+                           st), "tile copy");
+        CU(cudaStreamSynchronize(st), "tile copy");   // te is a host vector of this frame
+    }
     CU(cudaStreamSynchronize(st), "tile build");
     c->t_block_bytes = (int64_t)blob.size();
     c->t_max_block = mb;
@@ -580,6 +638,7 @@ int fedfem_set_mesh(fedfem_ctx* c, int elem_type, int64_t n_nodes, const double*
     c->dir_T.assign(n_nodes, 0.0);
     c->conv_faces.clear(); c->conv_nv = 0; c->conv_h = 0; c->conv_Tinf = 0;
     c->flux.clear(); c->qr.clear(); c->sources.clear(); c->groups.clear();
+    c->n_reg = 0; c->region.clear(); c->reg_mat.clear(); c->reg_perf.clear();
     for (auto& q : c->qr_lane) q.clear();
     c->has_mesh = true;
     free_device(c);
@@ -602,6 +661,36 @@ int fedfem_set_material(fedfem_ctx* c, const fedfem_material* m) {
         if (!is_finite(x)) return fail(c, FEDFEM_E_ARG, "non-finite material value");
     if (!(m->rho0 > 0 && m->c0 > 0 && m->k0 > 0)) return fail(c, FEDFEM_E_ARG, "rho0, c0 and k0 must be positive");
     c->mat = *m;
+    c->has_mat = true;
+    c->tab_n = 0;
+    c->n_reg = 0;
+    invalidate(c);
+    return FEDFEM_OK;
+}
+
+int fedfem_set_regions(fedfem_ctx* c, int n, const fedfem_material* mats, const fedfem_perfusion* perf,
+                       const int32_t* region) {
+    if (!c) return FEDFEM_E_ARG;
+    if (!c->has_mesh) return fail(c, FEDFEM_E_STATE, "set_mesh first");
+    if (n < 1 || n > kMaxRegions || !mats || !perf || !region)
+        return fail(c, FEDFEM_E_ARG, "regions: 1.." + std::to_string(kMaxRegions) + " materials and an id per element");
+    for (int r = 0; r < n; ++r) {
+        const fedfem_material& m = mats[r];
+        const double v[7] = {m.T_ref, m.rho0, m.drho, m.c0, m.dc, m.k0, m.dk};
+        for (double x : v)
+            if (!is_finite(x)) return fail(c, FEDFEM_E_ARG, "regions: non-finite material value");
+        if (!(m.rho0 > 0 && m.c0 > 0 && m.k0 > 0)) return fail(c, FEDFEM_E_ARG, "regions: rho0, c0, k0 must be positive");
+        const fedfem_perfusion& p = perf[r];
+        if (!(is_finite(p.w_b) && is_finite(p.c_b) && is_finite(p.Q_m)) || p.w_b < 0 || p.c_b < 0)
+            return fail(c, FEDFEM_E_ARG, "regions: perfusion values must be finite, w_b and c_b non-negative");
+    }
+    for (int64_t e = 0; e < c->E; ++e)
+        if (region[e] < 0 || region[e] >= n) return fail(c, FEDFEM_E_ARG, "regions: element region out of range");
+    c->n_reg = n;
+    c->reg_mat.assign(mats, mats + n);
+    c->reg_perf.assign(perf, perf + n);
+    c->region.assign(region, region + c->E);
+    c->mat = mats[0];
     c->has_mat = true;
     c->tab_n = 0;
     invalidate(c);
@@ -629,6 +718,7 @@ int fedfem_set_material_table(fedfem_ctx* c, int n, const double* T, const doubl
     }
     c->mat = fedfem_material{T[0], rho[0], 0.0, cp[0], 0.0, k[0], 0.0};
     c->has_mat = true;
+    c->n_reg = 0;
     invalidate(c);
     return FEDFEM_OK;
 }
@@ -952,7 +1042,7 @@ int fedfem_precompute(fedfem_ctx* c, double T_lo, double T_hi, double* dt_cr_out
     pa.V = c->V64; pa.Q = c->Q64; pa.hA = c->hA64;
     pa.qr_node = qr; pa.flux_node = flux; pa.src = src; pa.n_src = (int)c->sources.size(); pa.n_lanes = NL;
     pa.node_group = node_group;
-    pa.Q_m = c->perf.Q_m;
+    pa.Q_m = c->n_reg > 0 ? 0.0 : c->perf.Q_m;   // regions: added per element share below
     pa.n_faces = c->conv_nv ? (int64_t)fint.size() / c->conv_nv : 0;
     pa.face_nv = c->conv_nv; pa.faces = faces; pa.face_share = face_share;
     pa.conv_off = conv_off; pa.conv_face = conv_face; pa.h_film = c->conv_h;
@@ -976,6 +1066,39 @@ int fedfem_precompute(fedfem_ctx* c, double T_lo, double T_hi, double* dt_cr_out
         CU(launch_nodal(pc, st), "nodal kernel");
     }
     if (c->dose_on) CU(dalloc(c, &c->dose, sizeof(double) * std::max<int64_t>(1, NF * NL)), "alloc");
+    double wbcb_ref = c->perf.w_b * c->perf.c_b;
+    if (c->n_reg > 0) {
+        // element regions in internal order; per region: rho c expanded about the
+        // first region's T_ref (u = T - T_ref), w_b c_b and Q_m; its k law
+        c->emat_host.resize(E);
+        for (int64_t e = 0; e < E; ++e) c->emat_host[e] = (unsigned char)c->region[L.elem_of[e]];
+        const double Tr = c->reg_mat[0].T_ref;
+        std::vector<double> coef(5 * c->n_reg), kl(3 * c->n_reg);
+        wbcb_ref = 0.0;
+        for (int r = 0; r < c->n_reg; ++r) {
+            const fedfem_material& m = c->reg_mat[r];
+            const double a = m.rho0 + m.drho * (Tr - m.T_ref), b = m.drho;
+            const double al = m.c0 + m.dc * (Tr - m.T_ref), be = m.dc;
+            coef[5 * r + 0] = a * al;
+            coef[5 * r + 1] = a * be + b * al;
+            coef[5 * r + 2] = b * be;
+            coef[5 * r + 3] = c->reg_perf[r].w_b * c->reg_perf[r].c_b;
+            coef[5 * r + 4] = c->reg_perf[r].Q_m;
+            kl[3 * r + 0] = m.T_ref; kl[3 * r + 1] = m.k0; kl[3 * r + 2] = m.dk;
+            wbcb_ref = std::max(wbcb_ref, coef[5 * r + 3]);
+        }
+        double* coef_d = nullptr;
+        CU(dalloc(c, &c->emat, std::max<int64_t>(1, E)), "alloc");
+        CU(dalloc(c, &coef_d, sizeof(double) * coef.size()), "alloc");
+        CU(dalloc(c, &c->matk64, sizeof(double) * kl.size()), "alloc");
+        CU(dalloc(c, &c->Cq64, sizeof(double) * 4 * std::max<int64_t>(1, NF)), "alloc");
+        CU(cudaMemcpyAsync(c->emat, c->emat_host.data(), E, cudaMemcpyHostToDevice, st), "copy");
+        CU(cudaMemcpyAsync(coef_d, coef.data(), sizeof(double) * coef.size(), cudaMemcpyHostToDevice, st), "copy");
+        CU(cudaMemcpyAsync(c->matk64, kl.data(), sizeof(double) * kl.size(), cudaMemcpyHostToDevice, st), "copy");
+        CU(launch_regions(pa, c->emat, coef_d, c->Cq64, st), "region kernel");
+        CU(cudaStreamSynchronize(st), "region kernel");   // coef and kl are host vectors of this frame
+        release(c, coef_d, sizeof(double) * coef.size());
+    }
     if (c->tab_n > 0) {   // [T_j | rho_j | c_j | k_j | slopes of rho, c, k], kMaxTable each
         double h[7 * kMaxTable] = {};
         for (int j = 0; j < c->tab_n; ++j) {
@@ -998,7 +1121,9 @@ int fedfem_precompute(fedfem_ctx* c, double T_lo, double T_hi, double* dt_cr_out
     }
     CU(cudaStreamSynchronize(st), "nodal kernel");
     LanczosResult lr;
-    std::string lm = lanczos_lambda_max(pa, c->mat.k0, c->mat.rho0 * c->mat.c0, c->perf.w_b * c->perf.c_b,
+    // regions: the reference operator takes the first region's k0 and rho0 c0
+    // everywhere and the largest w_b c_b (property_scale bounds the rest)
+    std::string lm = lanczos_lambda_max(pa, c->mat.k0, c->mat.rho0 * c->mat.c0, wbcb_ref,
                                         3000, 1e-14, lr, st);
     if (!lm.empty()) return fail(c, FEDFEM_E_CUDA, lm);
     c->lambda = lr.lambda;
@@ -1025,6 +1150,12 @@ int fedfem_precompute(fedfem_ctx* c, double T_lo, double T_hi, double* dt_cr_out
             CU(dalloc(c, &c->Qs32, sizeof(float) * NF * NL), "alloc");
             CU(launch_pack_lanes(c->Qs64, c->Qs32, NL, NF, st), "convert");
         }
+        if (c->Cq64) {
+            CU(dalloc(c, &c->Cq32, sizeof(float) * 4 * std::max<int64_t>(1, NF)), "alloc");
+            CU(dalloc(c, &c->matk32, sizeof(float) * 3 * c->n_reg), "alloc");
+            CU(launch_to_f32(c->Cq64, c->Cq32, 4 * NF, st), "convert");
+            CU(launch_to_f32(c->matk64, c->matk32, 3 * c->n_reg, st), "convert");
+        }
         CU(dalloc(c, (float**)&c->T, sizeof(float) * N * NL), "alloc");
         CU(dalloc(c, (float**)&c->T2, sizeof(float) * N * NL), "alloc");
         CU(dalloc(c, &c->Tlo, sizeof(float) * N * NL), "alloc");
@@ -1048,6 +1179,10 @@ int fedfem_precompute(fedfem_ctx* c, double T_lo, double T_hi, double* dt_cr_out
         release(c, c->Q64, sizeof(double) * NF * NL); c->Q64 = nullptr;
         release(c, c->hA64, sizeof(double) * NC); c->hA64 = nullptr;
         if (c->Qs64) { release(c, c->Qs64, sizeof(double) * NF * NL); c->Qs64 = nullptr; }
+        if (c->Cq64) {
+            release(c, c->Cq64, sizeof(double) * 4 * std::max<int64_t>(1, NF)); c->Cq64 = nullptr;
+            release(c, c->matk64, sizeof(double) * 3 * c->n_reg); c->matk64 = nullptr;
+        }
     }
     c->pre = true;
     c->inited = false;
@@ -1318,7 +1453,8 @@ int fedfem_get_info(fedfem_ctx* c, fedfem_info* info) {
     const int64_t NL = c->n_lanes;   // lanes share V, hA and the element data
     info->algorithmic_bytes_per_step = E * (4 * c->nv + 6 * R) + NF * (NL * (node_state + R) + R) + NC * R;
     // a source schedule reads the source part of Q too; the dose is read and written in FP64
-    const int64_t extra = (c->sched_f.empty() ? 0 : NF * NL * R) + (c->dose ? NF * 16 : 0);
+    const int64_t extra = (c->sched_f.empty() ? 0 : NF * NL * R) + (c->dose ? NF * 16 : 0) +
+                          (c->n_reg > 0 ? NF * 4 * R + E : 0);   // regions: node coefficients, element ids
     info->algorithmic_bytes_per_step += extra;
     // two-phase / persistent model: + slot write and read, gather ids, their slice offsets, T gathered once
     info->bytes_per_step = info->algorithmic_bytes_per_step + E * c->nv * 2 * R + (int64_t)L.sell_ids.size() * 4 +

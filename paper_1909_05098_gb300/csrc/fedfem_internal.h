@@ -95,6 +95,7 @@ struct DevStatus {
 // temperature state -- R itself, or F4 for four scenario lanes.
 constexpr int kMaxSegments = 8;   // pieces of a source schedule
 constexpr int kMaxTable = 8;      // points of a piecewise-linear property table
+constexpr int kMaxRegions = 16;   // tissue regions of a heterogeneous mesh
 
 template <typename R, typename L = R>
 struct StepArgs {
@@ -134,6 +135,17 @@ struct StepArgs {
     int n_tab;
     R tab_T[kMaxTable];
     const R* tab;
+    // heterogeneous tissue (emat non-null): each element's region, in internal
+    // element order (emat) and in tile-element order (emat_tile, tile t's
+    // elements from emat_off[t]); each region's k law (T_ref, k0, dk) in
+    // mat_k; per free node i the capacity C_i(T) = Ca + u (Cb + u Cc),
+    // u = T - T_ref, and the perfusion beta_i, in Cq = [Ca | Cb | Cc | beta]
+    // (planes of N_free)
+    const unsigned char* emat;
+    const unsigned char* emat_tile;
+    const int32_t* emat_off;
+    const R* mat_k;
+    const R* Cq;
 };
 
 // Launchers (step.cu).  mode: FEDFEM_FP64 / FEDFEM_FP32_KAHAN / FEDFEM_FP32_PLAIN.
@@ -233,6 +245,10 @@ struct PreArgs {
 
 cudaError_t launch_geometry(const PreArgs& a, cudaStream_t s);
 cudaError_t launch_nodal(const PreArgs& a, cudaStream_t s);
+// heterogeneous tissue: per-node capacity coefficients and perfusion (Cq, 4
+// planes of N_free) and the metabolic heat added to a.Q; coef: 5 per region
+cudaError_t launch_regions(const PreArgs& a, const unsigned char* emat, const double* coef, double* Cq,
+                           cudaStream_t s);
 cudaError_t launch_to_f32(const double* src, float* dst, int64_t n, cudaStream_t s);
 
 // Largest eigenvalue of C0^-1/2 (K0 + diag(beta + hA)) C0^-1/2 on the free

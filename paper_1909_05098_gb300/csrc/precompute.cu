@@ -151,6 +151,31 @@ __global__ void k_nodal(PreArgs a) {
     }
 }
 
+// Heterogeneous tissue: for every free node, the sums over its elements (the
+// node's slot list) of the element share V_e / nv times its region's
+// coefficients coef[5 r + q]: rho c = q0 + q1 u + q2 u^2, w_b c_b (q3) and
+// Q_m (q4).  Cq receives the first four as planes of N_free; the metabolic
+// sum is added to every lane's load.
+__global__ void k_regions(PreArgs a, const unsigned char* emat, const double* coef, double* Cq) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.N_free) return;
+    const int64_t s = i >> 5;
+    const int lane = (int)(i & 31);
+    const int32_t off = a.sell_off[s];
+    const int w = (a.sell_off[s + 1] - off) >> 5;
+    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int k = 0; k < w; ++k) {
+        const int64_t e = a.sell_ids[off + 32 * k + lane] / a.nv;
+        if (e >= a.E) continue;   // pad slot
+        const double v = a.Vshare[e];
+        const double* q = coef + 5 * (int)emat[e];
+#pragma unroll
+        for (int j = 0; j < 5; ++j) acc[j] += v * q[j];
+    }
+    for (int j = 0; j < 4; ++j) Cq[j * a.N_free + i] = acc[j];
+    for (int l = 0; l < a.n_lanes; ++l) a.Q[l * a.N_free + i] += acc[4];
+}
+
 __global__ void k_to_f32(const double* src, float* dst, int64_t n) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) dst[i] = (float)src[i];
@@ -310,6 +335,12 @@ cudaError_t launch_geometry(const PreArgs& a, cudaStream_t s) {
 
 cudaError_t launch_nodal(const PreArgs& a, cudaStream_t s) {
     if (a.N_free > 0) k_nodal<<<blocks_for(a.N_free), kThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_regions(const PreArgs& a, const unsigned char* emat, const double* coef, double* Cq,
+                           cudaStream_t s) {
+    if (a.N_free > 0) k_regions<<<blocks_for(a.N_free), kThreads, 0, s>>>(a, emat, coef, Cq);
     return cudaGetLastError();
 }
 

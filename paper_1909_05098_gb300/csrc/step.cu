@@ -69,21 +69,33 @@ __device__ __forceinline__ F4 tab_law(const StepArgs<R, L>& a, F4 T) {
 }
 
 // k(T) of kernels built with the extensions: the table when one is set, else
-// the linear law
+// the element's linear law (its region's, or the material's)
 template <typename R, typename L>
 struct ExtKLaw {
     const StepArgs<R, L>& a;
+    R T_ref, k0, dk;
     template <typename X>
     __device__ __forceinline__ X at(X T) const {
         if (a.n_tab > 0) return tab_law<2>(a, T);
-        return fmadd(a.dk, T - a.T_ref, a.k0);
+        return fmadd(dk, T - T_ref, k0);
     }
 };
 
+// the k law of element j (em: region ids of the elements, or null)
 template <int MODE, typename R, typename L>
-__device__ __forceinline__ auto k_law(const StepArgs<R, L>& a) {
-    if constexpr ((MODE & 2) != 0) return ExtKLaw<R, L>{a};
-    else return Law<R>{a.T_ref, a.k0, a.dk};
+__device__ __forceinline__ auto k_law(const StepArgs<R, L>& a, const unsigned char* em, int64_t j) {
+    if constexpr ((MODE & 2) != 0) {
+        ExtKLaw<R, L> k{a, a.T_ref, a.k0, a.dk};
+        if (em) {
+            const R* q = a.mat_k + 3 * (int)em[j];
+            k.T_ref = __ldg(q);
+            k.k0 = __ldg(q + 1);
+            k.dk = __ldg(q + 2);
+        }
+        return k;
+    } else {
+        return Law<R>{a.T_ref, a.k0, a.dk};
+    }
 }
 
 template <typename R, int NV, int MODE>
@@ -102,7 +114,7 @@ __device__ __forceinline__ void element_phase(const StepArgs<R>& a, int64_t e) {
     R t[NV];
 #pragma unroll
     for (int n = 0; n < NV; ++n) t[n] = a.T[c[n]];
-    const auto k = k_law<MODE>(a);
+    const auto k = k_law<MODE>(a, a.emat, e);
     const R ke = element_k<R, NV>(t, k);
     R F[NV];
     if (NV == 8) hex8_loads<R>(t, m, ke, F);
@@ -176,19 +188,23 @@ __device__ __forceinline__ void node_update_v(const StepArgs<R, L>& a, int64_t i
     const L u = T - a.T_ref;
     L rho = fmadd(a.drho, u, a.rho0);
     L c = fmadd(a.dc, u, a.c0);
-    if constexpr ((MODE & 2) != 0) {
+    L C = (v.V * rho) * c;
+    R beta = a.wbcb * v.V;
+    L q = v.Q;
+    if constexpr ((MODE & 2) != 0) {   // kernels built with the extensions
         if (a.n_tab > 0) {
             rho = tab_law<0>(a, T);
             c = tab_law<1>(a, T);
+            C = (v.V * rho) * c;
+        } else if (a.Cq) {             // regions: C and beta summed from the element shares
+            const int64_t nf = a.N_free;
+            C = fmadd(fmadd(a.Cq[2 * nf + i], u, a.Cq[nf + i]), u, a.Cq[i]);
+            beta = a.Cq[3 * nf + i];
         }
-    }
-    const L C = (v.V * rho) * c;
-    L q = v.Q;
-    if constexpr ((MODE & 2) != 0) {   // kernels built with the time-varying / dose extensions
         if (a.Qs) q = fmadd(schedule_factor(a, step), a.Qs[i], q);
         if (a.dose) dose_add(a.dose, i, a.dose_dt, T);   // CEM43 at the step's start temperature
     }
-    L r = fmadd(a.wbcb * v.V, a.T_a - T, q) - F;
+    L r = fmadd(beta, a.T_a - T, q) - F;
     if (i >= a.N_plain) r = fmadd(v.hA, a.T_inf - T, r);
     const L dT = increment_div(a.dt * r, C);
     L Tn;
@@ -444,11 +460,18 @@ __device__ __forceinline__ void tile_fetch(const int32_t* halo, int nh, int64_t 
     }
 }
 
+// region ids of tile t's elements (null without regions)
+template <int MODE, typename R, typename L>
+__device__ __forceinline__ const unsigned char* tile_regions(const StepArgs<R, L>& a, int64_t t) {
+    if constexpr ((MODE & 2) != 0) return a.emat_tile ? a.emat_tile + a.emat_off[t] : nullptr;
+    else return nullptr;
+}
+
 // element phase of one tile: loads of every tile element; each owned corner's
 // load goes to Fn[rank * B + local id]
-template <typename R, typename L, int NV, bool SHARED, typename K>
-__device__ __forceinline__ void tile_elements(const TileView<R>& v, const K& k, int own, int B, int rank_shift,
-                                              const L* Ts, L* Fn) {
+template <typename R, typename L, int NV, int MODE, bool SHARED>
+__device__ __forceinline__ void tile_elements(const StepArgs<R, L>& a, const unsigned char* em, const TileView<R>& v,
+                                              int own, int B, int rank_shift, const L* Ts, L* Fn) {
     const int id_mask = (1 << rank_shift) - 1;
     for (int j = threadIdx.x; j < v.ne; j += blockDim.x) {
         int c[NV];
@@ -463,7 +486,7 @@ __device__ __forceinline__ void tile_elements(const TileView<R>& v, const K& k, 
             m[q] = p.x;
             m[q + 1] = p.y;
         }
-        const L ke = element_k<R, NV, L>(tt, k);
+        const L ke = element_k<R, NV, L>(tt, k_law<MODE>(a, em, j));
         L F[NV];
         if (NV == 8) hex8_loads<R, L>(tt, m, ke, F);
         else tet4_loads<R, L>(tt, m, ke, F);
@@ -539,7 +562,6 @@ __global__ void __launch_bounds__(256, DirectOccupancy<L>::min_blocks) k_tiled_d
     unsigned long long target = 0;
     long long done = 0;
     if (!grid_barrier(a.status, target, spin_limit)) return;   // also orders the zeroing before first use
-    const auto k = k_law<MODE>(a);
     for (long long s = 0; s < n_steps; ++s) {
         const L* Tin = (s & 1) ? a.T2 : a.T;
         L* Tout = (s & 1) ? a.T : a.T2;
@@ -552,7 +574,7 @@ __global__ void __launch_bounds__(256, DirectOccupancy<L>::min_blocks) k_tiled_d
             L T0 = lzero<L>();
             NodeVals<R, L> v0{};
             first_node<R, L, MODE>(a, base, own, Ts, T0, v0);
-            tile_elements<R, L, NV, false>(v, k, own, ta.B, ta.rank_shift, Ts, Fn);
+            tile_elements<R, L, NV, MODE, false>(a, tile_regions<MODE>(a, t), v, own, ta.B, ta.rank_shift, Ts, Fn);
             __syncthreads();   // loads complete; Ts is free for the next tile
             tile_nodes<R, L, MODE>(a, base, own, v.deg, ta.B, Fn, T0, v0, Tin, Tout, a.step0 + s);
             __syncthreads();   // table cleared before the next tile writes it
@@ -649,7 +671,6 @@ __global__ void __launch_bounds__(TPB, StagedOccupancy<L, TPB>::min_blocks)
         if (!land(0)) { fail_timeout(); stop = true; }
         else fetch(0, a.T);
     }
-    const auto k = k_law<MODE>(a);
     long long kk = 0;
     for (long long s = 0; s < n_steps && !stop; ++s) {
         const L* Tin = (s & 1) ? a.T2 : a.T;
@@ -665,7 +686,8 @@ __global__ void __launch_bounds__(TPB, StagedOccupancy<L, TPB>::min_blocks)
             L T0 = lzero<L>();
             NodeVals<R, L> v0{};
             first_node<R, L, MODE>(a, base, own, Ts, T0, v0);
-            tile_elements<R, L, NV, true>(v, k, own, ta.B, ta.rank_shift, Ts, Fn);
+            tile_elements<R, L, NV, MODE, true>(a, tile_regions<MODE>(a, tile_of(kk)), v, own, ta.B, ta.rank_shift,
+                                                Ts, Fn);
             __syncthreads();   // loads complete; this stage and Ts are free
             if (i + 1 < n_my) {   // the next tile of this step: its stage, then its temperatures
                 if (!land(buf_of(kk + 1))) { fail_timeout(); stop = true; break; }
@@ -698,8 +720,8 @@ __global__ void __launch_bounds__(TPB, StagedOccupancy<L, TPB>::min_blocks)
 }
 
 // MODE bit 0: Kahan-compensated state; bit 1: built with the time-varying
-// source, thermal-dose and tabulated-law paths (launched only when a context
-// enables one)
+// source, thermal-dose, tabulated-law and region paths (launched only when a
+// context enables one)
 template <typename R, typename L, int NV, int MODE>
 auto tiled_kernel(const TileArgs<R>& ta) {
     return !ta.staged           ? k_tiled_direct<R, L, NV, MODE>
@@ -712,7 +734,8 @@ template <typename R, typename L, int NV, bool KAHAN>
 cudaError_t launch_tiled_impl(const StepArgs<R, L>& a, const TileArgs<R>& ta, int64_t n_steps, LaunchCfg& cfg,
                               cudaStream_t s) {
     constexpr int M = KAHAN ? 1 : 0;
-    auto kern = (a.Qs || a.dose || a.n_tab > 0) ? tiled_kernel<R, L, NV, M | 2>(ta) : tiled_kernel<R, L, NV, M>(ta);
+    auto kern = (a.Qs || a.dose || a.n_tab > 0 || a.emat) ? tiled_kernel<R, L, NV, M | 2>(ta)
+                                                          : tiled_kernel<R, L, NV, M>(ta);
     const int b = ta.staged ? ta.threads : 256;
     cudaError_t err = cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)ta.smem_bytes);
@@ -740,7 +763,7 @@ inline int blocks_for(int64_t n, int t) {
 template <typename R, int NV, bool KAHAN>
 cudaError_t launch_impl(const StepArgs<R>& a, int64_t n_steps, LaunchCfg& cfg, cudaStream_t s) {
     constexpr int M = KAHAN ? 1 : 0;
-    const bool ext = a.Qs || a.dose || a.n_tab > 0;
+    const bool ext = a.Qs || a.dose || a.n_tab > 0 || a.emat;
     if (cfg.kernel == FEDFEM_KERNEL_TWO_PHASE) {
         const int b = cfg.block > 0 ? std::min(cfg.block, 256) : 256;
         auto node = ext ? k_node<R, M | 2> : k_node<R, M>;

@@ -110,6 +110,8 @@ _SIGS = {
     "fedfem_set_lanes": ([_ctx_p, C.c_int], C.c_int),
     "fedfem_set_source_schedule": ([_ctx_p, C.c_int, _dp, _dp], C.c_int),
     "fedfem_set_material_table": ([_ctx_p, C.c_int, _dp, _dp, _dp, _dp], C.c_int),
+    "fedfem_set_regions": ([_ctx_p, C.c_int, C.POINTER(fedfem_material), C.POINTER(fedfem_perfusion), _ip],
+                           C.c_int),
     "fedfem_enable_dose": ([_ctx_p, C.c_int], C.c_int),
     "fedfem_read_dose": ([_ctx_p, _dp], C.c_int),
     "fedfem_read_dose_lane": ([_ctx_p, C.c_int, _dp], C.c_int),
@@ -208,6 +210,28 @@ def fedfem_set_material_table(ctx, T, rho, c, k):
         raise ValueError("T, rho, c and k differ in length")
     ptrs = [_d(a)[1] for a in arrs]
     _check(ctx, _lib.fedfem_set_material_table(ctx, arrs[0].shape[0], *ptrs))
+
+
+def fedfem_set_regions(ctx, materials, perfusions, region):
+    """materials / perfusions: one per region, objects with the struct's field
+    names or tuples in its order; region: one id per element."""
+    def mat(m):
+        if hasattr(m, "k0"):
+            return fedfem_material(m.T_ref, m.rho0, m.drho, m.c0, m.dc, m.k0, m.dk)
+        return fedfem_material(*m)
+
+    def perf(p):
+        if hasattr(p, "w_b"):
+            return fedfem_perfusion(p.w_b, p.c_b, p.T_a, p.Q_m)
+        return fedfem_perfusion(*p)
+
+    n = len(materials)
+    if len(perfusions) != n:
+        raise ValueError("one perfusion per region")
+    M = (fedfem_material * n)(*[mat(m) for m in materials])
+    P = (fedfem_perfusion * n)(*[perf(p) for p in perfusions])
+    r, pr = _i(np.asarray(region).reshape(-1))
+    _check(ctx, _lib.fedfem_set_regions(ctx, n, M, P, pr))
 
 
 def apply_material(ctx, m):
@@ -483,6 +507,8 @@ class Solver:
             apply_material(self.ctx, p.material)
             pf = p.perfusion
             fedfem_set_perfusion(self.ctx, pf.w_b, pf.c_b, pf.T_a, pf.Q_m)
+            if getattr(p, "regions", None) is not None:
+                fedfem_set_regions(self.ctx, p.region_materials, p.region_perfusion, p.regions)
             for s in p.sources:
                 fedfem_add_gaussian_source(self.ctx, s.x0, s.sigma, s.peak)
             if p.q_r is not None:
@@ -563,6 +589,10 @@ class Batch:
             p = scen[0]
             if p.material != first.material or p.perfusion != first.perfusion:
                 raise ValueError("all runs of a batch must share material and perfusion")
+            if (getattr(p, "regions", None) is None) != (getattr(first, "regions", None) is None) or (
+                    p.regions is not None and (p.region_materials != first.region_materials
+                                               or p.region_perfusion != first.region_perfusion)):
+                raise ValueError("all runs of a batch must share the region materials")
             off = self.node_off[-1]
             xyz.append(p.xyz)
             conn.append(np.asarray(p.conn, dtype=np.int64) + off)
@@ -579,6 +609,9 @@ class Batch:
             apply_material(self.ctx, first.material)
             pf = first.perfusion
             fedfem_set_perfusion(self.ctx, pf.w_b, pf.c_b, pf.T_a, pf.Q_m)
+            if getattr(first, "regions", None) is not None:
+                fedfem_set_regions(self.ctx, first.region_materials, first.region_perfusion,
+                                   np.concatenate([np.asarray(scen[0].regions) for scen in meshes]))
             fedfem_set_dirichlet(self.ctx, np.concatenate(dn), np.concatenate(dT))
             for g, scen in enumerate(meshes):
                 for lane in range(4):

@@ -127,8 +127,8 @@ class Surrogate:
         self.D = torch.tensor(D, device="cuda")
         self.free = torch.tensor((1 - D).astype(np.float32), device="cuda")
         m = p.material
-        if m.table is not None:
-            raise ValueError("the surrogate's input features take linear laws, not a table")
+        if m.table is not None or p.regions is not None:
+            raise ValueError("the surrogate's input features take one material with linear laws")
         self.mat = (m.T_ref, m.rho0, m.drho, m.c0, m.dc, m.k0, m.dk)
         self._x = torch.empty((max_batch, self.N, 5), device="cuda")
         self._y = torch.empty((max_batch, self.N), device="cuda")
