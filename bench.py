@@ -783,6 +783,24 @@ def run_suite(args):
     p3 = copy.copy(w3.problem)
     p3.schedule_end, p3.schedule_factor = np.array([150.0, 1e30]), np.array([1.0, 0.0])
     measure("hex cube 128^3 elements, two-stage sources + CEM43 dose", p3, ff.FP32_KAHAN, 200, dose=True)
+    # the same cube with tabulated (piecewise-linear, four-point) laws
+    from synth.problem import Material, Perfusion
+    p4 = copy.copy(w3.problem)
+    p4.material = Material.tabulated((30.0, 40.0, 46.0, 70.0), (1060.0, 1050.0, 1030.0, 1000.0),
+                                     (3600.0, 3700.0, 3500.0, 3300.0), (0.50, 0.56, 0.70, 0.74))
+    measure("hex cube 128^3 elements, tabulated laws (4 points)", p4, ff.FP32_KAHAN, 200)
+    # and with three tissue regions: a tumour ball (r = 20 mm) in a perfused shell, in liver
+    p5 = copy.copy(w3.problem)
+    cen = p5.xyz[np.asarray(p5.conn)].mean(axis=1)
+    d = np.linalg.norm(cen - 0.064, axis=1)
+    p5.regions = np.where(d < 0.020, 1, np.where(d < 0.032, 2, 0)).astype(np.int32)
+    p5.region_materials = (w3.problem.material,
+                           Material(T_ref=37.0, rho0=1045.0, drho=-0.8, c0=3750.0, dc=6.0, k0=0.60, dk=0.0030),
+                           Material.constant(1050.0, 3617.0, 0.50))
+    pf = w3.problem.perfusion
+    p5.region_perfusion = (pf, Perfusion(w_b=0.2 * pf.w_b, c_b=pf.c_b, T_a=pf.T_a, Q_m=2.0 * pf.Q_m),
+                           Perfusion(w_b=4.0 * pf.w_b, c_b=pf.c_b, T_a=pf.T_a, Q_m=0.0))
+    measure("hex cube 128^3 elements, three tissue regions", p5, ff.FP32_KAHAN, 200)
     print(json.dumps({"workload": "suite", "n_gpus": 1, "data": "synthetic", "hbm_peak_gbs": peak, "rows": rows}))
 
 
