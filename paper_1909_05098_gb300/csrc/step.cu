@@ -68,33 +68,47 @@ __device__ __forceinline__ F4 tab_law(const StepArgs<R, L>& a, F4 T) {
     return F4{tab_law<P>(a, T.x), tab_law<P>(a, T.y), tab_law<P>(a, T.z), tab_law<P>(a, T.w)};
 }
 
-// k(T) of kernels built with the extensions: the table when one is set, else
-// the element's linear law (its region's, or the material's)
+// k(T) from the property table
 template <typename R, typename L>
-struct ExtKLaw {
+struct TabKLaw {
     const StepArgs<R, L>& a;
-    R T_ref, k0, dk;
     template <typename X>
-    __device__ __forceinline__ X at(X T) const {
-        if (a.n_tab > 0) return tab_law<2>(a, T);
-        return fmadd(dk, T - T_ref, k0);
-    }
+    __device__ __forceinline__ X at(X T) const { return tab_law<2>(a, T); }
 };
 
-// the k law of element j (em: region ids of the elements, or null)
-template <int MODE, typename R, typename L>
-__device__ __forceinline__ auto k_law(const StepArgs<R, L>& a, const unsigned char* em, int64_t j) {
+// The element k laws of a context, as functions of the element index j: the
+// material's law (Plain), each element's region law (Region), or the table
+// (Table).  Kernels built with the extensions pick one per launch or tile
+// (uniform), so no element pays a branch between them.
+template <typename R, typename L>
+struct PlainK {
+    const StepArgs<R, L>& a;
+    __device__ __forceinline__ Law<R> operator()(int64_t) const { return Law<R>{a.T_ref, a.k0, a.dk}; }
+};
+template <typename R, typename L>
+struct RegionK {
+    const StepArgs<R, L>& a;
+    const unsigned char* em;
+    __device__ __forceinline__ Law<R> operator()(int64_t j) const {
+        const R* q = a.mat_k + 3 * (int)em[j];
+        return Law<R>{__ldg(q), __ldg(q + 1), __ldg(q + 2)};
+    }
+};
+template <typename R, typename L>
+struct TableK {
+    const StepArgs<R, L>& a;
+    __device__ __forceinline__ TabKLaw<R, L> operator()(int64_t) const { return TabKLaw<R, L>{a}; }
+};
+
+// f(k) with the context's element k laws (em: region ids of the elements, or null)
+template <int MODE, typename R, typename L, typename Fn>
+__device__ __forceinline__ void with_k_laws(const StepArgs<R, L>& a, const unsigned char* em, Fn&& f) {
     if constexpr ((MODE & 2) != 0) {
-        ExtKLaw<R, L> k{a, a.T_ref, a.k0, a.dk};
-        if (em) {
-            const R* q = a.mat_k + 3 * (int)em[j];
-            k.T_ref = __ldg(q);
-            k.k0 = __ldg(q + 1);
-            k.dk = __ldg(q + 2);
-        }
-        return k;
+        if (a.n_tab > 0) f(TableK<R, L>{a});
+        else if (em) f(RegionK<R, L>{a, em});
+        else f(PlainK<R, L>{a});
     } else {
-        return Law<R>{a.T_ref, a.k0, a.dk};
+        f(PlainK<R, L>{a});
     }
 }
 
@@ -114,8 +128,8 @@ __device__ __forceinline__ void element_phase(const StepArgs<R>& a, int64_t e) {
     R t[NV];
 #pragma unroll
     for (int n = 0; n < NV; ++n) t[n] = a.T[c[n]];
-    const auto k = k_law<MODE>(a, a.emat, e);
-    const R ke = element_k<R, NV>(t, k);
+    R ke;
+    with_k_laws<MODE>(a, a.emat, [&](const auto& kl) { ke = element_k<R, NV>(t, kl(e)); });
     R F[NV];
     if (NV == 8) hex8_loads<R>(t, m, ke, F);
     else tet4_loads<R>(t, m, ke, F);
@@ -469,9 +483,9 @@ __device__ __forceinline__ const unsigned char* tile_regions(const StepArgs<R, L
 
 // element phase of one tile: loads of every tile element; each owned corner's
 // load goes to Fn[rank * B + local id]
-template <typename R, typename L, int NV, int MODE, bool SHARED>
-__device__ __forceinline__ void tile_elements(const StepArgs<R, L>& a, const unsigned char* em, const TileView<R>& v,
-                                              int own, int B, int rank_shift, const L* Ts, L* Fn) {
+template <typename R, typename L, int NV, bool SHARED, typename KL>
+__device__ __forceinline__ void tile_elements_k(const KL& kl, const TileView<R>& v, int own, int B, int rank_shift,
+                                                const L* Ts, L* Fn) {
     const int id_mask = (1 << rank_shift) - 1;
     for (int j = threadIdx.x; j < v.ne; j += blockDim.x) {
         int c[NV];
@@ -486,7 +500,7 @@ __device__ __forceinline__ void tile_elements(const StepArgs<R, L>& a, const uns
             m[q] = p.x;
             m[q + 1] = p.y;
         }
-        const L ke = element_k<R, NV, L>(tt, k_law<MODE>(a, em, j));
+        const L ke = element_k<R, NV, L>(tt, kl(j));
         L F[NV];
         if (NV == 8) hex8_loads<R, L>(tt, m, ke, F);
         else tet4_loads<R, L>(tt, m, ke, F);
@@ -497,6 +511,12 @@ __device__ __forceinline__ void tile_elements(const StepArgs<R, L>& a, const uns
             if (id < own) Fn[(c[n] >> rank_shift) * B + id] = F[n];
         }
     }
+}
+
+template <typename R, typename L, int NV, int MODE, bool SHARED>
+__device__ __forceinline__ void tile_elements(const StepArgs<R, L>& a, const unsigned char* em, const TileView<R>& v,
+                                              int own, int B, int rank_shift, const L* Ts, L* Fn) {
+    with_k_laws<MODE>(a, em, [&](const auto& kl) { tile_elements_k<R, L, NV, SHARED>(kl, v, own, B, rank_shift, Ts, Fn); });
 }
 
 // node phase: sum each owned node's column (rank order), clear it, Eq. 19.
