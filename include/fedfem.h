@@ -237,8 +237,21 @@ int fedfem_set_source_schedule(fedfem_ctx* ctx, int n, const double* t_end, cons
  * state's precision.  on != 0 enables it from the next fedfem_precompute;
  * fedfem_init resets it to 0; checkpoints carry it. */
 int fedfem_enable_dose(fedfem_ctx* ctx, int on);
-/* CEM43 in minutes, n_nodes doubles in input node order (caller-owned host
- * buffer).  Dirichlet nodes report their fixed temperature held for the
+
+#define FEDFEM_DOSE_CEM43 0
+#define FEDFEM_DOSE_ARRHENIUS 1
+/* The dose model (default CEM43).  FEDFEM_DOSE_ARRHENIUS: the thermal damage
+ * integral of Henriques and Moritz, Omega += dt A exp(-Ea / (R T_K)), A the
+ * frequency factor (1/s), Ea the activation energy (J/mol), R = 8.314462618
+ * J/(mol K), T_K = T + 273.15, at each step's start temperature, summed in
+ * FP64 (the exponential in the state's precision); fedfem_read_dose then
+ * returns Omega (dimensionless; 1 is the usual coagulation threshold).
+ * FEDFEM_DOSE_CEM43 ignores A and Ea.  E_ARG for another model or A, Ea not
+ * finite and positive.  Takes effect at the next step; fedfem_init resets
+ * the accumulated value, so set it before fedfem_init. */
+int fedfem_set_dose_model(fedfem_ctx* ctx, int model, double A, double Ea);
+/* CEM43 in minutes (or Omega, see fedfem_set_dose_model), n_nodes doubles in
+ * input node order (caller-owned host buffer).  Dirichlet nodes report their fixed temperature held for the
  * elapsed simulated time.  Waits for the context's stream.  E_STATE if the
  * dose is not enabled or before fedfem_init. */
 int fedfem_read_dose(fedfem_ctx* ctx, double* out);

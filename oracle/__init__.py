@@ -31,7 +31,7 @@ Readings of the paper it follows (each also listed in the design notes):
 * sources are lumped with the same V_i: Q_i = V_i (Q_m + Q_r(x_i)) + q_i.
 """
 from .elements import hex8_reduced, tet4_linear, element_matrices   # noqa: F401
-from .global_form import Oracle, cem43_increment, piecewise_linear   # noqa: F401
+from .global_form import Oracle, arrhenius_increment, cem43_increment, piecewise_linear   # noqa: F401
 from .critical_dt import critical_dt, td_scale, element_bound_dt     # noqa: F401
 from .metrics import eq20_error, table_stats                          # noqa: F401
 from .sampled import sampled_run                                      # noqa: F401

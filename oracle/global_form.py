@@ -29,7 +29,8 @@ time, Q(t) = Q_const + f(t) Q_src.  Thermal dose (the treatment-planning use
 named in Section 5; the paper gives no formula): cumulative equivalent minutes
 at 43 degC (Sapareto and Dewey, 1984), CEM43 += (dt / 60) R^(43 - T), R = 1/2
 for T >= 43 degC and 1/4 below, with T the node's temperature at the start of
-the step.
+the step.  Alternatively the Arrhenius damage integral (Henriques and
+Moritz, 1947), Omega += dt A exp(-Ea / (R T_K)), at the same temperature.
 """
 from __future__ import annotations
 
@@ -199,12 +200,15 @@ class Oracle:
         Tn[~self.free] = T[~self.free]
         return Tn
 
-    def run(self, dt: float, n_steps: int, T=None, dose: bool = False):
-        """n_steps steps from t = 0; with dose=True also returns CEM43 (minutes)."""
+    def run(self, dt: float, n_steps: int, T=None, dose=False):
+        """n_steps steps from t = 0; with dose=True also returns CEM43
+        (minutes), with dose=("arrhenius", A, Ea) the damage integral Omega."""
         T = self.initial_field() if T is None else np.array(T, dtype=np.float64)
         D = np.zeros(self.N)
         for k in range(n_steps):
-            if dose:
+            if isinstance(dose, tuple):
+                D = D + arrhenius_increment(T, dt, dose[1], dose[2])
+            elif dose:
                 D = D + cem43_increment(T, dt)
             T = self.step(T, dt, k * dt)
         return (T, D) if dose else T
@@ -220,6 +224,18 @@ def piecewise_linear(Tj, pj, T):
     i = np.clip(np.searchsorted(Tj, T, side="right") - 1, 0, len(Tj) - 2)
     slope = (pj[1:] - pj[:-1]) / (Tj[1:] - Tj[:-1])
     return pj[i] + slope[i] * (T - Tj[i])
+
+
+GAS_CONSTANT = 8.314462618   # J/(mol K), CODATA 2018
+KELVIN = 273.15
+
+
+def arrhenius_increment(T, dt: float, A: float, Ea: float) -> np.ndarray:
+    """Arrhenius thermal damage (Henriques and Moritz, 1947): the damage
+    integral Omega = int A exp(-Ea / (R T_K)) dt, one step at the step's start
+    temperature: dt A exp(-Ea / (R (T + 273.15)))."""
+    T = np.asarray(T, dtype=np.float64)
+    return dt * A * np.exp(-Ea / (GAS_CONSTANT * (T + KELVIN)))
 
 
 def cem43_increment(T, dt: float) -> np.ndarray:

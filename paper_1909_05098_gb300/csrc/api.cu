@@ -45,6 +45,8 @@ struct fedfem_ctx {
     std::vector<double> flux;                     // empty: none
     std::vector<double> sched_end, sched_f;       // source schedule (empty: sources always on)
     bool dose_on = false;
+    int dose_model = FEDFEM_DOSE_CEM43;
+    double dose_A = 0.0, dose_Ea = 0.0;           // Arrhenius frequency factor (1/s), activation energy (J/mol)
     int n_reg = 0;                                // heterogeneous tissue regions (0: mat everywhere)
     std::vector<fedfem_material> reg_mat;
     std::vector<fedfem_perfusion> reg_perf;       // w_b, c_b, Q_m per region (T_a from perf)
@@ -102,6 +104,8 @@ struct fedfem_ctx {
 };
 
 namespace {
+
+constexpr double kGasConstant = 8.314462618;   // J/(mol K), CODATA 2018
 
 int fail(fedfem_ctx* c, int code, const std::string& msg) {
     if (c) c->err = msg;
@@ -293,7 +297,10 @@ StepArgs<R, L> make_args(fedfem_ctx* c, const R* M, const R* V, const R* Q, cons
         a.seg_f[k] = (R)c->sched_f[k];
     }
     a.dose = c->dose;
-    a.dose_dt = dt / 60.0;
+    a.dose_model = c->dose_model;
+    a.dose_dt = c->dose_model == FEDFEM_DOSE_ARRHENIUS ? dt : dt / 60.0;
+    a.dose_lnA = c->dose_model == FEDFEM_DOSE_ARRHENIUS ? std::log(c->dose_A) : 0.0;
+    a.dose_EaR = c->dose_Ea / kGasConstant;
     a.E = c->E; a.N = c->N; a.N_plain = c->L.N_plain; a.N_free = c->L.N_free;
     a.conn4 = c->conn4; a.M = M; a.slots = (R*)c->slots;
     a.sell_off = c->sell_off; a.sell_ids = c->sell_ids;
@@ -872,6 +879,22 @@ int fedfem_enable_dose(fedfem_ctx* c, int on) {
     return FEDFEM_OK;
 }
 
+int fedfem_set_dose_model(fedfem_ctx* c, int model, double A, double Ea) {
+    if (!c) return FEDFEM_E_ARG;
+    if (model == FEDFEM_DOSE_CEM43) {
+        c->dose_model = model;
+        c->dose_A = c->dose_Ea = 0.0;
+        return FEDFEM_OK;
+    }
+    if (model != FEDFEM_DOSE_ARRHENIUS) return fail(c, FEDFEM_E_ARG, "unknown dose model");
+    if (!(is_finite(A) && is_finite(Ea) && A > 0 && Ea > 0))
+        return fail(c, FEDFEM_E_ARG, "Arrhenius A and Ea must be finite and positive");
+    c->dose_model = model;
+    c->dose_A = A;
+    c->dose_Ea = Ea;
+    return FEDFEM_OK;
+}
+
 int fedfem_read_dose_lane(fedfem_ctx* c, int lane, double* out) {
     if (!c || !out) return fail(c, FEDFEM_E_ARG, "null output");
     if (!c->dose) return fail(c, FEDFEM_E_STATE, "enable the dose before fedfem_precompute");
@@ -887,7 +910,9 @@ int fedfem_read_dose_lane(fedfem_ctx* c, int lane, double* out) {
     for (int64_t i = NF; i < c->N; ++i) {
         const int64_t o = c->L.node_of[i];
         const double T = c->dir_T[o];
-        out[o] = c->sim_time / 60.0 * std::exp2(T >= 43.0 ? T - 43.0 : 2.0 * (T - 43.0));
+        out[o] = c->dose_model == FEDFEM_DOSE_ARRHENIUS
+                     ? c->sim_time * std::exp(std::log(c->dose_A) - c->dose_Ea / kGasConstant / (T + 273.15))
+                     : c->sim_time / 60.0 * std::exp2(T >= 43.0 ? T - 43.0 : 2.0 * (T - 43.0));
     }
     return FEDFEM_OK;
 }

@@ -124,9 +124,13 @@ struct StepArgs {
     int n_seg;
     double seg_end[kMaxSegments];
     R seg_f[kMaxSegments];
-    // CEM43 thermal dose: dose[i * lanes + l] += dose_dt R^(43 - T_il), minutes
+    // thermal dose, dose[i * lanes + l] += dose_dt * rate(T_il): CEM43 minutes
+    // (dose_model 0, dose_dt = dt / 60) or the Arrhenius damage integral
+    // (dose_model 1, dose_dt = dt, rate = exp(dose_lnA - dose_EaR / T_K))
     double* dose;
-    double dose_dt;                  // dt / 60
+    double dose_dt;
+    int dose_model;
+    double dose_lnA, dose_EaR;
     // piecewise-linear laws (n_tab > 0): property P (0 rho, 1 c, 2 k) is
     // p_P[j] + s_P[j] (T - T_j) on the interval j that holds T (the first one
     // below the table, the last one above it).  tab: device array of 7 rows of

@@ -175,25 +175,35 @@ __device__ __forceinline__ R schedule_factor(const StepArgs<R, L>& a, long long 
     return a.seg_f[k];
 }
 
-// CEM43 increment of node i at the step's start temperature T, accumulated in
-// FP64; the power is taken in the state's precision (FP32 state: exp2f, whose
-// relative error is far below that of the FP32 temperature it is taken of)
-__device__ __forceinline__ void dose_add(double* dose, int64_t i, double dose_dt, double T) {
-    dose[i] += dose_dt * exp2(T >= 43.0 ? T - 43.0 : 2.0 * (T - 43.0));
+// Dose rate at the step's start temperature T: CEM43 (model 0), R^(43 - T)
+// with R = 1/2 at or above 43 degC and 1/4 below, in equivalent minutes per
+// minute; or the Arrhenius damage rate (model 1), A exp(-Ea / (R_gas T_K)) =
+// exp(lnA - EaR / (T + 273.15)), per second.  The power is taken in the
+// state's precision (FP32 state: exp2f / expf, whose relative error is far
+// below that of the FP32 temperature it is taken of); sums are FP64.
+__device__ __forceinline__ double dose_rate(int model, double lnA, double EaR, double T) {
+    if (model == 1) return exp(lnA - EaR / (T + 273.15));
+    return exp2(T >= 43.0 ? T - 43.0 : 2.0 * (T - 43.0));
 }
-__device__ __forceinline__ void dose_add(double* dose, int64_t i, double dose_dt, float T) {
-    dose[i] += dose_dt * (double)exp2f(T >= 43.0f ? T - 43.0f : 2.0f * (T - 43.0f));
+__device__ __forceinline__ double dose_rate(int model, double lnA, double EaR, float T) {
+    if (model == 1) return (double)expf((float)lnA - (float)EaR / (T + 273.15f));
+    return (double)exp2f(T >= 43.0f ? T - 43.0f : 2.0f * (T - 43.0f));
+}
+template <typename R, typename L>
+__device__ __forceinline__ void dose_add(const StepArgs<R, L>& a, int64_t i, R T) {
+    a.dose[i] += a.dose_dt * dose_rate(a.dose_model, a.dose_lnA, a.dose_EaR, T);
 }
 // four scenario lanes: the node's four doses are contiguous
-__device__ __forceinline__ void dose_add(double* dose, int64_t i, double dose_dt, F4 T) {
-    double2* d = reinterpret_cast<double2*>(dose + 4 * i);
-    double2 a = d[0], b = d[1];
-    a.x += dose_dt * (double)exp2f(T.x >= 43.0f ? T.x - 43.0f : 2.0f * (T.x - 43.0f));
-    a.y += dose_dt * (double)exp2f(T.y >= 43.0f ? T.y - 43.0f : 2.0f * (T.y - 43.0f));
-    b.x += dose_dt * (double)exp2f(T.z >= 43.0f ? T.z - 43.0f : 2.0f * (T.z - 43.0f));
-    b.y += dose_dt * (double)exp2f(T.w >= 43.0f ? T.w - 43.0f : 2.0f * (T.w - 43.0f));
-    d[0] = a;
-    d[1] = b;
+template <typename R, typename L>
+__device__ __forceinline__ void dose_add(const StepArgs<R, L>& a, int64_t i, F4 T) {
+    double2* d = reinterpret_cast<double2*>(a.dose + 4 * i);
+    double2 p = d[0], q = d[1];
+    p.x += a.dose_dt * dose_rate(a.dose_model, a.dose_lnA, a.dose_EaR, T.x);
+    p.y += a.dose_dt * dose_rate(a.dose_model, a.dose_lnA, a.dose_EaR, T.y);
+    q.x += a.dose_dt * dose_rate(a.dose_model, a.dose_lnA, a.dose_EaR, T.z);
+    q.y += a.dose_dt * dose_rate(a.dose_model, a.dose_lnA, a.dose_EaR, T.w);
+    d[0] = p;
+    d[1] = q;
 }
 
 template <typename R, typename L, int MODE>
@@ -216,7 +226,7 @@ __device__ __forceinline__ void node_update_v(const StepArgs<R, L>& a, int64_t i
             beta = a.Cq[3 * nf + i];
         }
         if (a.Qs) q = fmadd(schedule_factor(a, step), a.Qs[i], q);
-        if (a.dose) dose_add(a.dose, i, a.dose_dt, T);   // CEM43 at the step's start temperature
+        if (a.dose) dose_add(a, i, T);   // at the step's start temperature
     }
     L r = fmadd(beta, a.T_a - T, q) - F;
     if (i >= a.N_plain) r = fmadd(v.hA, a.T_inf - T, r);

@@ -24,6 +24,7 @@ TET4, HEX8 = 4, 8
 FP64, FP32_KAHAN, FP32_PLAIN = 0, 1, 2
 ORDER_INPUT, ORDER_MORTON, ORDER_RCM = 0, 1, 2
 KERNEL_TWO_PHASE, KERNEL_PERSISTENT, KERNEL_TILED, KERNEL_TILED_STAGED = 0, 1, 2, 3
+DOSE_CEM43, DOSE_ARRHENIUS = 0, 1
 
 STATUS_NAMES = {0: "OK", -1: "E_ARG", -2: "E_MESH", -3: "E_STATE", -4: "E_UNSTABLE_DT", -5: "E_RANGE",
                 -6: "E_TIMEOUT", -7: "E_CUDA", -8: "E_OOM", -9: "E_UNSUPPORTED"}
@@ -113,6 +114,7 @@ _SIGS = {
     "fedfem_set_regions": ([_ctx_p, C.c_int, C.POINTER(fedfem_material), C.POINTER(fedfem_perfusion), _ip],
                            C.c_int),
     "fedfem_enable_dose": ([_ctx_p, C.c_int], C.c_int),
+    "fedfem_set_dose_model": ([_ctx_p, C.c_int, C.c_double, C.c_double], C.c_int),
     "fedfem_read_dose": ([_ctx_p, _dp], C.c_int),
     "fedfem_read_dose_lane": ([_ctx_p, C.c_int, _dp], C.c_int),
     "fedfem_add_gaussian_source_lane": ([_ctx_p, C.c_int, C.c_int, _dp, C.c_double, C.c_double], C.c_int),
@@ -481,6 +483,21 @@ def fedfem_enable_dose(ctx, on=True):
     _check(ctx, _lib.fedfem_enable_dose(ctx, 1 if on else 0))
 
 
+def fedfem_set_dose_model(ctx, model, A=0.0, Ea=0.0):
+    _check(ctx, _lib.fedfem_set_dose_model(ctx, int(model), float(A), float(Ea)))
+
+
+def _apply_dose(ctx, dose):
+    """dose: False, True / "cem43" (CEM43 minutes) or ("arrhenius", A, Ea)."""
+    if not (isinstance(dose, tuple) or dose):
+        return
+    fedfem_enable_dose(ctx, True)
+    if isinstance(dose, tuple):
+        if dose[0] != "arrhenius":
+            raise ValueError("dose: True, 'cem43' or ('arrhenius', A, Ea)")
+        fedfem_set_dose_model(ctx, DOSE_ARRHENIUS, dose[1], dose[2])
+
+
 def fedfem_read_dose(ctx, lane=0) -> np.ndarray:
     n = fedfem_get_info(ctx)["n_nodes"]
     out = np.empty(n, dtype=np.float64)
@@ -521,8 +538,7 @@ class Solver:
                 fedfem_set_nodal_flux(self.ctx, p.flux_nodes, p.flux_q)
             if len(getattr(p, "schedule_factor", ())):
                 fedfem_set_source_schedule(self.ctx, p.schedule_end, p.schedule_factor)
-            if dose:
-                fedfem_enable_dose(self.ctx, True)
+            _apply_dose(self.ctx, dose)
             fedfem_set_tile(self.ctx, kernel)
             self.dt_cr = fedfem_precompute(self.ctx, p.T_lo if T_lo is None else T_lo,
                                            p.T_hi if T_hi is None else T_hi)
@@ -550,7 +566,7 @@ class Solver:
         return fedfem_read_temperature(self.ctx)
 
     def dose(self):
-        """CEM43 minutes per node (input order); needs dose=True."""
+        """CEM43 minutes (or the Arrhenius Omega) per node, input order; needs dose."""
         return fedfem_read_dose(self.ctx)
 
     def info(self):
@@ -620,8 +636,7 @@ class Batch:
                         fedfem_add_gaussian_source_lane(self.ctx, lane, g, s.x0, s.sigma, s.peak)
             if schedule is not None:       # (t_end, factor): every run's sources follow it
                 fedfem_set_source_schedule(self.ctx, *schedule)
-            if dose:
-                fedfem_enable_dose(self.ctx, True)
+            _apply_dose(self.ctx, dose)
             fedfem_set_tile(self.ctx, kernel)
             self.dt_cr = fedfem_precompute(self.ctx, min(p[0].T_lo for p in meshes),
                                            max(p[0].T_hi for p in meshes))
@@ -636,7 +651,7 @@ class Batch:
         return T[self.node_off[mesh]: self.node_off[mesh + 1]]
 
     def dose(self, mesh: int, scenario: int) -> np.ndarray:
-        """CEM43 minutes of one run (needs dose=True)."""
+        """CEM43 minutes (or the Arrhenius Omega) of one run (needs dose)."""
         D = fedfem_read_dose(self.ctx, scenario)
         return D[self.node_off[mesh]: self.node_off[mesh + 1]]
 

@@ -140,3 +140,55 @@ def test_unsupported_combinations_are_refused(two_stage):
         assert e.value.code == f.E_ARG
     finally:
         b.close()
+
+
+ARR = ("arrhenius", 7.39e39, 2.577e5)   # liver coagulation parameters often used
+
+
+@pytest.fixture(scope="module")
+def two_stage_damage(two_stage):
+    p, dt, _, _ = two_stage
+    T, D = Oracle(p).run(dt, N_STEPS, dose=ARR)
+    return p, dt, T, D
+
+
+@pytest.mark.parametrize("prec_name", ["FP64", "FP32_KAHAN"])
+def test_arrhenius_damage_matches_the_oracle(two_stage_damage, prec_name):
+    p, dt, T_ref, D_ref = two_stage_damage
+    f = ff()
+    s = f.Solver(p, precision=getattr(f, prec_name), dose=ARR)
+    try:
+        s.step(dt, N_STEPS)
+        assert s.sync() == N_STEPS
+        T, D = s.temperature(), s.dose()
+    finally:
+        s.close()
+    rel = np.max(np.abs(D - D_ref) / D_ref)
+    print(f"Arrhenius {prec_name}: Omega in [{D_ref.min():.3e}, {D_ref.max():.3e}], max rel error {rel:.2e}")
+    assert D_ref.max() > 1.0                      # the heated core coagulates
+    if prec_name == "FP64":
+        assert max_abs(T, T_ref) <= TOL64 and rel <= 1e-12
+    else:
+        assert max_abs(T, T_ref) <= TOL32 and rel <= 1e-4
+
+
+def test_arrhenius_is_the_same_in_every_kernel_and_arguments_are_checked(two_stage):
+    p, dt, _, _ = two_stage
+    f = ff()
+    out = []
+    for kern in (f.KERNEL_PERSISTENT, f.KERNEL_TWO_PHASE, f.KERNEL_TILED, f.KERNEL_TILED_STAGED):
+        s = f.Solver(p, precision=f.FP32_KAHAN, kernel=kern, dose=ARR)
+        try:
+            s.step(dt, 150)
+            s.sync()
+            out.append(s.dose())
+            if kern == f.KERNEL_PERSISTENT:
+                for args in [(2, 1.0, 1.0), (f.DOSE_ARRHENIUS, 0.0, 1.0), (f.DOSE_ARRHENIUS, 1.0, -1.0),
+                             (f.DOSE_ARRHENIUS, float("inf"), 1.0)]:
+                    with pytest.raises(f.FedfemError) as e:
+                        f.fedfem_set_dose_model(s.ctx, *args)
+                    assert e.value.code == f.E_ARG, args
+        finally:
+            s.close()
+    for D in out[1:]:
+        assert np.array_equal(D, out[0])

@@ -94,3 +94,54 @@ def test_cem43_increment_switches_base_at_43():
     d = cem43_increment(np.array([42.999999, 43.0, 43.000001]), 60.0)
     assert d[1] == 1.0
     assert d[0] == pytest.approx(0.25 ** 1e-6, rel=1e-12) and d[2] == pytest.approx(0.5 ** -1e-6, rel=1e-12)
+
+
+# --- Arrhenius damage integral (Henriques and Moritz) -----------------------
+# liver coagulation parameters often used with this model
+A_LIVER, EA_LIVER = 7.39e39, 2.577e5
+
+
+def test_arrhenius_during_linear_heating_meets_the_exponential_integral():
+    """Insulated uniform heating at a constant rate h: T(t) = T0 + h t, so
+    Omega(t) = (A / h) [F(theta_1) - F(theta_0)] with theta = T + 273.15 K,
+    b = Ea / R and F(theta) = theta exp(-b / theta) - b E1(b / theta) (the
+    exponential integral).  The oracle sums the rate at each step's start
+    temperature, a first-order rule, so Richardson's 2 Omega(dt/2) - Omega(dt)
+    meets the closed form to O(dt^2)."""
+    from scipy.special import exp1
+    from oracle.global_form import GAS_CONSTANT
+    Q0, T0, t_end, dt = 4e6, 40.0, 20.0, 0.1
+    p = _insulated_box(Q0, T0)
+    h = Q0 / (1000.0 * 4000.0)                          # K/s
+    _, D1 = Oracle(p).run(dt, int(round(t_end / dt)), dose=("arrhenius", A_LIVER, EA_LIVER))
+    T2, D2 = Oracle(p).run(dt / 2, int(round(2 * t_end / dt)), dose=("arrhenius", A_LIVER, EA_LIVER))
+    assert np.allclose(T2, T0 + h * t_end, rtol=1e-12)  # 40 -> 60 degC
+    b = EA_LIVER / GAS_CONSTANT
+
+    def F(theta):
+        return theta * np.exp(-b / theta) - b * exp1(b / theta)
+
+    exact = A_LIVER / h * (F(T0 + h * t_end + 273.15) - F(T0 + 273.15))
+    assert 0.1 < exact < 100.0                            # coagulation (Omega = 1) is crossed
+    assert np.max(np.abs(2 * D2 - D1 - exact)) <= 1e-4 * exact
+    assert np.max(np.abs(D2 - exact)) >= 1e-3 * exact     # the step is coarse enough to be informative
+
+
+def test_arrhenius_of_a_constant_field_and_its_rate_ratio():
+    """At constant T the damage after n steps is n dt A exp(-Ea / (R T_K)),
+    and one kelvin more multiplies the rate by exp(b / (T_K (T_K + 1)))."""
+    from oracle.global_form import GAS_CONSTANT
+    w = cube_hex_fp64()
+    out = []
+    for Tc in (50.0, 51.0):
+        p = copy.copy(w.problem)
+        p.sources = []
+        p.T0 = Tc
+        p.dirichlet_T = np.full(len(p.dirichlet_nodes), Tc)
+        p.perfusion = Perfusion(w_b=p.perfusion.w_b, c_b=p.perfusion.c_b, T_a=Tc, Q_m=0.0)
+        T, D = Oracle(p).run(0.5, 40, dose=("arrhenius", A_LIVER, EA_LIVER))
+        assert np.all(T == Tc) and np.ptp(D) == 0.0
+        out.append(D[0])
+    b = EA_LIVER / GAS_CONSTANT
+    assert out[1] / out[0] == pytest.approx(np.exp(b / (323.15 * 324.15)), rel=1e-12)
+    assert out[0] == pytest.approx(40 * 0.5 * A_LIVER * np.exp(-b / 323.15), rel=1e-13)
