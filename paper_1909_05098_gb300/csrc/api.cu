@@ -301,6 +301,10 @@ StepArgs<R, L> make_args(fedfem_ctx* c, const R* M, const R* V, const R* Q, cons
     a.dose_dt = c->dose_model == FEDFEM_DOSE_ARRHENIUS ? dt : dt / 60.0;
     a.dose_lnA = c->dose_model == FEDFEM_DOSE_ARRHENIUS ? std::log(c->dose_A) : 0.0;
     a.dose_EaR = c->dose_Ea / kGasConstant;
+    const bool arr = c->dose_model == FEDFEM_DOSE_ARRHENIUS;
+    a.dose_c43 = arr ? 0.0f : 1.0f;
+    a.dose_a2 = arr ? (float)std::log2(c->dose_A) : 0.0f;
+    a.dose_g2 = arr ? (float)(a.dose_EaR / std::log(2.0)) : 0.0f;
     a.E = c->E; a.N = c->N; a.N_plain = c->L.N_plain; a.N_free = c->L.N_free;
     a.conn4 = c->conn4; a.M = M; a.slots = (R*)c->slots;
     a.sell_off = c->sell_off; a.sell_ids = c->sell_ids;

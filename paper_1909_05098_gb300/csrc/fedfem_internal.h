@@ -131,6 +131,7 @@ struct StepArgs {
     double dose_dt;
     int dose_model;
     double dose_lnA, dose_EaR;
+    float dose_c43, dose_a2, dose_g2;   // FP32 state: the rate as 2^(c43 s (T - 43) + a2 - g2 / T_K)
     // piecewise-linear laws (n_tab > 0): property P (0 rho, 1 c, 2 k) is
     // p_P[j] + s_P[j] (T - T_j) on the interval j that holds T (the first one
     // below the table, the last one above it).  tab: device array of 7 rows of

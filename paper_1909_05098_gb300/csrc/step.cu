@@ -179,29 +179,37 @@ __device__ __forceinline__ R schedule_factor(const StepArgs<R, L>& a, long long 
 // with R = 1/2 at or above 43 degC and 1/4 below, in equivalent minutes per
 // minute; or the Arrhenius damage rate (model 1), A exp(-Ea / (R_gas T_K)) =
 // exp(lnA - EaR / (T + 273.15)), per second.  The power is taken in the
-// state's precision (FP32 state: exp2f / expf, whose relative error is far
-// below that of the FP32 temperature it is taken of); sums are FP64.
+// state's precision (FP32 state: exp2f, whose relative error is far below
+// that of the FP32 temperature it is taken of); sums are FP64.
 __device__ __forceinline__ double dose_rate(int model, double lnA, double EaR, double T) {
     if (model == 1) return exp(lnA - EaR / (T + 273.15));
     return exp2(T >= 43.0 ? T - 43.0 : 2.0 * (T - 43.0));
 }
-__device__ __forceinline__ double dose_rate(int model, double lnA, double EaR, float T) {
-    if (model == 1) return (double)expf((float)lnA - (float)EaR / (T + 273.15f));
-    return (double)exp2f(T >= 43.0f ? T - 43.0f : 2.0f * (T - 43.0f));
+// FP32 state, both models as one power of 2 without a branch:
+// 2^(c43 s (T - 43) + a2 - g2 / T_K), s = 1 at or above 43 degC and 2 below;
+// CEM43: c43 = 1, a2 = g2 = 0 (exactly the CEM43 exponent); Arrhenius:
+// c43 = 0, a2 = log2 A, g2 = (Ea / R) / ln 2
+__device__ __forceinline__ double dose_rate(float c43, float a2, float g2, float T) {
+    const float e = c43 * (T >= 43.0f ? T - 43.0f : 2.0f * (T - 43.0f));
+    return (double)exp2f((e + a2) - g2 * __frcp_rn(T + 273.15f));
 }
-template <typename R, typename L>
-__device__ __forceinline__ void dose_add(const StepArgs<R, L>& a, int64_t i, R T) {
+template <typename L>
+__device__ __forceinline__ void dose_add(const StepArgs<double, L>& a, int64_t i, double T) {
     a.dose[i] += a.dose_dt * dose_rate(a.dose_model, a.dose_lnA, a.dose_EaR, T);
 }
+template <typename L>
+__device__ __forceinline__ void dose_add(const StepArgs<float, L>& a, int64_t i, float T) {
+    a.dose[i] += a.dose_dt * dose_rate(a.dose_c43, a.dose_a2, a.dose_g2, T);
+}
 // four scenario lanes: the node's four doses are contiguous
-template <typename R, typename L>
-__device__ __forceinline__ void dose_add(const StepArgs<R, L>& a, int64_t i, F4 T) {
+template <typename L>
+__device__ __forceinline__ void dose_add(const StepArgs<float, L>& a, int64_t i, F4 T) {
     double2* d = reinterpret_cast<double2*>(a.dose + 4 * i);
     double2 p = d[0], q = d[1];
-    p.x += a.dose_dt * dose_rate(a.dose_model, a.dose_lnA, a.dose_EaR, T.x);
-    p.y += a.dose_dt * dose_rate(a.dose_model, a.dose_lnA, a.dose_EaR, T.y);
-    q.x += a.dose_dt * dose_rate(a.dose_model, a.dose_lnA, a.dose_EaR, T.z);
-    q.y += a.dose_dt * dose_rate(a.dose_model, a.dose_lnA, a.dose_EaR, T.w);
+    p.x += a.dose_dt * dose_rate(a.dose_c43, a.dose_a2, a.dose_g2, T.x);
+    p.y += a.dose_dt * dose_rate(a.dose_c43, a.dose_a2, a.dose_g2, T.y);
+    q.x += a.dose_dt * dose_rate(a.dose_c43, a.dose_a2, a.dose_g2, T.z);
+    q.y += a.dose_dt * dose_rate(a.dose_c43, a.dose_a2, a.dose_g2, T.w);
     d[0] = p;
     d[1] = q;
 }
