@@ -3,7 +3,10 @@
 Oracle code (test infrastructure only).  Every function here is pinned by
 tests/test_oracle_elements.py against closed forms: the unit right tetrahedron,
 the unit cube, exact gradient energy for affine fields, and the hourglass
-null-space of the one-point hexahedron.
+null-space of the one-point hexahedron; the fully integrated hexahedron
+(2 x 2 x 2 Gauss points) against the textbook unit-cube matrix, exact
+energies and volumes of distorted elements, and a null space of constants
+only.
 """
 from __future__ import annotations
 
@@ -36,6 +39,31 @@ def hex8_reduced(xe: np.ndarray):
     return A, detJ, 8.0 * detJ
 
 
+def hex8_full(xe: np.ndarray):
+    """Fully integrated hexahedron: A = sum over the 2 x 2 x 2 Gauss points
+    (xi, eta, zeta in {-1, +1} / sqrt 3, unit weights) of det J B^T B, with J
+    and B = J^-T dN/dxi taken at each point -- the textbook rule, exact for
+    the trilinear element's gradient energy, so no hourglass modes remain.
+    Returns (A, min det J over the points, V_e = sum of det J)."""
+    g = 1.0 / np.sqrt(3.0)
+    A = 0.0
+    V = 0.0
+    dmin = None
+    for p in HEX8_NATURAL * g:                                   # the 8 Gauss points
+        f = 1.0 + HEX8_NATURAL * p                               # (8, 3): 1 + s_n,j p_j
+        dN = np.empty((3, 8))
+        dN[0] = HEX8_NATURAL[:, 0] * f[:, 1] * f[:, 2] / 8.0
+        dN[1] = HEX8_NATURAL[:, 1] * f[:, 0] * f[:, 2] / 8.0
+        dN[2] = HEX8_NATURAL[:, 2] * f[:, 0] * f[:, 1] / 8.0
+        J = np.einsum("...ni,jn->...ij", xe, dN)
+        detJ = np.linalg.det(J)
+        B = np.einsum("...ji,jn->...in", np.linalg.inv(J), dN)
+        A = A + detJ[..., None, None] * np.einsum("...in,...im->...nm", B, B)
+        V = V + detJ
+        dmin = detJ if dmin is None else np.minimum(dmin, detJ)
+    return A, dmin, V
+
+
 def tet4_linear(xe: np.ndarray):
     """Linear tetrahedron, Eq. 15 and Eq. 16.
 
@@ -52,13 +80,16 @@ def tet4_linear(xe: np.ndarray):
     return A, detE, V
 
 
-def element_matrices(elem_type: int, xyz: np.ndarray, conn: np.ndarray):
-    """A_e, the orientation determinant and V_e for every element of a mesh.
+def element_matrices(elem_type: int, xyz: np.ndarray, conn: np.ndarray, hex_rule: str = "one-point"):
+    """A_e, the orientation determinant and V_e for every element of a mesh
+    (hex_rule: "one-point", Eq. 14, or "full", 2 x 2 x 2 Gauss points).
 
     Raises ValueError for an element with det <= 0 (inverted or degenerate),
     which the method cannot use (Algorithm 1, pre-computation)."""
     xe = xyz[conn]
-    if elem_type == 8:
+    if elem_type == 8 and hex_rule == "full":
+        A, det, V = hex8_full(xe)
+    elif elem_type == 8:
         A, det, V = hex8_reduced(xe)
     elif elem_type == 4:
         A, det, V = tet4_linear(xe)

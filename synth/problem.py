@@ -113,6 +113,8 @@ class Problem:
     regions: Optional[np.ndarray] = None
     region_materials: tuple = ()
     region_perfusion: tuple = ()
+    # hex8 integration: "one-point" (Eq. 14, the paper's) or "full" (2 x 2 x 2 Gauss)
+    hex_rule: str = "one-point"
 
     @property
     def n_nodes(self) -> int:

@@ -93,3 +93,77 @@ def test_inverted_element_is_rejected():
         element_matrices(4, xyz, np.array([[0, 2, 1, 3]], dtype=np.int32))
     with pytest.raises(ValueError):
         element_matrices(4, xyz, np.array([[0, 1, 2, 2]], dtype=np.int32))
+
+
+# --- fully integrated hexahedron (2 x 2 x 2 Gauss points) -------------------
+
+def test_full_hex_unit_cube_is_the_textbook_matrix():
+    """The trilinear unit cube's exact conduction matrix: 1/3 on the diagonal,
+    0 between corners sharing an edge, -1/12 across a face diagonal and across
+    the body diagonal."""
+    from oracle.elements import hex8_full
+    xe = (HEX8_NATURAL + 1.0) / 2.0
+    A, _, V = hex8_full(xe)
+    s = HEX8_NATURAL
+    diff = (s[:, None, :] != s[None, :, :]).sum(axis=2)      # 0 same, 1 edge, 2 face diagonal, 3 body diagonal
+    expect = np.select([diff == 0, diff == 1], [1.0 / 3.0, 0.0], -1.0 / 12.0)
+    np.testing.assert_allclose(A, expect, rtol=0, atol=1e-15)
+    assert V == pytest.approx(1.0, rel=1e-15)
+
+
+def test_full_hex_frustum_volume_and_affine_energy_are_exact():
+    """A square frustum (base 2 x 2, top 1 x 1, height 1, planar faces) has
+    volume (4 + 1 + 2) / 3; the full rule integrates the trilinear element's
+    det J exactly, so V_e and the energy |g|^2 V_e of an affine field are
+    exact, while the one-point rule gives 8 det J(centre) = 9/4."""
+    from oracle.elements import hex8_full
+    xe = np.array([[-1, -1, 0], [1, -1, 0], [1, 1, 0], [-1, 1, 0],
+                   [-.5, -.5, 1], [.5, -.5, 1], [.5, .5, 1], [-.5, .5, 1]], dtype=float)
+    A, det_min, V = hex8_full(xe)
+    assert V == pytest.approx(7.0 / 3.0, rel=1e-14)
+    assert hex8_reduced(xe)[2] == pytest.approx(9.0 / 4.0, rel=1e-14)
+    rng = np.random.default_rng(3)
+    for _ in range(5):
+        g = rng.normal(size=3)
+        T = xe @ g + rng.normal()
+        assert T @ A @ T == pytest.approx(g @ g * 7.0 / 3.0, rel=1e-12)
+    assert det_min > 0
+
+
+def test_full_hex_has_no_hourglass_modes():
+    """Only constants are in the null space: the four hourglass patterns that
+    the one-point rule cannot see carry energy, on a cube and a distorted hex."""
+    from oracle.elements import hex8_full
+    s = HEX8_NATURAL
+    hourglass = [s[:, 0] * s[:, 1], s[:, 1] * s[:, 2], s[:, 0] * s[:, 2], s[:, 0] * s[:, 1] * s[:, 2]]
+    rng = np.random.default_rng(7)
+    cube = (s + 1.0) / 2.0
+    for xe in (cube, cube + 0.15 * rng.uniform(-1, 1, size=(8, 3))):
+        A, _, _ = hex8_full(xe)
+        w = np.linalg.eigvalsh(A)
+        assert abs(w[0]) < 1e-14 * w[-1] and w[1] > 1e-3 * w[-1]
+        for h in hourglass:
+            assert h @ A @ h > 1e-3 * w[-1]
+    for h in hourglass:                                         # the one-point rule does not see them
+        assert abs(h @ hex8_reduced(cube)[0] @ h) < 1e-14
+
+
+def test_full_hex_kirchhoff_bar_is_unchanged():
+    """A field linear in x inside every element is affine, so both rules give
+    it the same exact energy: the Dirichlet bar's steady state under the full
+    rule is the same Kirchhoff-transform solution."""
+    from oracle import Oracle, critical_dt
+    from synth.meshes import box_face_nodes, hex_box
+    from synth.problem import Material, Problem
+    n, H = 8, 1e-3
+    m = hex_box(n, 1, 1, H)
+    mat = Material(T_ref=37.0, rho0=1060.0, drho=-1.4286, c0=3600.0, dc=7.14286, k0=0.53, dk=0.02)
+    left, right = box_face_nodes(m, ("x0",)), box_face_nodes(m, ("x1",))
+    p = Problem(m.elem_type, m.xyz, m.conn, mat, dirichlet_nodes=np.concatenate([left, right]),
+                dirichlet_T=np.concatenate([np.full(4, 37.0), np.full(4, 65.0)]), T0=40.0, hex_rule="full")
+    orc = Oracle(p)
+    T = orc.run(0.9 * critical_dt(orc, 30.0, 70.0), 6000)
+    u = lambda t: mat.k0 * (t - 37.0) + 0.5 * mat.dk * (t - 37.0) ** 2   # noqa: E731
+    target = u(37.0) + (u(65.0) - u(37.0)) * m.grid_index[:, 0] / n
+    expect = 37.0 + (-mat.k0 + np.sqrt(mat.k0 ** 2 + 2 * mat.dk * target)) / mat.dk
+    np.testing.assert_allclose(T, expect, rtol=0, atol=1e-10)
