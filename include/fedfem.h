@@ -139,6 +139,20 @@ int fedfem_create(fedfem_ctx** out, int device, int precision, void* cuda_stream
 int fedfem_set_mesh(fedfem_ctx* ctx, int elem_type, int64_t n_nodes, const double* xyz,
                     int64_t n_elems, const int32_t* conn);
 
+#define FEDFEM_HEX_ONE_POINT 0
+#define FEDFEM_HEX_FULL 1
+/* Integration rule of hex8 elements: FEDFEM_HEX_ONE_POINT (default; Eq. 14,
+ * J at the centre, V_e = 8 det J, the factored 6-value element matrix) or
+ * FEDFEM_HEX_FULL (2 x 2 x 2 Gauss points: A_e = sum of det J B^T B, exact for
+ * the trilinear element, no hourglass modes, V_e = sum of det J; an element
+ * with det J <= 0 at any point is E_MESH).  The full rule stores the 28
+ * off-diagonal entries per element (the diagonal follows from the zero row
+ * sums) and runs on the two-phase and persistent kernels (the tiled kernels
+ * refuse it with E_UNSUPPORTED at the next step); the critical step uses the
+ * full matrices.  Ignored for tet4.  E_ARG for another rule.  Takes effect at
+ * the next fedfem_precompute. */
+int fedfem_set_hex_integration(fedfem_ctx* ctx, int rule);
+
 /* Element order used internally (FEDFEM_ORDER_*; default MORTON). */
 int fedfem_set_order(fedfem_ctx* ctx, int order);
 

@@ -46,6 +46,7 @@ struct fedfem_ctx {
     std::vector<double> sched_end, sched_f;       // source schedule (empty: sources always on)
     bool dose_on = false;
     int dose_model = FEDFEM_DOSE_CEM43;
+    int hex_rule = FEDFEM_HEX_ONE_POINT;
     double dose_A = 0.0, dose_Ea = 0.0;           // Arrhenius frequency factor (1/s), activation energy (J/mol)
     int n_reg = 0;                                // heterogeneous tissue regions (0: mat everywhere)
     std::vector<fedfem_material> reg_mat;
@@ -72,6 +73,8 @@ struct fedfem_ctx {
     double* tab64 = nullptr;   // device copy of the property table (7 x kMaxTable), state precision
     float* tab32 = nullptr;
     unsigned char* emat = nullptr;             // regions: per internal element
+    double* A28_64 = nullptr;                  // fully integrated hex8: 28 planes of E
+    float* A28_32 = nullptr;
     double *Cq64 = nullptr, *matk64 = nullptr;   // regions: node coefficients (4 x N_free), k laws (3 each)
     float *Cq32 = nullptr, *matk32 = nullptr;
     double* dose = nullptr;                       // CEM43 minutes per free node
@@ -150,6 +153,7 @@ void free_device(fedfem_ctx* c) {
     c->V64 = c->Q64 = c->hA64 = c->Qs64 = nullptr; c->V32 = c->Q32 = c->hA32 = c->Qs32 = nullptr;
     c->tab64 = nullptr; c->tab32 = nullptr;
     c->emat = nullptr; c->Cq64 = c->matk64 = nullptr; c->Cq32 = c->matk32 = nullptr;
+    c->A28_64 = nullptr; c->A28_32 = nullptr;
     c->dose = nullptr;
     c->T = nullptr; c->T2 = nullptr; c->Tlo = nullptr; c->slots = nullptr; c->node_of = nullptr; c->T_dir = nullptr;
     c->io = nullptr; c->st = nullptr;
@@ -319,6 +323,7 @@ StepArgs<R, L> make_args(fedfem_ctx* c, const R* M, const R* V, const R* Q, cons
     a.n_tab = c->tab_n;
     for (int j = 0; j < c->tab_n; ++j) a.tab_T[j] = (R)c->tab_T[j];
     a.tab = std::is_same<R, double>::value ? (const R*)c->tab64 : (const R*)c->tab32;
+    a.A28 = std::is_same<R, double>::value ? (const R*)c->A28_64 : (const R*)c->A28_32;
     if (c->n_reg > 0 && c->emat) {
         a.emat = c->emat;
         a.emat_tile = c->t_emat;
@@ -505,6 +510,8 @@ int prepare_launch(fedfem_ctx* c, LaunchCfg& cfg) {
     cfg.spin_limit = c->spin_limit;
     const bool tiled = cfg.kernel == FEDFEM_KERNEL_TILED || cfg.kernel == FEDFEM_KERNEL_TILED_STAGED;
     if (c->n_lanes > 1 && !tiled) return fail(c, FEDFEM_E_UNSUPPORTED, "scenario lanes need a tiled kernel");
+    if (tiled && (c->A28_64 || c->A28_32))
+        return fail(c, FEDFEM_E_UNSUPPORTED, "the fully integrated hexahedron runs on the two-phase and persistent kernels");
     if (tiled) return plan_tiles(c);
     return FEDFEM_OK;
 }
@@ -883,6 +890,14 @@ int fedfem_enable_dose(fedfem_ctx* c, int on) {
     return FEDFEM_OK;
 }
 
+int fedfem_set_hex_integration(fedfem_ctx* c, int rule) {
+    if (!c) return FEDFEM_E_ARG;
+    if (rule != FEDFEM_HEX_ONE_POINT && rule != FEDFEM_HEX_FULL) return fail(c, FEDFEM_E_ARG, "unknown hex rule");
+    c->hex_rule = rule;
+    invalidate(c);
+    return FEDFEM_OK;
+}
+
 int fedfem_set_dose_model(fedfem_ctx* c, int model, double A, double Ea) {
     if (!c) return FEDFEM_E_ARG;
     if (model == FEDFEM_DOSE_CEM43) {
@@ -1076,6 +1091,11 @@ int fedfem_precompute(fedfem_ctx* c, double T_lo, double T_hi, double* dt_cr_out
     pa.face_nv = c->conv_nv; pa.faces = faces; pa.face_share = face_share;
     pa.conv_off = conv_off; pa.conv_face = conv_face; pa.h_film = c->conv_h;
     CU(launch_geometry(pa, st), "geometry kernel");
+    if (nv == 8 && c->hex_rule == FEDFEM_HEX_FULL) {   // A_e by 2 x 2 x 2 Gauss points, exact V_e
+        CU(dalloc(c, &c->A28_64, sizeof(double) * 28 * std::max<int64_t>(1, E)), "alloc");
+        pa.A28 = c->A28_64;
+        CU(launch_geometry_full(pa, st), "geometry kernel");
+    }
     int bad_h = INT_MAX;
     CU(cudaMemcpyAsync(&bad_h, bad, sizeof(int), cudaMemcpyDeviceToHost, st), "copy");
     CU(cudaStreamSynchronize(st), "geometry kernel");
@@ -1172,6 +1192,10 @@ int fedfem_precompute(fedfem_ctx* c, double T_lo, double T_hi, double* dt_cr_out
         CU(dalloc(c, &c->Q32, sizeof(float) * NF * NL), "alloc");
         CU(dalloc(c, &c->hA32, sizeof(float) * NC), "alloc");
         CU(launch_to_f32(c->M64, c->M32, 6 * E, st), "convert");
+        if (c->A28_64) {
+            CU(dalloc(c, &c->A28_32, sizeof(float) * 28 * std::max<int64_t>(1, E)), "alloc");
+            CU(launch_to_f32(c->A28_64, c->A28_32, 28 * E, st), "convert");
+        }
         CU(launch_to_f32(c->V64, c->V32, NF, st), "convert");
         CU(launch_pack_lanes(c->Q64, c->Q32, NL, NF, st), "convert");
         CU(launch_to_f32(c->hA64, c->hA32, NC, st), "convert");
@@ -1204,6 +1228,7 @@ int fedfem_precompute(fedfem_ctx* c, double T_lo, double T_hi, double* dt_cr_out
     release(c, node_group, sizeof(int32_t) * std::max<int64_t>(1, NF));
     if (c->precision != FEDFEM_FP64) {
         release(c, c->M64, sizeof(double) * 6 * E); c->M64 = nullptr;
+        if (c->A28_64) { release(c, c->A28_64, sizeof(double) * 28 * std::max<int64_t>(1, E)); c->A28_64 = nullptr; }
         release(c, c->V64, sizeof(double) * NF); c->V64 = nullptr;
         release(c, c->Q64, sizeof(double) * NF * NL); c->Q64 = nullptr;
         release(c, c->hA64, sizeof(double) * NC); c->hA64 = nullptr;
@@ -1480,7 +1505,8 @@ int fedfem_get_info(fedfem_ctx* c, fedfem_info* info) {
     const int64_t node_state = c->precision == FEDFEM_FP32_KAHAN ? 4 * R : 2 * R;   // T (+lo) read+write
     const int64_t E = c->E, NF = L.N_free, NC = L.N_free - L.N_plain;
     const int64_t NL = c->n_lanes;   // lanes share V, hA and the element data
-    info->algorithmic_bytes_per_step = E * (4 * c->nv + 6 * R) + NF * (NL * (node_state + R) + R) + NC * R;
+    const int64_t nm = (c->A28_64 || c->A28_32) ? 28 : 6;   // element matrix values
+    info->algorithmic_bytes_per_step = E * (4 * c->nv + nm * R) + NF * (NL * (node_state + R) + R) + NC * R;
     // a source schedule reads the source part of Q too; the dose is read and written in FP64
     const int64_t extra = (c->sched_f.empty() ? 0 : NF * NL * R) + (c->dose ? NF * 16 : 0) +
                           (c->n_reg > 0 ? NF * 4 * R + E : 0);   // regions: node coefficients, element ids

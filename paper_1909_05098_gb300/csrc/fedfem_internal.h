@@ -151,6 +151,10 @@ struct StepArgs {
     const int32_t* emat_off;
     const R* mat_k;
     const R* Cq;
+    // fully integrated hex8 (element-parallel kernels only): the 28 entries
+    // A_ab, a < b, of each element matrix as planes of E (pair order a-major);
+    // the diagonal is implied by the zero row sums.  Null: the factored M.
+    const R* A28;
 };
 
 // Launchers (step.cu).  mode: FEDFEM_FP64 / FEDFEM_FP32_KAHAN / FEDFEM_FP32_PLAIN.
@@ -227,6 +231,7 @@ struct PreArgs {
     const int4* conn4;
     const double* x; const double* y; const double* z;      // internal node order
     double* M64;                 // 6 planes of E
+    double* A28;                 // fully integrated hex8: 28 planes of E (pairs a < b of A_e), else null
     double* Vshare;              // E + 1 (last = 0): V_e / nv
     int* bad_elem;               // smallest internal element with det <= 0 (init INT_MAX)
     const int32_t* sell_off; const int32_t* sell_ids;
@@ -249,6 +254,8 @@ struct PreArgs {
 };
 
 cudaError_t launch_geometry(const PreArgs& a, cudaStream_t s);
+// fully integrated hex8: A28 and the exact V_e (2 x 2 x 2 Gauss points); run after launch_geometry
+cudaError_t launch_geometry_full(const PreArgs& a, cudaStream_t s);
 cudaError_t launch_nodal(const PreArgs& a, cudaStream_t s);
 // heterogeneous tissue: per-node capacity coefficients and perfusion (Cq, 4
 // planes of N_free) and the metabolic heat added to a.Q; coef: 5 per region

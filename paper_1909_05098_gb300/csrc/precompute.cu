@@ -99,6 +99,73 @@ __global__ void k_geometry(PreArgs a) {
     a.Vshare[e] = Ve / a.nv;
 }
 
+// Fully integrated hex8: A_e = sum over the 2 x 2 x 2 Gauss points
+// (natural coordinates +-1/sqrt 3, unit weights) of det J B^T B, B = J^-T
+// dN/dxi at the point; V_e = sum of det J (exact for the trilinear element).
+// Writes the 28 entries a < b (pair order a-major) and V_e / 8; an element
+// with det J <= 0 at any point is reported like an inverted one.
+__global__ void k_geometry_full(PreArgs a) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= a.E) return;
+    int c[8];
+    load_conn(a.conn4, a.E, e, 8, c);
+    double X[8][3];
+    for (int n = 0; n < 8; ++n) { X[n][0] = a.x[c[n]]; X[n][1] = a.y[c[n]]; X[n][2] = a.z[c[n]]; }
+    double A[28];
+    for (int q = 0; q < 28; ++q) A[q] = 0.0;
+    double V = 0.0;
+    bool bad = false;
+    const double gp = 0.57735026918962576451;   // 1 / sqrt 3
+    for (int g = 0; g < 8; ++g) {
+        const double p0 = (g == 1 || g == 2 || g == 5 || g == 6) ? gp : -gp;
+        const double p1 = (g == 2 || g == 3 || g == 6 || g == 7) ? gp : -gp;
+        const double p2 = (g >= 4) ? gp : -gp;
+        double dN[3][8];
+        for (int n = 0; n < 8; ++n) {
+            const double s0 = (n == 1 || n == 2 || n == 5 || n == 6) ? 1.0 : -1.0;
+            const double s1 = (n == 2 || n == 3 || n == 6 || n == 7) ? 1.0 : -1.0;
+            const double s2 = (n >= 4) ? 1.0 : -1.0;
+            const double f0 = 1.0 + s0 * p0, f1 = 1.0 + s1 * p1, f2 = 1.0 + s2 * p2;
+            dN[0][n] = 0.125 * s0 * f1 * f2;
+            dN[1][n] = 0.125 * s1 * f0 * f2;
+            dN[2][n] = 0.125 * s2 * f0 * f1;
+        }
+        double J[3][3];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                double t = 0.0;
+                for (int n = 0; n < 8; ++n) t += X[n][i] * dN[j][n];
+                J[i][j] = t;
+            }
+        const double c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+        const double c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+        const double c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+        const double det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+        if (!(det > 0.0)) { bad = true; break; }
+        double inv[3][3];   // inverse = adjugate / det
+        inv[0][0] = c00 / det; inv[1][0] = c01 / det; inv[2][0] = c02 / det;
+        inv[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / det;
+        inv[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / det;
+        inv[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / det;
+        inv[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / det;
+        inv[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det;
+        inv[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
+        double B[3][8];     // grad N_n = J^-T dN/dxi: B[i][n] = sum_j inv[j][i] dN[j][n]
+        for (int i = 0; i < 3; ++i)
+            for (int n = 0; n < 8; ++n) B[i][n] = inv[0][i] * dN[0][n] + inv[1][i] * dN[1][n] + inv[2][i] * dN[2][n];
+        int q = 0;
+        for (int m = 0; m < 8; ++m)
+            for (int n = m + 1; n < 8; ++n, ++q) A[q] += det * (B[0][m] * B[0][n] + B[1][m] * B[1][n] + B[2][m] * B[2][n]);
+        V += det;
+    }
+    if (bad) {
+        atomicMin(a.bad_elem, (int)e);
+        return;
+    }
+    for (int q = 0; q < 28; ++q) a.A28[q * a.E + e] = A[q];
+    a.Vshare[e] = V / 8.0;
+}
+
 __global__ void k_faces(PreArgs a) {
     const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= a.n_faces) return;
@@ -221,7 +288,18 @@ __global__ void k_lz_elem(LzArgs a) {
     for (int j = 0; j < 6; ++j) m[j] = a.p.M64[j * E + e];
     int c[8];
     load_conn(a.p.conn4, E, e, a.p.nv, c);
-    if (a.p.nv == 8) {
+    if (a.p.nv == 8 && a.p.A28) {   // fully integrated: F_m = k0 sum_n A_mn (u_n - u_m)
+        double t[8], F[8];
+        for (int n = 0; n < 8; ++n) { t[n] = a.u[c[n]]; F[n] = 0.0; }
+        int q = 0;
+        for (int m2 = 0; m2 < 8; ++m2)
+            for (int n = m2 + 1; n < 8; ++n, ++q) {
+                const double w = a.p.A28[q * E + e] * (t[n] - t[m2]);
+                F[m2] += w;
+                F[n] -= w;
+            }
+        for (int n = 0; n < 8; ++n) a.slots[e * 8 + n] = a.k0 * F[n];
+    } else if (a.p.nv == 8) {
         double t[8], F[8];
         for (int n = 0; n < 8; ++n) t[n] = a.u[c[n]];
         hex8_loads<double>(t, m, a.k0, F);
@@ -330,6 +408,11 @@ double tridiag_max(const std::vector<double>& a, const std::vector<double>& b) {
 cudaError_t launch_geometry(const PreArgs& a, cudaStream_t s) {
     k_geometry<<<blocks_for(a.E + 1), kThreads, 0, s>>>(a);
     if (a.n_faces > 0) k_faces<<<blocks_for(a.n_faces), kThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_geometry_full(const PreArgs& a, cudaStream_t s) {
+    if (a.E > 0) k_geometry_full<<<blocks_for(a.E), kThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 

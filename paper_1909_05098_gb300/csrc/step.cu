@@ -112,6 +112,26 @@ __device__ __forceinline__ void with_k_laws(const StepArgs<R, L>& a, const unsig
     }
 }
 
+// Fully integrated hex8: F_m = k_e sum_n A_mn (T_n - T_m) over the 28 pairs
+// (the zero row sums give the diagonal; a uniform field gives exactly 0)
+template <typename R>
+__device__ __forceinline__ void hex8_full_loads(const StepArgs<R>& a, int64_t e, const R t[8], R ke, R F[8]) {
+    const int64_t E = a.E;
+#pragma unroll
+    for (int n = 0; n < 8; ++n) F[n] = R(0);
+    int q = 0;
+#pragma unroll
+    for (int m = 0; m < 8; ++m)
+#pragma unroll
+        for (int n = m + 1; n < 8; ++n, ++q) {
+            const R w = a.A28[q * E + e] * (t[n] - t[m]);
+            F[m] = F[m] + w;
+            F[n] = F[n] - w;
+        }
+#pragma unroll
+    for (int n = 0; n < 8; ++n) F[n] = ke * F[n];
+}
+
 template <typename R, int NV, int MODE>
 __device__ __forceinline__ void element_phase(const StepArgs<R>& a, int64_t e) {
     const int64_t E = a.E;
@@ -131,8 +151,14 @@ __device__ __forceinline__ void element_phase(const StepArgs<R>& a, int64_t e) {
     R ke;
     with_k_laws<MODE>(a, a.emat, [&](const auto& kl) { ke = element_k<R, NV>(t, kl(e)); });
     R F[NV];
-    if (NV == 8) hex8_loads<R>(t, m, ke, F);
-    else tet4_loads<R>(t, m, ke, F);
+    bool full = false;
+    if constexpr ((MODE & 2) != 0 && NV == 8) full = a.A28 != nullptr;
+    if constexpr (NV == 8) {
+        if (full) hex8_full_loads<R>(a, e, t, ke, F);
+        else hex8_loads<R>(t, m, ke, F);
+    } else {
+        tet4_loads<R>(t, m, ke, F);
+    }
     R* out = a.slots + e * NV;
     Vec<R>::store4(out, F);
     if (NV == 8) Vec<R>::store4(out + 4, F + 4);
@@ -801,7 +827,7 @@ inline int blocks_for(int64_t n, int t) {
 template <typename R, int NV, bool KAHAN>
 cudaError_t launch_impl(const StepArgs<R>& a, int64_t n_steps, LaunchCfg& cfg, cudaStream_t s) {
     constexpr int M = KAHAN ? 1 : 0;
-    const bool ext = a.Qs || a.dose || a.n_tab > 0 || a.emat;
+    const bool ext = a.Qs || a.dose || a.n_tab > 0 || a.emat || a.A28;
     if (cfg.kernel == FEDFEM_KERNEL_TWO_PHASE) {
         const int b = cfg.block > 0 ? std::min(cfg.block, 256) : 256;
         auto node = ext ? k_node<R, M | 2> : k_node<R, M>;

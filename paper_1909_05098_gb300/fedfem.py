@@ -25,6 +25,7 @@ FP64, FP32_KAHAN, FP32_PLAIN = 0, 1, 2
 ORDER_INPUT, ORDER_MORTON, ORDER_RCM = 0, 1, 2
 KERNEL_TWO_PHASE, KERNEL_PERSISTENT, KERNEL_TILED, KERNEL_TILED_STAGED = 0, 1, 2, 3
 DOSE_CEM43, DOSE_ARRHENIUS = 0, 1
+HEX_ONE_POINT, HEX_FULL = 0, 1
 
 STATUS_NAMES = {0: "OK", -1: "E_ARG", -2: "E_MESH", -3: "E_STATE", -4: "E_UNSTABLE_DT", -5: "E_RANGE",
                 -6: "E_TIMEOUT", -7: "E_CUDA", -8: "E_OOM", -9: "E_UNSUPPORTED"}
@@ -115,6 +116,7 @@ _SIGS = {
                            C.c_int),
     "fedfem_enable_dose": ([_ctx_p, C.c_int], C.c_int),
     "fedfem_set_dose_model": ([_ctx_p, C.c_int, C.c_double, C.c_double], C.c_int),
+    "fedfem_set_hex_integration": ([_ctx_p, C.c_int], C.c_int),
     "fedfem_read_dose": ([_ctx_p, _dp], C.c_int),
     "fedfem_read_dose_lane": ([_ctx_p, C.c_int, _dp], C.c_int),
     "fedfem_add_gaussian_source_lane": ([_ctx_p, C.c_int, C.c_int, _dp, C.c_double, C.c_double], C.c_int),
@@ -483,6 +485,10 @@ def fedfem_enable_dose(ctx, on=True):
     _check(ctx, _lib.fedfem_enable_dose(ctx, 1 if on else 0))
 
 
+def fedfem_set_hex_integration(ctx, rule):
+    _check(ctx, _lib.fedfem_set_hex_integration(ctx, int(rule)))
+
+
 def fedfem_set_dose_model(ctx, model, A=0.0, Ea=0.0):
     _check(ctx, _lib.fedfem_set_dose_model(ctx, int(model), float(A), float(Ea)))
 
@@ -521,6 +527,8 @@ class Solver:
             p = problem
             fedfem_set_mesh(self.ctx, p.elem_type, p.xyz, p.conn)
             fedfem_set_order(self.ctx, order)
+            if getattr(p, "hex_rule", "one-point") == "full":
+                fedfem_set_hex_integration(self.ctx, HEX_FULL)
             apply_material(self.ctx, p.material)
             pf = p.perfusion
             fedfem_set_perfusion(self.ctx, pf.w_b, pf.c_b, pf.T_a, pf.Q_m)
