@@ -261,8 +261,10 @@ int fedfem_enable_dose(fedfem_ctx* ctx, int on);
  * FP64 (the exponential in the state's precision); fedfem_read_dose then
  * returns Omega (dimensionless; 1 is the usual coagulation threshold).
  * FEDFEM_DOSE_CEM43 ignores A and Ea.  E_ARG for another model or A, Ea not
- * finite and positive.  Takes effect at the next step; fedfem_init resets
- * the accumulated value, so set it before fedfem_init. */
+ * finite and positive.  Takes effect at the next fedfem_step; fedfem_init
+ * resets the accumulated value, so set it before fedfem_init.  A graph
+ * captured before the change keeps the model it was captured with: capture
+ * again after changing it. */
 int fedfem_set_dose_model(fedfem_ctx* ctx, int model, double A, double Ea);
 /* CEM43 in minutes (or Omega, see fedfem_set_dose_model), n_nodes doubles in
  * input node order (caller-owned host buffer).  Dirichlet nodes report their fixed temperature held for the
