@@ -8,7 +8,6 @@ two-point or collinear table, the discrete steady state of a Dirichlet bar
 of a uniform perfused block, and the critical-step scale against brute force."""
 import numpy as np
 import pytest
-from scipy.integrate import quad
 from scipy.optimize import brentq
 
 from oracle import Oracle, critical_dt, piecewise_linear
@@ -91,8 +90,9 @@ def test_tabulated_bar_has_equal_element_fluxes_at_steady_state():
 
 def test_tabulated_capacity_relaxation_follows_the_separated_ode():
     """Uniform and insulated, each node obeys rho(T) c(T) dT/dt = w_b c_b (T_a - T),
-    so t = 1/(w_b c_b) int_T0^T rho c / (T_a - s) ds; both laws have a kink
-    at 42 degC on the way from 37 to 45.  Explicit Euler is first order:
+    so t = 1/(w_b c_b) int_T0^T rho c / (T_a - s) ds, in closed form on each
+    piece where rho c is a quadratic; both laws have a kink at 42 degC on
+    the way from 37 to 45.  Explicit Euler is first order:
     Richardson's 2 T(dt/2) - T(dt) hits the closed form to O(dt^2)."""
     m = hex_box(2, 1, 1, H)
     pf = Perfusion(w_b=26.6, c_b=3617.0, T_a=45.0)
@@ -101,11 +101,21 @@ def test_tabulated_capacity_relaxation_follows_the_separated_ode():
     T1 = Oracle(p).run(dt, int(round(t_end / dt)))
     T2 = Oracle(p).run(dt / 2, int(round(t_end / dt * 2)))
 
-    def rc(s):
-        return np.interp(s, TAB["T"], TAB["rho"]) * np.interp(s, TAB["T"], TAB["c"])
+    from numpy.polynomial import Polynomial as P
 
-    def integral(a, b):   # smooth on each piece: split at the kink
-        return quad(lambda s: rc(s) / (pf.T_a - s), a, b, epsabs=0.0, epsrel=1e-11, limit=200)[0]
+    def piece(lo, hi):   # rho(s) c(s) on one table interval, as a polynomial in s
+        i = int(np.searchsorted(TAB["T"], lo, side="right") - 1)
+        T0, T1 = TAB["T"][i], TAB["T"][i + 1]
+        r = P([TAB["rho"][i], (TAB["rho"][i + 1] - TAB["rho"][i]) / (T1 - T0)])
+        c = P([TAB["c"][i], (TAB["c"][i + 1] - TAB["c"][i]) / (T1 - T0)])
+        return (r * c)(P([-T0, 1.0]))
+
+    def integral(a, b):
+        """int_a^b p(s) / (T_a - s) ds in closed form: p = q (T_a - s) + p(T_a)."""
+        p = piece(a, b)
+        q, rem = divmod(p, P([pf.T_a, -1.0]))
+        Q = q.integ()
+        return (Q(b) - Q(a)) - rem.coef[0] * (np.log(pf.T_a - b) - np.log(pf.T_a - a))
 
     def t_of(T):
         return (integral(37.0, min(T, 42.0)) + (integral(42.0, T) if T > 42.0 else 0.0)) / (pf.w_b * pf.c_b)
