@@ -15,6 +15,10 @@ time-stepping block, taken in its global matrix form):
 Material laws are linear in T (Section 3.1.6) or, optionally, piecewise
 linear through tabulated points, extended linearly beyond the table.
 
+Perfusion and metabolic heat may instead take the same share V / N at every
+node (the form of the paper's verification runs, Sections 3.1.3-3.1.4); C
+stays lumped by element shares.
+
 Heterogeneous tissue (finite elements let the properties vary from element to
 element, as the introduction notes): each element belongs to a region with its
 own laws and perfusion.  Step 1 averages the element's own k law over its
@@ -46,6 +50,12 @@ def lumped_volumes(conn: np.ndarray, V_e: np.ndarray, n_nodes: int) -> np.ndarra
     V = np.zeros(n_nodes)
     np.add.at(V, conn.ravel(), np.repeat(V_e / nv, nv))
     return V
+
+
+def uniform_share(V_total: float, n_nodes: int) -> float:
+    """The volume V / N that the paper's verification runs give every node
+    (Sections 3.1.3-3.1.4: the film h and the nodal heat flow q per node)."""
+    return V_total / n_nodes
 
 
 def lumped_face_areas(xyz: np.ndarray, faces: np.ndarray, n_nodes: int) -> np.ndarray:
@@ -89,7 +99,17 @@ class Oracle:
                                                           getattr(p, "hex_rule", "one-point"))
         self.V = lumped_volumes(self.conn, self.V_e, N)
         self.hA = p.conv_h * lumped_face_areas(p.xyz, np.asarray(p.conv_faces, dtype=np.int64), N)
-        if p.regions is None:
+        lumping = getattr(p, "lumping", "element")
+        if lumping == "uniform" and p.regions is not None:
+            raise ValueError("uniform lumping takes one material")
+        if p.regions is None and lumping == "uniform":
+            # the paper's verification runs (Sections 3.1.3-3.1.4): every node
+            # gets the same share V / N of the perfusion and the metabolic heat
+            self.regions = None
+            share = uniform_share(self.V_e.sum(), N)
+            self.beta = np.full(N, p.perfusion.w_b * p.perfusion.c_b * share)
+            metabolic = np.full(N, p.perfusion.Q_m * share)
+        elif p.regions is None:
             self.regions = None
             self.beta = p.perfusion.w_b * p.perfusion.c_b * self.V
             metabolic = self.V * p.perfusion.Q_m

@@ -115,6 +115,9 @@ class Problem:
     region_perfusion: tuple = ()
     # hex8 integration: "one-point" (Eq. 14, the paper's) or "full" (2 x 2 x 2 Gauss)
     hex_rule: str = "one-point"
+    # perfusion and metabolic heat per node: "element" (V_e / nv shares, as C)
+    # or "uniform" (V / N for every node, the paper's verification runs)
+    lumping: str = "element"
 
     @property
     def n_nodes(self) -> int:

@@ -256,3 +256,38 @@ def test_temperature_dependent_capacity_converges_to_the_ode_solution():
     exact = pf.T_a - u
     assert np.max(np.abs(2 * T2 - T1 - exact)) < 1e-6
     assert np.max(np.abs(T2 - exact)) > 1e-5   # the step is coarse enough to be informative
+
+
+def test_uniform_lumping_reproduces_the_papers_per_node_values():
+    """Sections 3.1.3-3.1.4 give every node the share V / N of the liver's
+    volume: with their w_b, c_b, Q_m, V and N that is the printed film
+    coefficient (per 1 m^2) and nodal heat flow."""
+    import json
+    import os
+    from oracle.global_form import uniform_share
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
+    pf, mt = g["perfusion_as_film_sec_3_1_3"], g["metabolic_as_nodal_flux_sec_3_1_4"]
+    assert pf["w_b"] * pf["c_b"] * uniform_share(pf["V"], pf["n_nodes"]) == pytest.approx(pf["h_printed"], rel=2e-3)
+    assert mt["Q_m"] * uniform_share(mt["V"], mt["n_nodes"]) == pytest.approx(mt["q_printed"], rel=5e-3)
+
+
+def test_uniform_lumping_on_a_uniform_grid_block():
+    """On a single hex every node's element share is V / 8 = V / N, so the two
+    lumpings coincide; on a larger block the uniform one moves perfusion from
+    interior to boundary nodes but keeps its total w_b c_b V, and a uniform
+    field at T_a with Q_m = 0 stays exactly unchanged."""
+    m1 = hex_box(1, 1, 1, H)
+    pf = Perfusion(w_b=26.6, c_b=3617.0, T_a=39.0, Q_m=33800.0)
+    base = _problem(m1, TISSUE_CONST, perfusion=pf, T0=37.0)
+    uni = copy.copy(base)
+    uni.lumping = "uniform"
+    np.testing.assert_allclose(Oracle(uni).run(0.05, 200), Oracle(base).run(0.05, 200), rtol=0, atol=1e-13)
+    m = hex_box(4, 3, 2, H)
+    p = _problem(m, TISSUE_CONST, perfusion=pf, T0=37.0)
+    p.lumping = "uniform"
+    orc = Oracle(p)
+    assert np.ptp(orc.beta) == 0.0 and orc.beta.sum() == pytest.approx(pf.w_b * pf.c_b * orc.V.sum(), rel=1e-13)
+    assert orc.Q.sum() == pytest.approx(pf.Q_m * orc.V.sum(), rel=1e-13)
+    q = copy.copy(p)
+    q.perfusion = Perfusion(w_b=26.6, c_b=3617.0, T_a=37.0, Q_m=0.0)
+    assert np.all(Oracle(q).run(0.05, 50) == 37.0)
