@@ -200,6 +200,20 @@ int fedfem_set_material_table(fedfem_ctx* ctx, int n, const double* T, const dou
 int fedfem_set_regions(fedfem_ctx* ctx, int n, const fedfem_material* mats, const fedfem_perfusion* perf,
                        const int32_t* region);
 
+#define FEDFEM_LUMP_ELEMENT 0
+#define FEDFEM_LUMP_UNIFORM 1
+/* How perfusion and metabolic heat reach the nodes: FEDFEM_LUMP_ELEMENT
+ * (default) lumps them like C, beta_i = w_b c_b V_i and Q_m V_i with V_i the
+ * sum of the element shares V_e / nv (Section 2.3.5); FEDFEM_LUMP_UNIFORM
+ * gives every node the same share V / N of the mesh volume V over its N nodes
+ * (the form of the paper's verification runs, Sections 3.1.3-3.1.4: a film
+ * w_b c_b V / N and a heat flow Q_m V / N per node).  C stays lumped by
+ * element shares.  The uniform form runs on the kernel builds that hold the
+ * source-schedule and dose paths; the critical step takes its exact per-node
+ * perfusion.  E_ARG for another mode; E_UNSUPPORTED at fedfem_precompute with
+ * regions or a property table.  Takes effect at the next fedfem_precompute. */
+int fedfem_set_lumping(fedfem_ctx* ctx, int mode);
+
 /* Perfusion and metabolism (Eq. 1); K_b and Q_b are lumped (Section 2.3.5). */
 int fedfem_set_perfusion(fedfem_ctx* ctx, const fedfem_perfusion* p);
 

@@ -49,6 +49,8 @@ struct fedfem_ctx {
     int hex_rule = FEDFEM_HEX_ONE_POINT;
     double dose_A = 0.0, dose_Ea = 0.0;           // Arrhenius frequency factor (1/s), activation energy (J/mol)
     int n_reg = 0;                                // heterogeneous tissue regions (0: mat everywhere)
+    int lumping = FEDFEM_LUMP_ELEMENT;            // perfusion / metabolic heat per node
+    int n_cq = 0;                                 // regions of the per-node coefficient path (pre-computed)
     std::vector<fedfem_material> reg_mat;
     std::vector<fedfem_perfusion> reg_perf;       // w_b, c_b, Q_m per region (T_a from perf)
     std::vector<int32_t> region;                  // per input element
@@ -324,7 +326,7 @@ StepArgs<R, L> make_args(fedfem_ctx* c, const R* M, const R* V, const R* Q, cons
     for (int j = 0; j < c->tab_n; ++j) a.tab_T[j] = (R)c->tab_T[j];
     a.tab = std::is_same<R, double>::value ? (const R*)c->tab64 : (const R*)c->tab32;
     a.A28 = std::is_same<R, double>::value ? (const R*)c->A28_64 : (const R*)c->A28_32;
-    if (c->n_reg > 0 && c->emat) {
+    if (c->n_cq > 0 && c->emat) {
         a.emat = c->emat;
         a.emat_tile = c->t_emat;
         a.emat_off = c->t_emat_off;
@@ -465,7 +467,7 @@ int plan_tiles(fedfem_ctx* c) {
     CU(cudaMemcpyAsync(c->t_blocks, blob.data(), blob.size(), cudaMemcpyHostToDevice, st), "tile copy");
     CU(cudaMemcpyAsync(c->t_block_off, off.data(), sizeof(int64_t) * off.size(), cudaMemcpyHostToDevice, st),
        "tile copy");
-    if (c->n_reg > 0 && !c->emat_host.empty()) {   // regions of the tile elements, tile t's from e_off[t]
+    if (c->n_cq > 0 && !c->emat_host.empty()) {   // regions of the tile elements, tile t's from e_off[t]
         std::vector<unsigned char> te(std::max<size_t>(1, t.e_glob.size()));
         for (size_t j = 0; j < t.e_glob.size(); ++j) te[j] = c->emat_host[t.e_glob[j]];
         CU(talloc(c, &c->t_emat, te.size()), "tile alloc");
@@ -890,6 +892,14 @@ int fedfem_enable_dose(fedfem_ctx* c, int on) {
     return FEDFEM_OK;
 }
 
+int fedfem_set_lumping(fedfem_ctx* c, int mode) {
+    if (!c) return FEDFEM_E_ARG;
+    if (mode != FEDFEM_LUMP_ELEMENT && mode != FEDFEM_LUMP_UNIFORM) return fail(c, FEDFEM_E_ARG, "unknown lumping");
+    c->lumping = mode;
+    invalidate(c);
+    return FEDFEM_OK;
+}
+
 int fedfem_set_hex_integration(fedfem_ctx* c, int rule) {
     if (!c) return FEDFEM_E_ARG;
     if (rule != FEDFEM_HEX_ONE_POINT && rule != FEDFEM_HEX_FULL) return fail(c, FEDFEM_E_ARG, "unknown hex rule");
@@ -962,6 +972,8 @@ int fedfem_precompute(fedfem_ctx* c, double T_lo, double T_hi, double* dt_cr_out
     if (!c) return FEDFEM_E_ARG;
     if (!c->has_mesh || !c->has_mat) return fail(c, FEDFEM_E_STATE, "set_mesh and set_material first");
     if (!(is_finite(T_lo) && is_finite(T_hi) && T_lo < T_hi)) return fail(c, FEDFEM_E_ARG, "need T_lo < T_hi");
+    if (c->lumping == FEDFEM_LUMP_UNIFORM && (c->n_reg > 0 || c->tab_n > 0))
+        return fail(c, FEDFEM_E_UNSUPPORTED, "uniform lumping takes one material with linear laws");
     double s = 1.0;
     int rc = property_scale(c, T_lo, T_hi, &s);
     if (rc) return rc;
@@ -1086,7 +1098,8 @@ int fedfem_precompute(fedfem_ctx* c, double T_lo, double T_hi, double* dt_cr_out
     pa.V = c->V64; pa.Q = c->Q64; pa.hA = c->hA64;
     pa.qr_node = qr; pa.flux_node = flux; pa.src = src; pa.n_src = (int)c->sources.size(); pa.n_lanes = NL;
     pa.node_group = node_group;
-    pa.Q_m = c->n_reg > 0 ? 0.0 : c->perf.Q_m;   // regions: added per element share below
+    const bool uniform = c->lumping == FEDFEM_LUMP_UNIFORM;
+    pa.Q_m = c->n_reg > 0 || uniform ? 0.0 : c->perf.Q_m;   // regions, uniform lumping: added below
     pa.n_faces = c->conv_nv ? (int64_t)fint.size() / c->conv_nv : 0;
     pa.face_nv = c->conv_nv; pa.faces = faces; pa.face_share = face_share;
     pa.conv_off = conv_off; pa.conv_face = conv_face; pa.h_film = c->conv_h;
@@ -1116,25 +1129,29 @@ int fedfem_precompute(fedfem_ctx* c, double T_lo, double T_hi, double* dt_cr_out
     }
     if (c->dose_on) CU(dalloc(c, &c->dose, sizeof(double) * std::max<int64_t>(1, NF * NL)), "alloc");
     double wbcb_ref = c->perf.w_b * c->perf.c_b;
-    if (c->n_reg > 0) {
-        // element regions in internal order; per region: rho c expanded about the
-        // first region's T_ref (u = T - T_ref), w_b c_b and Q_m; its k law
-        c->emat_host.resize(E);
-        for (int64_t e = 0; e < E; ++e) c->emat_host[e] = (unsigned char)c->region[L.elem_of[e]];
-        const double Tr = c->reg_mat[0].T_ref;
-        std::vector<double> coef(5 * c->n_reg), kl(3 * c->n_reg);
-        wbcb_ref = 0.0;
-        for (int r = 0; r < c->n_reg; ++r) {
-            const fedfem_material& m = c->reg_mat[r];
+    const double* beta_ref = nullptr;   // exact per-node perfusion for the Lanczos operator (uniform lumping)
+    c->n_cq = c->n_reg > 0 ? c->n_reg : (uniform ? 1 : 0);
+    if (c->n_cq > 0) {
+        // element regions in internal order (uniform lumping: one region, the
+        // material); per region: rho c expanded about the first region's T_ref
+        // (u = T - T_ref), w_b c_b and Q_m; its k law
+        c->emat_host.assign(E, 0);
+        if (c->n_reg > 0)
+            for (int64_t e = 0; e < E; ++e) c->emat_host[e] = (unsigned char)c->region[L.elem_of[e]];
+        const double Tr = c->n_reg > 0 ? c->reg_mat[0].T_ref : c->mat.T_ref;
+        std::vector<double> coef(5 * c->n_cq), kl(3 * c->n_cq);
+        if (c->n_reg > 0) wbcb_ref = 0.0;
+        for (int r = 0; r < c->n_cq; ++r) {
+            const fedfem_material& m = c->n_reg > 0 ? c->reg_mat[r] : c->mat;
             const double a = m.rho0 + m.drho * (Tr - m.T_ref), b = m.drho;
             const double al = m.c0 + m.dc * (Tr - m.T_ref), be = m.dc;
             coef[5 * r + 0] = a * al;
             coef[5 * r + 1] = a * be + b * al;
             coef[5 * r + 2] = b * be;
-            coef[5 * r + 3] = c->reg_perf[r].w_b * c->reg_perf[r].c_b;
-            coef[5 * r + 4] = c->reg_perf[r].Q_m;
+            coef[5 * r + 3] = c->n_reg > 0 ? c->reg_perf[r].w_b * c->reg_perf[r].c_b : 0.0;   // uniform: below
+            coef[5 * r + 4] = c->n_reg > 0 ? c->reg_perf[r].Q_m : 0.0;
             kl[3 * r + 0] = m.T_ref; kl[3 * r + 1] = m.k0; kl[3 * r + 2] = m.dk;
-            wbcb_ref = std::max(wbcb_ref, coef[5 * r + 3]);
+            if (c->n_reg > 0) wbcb_ref = std::max(wbcb_ref, coef[5 * r + 3]);
         }
         double* coef_d = nullptr;
         CU(dalloc(c, &c->emat, std::max<int64_t>(1, E)), "alloc");
@@ -1147,6 +1164,19 @@ int fedfem_precompute(fedfem_ctx* c, double T_lo, double T_hi, double* dt_cr_out
         CU(launch_regions(pa, c->emat, coef_d, c->Cq64, st), "region kernel");
         CU(cudaStreamSynchronize(st), "region kernel");   // coef and kl are host vectors of this frame
         release(c, coef_d, sizeof(double) * coef.size());
+        if (uniform) {   // every node: beta = w_b c_b V / N, metabolic Q_m V / N (V the mesh volume, N its nodes)
+            std::vector<double> vs(E), q(NF * NL), b(NF);
+            CU(cudaMemcpy(vs.data(), Vshare, sizeof(double) * E, cudaMemcpyDeviceToHost), "copy");
+            double V_total = 0.0;
+            for (int64_t e = 0; e < E; ++e) V_total += vs[e];
+            const double share = V_total * nv / (double)N;
+            std::fill(b.begin(), b.end(), c->perf.w_b * c->perf.c_b * share);
+            CU(cudaMemcpy(q.data(), c->Q64, sizeof(double) * NF * NL, cudaMemcpyDeviceToHost), "copy");
+            for (double& x : q) x += c->perf.Q_m * share;
+            CU(cudaMemcpy(c->Q64, q.data(), sizeof(double) * NF * NL, cudaMemcpyHostToDevice), "copy");
+            CU(cudaMemcpy(c->Cq64 + 3 * NF, b.data(), sizeof(double) * NF, cudaMemcpyHostToDevice), "copy");
+            beta_ref = c->Cq64 + 3 * NF;
+        }
     }
     if (c->tab_n > 0) {   // [T_j | rho_j | c_j | k_j | slopes of rho, c, k], kMaxTable each
         double h[7 * kMaxTable] = {};
@@ -1172,7 +1202,7 @@ int fedfem_precompute(fedfem_ctx* c, double T_lo, double T_hi, double* dt_cr_out
     LanczosResult lr;
     // regions: the reference operator takes the first region's k0 and rho0 c0
     // everywhere and the largest w_b c_b (property_scale bounds the rest)
-    std::string lm = lanczos_lambda_max(pa, c->mat.k0, c->mat.rho0 * c->mat.c0, wbcb_ref,
+    std::string lm = lanczos_lambda_max(pa, c->mat.k0, c->mat.rho0 * c->mat.c0, wbcb_ref, beta_ref,
                                         3000, 1e-14, lr, st);
     if (!lm.empty()) return fail(c, FEDFEM_E_CUDA, lm);
     c->lambda = lr.lambda;
@@ -1205,9 +1235,9 @@ int fedfem_precompute(fedfem_ctx* c, double T_lo, double T_hi, double* dt_cr_out
         }
         if (c->Cq64) {
             CU(dalloc(c, &c->Cq32, sizeof(float) * 4 * std::max<int64_t>(1, NF)), "alloc");
-            CU(dalloc(c, &c->matk32, sizeof(float) * 3 * c->n_reg), "alloc");
+            CU(dalloc(c, &c->matk32, sizeof(float) * 3 * c->n_cq), "alloc");
             CU(launch_to_f32(c->Cq64, c->Cq32, 4 * NF, st), "convert");
-            CU(launch_to_f32(c->matk64, c->matk32, 3 * c->n_reg, st), "convert");
+            CU(launch_to_f32(c->matk64, c->matk32, 3 * c->n_cq, st), "convert");
         }
         CU(dalloc(c, (float**)&c->T, sizeof(float) * N * NL), "alloc");
         CU(dalloc(c, (float**)&c->T2, sizeof(float) * N * NL), "alloc");
@@ -1235,7 +1265,7 @@ int fedfem_precompute(fedfem_ctx* c, double T_lo, double T_hi, double* dt_cr_out
         if (c->Qs64) { release(c, c->Qs64, sizeof(double) * NF * NL); c->Qs64 = nullptr; }
         if (c->Cq64) {
             release(c, c->Cq64, sizeof(double) * 4 * std::max<int64_t>(1, NF)); c->Cq64 = nullptr;
-            release(c, c->matk64, sizeof(double) * 3 * c->n_reg); c->matk64 = nullptr;
+            release(c, c->matk64, sizeof(double) * 3 * c->n_cq); c->matk64 = nullptr;
         }
     }
     c->pre = true;
@@ -1509,7 +1539,7 @@ int fedfem_get_info(fedfem_ctx* c, fedfem_info* info) {
     info->algorithmic_bytes_per_step = E * (4 * c->nv + nm * R) + NF * (NL * (node_state + R) + R) + NC * R;
     // a source schedule reads the source part of Q too; the dose is read and written in FP64
     const int64_t extra = (c->sched_f.empty() ? 0 : NF * NL * R) + (c->dose ? NF * 16 : 0) +
-                          (c->n_reg > 0 ? NF * 4 * R + E : 0);   // regions: node coefficients, element ids
+                          (c->n_cq > 0 ? NF * 4 * R + E : 0);   // regions: node coefficients, element ids
     info->algorithmic_bytes_per_step += extra;
     // two-phase / persistent model: + slot write and read, gather ids, their slice offsets, T gathered once
     info->bytes_per_step = info->algorithmic_bytes_per_step + E * c->nv * 2 * R + (int64_t)L.sell_ids.size() * 4 +

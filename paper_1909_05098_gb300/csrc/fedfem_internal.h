@@ -264,9 +264,10 @@ cudaError_t launch_regions(const PreArgs& a, const unsigned char* emat, const do
 cudaError_t launch_to_f32(const double* src, float* dst, int64_t n, cudaStream_t s);
 
 // Largest eigenvalue of C0^-1/2 (K0 + diag(beta + hA)) C0^-1/2 on the free
-// nodes by Lanczos (FP64).  Returns an error message or "".
+// nodes by Lanczos (FP64); beta = wbcb V, or the given per-node beta (free
+// nodes) when not null.  Returns an error message or "".
 struct LanczosResult { double lambda = 0; int iterations = 0; };
-std::string lanczos_lambda_max(const PreArgs& a, double k0, double rho0c0, double wbcb,
+std::string lanczos_lambda_max(const PreArgs& a, double k0, double rho0c0, double wbcb, const double* beta,
                                int max_iter, double rel_tol, LanczosResult& out, cudaStream_t s);
 
 // Init / output helpers (precompute.cu)

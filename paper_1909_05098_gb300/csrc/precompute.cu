@@ -268,11 +268,11 @@ struct LzArgs {
 };
 
 __global__ void k_lz_prep(double* sinv, double* diag, const double* V, const double* hA, int64_t N_free,
-                          int64_t N_plain, double rho0c0, double wbcb) {
+                          int64_t N_plain, double rho0c0, double wbcb, const double* beta) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N_free) return;
     sinv[i] = 1.0 / sqrt(V[i] * rho0c0);
-    diag[i] = wbcb * V[i] + (i >= N_plain ? hA[i - N_plain] : 0.0);
+    diag[i] = (beta ? beta[i] : wbcb * V[i]) + (i >= N_plain ? hA[i - N_plain] : 0.0);
 }
 
 __global__ void k_lz_scatter(LzArgs a) {
@@ -437,7 +437,7 @@ cudaError_t launch_pack_lanes(const double* src, float* dst, int n_lanes, int64_
     return cudaGetLastError();
 }
 
-std::string lanczos_lambda_max(const PreArgs& p, double k0, double rho0c0, double wbcb, int max_iter,
+std::string lanczos_lambda_max(const PreArgs& p, double k0, double rho0c0, double wbcb, const double* beta, int max_iter,
                                double rel_tol, LanczosResult& out, cudaStream_t s) {
     const int64_t n = p.N_free;
     out = LanczosResult();
@@ -461,7 +461,7 @@ std::string lanczos_lambda_max(const PreArgs& p, double k0, double rho0c0, doubl
     LZ_CHECK(cudaMemsetAsync(u, 0, sizeof(double) * p.N, s));
     LZ_CHECK(cudaMemsetAsync(slots, 0, sizeof(double) * (p.E * p.nv + 1), s));
     LZ_CHECK(cudaMemsetAsync(vp, 0, sizeof(double) * n, s));
-    k_lz_prep<<<blocks_for(n), kThreads, 0, s>>>(sinv, diag, p.V, p.hA, n, p.N_plain, rho0c0, wbcb);
+    k_lz_prep<<<blocks_for(n), kThreads, 0, s>>>(sinv, diag, p.V, p.hA, n, p.N_plain, rho0c0, wbcb, beta);
     k_lz_start<<<blocks_for(n), kThreads, 0, s>>>(v, n);
     LZ_CHECK(cudaGetLastError());
     const int rb = (int)std::min<int64_t>(kRedBlocks, (n + kThreads - 1) / kThreads);

@@ -26,6 +26,7 @@ ORDER_INPUT, ORDER_MORTON, ORDER_RCM = 0, 1, 2
 KERNEL_TWO_PHASE, KERNEL_PERSISTENT, KERNEL_TILED, KERNEL_TILED_STAGED = 0, 1, 2, 3
 DOSE_CEM43, DOSE_ARRHENIUS = 0, 1
 HEX_ONE_POINT, HEX_FULL = 0, 1
+LUMP_ELEMENT, LUMP_UNIFORM = 0, 1
 
 STATUS_NAMES = {0: "OK", -1: "E_ARG", -2: "E_MESH", -3: "E_STATE", -4: "E_UNSTABLE_DT", -5: "E_RANGE",
                 -6: "E_TIMEOUT", -7: "E_CUDA", -8: "E_OOM", -9: "E_UNSUPPORTED"}
@@ -117,6 +118,7 @@ _SIGS = {
     "fedfem_enable_dose": ([_ctx_p, C.c_int], C.c_int),
     "fedfem_set_dose_model": ([_ctx_p, C.c_int, C.c_double, C.c_double], C.c_int),
     "fedfem_set_hex_integration": ([_ctx_p, C.c_int], C.c_int),
+    "fedfem_set_lumping": ([_ctx_p, C.c_int], C.c_int),
     "fedfem_read_dose": ([_ctx_p, _dp], C.c_int),
     "fedfem_read_dose_lane": ([_ctx_p, C.c_int, _dp], C.c_int),
     "fedfem_add_gaussian_source_lane": ([_ctx_p, C.c_int, C.c_int, _dp, C.c_double, C.c_double], C.c_int),
@@ -489,6 +491,10 @@ def fedfem_set_hex_integration(ctx, rule):
     _check(ctx, _lib.fedfem_set_hex_integration(ctx, int(rule)))
 
 
+def fedfem_set_lumping(ctx, mode):
+    _check(ctx, _lib.fedfem_set_lumping(ctx, int(mode)))
+
+
 def fedfem_set_dose_model(ctx, model, A=0.0, Ea=0.0):
     _check(ctx, _lib.fedfem_set_dose_model(ctx, int(model), float(A), float(Ea)))
 
@@ -529,6 +535,8 @@ class Solver:
             fedfem_set_order(self.ctx, order)
             if getattr(p, "hex_rule", "one-point") == "full":
                 fedfem_set_hex_integration(self.ctx, HEX_FULL)
+            if getattr(p, "lumping", "element") == "uniform":
+                fedfem_set_lumping(self.ctx, LUMP_UNIFORM)
             apply_material(self.ctx, p.material)
             pf = p.perfusion
             fedfem_set_perfusion(self.ctx, pf.w_b, pf.c_b, pf.T_a, pf.Q_m)
@@ -613,6 +621,8 @@ class Batch:
             p = scen[0]
             if p.material != first.material or p.perfusion != first.perfusion:
                 raise ValueError("all runs of a batch must share material and perfusion")
+            if getattr(p, "lumping", "element") != "element" or getattr(p, "hex_rule", "one-point") != "one-point":
+                raise ValueError("a batch takes element lumping and the one-point hex rule")
             if (getattr(p, "regions", None) is None) != (getattr(first, "regions", None) is None) or (
                     p.regions is not None and (p.region_materials != first.region_materials
                                                or p.region_perfusion != first.region_perfusion)):
