@@ -210,8 +210,10 @@ int fedfem_set_regions(fedfem_ctx* ctx, int n, const fedfem_material* mats, cons
  * w_b c_b V / N and a heat flow Q_m V / N per node).  C stays lumped by
  * element shares.  The uniform form runs on the kernel builds that hold the
  * source-schedule and dose paths; the critical step takes its exact per-node
- * perfusion.  E_ARG for another mode; E_UNSUPPORTED at fedfem_precompute with
- * regions or a property table.  Takes effect at the next fedfem_precompute. */
+ * perfusion.  With element groups (several meshes in one context) V and N
+ * are those of the whole context, not of each group.  E_ARG for another
+ * mode; E_UNSUPPORTED at fedfem_precompute with regions or a property table.
+ * Takes effect at the next fedfem_precompute. */
 int fedfem_set_lumping(fedfem_ctx* ctx, int mode);
 
 /* Perfusion and metabolism (Eq. 1); K_b and Q_b are lumped (Section 2.3.5). */
