@@ -33,9 +33,31 @@ def candidates(elem_type: int, precision: int):
     return out
 
 
-def signature(info: dict, device_name: str) -> str:
+def variant(solver) -> str:
+    """The options of a solver's problem that change which kernel builds run
+    (and so which configuration is fastest, or allowed at all)."""
+    p = getattr(solver, "problem", None)
+    parts = []
+    if p is not None:
+        if getattr(getattr(p, "material", None), "table", None) is not None:
+            parts.append("table")
+        if getattr(p, "regions", None) is not None:
+            parts.append(f"regions{len(p.region_materials)}")
+        if getattr(p, "hex_rule", "one-point") != "one-point":
+            parts.append("hexfull")
+        if getattr(p, "lumping", "element") != "element":
+            parts.append("uniform")
+        if len(getattr(p, "schedule_factor", ())):
+            parts.append("schedule")
+    if getattr(solver, "dose_model", False):
+        parts.append("dose")
+    return "+".join(parts)
+
+
+def signature(info: dict, device_name: str, variant_tag: str = "") -> str:
     return (f"{device_name}|nv{info['elem_type']}|p{info['precision']}|N{info['n_nodes']}|E{info['n_elems']}|"
-            f"F{info['n_free']}|C{info['n_convective']}|o{info['order']}")
+            f"F{info['n_free']}|C{info['n_convective']}|o{info['order']}|b{info['algorithmic_bytes_per_step']}|"
+            f"v{variant_tag}")
 
 
 def _load_cache():
@@ -59,7 +81,7 @@ def tune(solver, dt: float, steps: int = 30, use_cache: bool = True, stream=None
     import torch
     ctx = solver.ctx
     info = ff.fedfem_get_info(ctx)
-    sig = signature(info, torch.cuda.get_device_name())
+    sig = signature(info, torch.cuda.get_device_name(), variant(solver))
     cache = _load_cache() if use_cache else {}
     if sig in cache:
         best = cache[sig]

@@ -529,6 +529,7 @@ class Solver:
                  kernel=KERNEL_PERSISTENT, T_lo=None, T_hi=None, dose=False):
         self.ctx = fedfem_create(device, precision, stream)
         self.problem = problem
+        self.dose_model = dose
         try:
             p = problem
             fedfem_set_mesh(self.ctx, p.elem_type, p.xyz, p.conn)
