@@ -83,3 +83,24 @@ def test_explicit_scheme_is_stable_below_and_unstable_above():
     Ta = orc.run(1.02 * dt, 400)
     assert np.abs(Tb - Tb.mean()).max() < dev0
     assert np.abs(Ta - Ta.mean()).max() > 10 * dev0
+
+
+def test_full_hex_critical_step_is_the_tensor_product_symbol():
+    """With exact integration the trilinear stiffness on a uniform grid is
+    K1 x M1 x M1 + M1 x K1 x M1 + M1 x M1 x K1 (1-D stiffness K1 and consistent
+    mass M1), whose Dirichlet modes sin(j pi i / n) have eigenvalues
+    (4/h) sin^2(theta/2) and (h/3)(2 + cos theta); with the lumped C = rho c h^3
+    and beta = w_b c_b h^3 the largest mode gives dt_cr = 2 / lambda_max."""
+    import copy
+    p = copy.copy(cube_hex_fp64().problem)
+    p.hex_rule = "full"
+    m, pf = p.material, p.perfusion
+    assert m.dk == 0.0 and m.dc == 0.0 and m.drho == 0.0
+    n, h = 10, 1e-3
+    th = np.arange(1, n) * np.pi / n
+    S = (4.0 / h) * np.sin(th / 2) ** 2
+    Mv = (h / 3.0) * (2.0 + np.cos(th))
+    lam_K = (S[:, None, None] * Mv[None, :, None] * Mv[None, None, :] + Mv[:, None, None] * S[None, :, None] *
+             Mv[None, None, :] + Mv[:, None, None] * Mv[None, :, None] * S[None, None, :])
+    lam = (m.k0 * lam_K + pf.w_b * pf.c_b * h ** 3) / (m.rho0 * m.c0 * h ** 3)
+    assert critical_dt(Oracle(p)) == pytest.approx(2.0 / lam.max(), rel=1e-12)
