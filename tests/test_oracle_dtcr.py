@@ -104,3 +104,24 @@ def test_full_hex_critical_step_is_the_tensor_product_symbol():
              Mv[None, None, :] + Mv[:, None, None] * Mv[None, :, None] * S[None, None, :])
     lam = (m.k0 * lam_K + pf.w_b * pf.c_b * h ** 3) / (m.rho0 * m.c0 * h ** 3)
     assert critical_dt(Oracle(p)) == pytest.approx(2.0 / lam.max(), rel=1e-12)
+
+
+def test_uniform_lumping_shifts_the_cube_spectrum_by_a_constant():
+    """Uniform lumping gives every free node of the 10^3 cube the perfusion
+    w_b c_b V/N with V = (10 h)^3 and N = 11^3, while C stays rho c h^3 on
+    every free (interior) node: the one-point symbol of the test above is
+    shifted by w_b c_b (V/N) / (rho c h^3) instead of w_b c_b / (rho c)."""
+    import copy
+    p = copy.copy(cube_hex_fp64().problem)
+    p.lumping = "uniform"
+    h = 1e-3
+    m, pf = p.material, p.perfusion
+    alpha = m.k0 / (m.rho0 * m.c0)
+    th = np.arange(1, 10) * np.pi / 10
+    s2, c2 = np.sin(th / 2) ** 2, np.cos(th / 2) ** 2
+    S = (s2[:, None, None] * c2[None, :, None] * c2[None, None, :]
+         + c2[:, None, None] * s2[None, :, None] * c2[None, None, :]
+         + c2[:, None, None] * c2[None, :, None] * s2[None, None, :])
+    share = (10 * h) ** 3 / 11 ** 3
+    lam = 4 * alpha / h ** 2 * S.max() + pf.w_b * pf.c_b * share / (m.rho0 * m.c0 * h ** 3)
+    assert critical_dt(p) == pytest.approx(2.0 / lam, rel=1e-10)
