@@ -106,7 +106,9 @@ class Oracle:
             # the paper's verification runs (Sections 3.1.3-3.1.4): every node
             # gets the same share V / N of the perfusion and the metabolic heat
             self.regions = None
-            share = uniform_share(self.V_e.sum(), N)
+            share = getattr(p, "uniform_volume_per_node", None)   # given for a sub-mesh of a larger mesh
+            if share is None:
+                share = uniform_share(self.V_e.sum(), N)
             self.beta = np.full(N, p.perfusion.w_b * p.perfusion.c_b * share)
             metabolic = np.full(N, p.perfusion.Q_m * share)
         elif p.regions is None:

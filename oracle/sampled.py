@@ -60,6 +60,11 @@ def sampled_run(problem, dt: float, n_steps: int, samples: np.ndarray) -> np.nda
     if len(cf):
         keep = np.all(local[cf] >= 0, axis=1)
         sub.conv_faces = local[cf[keep]].astype(np.int32)
+    if getattr(problem, "regions", None) is not None:
+        sub.regions = np.asarray(problem.regions)[elems]
+    if getattr(problem, "lumping", "element") == "uniform":
+        # the share V / N belongs to the whole mesh, not to the sub-mesh
+        sub.uniform_volume_per_node = Oracle(problem).V_e.sum() / N
     orc = Oracle(sub)
     T = orc.run(dt, n_steps)
     return T[local[np.asarray(samples, dtype=np.int64)]]

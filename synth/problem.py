@@ -118,6 +118,7 @@ class Problem:
     # perfusion and metabolic heat per node: "element" (V_e / nv shares, as C)
     # or "uniform" (V / N for every node, the paper's verification runs)
     lumping: str = "element"
+    uniform_volume_per_node: Optional[float] = None   # V / N of the whole mesh (for sub-meshes); None: this mesh's
 
     @property
     def n_nodes(self) -> int:
