@@ -169,7 +169,8 @@ int fedfem_set_material(fedfem_ctx* ctx, const fedfem_material* m);
  * the reference state of the critical step (k0 = k[0], rho0 c0 = rho[0]
  * c[0]), which fedfem_precompute bounds over [T_lo, T_hi] as for linear
  * laws; E_RANGE there if rho c or k is not positive on that range.
- * Replaces the material (a later fedfem_set_material replaces the table).
+ * Replaces the material and any regions (a later fedfem_set_material or
+ * fedfem_set_regions replaces the table).
  * Host arrays, copied; E_ARG for non-finite values, T not increasing, or
  * rho[0], c[0], k[0] not positive.  Steps of a context with a table run the
  * kernel builds that hold the source-schedule and dose paths.
