@@ -128,3 +128,57 @@ def test_translation_and_rotation_of_the_mesh_change_nothing_that_they_should_no
     rot = m.xyz[:, [1, 0, 2]] * np.array([-1.0, 1.0, 1.0])
     yr, _ = mpnn.forward(flat, x, feats(rot), src, dst, H, L)
     assert np.max(np.abs(yr - y)) > 1e-6
+
+
+def _hand_params(L):
+    """Weights for the worked example (H = 2): with a = ln 3 every
+    pre-activation below is 0 or +-a, and SiLU(a) = a sigma(a) = 3a/4,
+    SiLU(-a) = -a/4, SiLU(0) = 0."""
+    a = np.log(3.0)
+    q = 4.0 / 3.0
+    p = {
+        "W_ne": np.array([[a, 0, 0, 0, 0], [0, -a, 0, 0, 0]]), "b_ne": np.zeros(2),
+        "W_ee": np.array([[0, 0, 0, 0], [a, 0, 0, 0]]), "b_ee": np.zeros(2),
+        # layer 0: message from the edge's second feature and the SOURCE node's first feature
+        "W_e0": np.array([[0, q, 0, 0, 0, 0], [0, 0, q, 0, 0, 0]]), "b_e0": np.zeros(2),
+        # node update: [h_i ; a_i] -> (q h_i0 + q a_i0, -q a_i1)
+        "W_n0": np.array([[q, 0, q, 0], [0, 0, 0, -q]]), "b_n0": np.zeros(2),
+        "w_d": np.array([1.0, 2.0]), "b_d": np.array([0.5]),
+    }
+    if L == 2:
+        # layer 1 reads only the updated edge state e_1 (= 2 SiLU(a) after layer 0)
+        p["W_e1"] = np.array([[0, 2.0 / 3.0, 0, 0, 0, 0], [0, 0, 0, 0, 0, 0]])
+        p["b_e1"] = np.zeros(2)
+        p["W_n1"] = np.array([[0, 0, q, 0], [0, 0, 0, 0]])
+        p["b_n1"] = np.zeros(2)
+    return mpnn.flatten({k: np.asarray(v, dtype=np.float64) for k, v in p.items()}, 2, L)
+
+
+def test_forward_values_of_a_worked_example():
+    """Two nodes, one edge 0 -> 1, H = 2; x_0 = e_1, x_1 = e_2, edge input
+    f = e_1; a = ln 3, s = SiLU(a) = 3a/4, t = -SiLU(-a) = a/4.
+
+      encoders:  h_0 = SiLU(a, 0) = (s, 0),  h_1 = SiLU(0, -a) = (0, -t),
+                 e = SiLU(0, a) = (0, s)
+      layer 0:   msg = SiLU(4/3 e_1, 4/3 h_src,0) = SiLU(a, a) = (s, s)
+                 e <- e + msg = (s, 2s);  aggregate into node 1: a_1 = (s, s), a_0 = 0
+                 z_0 = (4/3 s, 0) = (a, 0)       -> h_0 = (s, 0) + (s, 0) = (2s, 0)
+                 z_1 = (4/3 s, -4/3 s) = (a, -a) -> h_1 = (0, -t) + (s, -t) = (s, -2t)
+      decoder:   y_0 = 2s + 0.5 = 1.5a + 0.5,  y_1 = s - 4t + 0.5 = 0.5 - a/4
+
+    With a second layer that reads only e_1 (2/3 e_1 = 4/3 s = a, so
+    msg = (s, 0)) and adds 4/3 a_i0 to the first hidden unit: node 1 gets
+    z = (a, 0) -> h_1 = (2s, -2t), node 0 is unchanged, so
+    y = (1.5a + 0.5, 0.5a + 0.5).  A dropped residual, a message aggregated
+    at the source, swapped source and destination, a missing edge update or
+    a missing activation each changes one of these numbers."""
+    a = np.log(3.0)
+    x = np.zeros((1, 2, 5))
+    x[0, 0, 0] = 1.0
+    x[0, 1, 1] = 1.0
+    f = np.array([[1.0, 0.0, 0.0, 0.0]])
+    src, dst = np.array([0]), np.array([1])
+    y1, _ = mpnn.forward(_hand_params(1), x, f, src, dst, H=2, L=1)
+    np.testing.assert_allclose(y1[0], [1.5 * a + 0.5, 0.5 - 0.25 * a], rtol=1e-15, atol=1e-15)
+    y2, _ = mpnn.forward(_hand_params(2), x, f, src, dst, H=2, L=2)
+    np.testing.assert_allclose(y2[0], [1.5 * a + 0.5, 0.5 * a + 0.5], rtol=1e-15, atol=1e-15)
