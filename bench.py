@@ -46,7 +46,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--steps-per-launch", type=int, default=STEPS_PER_LAUNCH)
     ap.add_argument("--n", type=int, default=WORKLOAD_N, help="cube edge in elements")
-    ap.add_argument("--kernel", default="auto", choices=["auto", "two_phase", "persistent", "tiled", "tiled_staged"])
+    ap.add_argument("--kernel", default="auto",
+                    choices=["auto", "two_phase", "persistent", "tiled", "tiled_staged", "tiled_rep"])
     ap.add_argument("--tile-nodes", type=int, default=0)
     ap.add_argument("--block", type=int, default=0, help="threads per block (0 = the kernel's default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -239,60 +240,128 @@ def ncu_traffic(kernel, n, tile_nodes, block, steps_per_launch):
 # CPU baseline: the oracle, bounded sample
 # ---------------------------------------------------------------------------
 
-def cpu_baseline(budget_s=12.0, n_sample=64):
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def _oracle_loop(n_sample, budget_s, max_steps=200):
+    """The oracle stepping the sample cube for about budget_s seconds:
+    (nodes, steps, seconds)."""
     from oracle import Oracle
     from synth.scenarios import cube_hex_td_convective
     w = cube_hex_td_convective(n=n_sample)
     orc = Oracle(w.problem)
     T = orc.initial_field()
-    dt = 1.0
     steps = 0
     t0 = time.perf_counter()
     while True:
-        T = orc.step(T, dt)
+        T = orc.step(T, 1.0)
         steps += 1
         el = time.perf_counter() - t0
-        if el >= budget_s or steps >= 200:
+        if el >= budget_s or steps >= max_steps:
             break
-    return {"value": w.problem.n_nodes * steps / el, "unit": "node-steps/s", "cores": 1, "kind": "oracle",
-            "sample": f"FP64 oracle (global K(T) assembled each step, Eq. 7-8), {steps} steps of the same recipe "
-                      f"on a {n_sample}^3-element cube ({w.problem.n_nodes} nodes), single host thread, "
-                      f"{el:.1f} s"}
+    return w.problem.n_nodes, steps, el
+
+
+def _oracle_worker(job):
+    return _oracle_loop(*job)
+
+
+def cpu_baseline(budget_s=12.0, n_sample=64):
+    """The oracle as it stands on the host cores: one process on one thread,
+    then one process per core, each stepping its own copy of the sample (the
+    oracle has no parallel step of its own; independent copies use every
+    core).  value = the all-cores throughput."""
+    n, steps, el = _oracle_loop(n_sample, budget_s)
+    single = n * steps / el
+    cores = os.cpu_count() or 1
+    multi, multi_note = None, ""
+    if cores > 1:
+        import multiprocessing as mp
+        for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ[k] = "1"
+        with mp.get_context("spawn").Pool(cores) as pool:
+            res = pool.map(_oracle_worker, [(n_sample, budget_s)] * cores)
+        multi = sum(r[0] * r[1] for r in res) / max(r[2] for r in res)
+        multi_note = (f"; all cores: {cores} processes, each the same oracle loop on its own copy of the "
+                      f"sample, {min(r[1] for r in res)}-{max(r[1] for r in res)} steps each in "
+                      f"{max(r[2] for r in res):.1f} s")
+    return {"value": multi if multi else single, "unit": "node-steps/s", "cores": cores if multi else 1,
+            "kind": "oracle", "cpu_model": cpu_model(),
+            "single_thread": {"value": single, "cores": 1},
+            "sample": f"FP64 oracle (global K(T) assembled each step, Eq. 7-8) on a {n_sample}^3-element cube "
+                      f"of the same recipe ({n} nodes); one thread: {steps} steps in {el:.1f} s{multi_note}"}
 
 
 # ---------------------------------------------------------------------------
 # reference arm
 # ---------------------------------------------------------------------------
 
-def run_reference(args):
-    rank, world, _ = int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), 0
-    if rank != 0:
-        return
+_REF = {}
+
+
+def _ref_init(n_sample):
     from oracle import Oracle
     from synth.scenarios import cube_hex_td_convective
-    n_sample = 48
     w = cube_hex_td_convective(n=n_sample)
-    orc = Oracle(w.problem)
-    T = orc.initial_field()
+    _REF["orc"] = Oracle(w.problem)
+    _REF["T"] = _REF["orc"].initial_field()
+
+
+def _ref_steps(per):
+    for _ in range(per):
+        _REF["T"] = _REF["orc"].step(_REF["T"], 1.0)
+    return per
+
+
+def run_reference(args):
+    """The oracle as it stands on every host core: one process per core, each
+    stepping its own copy of a bounded sample of the cube recipe; one bench
+    step = `per` oracle steps in every process."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import multiprocessing as mp
+    from synth.scenarios import cube_hex_td_convective
+    n_sample = 48
+    n_nodes = cube_hex_td_convective(n=n_sample).problem.n_nodes
+    cores = os.cpu_count() or 1
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
     per = 2   # oracle time steps per bench step (bounded sample)
-    for _ in range(args.warmup):
-        for _ in range(per):
-            T = orc.step(T, 1.0)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        for _ in range(per):
-            T = orc.step(T, 1.0)
-    el = time.perf_counter() - t0
-    value = w.problem.n_nodes * per * args.steps / el
-    sample = (f"FP64 oracle on a {n_sample}^3-element cube of the same recipe ({w.problem.n_nodes} nodes), "
-              f"{per} time steps per bench step, single host thread")
+    with mp.get_context("spawn").Pool(cores, initializer=_ref_init, initargs=(n_sample,)) as pool:
+        for _ in range(args.warmup):
+            pool.map(_ref_steps, [per] * cores, chunksize=1)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            pool.map(_ref_steps, [per] * cores, chunksize=1)
+        el = time.perf_counter() - t0
+    value = cores * n_nodes * per * args.steps / el
+    sample = (f"FP64 oracle on a {n_sample}^3-element cube of the same recipe ({n_nodes} nodes), "
+              f"{per} time steps per bench step in each of {cores} processes (one per host core, "
+              f"each on its own copy of the sample)")
     print(json.dumps({
         "impl": "reference", "metric": "node-steps/s", "value": value, "unit": "node-steps/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_name(args.n), "sample_nodes": w.problem.n_nodes},
-        "cpu_baseline": {"value": value, "unit": "node-steps/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "config": {"workload": workload_name(args.n), "sample_nodes": n_nodes},
+        "cpu_baseline": {"value": value, "unit": "node-steps/s", "cores": cores, "kind": "oracle",
+                         "cpu_model": cpu_model(), "sample": sample},
         "e2e": {"value": value, "unit": "node-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
@@ -315,7 +384,7 @@ def run_ours(args):
     from synth.scenarios import cube_hex_td_convective
 
     names = {ff.KERNEL_TWO_PHASE: "two_phase", ff.KERNEL_PERSISTENT: "persistent", ff.KERNEL_TILED: "tiled",
-             ff.KERNEL_TILED_STAGED: "tiled_staged"}
+             ff.KERNEL_TILED_STAGED: "tiled_staged", ff.KERNEL_TILED_REP: "tiled_rep"}
     S = args.steps_per_launch
     w = cube_hex_td_convective(n=args.n)
     p = w.problem
@@ -711,7 +780,7 @@ def run_suite(args):
     torch.cuda.set_device(0)
     log = lambda m: print(m, file=sys.stderr, flush=True)
     names = {ff.KERNEL_TWO_PHASE: "two_phase", ff.KERNEL_PERSISTENT: "persistent", ff.KERNEL_TILED: "tiled",
-             ff.KERNEL_TILED_STAGED: "tiled_staged"}
+             ff.KERNEL_TILED_STAGED: "tiled_staged", ff.KERNEL_TILED_REP: "tiled_rep"}
     peak = measured_peak()[0]
     stream = torch.cuda.Stream()
     rows = []

@@ -80,7 +80,10 @@ enum {
     FEDFEM_KERNEL_TWO_PHASE = 0,   /* one element launch and one node launch per step */
     FEDFEM_KERNEL_PERSISTENT = 1,  /* one cooperative launch for n steps, bounded grid barriers */
     FEDFEM_KERNEL_TILED = 2,       /* persistent, node tiles: T and element loads in shared memory, no global slots */
-    FEDFEM_KERNEL_TILED_STAGED = 3 /* as TILED, each tile's constant data streamed into shared memory by bulk copies */
+    FEDFEM_KERNEL_TILED_STAGED = 3,/* as TILED, each tile's constant data streamed into shared memory by bulk copies */
+    FEDFEM_KERNEL_TILED_REP = 4    /* as TILED_STAGED, with the tile's owned temperatures copied into one row per
+                                      rank, so that one 16-bit offset per element corner addresses both its
+                                      temperature and its load slot; one lane; at most one owned node per thread */
 };
 
 /* Linear laws p(T) = p0 + dp (T - T_ref) for density rho [kg/m^3], specific
@@ -96,7 +99,8 @@ typedef struct { double w_b, c_b, T_a, Q_m; } fedfem_perfusion;
 typedef struct {
     int kernel;        /* FEDFEM_KERNEL_* */
     int block;         /* threads per block: 64..1024, multiple of 32 (0 = default); the
-                          staged tiled kernel is built for 256, 512 (default) and 1024 */
+                          staged tiled kernel is built for 256, 512 (default) and 1024, the
+                          replicated-row kernel for 256 and 512 (default) */
     int tile_nodes;    /* TILED: owned nodes per tile, multiple of 8 (0 = default: the library
                           picks a size near 512 (hex) / 256 (tet), smaller when such tiles
                           do not fit in shared memory, that gives every resident block the
@@ -441,28 +445,38 @@ int fedfem_plan_layout(int elem_type, int64_t n_nodes, const double* xyz, int64_
  * (about 18.3 MB, held by every GPU that loads the library until the process
  * exits).  Nothing is allocated or freed by the call.
  *
- * Runs n_steps explicit FP64 steps (Eq. 17 with k_e of Eq. 13, Eq. 19) on the
- * CURRENT CUDA device, on `cuda_stream` (NULL = legacy default stream), and
- * returns after they have completed.  The element matrices and lumped volumes
- * are recomputed at the start of every call.
+ * What it computes: n_steps explicit steps in FP64 of the same element loads
+ * and nodal update as fedfem_step, restricted to one material with linear
+ * laws (mat), uniform perfusion and metabolism (perf), hex8 with the one-point
+ * rule only, and the element-share lumped volume (V_i = sum of V_e / nv over
+ * the node's elements).  No film condition, nodal flux, tables, regions,
+ * uniform V/N lumping, source schedule or dose; no temperature range check.
+ * It runs on the CURRENT CUDA device, on `cuda_stream` (NULL = legacy default
+ * stream), and returns after its work has completed.  Each call looks up the
+ * array's device address on the current device and recomputes the element
+ * matrices and lumped volumes.
  *   xyz_dev     n_nodes x 3 coordinates (m), row-major
  *   conn_dev    n_elems x elem_type node ids, as in fedfem_set_mesh
- *   row_ptr_dev n_nodes + 1 offsets into slot_dev
- *   slot_dev    for node i, entries row_ptr[i] .. row_ptr[i+1]-1 are
- *               e * elem_type + corner for every (element e, corner) that is
- *               node i, sorted by e (this fixes the summation order)
+ *   row_ptr_dev n_nodes + 1 offsets into slot_dev: row_ptr[0] = 0,
+ *               non-decreasing, row_ptr[n_nodes] = n_elems * elem_type
+ *   slot_dev    n_elems * elem_type entries; for node i, entries
+ *               row_ptr[i] .. row_ptr[i+1]-1 are e * elem_type + corner for
+ *               every (element e, corner) that is node i, in increasing order
+ *               (this fixes the summation order)
  *   q_r_dev     n_nodes source densities (W/m^3) or NULL; loads are
  *               V_i (Q_m + q_r[i]) with V_i the lumped volume
  *   held_dev    n_nodes bytes, 1 = Dirichlet node kept at its value in T, or NULL
  *   T_dev       n_nodes temperatures, updated in place
- * No film condition or nodal flux; no range check.
  * Limits: n_elems <= 131072 and n_nodes <= 160000; larger meshes get
  * FEDFEM_E_ARG ("beyond the fixed scratch") without touching the device.
- * FEDFEM_E_MESH: an element had det J <= 0 (T is then not meaningful).
- * All calls share the one array and it keeps the last call's contents; two
- * calls whose work overlaps on the GPU (other streams or other host threads)
- * race.  The first call on each device looks up the array's device address;
- * make that first call before any stream capture. */
+ * FEDFEM_E_MESH: a corner or slot index out of range, a gather row that is
+ * not the node's corners in increasing order, a node with no element that is
+ * not held, or an element with det J <= 0.  The indices are checked on the
+ * device before anything is read through them, and T_dev is then left
+ * unchanged.
+ * All calls share the one array and it keeps the last call's contents (each
+ * call clears its own flag word first); two calls whose work overlaps on the
+ * GPU (other streams or other host threads) race. */
 int fedfem_step_static(int elem_type, int64_t n_nodes, int64_t n_elems, const double* xyz_dev,
                        const int32_t* conn_dev, const int32_t* row_ptr_dev, const int32_t* slot_dev,
                        const fedfem_material* mat, const fedfem_perfusion* perf, const double* q_r_dev,

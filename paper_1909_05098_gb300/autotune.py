@@ -30,6 +30,12 @@ def candidates(elem_type: int, precision: int):
     out += [(ff.KERNEL_TILED, 0, b, 0) for b in sizes]
     out += [(ff.KERNEL_TILED_STAGED, 0, b, 0) for b in staged]
     out += [(ff.KERNEL_TILED_STAGED, 1024, b, 0) for b in staged1024]
+    # replicated rows: at most one owned node per thread (512 or 256 threads)
+    if elem_type == ff.HEX8:
+        rep = [(0, b) for b in ((0, 448, 480, 512) if precision != ff.FP64 else (0, 256))]
+    else:
+        rep = [(256, b) for b in (0, 96, 128, 192)]
+    out += [(ff.KERNEL_TILED_REP, blk, b, 0) for blk, b in rep]
     return out
 
 

@@ -93,7 +93,7 @@ struct fedfem_ctx {
     unsigned char* t_emat = nullptr;   // regions of the tile elements
     int32_t* t_emat_off = nullptr;
     int64_t t_block_bytes = 0;
-    int t_max_block = 0, t_max_local = 0;
+    int t_max_block = 0, t_max_local = 0, t_max_halo = 0;
     size_t t_smem = 0;
     void* slots = nullptr;
     int32_t* node_of = nullptr;
@@ -357,20 +357,43 @@ int64_t tile_block_bytes(const Tiles& t, int64_t i, size_t rs) {
     return (b + 15) / 16 * 16;
 }
 
-// dynamic shared memory of the tiled kernels: (staged) two block stages, the
-// tile temperatures and the per-node load table (max_deg rows of B)
-size_t tile_smem(const Tiles& t, size_t rs, size_t ls, int* max_block, bool staged) {
+// largest halo of any tile
+int tile_max_halo(const Tiles& t) {
+    int h = 0;
+    for (int64_t i = 0; i < t.n_tiles; ++i) h = std::max(h, t.h_off[i + 1] - t.h_off[i]);
+    return h;
+}
+
+// bytes of one replicated-row array (temperature copies or load table): rows
+// of stride S plus the halo, 16-byte multiple
+size_t rep_bytes(const Tiles& t, size_t ls, int S) {
+    return (((size_t)std::max(1, t.max_deg) * S + tile_max_halo(t)) * ls + 15) / 16 * 16;
+}
+
+// dynamic shared memory of the tiled kernels (kind: 0 direct, 1 staged, 2 staged
+// with replicated rows of stride S): two block stages when staged; the tile
+// temperatures and the per-node load table (max_deg rows of B), or the two
+// replicated-row arrays
+size_t tile_smem(const Tiles& t, size_t rs, size_t ls, int* max_block, int kind, int S) {
     int64_t mb = 0;
     for (int64_t i = 0; i < t.n_tiles; ++i) mb = std::max(mb, tile_block_bytes(t, i, rs));
     *max_block = (int)mb;
+    if (kind == 2) return 128 + 2 * rep_bytes(t, ls, S) + 2 * (size_t)mb;
     const size_t ts = ((size_t)t.max_local * ls + 15) / 16 * 16;
-    const size_t b = (staged ? 128 + 2 * (size_t)mb : 0) + ts + ls * (size_t)std::max(1, t.max_deg) * t.B;
+    const size_t b = (kind ? 128 + 2 * (size_t)mb : 0) + ts + ls * (size_t)std::max(1, t.max_deg) * t.B;
     return (b + 15) / 16 * 16;
 }
 
-// threads per block of the staged kernel: the block knob if it names a built size
+// threads per block of the staged kernels: the block knob if it names a built
+// size (the replicated-row kernel: 256 or 512)
 int staged_threads(const fedfem_ctx* c) {
+    if (c->tile.kernel == FEDFEM_KERNEL_TILED_REP) return c->tile.block == 256 ? 256 : tiled_threads();
     return c->tile.block == 256 || c->tile.block == 1024 ? c->tile.block : tiled_threads();
+}
+
+// kind of tiled kernel selected: 0 direct, 1 staged, 2 replicated rows
+int tile_kind(const fedfem_ctx* c) {
+    return c->tile.kernel == FEDFEM_KERNEL_TILED_REP ? 2 : c->tile.kernel == FEDFEM_KERNEL_TILED_STAGED ? 1 : 0;
 }
 
 // Tiles for the tiled kernels.  The requested size is used as given; the
@@ -381,9 +404,12 @@ int staged_threads(const fedfem_ctx* c) {
 // is packed into one 16-byte-aligned block (see tile_block_bytes).
 int plan_tiles(fedfem_ctx* c) {
     if (c->tiles_ok) return FEDFEM_OK;
-    const bool staged = c->tile.kernel == FEDFEM_KERNEL_TILED_STAGED;
+    const int kind = tile_kind(c);
+    const bool staged = kind != 0;
+    const int S = staged_threads(c);    // replicated-row stride: one owned node per thread
     const size_t rs = c->precision == FEDFEM_FP64 ? sizeof(double) : sizeof(float);
     const size_t ls = rs * c->n_lanes;
+    if (kind == 2 && c->n_lanes > 1) return fail(c, FEDFEM_E_UNSUPPORTED, "the replicated-row kernel takes one lane");
     const int64_t NF = c->L.N_free;
     if (NF == 0) return fail(c, FEDFEM_E_ARG, "no free nodes");
     int B = c->tile.tile_nodes;
@@ -399,14 +425,16 @@ int plan_tiles(fedfem_ctx* c) {
             B0 = c->nv == 8 ? (staged ? 512 : 256) : (staged ? 256 : 128);
             if (c->precision == FEDFEM_FP64) B0 /= 2;
             if (c->n_lanes > 1) B0 /= 2;
+            if (kind == 2) B0 = std::min(B0, S);
         }
+        if (kind == 2 && B0 > S) return fail(c, FEDFEM_E_ARG, "replicated-row tiles hold at most one owned node per thread");
         B0 = (int)std::max<int64_t>(8, std::min<int64_t>(B0, (NF + 7) / 8 * 8));
         int per_sm = 0;
         for (;;) {   // the default size halves while its tiles do not fit (meshes whose tiles hold many elements)
             m = build_tiles(c->L, B0, t);
             if (!m.empty()) return fail(c, FEDFEM_E_ARG, m);
-            size_t smem = tile_smem(t, rs, ls, &mb, staged);
-            per_sm = tiled_blocks_per_sm(c->precision, c->nv, staged, staged_threads(c), c->n_lanes, smem);
+            size_t smem = tile_smem(t, rs, ls, &mb, kind, S);
+            per_sm = tiled_blocks_per_sm(c->precision, c->nv, kind, S, c->n_lanes, smem);
             if (c->tile.blocks_per_sm > 0) per_sm = std::min(per_sm, c->tile.blocks_per_sm);
             if (per_sm >= 1 || c->tile.tile_nodes > 0 || B0 <= 32) break;
             B0 = std::max(32, B0 / 2 / 8 * 8);
@@ -418,10 +446,11 @@ int plan_tiles(fedfem_ctx* c) {
         for (int64_t waves = w0; waves <= w0 + 1 && c->tile.tile_nodes <= 0; ++waves) {
             const int64_t Bw = ((NF + waves * grid - 1) / (waves * grid) + 7) / 8 * 8;
             if (Bw < 32 || Bw > 2 * (int64_t)B0) continue;                 // small meshes: keep the target
+            if (kind == 2 && Bw > S) continue;
             Tiles tw;
             if (!build_tiles(c->L, (int)Bw, tw).empty()) continue;
             int mbw = 0;
-            int pw = tiled_blocks_per_sm(c->precision, c->nv, staged, staged_threads(c), c->n_lanes, tile_smem(tw, rs, ls, &mbw, staged));
+            int pw = tiled_blocks_per_sm(c->precision, c->nv, kind, S, c->n_lanes, tile_smem(tw, rs, ls, &mbw, kind, S));
             if (c->tile.blocks_per_sm > 0) pw = std::min(pw, c->tile.blocks_per_sm);
             if (pw != per_sm) continue;
             B = (int)Bw;
@@ -433,8 +462,12 @@ int plan_tiles(fedfem_ctx* c) {
         m = build_tiles(c->L, B, t);
         if (!m.empty()) return fail(c, FEDFEM_E_ARG, m);
     }
-    const size_t smem = tile_smem(t, rs, ls, &mb, staged);
-    if (tiled_blocks_per_sm(c->precision, c->nv, staged, staged_threads(c), c->n_lanes, smem) < 1)
+    const size_t smem = tile_smem(t, rs, ls, &mb, kind, S);
+    if (kind == 2 && t.max_deg > (c->nv == 8 ? 8 : 32))
+        return fail(c, FEDFEM_E_UNSUPPORTED, "the replicated-row kernel takes at most 8 (hex) or 32 (tet) elements per node");
+    if (kind == 2 && ls * ((size_t)std::max(1, t.max_deg) * S + tile_max_halo(t)) > 65536)
+        return fail(c, FEDFEM_E_UNSUPPORTED, "replicated-row offsets exceed 16 bits; use smaller tiles or 256 threads");
+    if (tiled_blocks_per_sm(c->precision, c->nv, kind, S, c->n_lanes, smem) < 1)
         return fail(c, FEDFEM_E_UNSUPPORTED, "tile does not fit in shared memory; use smaller tile_nodes");
     free_tiles(c);
     cudaStream_t st = c->stream;
@@ -458,7 +491,18 @@ int plan_tiles(fedfem_ctx* c) {
             for (int64_t j = 0; j < ne; ++j)
                 std::memcpy(Mb + rs * (6 * j + q), Mh.data() + rs * (q * E + t.e_glob[e0 + j]), rs);
         uint16_t* lc = (uint16_t*)(Mb + rs * 6 * ne_pad);
-        std::memcpy(lc, t.lconn.data() + e0 * t.nv, sizeof(uint16_t) * ne * t.nv);
+        if (kind == 2) {   // byte offsets into the replicated rows (see TileArgs::rep)
+            const int64_t own = std::min<int64_t>(t.B, NF - i * (int64_t)t.B);
+            const int id_mask = (1 << t.rank_shift) - 1, D = std::max(1, t.max_deg);
+            for (int64_t q = 0; q < ne * t.nv; ++q) {
+                const int code = t.lconn[e0 * t.nv + q];
+                const int lid = code & id_mask, rank = code >> t.rank_shift;
+                const int64_t slot = lid < own ? (int64_t)rank * S + lid : (int64_t)D * S + (lid - own);
+                lc[q] = (uint16_t)(slot * (int64_t)ls);
+            }
+        } else {
+            std::memcpy(lc, t.lconn.data() + e0 * t.nv, sizeof(uint16_t) * ne * t.nv);
+        }
         int32_t* h = (int32_t*)(lc + t.nv * ne_pad);
         std::memcpy(h, t.halo.data() + h0, sizeof(int32_t) * nh);
     }
@@ -481,6 +525,7 @@ int plan_tiles(fedfem_ctx* c) {
     c->t_block_bytes = (int64_t)blob.size();
     c->t_max_block = mb;
     c->t_max_local = t.max_local;
+    c->t_max_halo = tile_max_halo(t);
     c->t_smem = smem;
     c->tiles_B = t.B;
     c->tiles_host = std::move(t);
@@ -497,8 +542,11 @@ TileArgs<R> make_tile_args(fedfem_ctx* c) {
     t.blocks = c->t_blocks; t.block_off = c->t_block_off;
     t.max_block = c->t_max_block; t.max_local = c->t_max_local;
     t.smem_bytes = c->t_smem;
-    t.staged = c->tile.kernel == FEDFEM_KERNEL_TILED_STAGED;
+    t.staged = tile_kind(c) != 0;
     t.threads = staged_threads(c);
+    t.rep = tile_kind(c) == 2;
+    t.rep_rows = std::max(1, h.max_deg);
+    t.max_halo = c->t_max_halo;
     return t;
 }
 
@@ -510,7 +558,8 @@ int prepare_launch(fedfem_ctx* c, LaunchCfg& cfg) {
     cfg.blocks_per_sm = c->tile.blocks_per_sm;
     cfg.sm_count = c->sm_count;
     cfg.spin_limit = c->spin_limit;
-    const bool tiled = cfg.kernel == FEDFEM_KERNEL_TILED || cfg.kernel == FEDFEM_KERNEL_TILED_STAGED;
+    const bool tiled = cfg.kernel == FEDFEM_KERNEL_TILED || cfg.kernel == FEDFEM_KERNEL_TILED_STAGED ||
+                       cfg.kernel == FEDFEM_KERNEL_TILED_REP;
     if (c->n_lanes > 1 && !tiled) return fail(c, FEDFEM_E_UNSUPPORTED, "scenario lanes need a tiled kernel");
     if (tiled && (c->A28_64 || c->A28_32))
         return fail(c, FEDFEM_E_UNSUPPORTED, "the fully integrated hexahedron runs on the two-phase and persistent kernels");
@@ -520,7 +569,8 @@ int prepare_launch(fedfem_ctx* c, LaunchCfg& cfg) {
 
 // Enqueue n_steps of the selected kernel on the context's stream.
 cudaError_t launch_all(fedfem_ctx* c, double dt, int64_t n_steps, LaunchCfg& cfg) {
-    const bool tiled = cfg.kernel == FEDFEM_KERNEL_TILED || cfg.kernel == FEDFEM_KERNEL_TILED_STAGED;
+    const bool tiled = cfg.kernel == FEDFEM_KERNEL_TILED || cfg.kernel == FEDFEM_KERNEL_TILED_STAGED ||
+                       cfg.kernel == FEDFEM_KERNEL_TILED_REP;
     if (tiled) {
         if (c->precision == FEDFEM_FP64) {
             StepArgs<double> a = make_args<double>(c, c->M64, c->V64, c->Q64, c->hA64, dt, c->Qs64);
@@ -950,12 +1000,13 @@ int fedfem_read_dose(fedfem_ctx* c, double* out) { return fedfem_read_dose_lane(
 
 int fedfem_set_tile(fedfem_ctx* c, const fedfem_tile* t) {
     if (!c || !t) return fail(c, FEDFEM_E_ARG, "null tile");
-    if (t->kernel < FEDFEM_KERNEL_TWO_PHASE || t->kernel > FEDFEM_KERNEL_TILED_STAGED) return fail(c, FEDFEM_E_ARG, "unknown kernel");
+    if (t->kernel < FEDFEM_KERNEL_TWO_PHASE || t->kernel > FEDFEM_KERNEL_TILED_REP) return fail(c, FEDFEM_E_ARG, "unknown kernel");
     if (t->block != 0 && (t->block < 64 || t->block > 1024 || t->block % 32)) return fail(c, FEDFEM_E_ARG, "block must be 64..1024, multiple of 32");
     if (t->blocks_per_sm < 0 || t->tile_nodes < 0 || t->tile_nodes % 8) return fail(c, FEDFEM_E_ARG, "bad tile knobs");
     if (t->tile_nodes != c->tile.tile_nodes || t->blocks_per_sm != c->tile.blocks_per_sm ||
         t->block != c->tile.block ||
-        (t->kernel == FEDFEM_KERNEL_TILED_STAGED) != (c->tile.kernel == FEDFEM_KERNEL_TILED_STAGED))
+        (t->kernel == FEDFEM_KERNEL_TILED_STAGED) != (c->tile.kernel == FEDFEM_KERNEL_TILED_STAGED) ||
+        (t->kernel == FEDFEM_KERNEL_TILED_REP) != (c->tile.kernel == FEDFEM_KERNEL_TILED_REP))
         free_tiles(c);
     c->tile = *t;
     return FEDFEM_OK;
@@ -1544,16 +1595,18 @@ int fedfem_get_info(fedfem_ctx* c, fedfem_info* info) {
     // two-phase / persistent model: + slot write and read, gather ids, their slice offsets, T gathered once
     info->bytes_per_step = info->algorithmic_bytes_per_step + E * c->nv * 2 * R + (int64_t)L.sell_ids.size() * 4 +
                            (int64_t)L.sell_off.size() * 4;
-    if ((c->tile.kernel == FEDFEM_KERNEL_TILED || c->tile.kernel == FEDFEM_KERNEL_TILED_STAGED) && c->tiles_ok) {
+    if (tile_kind(c) > 0 || c->tile.kernel == FEDFEM_KERNEL_TILED) {
+      if (c->tiles_ok) {
         const Tiles& t = c->tiles_host;
         // every packed block once, halo values, owned T read; then T written, lo read+write, V, Q, hA
         const int64_t node_rest = NF * (NL * (node_state - R + R) + R) + NC * R;
         info->bytes_per_step =
             c->t_block_bytes + (int64_t)t.halo.size() * R * NL + NF * R * NL + node_rest + extra;
+      }
     }
     info->sm_count = c->sm_count;
     info->grid_blocks = c->last.grid_used;
-    info->block_threads = c->tile.kernel == FEDFEM_KERNEL_TILED_STAGED ? staged_threads(c) : 256;
+    info->block_threads = tile_kind(c) > 0 ? staged_threads(c) : 256;
     info->kernel = c->tile.kernel;
     info->tile_nodes = c->tiles_ok ? c->tiles_B : 0;
     info->lanes = c->n_lanes;

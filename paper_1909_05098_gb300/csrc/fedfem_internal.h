@@ -185,6 +185,11 @@ struct TileArgs {
     int staged;                      // 1: blocks bulk-copied into shared-memory stages; 0: read from global
     int threads;                     // staged kernel: threads per block (256 or 512)
     size_t smem_bytes;
+    // replicated-row kernel (rep = 1): codes are byte offsets into rows of stride `threads`
+    // (owned corner: rank * threads + l; halo node h: rep_rows * threads + h)
+    int rep;
+    int rep_rows;                    // rows of the temperature copies and of the load table (largest rank count)
+    int max_halo;                    // largest halo of any tile
 };
 
 struct F4;

@@ -10,8 +10,14 @@
 // (about 18.3 MB) is held by every GPU that loads this library until the
 // process exits.  All calls share it: two calls whose work overlaps on the GPU
 // (different streams, or different host threads) race and corrupt each other.
+//
+// Every index the caller passes is checked on the device before it is used
+// (k_static_check); a bad index, a node that no element uses (and that is not
+// held) or an element with det J <= 0 raises the flag word, after which every
+// later kernel of the call returns at once, so the caller's temperatures are
+// left as they were.
+#include <algorithm>
 #include <climits>
-#include <mutex>
 
 #include "elem_math.cuh"
 #include "fedfem_internal.h"
@@ -33,9 +39,6 @@ constexpr int64_t kStaticWords = kOffFlag + 8;
 
 static __device__ __align__(256) double g_static_scratch[kStaticWords];
 
-std::mutex g_static_mu;
-double* g_static_addr[64] = {nullptr};
-
 struct StaticArgs {
     int nv;
     int64_t N, E;
@@ -52,9 +55,43 @@ struct StaticArgs {
     double wbcb, T_a, Q_m, dt;
 };
 
+// a mesh defect found earlier in this call: leave everything untouched
+__device__ __forceinline__ bool static_failed(const StaticArgs& a) { return a.s[kOffFlag] != 0.0; }
+
+// Index checks of the caller's mesh and gather, before anything reads through
+// them: every corner names a node in [0, N); row_ptr starts at 0, never
+// decreases and ends at E * nv; each row lists slots in [0, E * nv) in
+// increasing order whose corner is that row's node (so every (element,
+// corner) appears exactly once); a node with an empty row must be held.
+// Each access is bounded on its own, so a malformed array is read in range.
+__global__ void k_static_check(StaticArgs a) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nslot = a.E * a.nv;
+    bool bad = false;
+    if (t < nslot) {
+        const int32_t g = a.conn[t];
+        bad = g < 0 || g >= a.N;
+    }
+    if (t < a.N) {
+        const int64_t r0 = a.row_ptr[t], r1 = a.row_ptr[t + 1];
+        if ((t == 0 && r0 != 0) || (t == a.N - 1 && r1 != nslot) || r0 < 0 || r1 < r0 || r1 > nslot) {
+            bad = true;
+        } else {
+            if (r1 == r0 && !(a.held && a.held[t])) bad = true;   // no element: zero capacity
+            int64_t prev = -1;
+            for (int64_t p = r0; p < r1 && !bad; ++p) {
+                const int64_t q = a.slot[p];
+                if (q <= prev || q >= nslot || a.conn[q] != (int32_t)t) bad = true;
+                prev = q;
+            }
+        }
+    }
+    if (bad) a.s[kOffFlag] = 1.0;
+}
+
 __global__ void k_static_geom(StaticArgs a) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= a.E) return;
+    if (e >= a.E || static_failed(a)) return;
     const int32_t* cn = a.conn + e * a.nv;
     double J[3][3];
     if (a.nv == 8) {
@@ -109,7 +146,7 @@ __global__ void k_static_geom(StaticArgs a) {
 
 __global__ void k_static_nodal(StaticArgs a) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.N) return;
+    if (i >= a.N || static_failed(a)) return;
     double V = 0.0;
     for (int32_t p = a.row_ptr[i]; p < a.row_ptr[i + 1]; ++p) V += a.s[kOffVshare + a.slot[p] / a.nv];
     a.s[kOffV + i] = V;
@@ -118,7 +155,7 @@ __global__ void k_static_nodal(StaticArgs a) {
 
 __global__ void k_static_elem(StaticArgs a) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= a.E) return;
+    if (e >= a.E || static_failed(a)) return;
     const int32_t* cn = a.conn + e * a.nv;
     double m[6];
     for (int j = 0; j < 6; ++j) m[j] = a.s[kOffM + j * kStaticMaxElems + e];
@@ -138,7 +175,7 @@ __global__ void k_static_elem(StaticArgs a) {
 
 __global__ void k_static_node(StaticArgs a) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.N || (a.held && a.held[i])) return;
+    if (i >= a.N || (a.held && a.held[i]) || static_failed(a)) return;
     double F = 0.0;
     for (int32_t p = a.row_ptr[i]; p < a.row_ptr[i + 1]; ++p) F = F + a.s[kOffSlots + a.slot[p]];
     const double T = a.T[i];
@@ -148,20 +185,15 @@ __global__ void k_static_node(StaticArgs a) {
     a.T[i] = T + (a.dt * r) / C;
 }
 
-// Address of the scratch array on the current device, looked up once per device.
+// Device address of the scratch array on the current device.  Looked up on
+// every call: the lookup is cheap next to the launches, and an address kept
+// from an earlier call would be stale once the device's context is recreated
+// (after cudaDeviceReset, the module is loaded again elsewhere).
 cudaError_t static_scratch(double** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    double* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress((void**)&p, g_static_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_static_mu);
-    if (!g_static_addr[dev]) {
-        double* p = nullptr;
-        e = cudaGetSymbolAddress((void**)&p, g_static_scratch);
-        if (e != cudaSuccess) return e;
-        g_static_addr[dev] = p;
-    }
-    *out = g_static_addr[dev];
+    *out = p;
     return cudaSuccess;
 }
 
@@ -194,6 +226,7 @@ extern "C" int fedfem_step_static(int elem_type, int64_t n_nodes, int64_t n_elem
     a.wbcb = perf->w_b * perf->c_b; a.T_a = perf->T_a; a.Q_m = perf->Q_m; a.dt = dt;
     // the flag word keeps the previous call's value: clear it first
     if (cudaMemsetAsync(s + kOffFlag, 0, sizeof(double), st) != cudaSuccess) return FEDFEM_E_CUDA;
+    k_static_check<<<grid_for(std::max(n_nodes, n_elems * elem_type)), 256, 0, st>>>(a);
     k_static_geom<<<grid_for(n_elems), 256, 0, st>>>(a);
     k_static_nodal<<<grid_for(n_nodes), 256, 0, st>>>(a);
     for (int64_t k = 0; k < n_steps; ++k) {

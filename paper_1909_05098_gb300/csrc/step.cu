@@ -684,8 +684,9 @@ __global__ void __launch_bounds__(TPB, StagedOccupancy<L, TPB>::min_blocks)
     long long done = 0;
     if (!grid_barrier(a.status, target, spin_limit)) return;
     const int64_t first = blockIdx.x;
-    const int64_t n_my = first < ta.n_tiles ? (ta.n_tiles - 1 - first) / gridDim.x + 1 : 0;
-    // Tiles in launch order: kk = s * n_my + i is tile first + i * gridDim.x of step s.  With at
+    const int n_my = first < ta.n_tiles ? (int)((ta.n_tiles - 1 - first) / gridDim.x + 1) : 0;
+    // Tiles in launch order: kk = s * n_my + p is tile first + p * gridDim.x of step s (p, the
+    // position in the step, is carried along with kk: no 64-bit division in the loop).  With at
     // most two tiles per block both stay in their stages for the whole launch; otherwise tile kk
     // uses stage kk & 1 and its copy is issued two tiles ahead.
     const bool resident = n_my <= 2;
@@ -693,13 +694,13 @@ __global__ void __launch_bounds__(TPB, StagedOccupancy<L, TPB>::min_blocks)
     const uint64_t policy = policy_evict_first();
     uint32_t ph0 = 0u, ph1 = 0u;      // per stage: parity of the next completion
     bool pend0 = false, pend1 = false;   // per stage: copy issued and not yet waited for
-    auto tile_of = [&](long long kk) { return first + (kk % n_my) * (int64_t)gridDim.x; };
-    auto buf_of = [&](long long kk) { return resident ? (int)(kk % n_my) : (int)(kk & 1); };
-    // tile kk's block into its stage (thread 0 copies; every thread records it)
-    auto issue = [&](long long kk) {
-        const int buf = buf_of(kk);
+    auto tile_at = [&](int p) { return first + (int64_t)p * gridDim.x; };
+    auto buf_of = [&](long long kk, int p) { return resident ? p : (int)(kk & 1); };
+    // tile kk (position p)'s block into its stage (thread 0 copies; every thread records it)
+    auto issue = [&](long long kk, int p) {
+        const int buf = buf_of(kk, p);
         if (threadIdx.x == 0) {
-            const int64_t t = tile_of(kk);
+            const int64_t t = tile_at(p);
             const int64_t o0 = ta.block_off[t], o1 = ta.block_off[t + 1];
             fence_proxy_async();
             mbar_expect_tx(&bar[buf], (uint32_t)(o1 - o0));
@@ -709,55 +710,57 @@ __global__ void __launch_bounds__(TPB, StagedOccupancy<L, TPB>::min_blocks)
     };
     // wait for stage buf's outstanding copy: one thread polls, the block
     // synchronises on it; false (in every thread alike) when the wait gave up
+    // (a copy whose wait gave up stays pending, so that the drain at exit waits for it again)
     auto land = [&](int buf) -> bool {
         bool ok = true;
-        if (buf ? pend1 : pend0) {
-            if (threadIdx.x == 0) ok = mbar_wait(&bar[buf], buf ? ph1 : ph0, spin_limit);
+        const bool pend = buf ? pend1 : pend0;
+        if (pend && threadIdx.x == 0) ok = mbar_wait(&bar[buf], buf ? ph1 : ph0, spin_limit);
+        const bool failed = __syncthreads_or(!ok) != 0;
+        if (pend && !failed) {
             if (buf) { ph1 ^= 1u; pend1 = false; }
             else { ph0 ^= 1u; pend0 = false; }
         }
-        return !__syncthreads_or(!ok);
+        return !failed;
     };
     auto fail_timeout = [&]() {
         if (threadIdx.x == 0) atomicOr(&a.status->flags, STATUS_TIMEOUT);
     };
-    auto view_of = [&](long long kk) { return tile_view<R, NV>(buf_of(kk) ? stage1 : stage0); };
+    auto view_of = [&](long long kk, int p) { return tile_view<R, NV>(buf_of(kk, p) ? stage1 : stage0); };
     // temperatures of tile kk (its stage has landed) into Ts, asynchronously
-    auto fetch = [&](long long kk, const L* Tin) {
-        const TileView<R> v = view_of(kk);
-        const int64_t base = tile_of(kk) * ta.B;
+    auto fetch = [&](long long kk, int p, const L* Tin) {
+        const TileView<R> v = view_of(kk, p);
+        const int64_t base = tile_at(p) * ta.B;
         tile_fetch<L, true>(v.halo, v.nh, base, (int)min((int64_t)ta.B, a.N_free - base), Tin, Ts);
         cp_async_commit();
     };
     bool stop = false;
     if (total > 0) {
-        for (long long kk = 0; kk < 2 && kk < n_my; ++kk) issue(kk);
+        for (int p = 0; p < 2 && p < n_my; ++p) issue(p, p);
         if (!land(0)) { fail_timeout(); stop = true; }
-        else fetch(0, a.T);
+        else fetch(0, 0, a.T);
     }
     long long kk = 0;
     for (long long s = 0; s < n_steps && !stop; ++s) {
         const L* Tin = (s & 1) ? a.T2 : a.T;
         L* Tout = (s & 1) ? a.T : a.T2;
-        for (int64_t i = 0; i < n_my; ++i, ++kk) {
-            const int buf = buf_of(kk);
+        for (int i = 0; i < n_my; ++i, ++kk) {
             cp_async_wait_all();
             __syncthreads();   // Ts of this tile complete; the table is clear
-            const TileView<R> v = view_of(kk);
-            const int64_t base = tile_of(kk) * ta.B;
+            const TileView<R> v = view_of(kk, i);
+            const int64_t t = tile_at(i);
+            const int64_t base = t * ta.B;
             const int own = (int)min((int64_t)ta.B, a.N_free - base);
             const int deg = v.deg;
             L T0 = lzero<L>();
             NodeVals<R, L> v0{};
             first_node<R, L, MODE>(a, base, own, Ts, T0, v0);
-            tile_elements<R, L, NV, MODE, true>(a, tile_regions<MODE>(a, tile_of(kk)), v, own, ta.B, ta.rank_shift,
-                                                Ts, Fn);
+            tile_elements<R, L, NV, MODE, true>(a, tile_regions<MODE>(a, t), v, own, ta.B, ta.rank_shift, Ts, Fn);
             __syncthreads();   // loads complete; this stage and Ts are free
             if (i + 1 < n_my) {   // the next tile of this step: its stage, then its temperatures
-                if (!land(buf_of(kk + 1))) { fail_timeout(); stop = true; break; }
-                fetch(kk + 1, Tin);
+                if (!land(buf_of(kk + 1, i + 1))) { fail_timeout(); stop = true; break; }
+                fetch(kk + 1, i + 1, Tin);
             }
-            if (!resident && kk + 2 < total) issue(kk + 2);
+            if (!resident && kk + 2 < total) issue(kk + 2, i + 2 < n_my ? i + 2 : i + 2 - n_my);
             tile_nodes<R, L, MODE>(a, base, own, deg, ta.B, Fn, T0, v0, Tin, Tout, a.step0 + s);
         }
         if (stop) break;
@@ -766,8 +769,8 @@ __global__ void __launch_bounds__(TPB, StagedOccupancy<L, TPB>::min_blocks)
         done = s + 1;
         if (!ok) break;
         if (s + 1 < n_steps && n_my > 0) {   // the first tile of the next step reads this step's result
-            if (!land(buf_of(kk))) { fail_timeout(); break; }
-            fetch(kk, Tout);
+            if (!land(buf_of(kk, 0))) { fail_timeout(); break; }
+            fetch(kk, 0, Tout);
         }
     }
     cp_async_wait_all();
@@ -783,11 +786,224 @@ __global__ void __launch_bounds__(TPB, StagedOccupancy<L, TPB>::min_blocks)
     if (blockIdx.x == 0 && threadIdx.x == 0) a.status->steps_done = a.step0 + done;
 }
 
+// ---- replicated-row tiles ------------------------------------------------------
+// The staged kernel's data flow with a layout that needs no arithmetic on a
+// corner's code.  Two shared arrays share one shape, row stride S (>= the
+// tile's owned nodes):
+//   Tr: rows 0 .. D-1 each hold the owned nodes' temperatures (row r, entry
+//       l: owned node l), then the halo temperatures from entry D*S;
+//   Fr: row r, entry l holds owned node l's rank-r element load; from entry
+//       D*S a dump area that halo corners write and nobody reads.
+// D is the largest rank count of any tile.  Each corner's 16-bit code is the
+// byte offset of entry r*S + l (owned corner of rank r) or D*S + h (halo node
+// h), so one offset gives both a corner's temperature (Tr) and its load slot
+// (Fr): every corner writes its load unconditionally, and owned node l sums
+// column l of Fr in rank order (= input element order, as in every other
+// kernel) and clears it.  The owned temperatures are fetched into row 0 and
+// copied into rows 1 .. deg-1 by the thread that fetched them.
+
+// a corner's byte offset, extracted from the packed codes of an element
+template <int NV>
+struct RepCodes;
+template <>
+struct RepCodes<8> {
+    static __device__ __forceinline__ void load(const uint16_t* p, int j, uint32_t o[8]) {
+        const uint4 v = reinterpret_cast<const uint4*>(p)[j];
+        o[0] = v.x & 0xffffu; o[1] = v.x >> 16; o[2] = v.y & 0xffffu; o[3] = v.y >> 16;
+        o[4] = v.z & 0xffffu; o[5] = v.z >> 16; o[6] = v.w & 0xffffu; o[7] = v.w >> 16;
+    }
+};
+template <>
+struct RepCodes<4> {
+    static __device__ __forceinline__ void load(const uint16_t* p, int j, uint32_t o[4]) {
+        const uint2 v = reinterpret_cast<const uint2*>(p)[j];
+        o[0] = v.x & 0xffffu; o[1] = v.x >> 16; o[2] = v.y & 0xffffu; o[3] = v.y >> 16;
+    }
+};
+
+// element phase of one replicated-row tile
+template <typename R, typename L, int NV, int TPB, typename KL>
+__device__ __forceinline__ void rep_elements_k(const KL& kl, const TileView<R>& v, const unsigned char* Tr,
+                                               unsigned char* Fr) {
+    for (int j = threadIdx.x; j < v.ne; j += TPB) {
+        uint32_t o[NV];
+        RepCodes<NV>::load(v.lc, j, o);
+        L tt[NV];
+#pragma unroll
+        for (int n = 0; n < NV; ++n) tt[n] = *reinterpret_cast<const L*>(Tr + o[n]);
+        R m[6];
+#pragma unroll
+        for (int q = 0; q < 6; q += 2) {
+            const typename Vec2<R>::type p = reinterpret_cast<const typename Vec2<R>::type*>(v.M + 6 * j)[q / 2];
+            m[q] = p.x;
+            m[q + 1] = p.y;
+        }
+        const L ke = element_k<R, NV, L>(tt, kl(j));
+        L F[NV];
+        if (NV == 8) hex8_loads<R, L>(tt, m, ke, F);
+        else tet4_loads<R, L>(tt, m, ke, F);
+#pragma unroll
+        for (int n = 0; n < NV; ++n) *reinterpret_cast<L*>(Fr + o[n]) = F[n];
+    }
+}
+
+// largest rank count the replicated-row kernels are built for (the host
+// refuses meshes with more elements at one node)
+template <int NV>
+struct RepRows {
+    static constexpr int value = NV == 8 ? 8 : 32;
+};
+
+template <typename R, typename L, int NV, int MODE, int TPB>
+__global__ void __launch_bounds__(TPB, StagedOccupancy<L, TPB>::min_blocks)
+    k_tiled_rep(StepArgs<R, L> a, TileArgs<R> ta, long long n_steps, long long spin_limit) {
+    constexpr int S = TPB;                      // row stride: one owned node per thread
+    constexpr int DMAX = RepRows<NV>::value;
+    // shared memory: 2 mbarriers | Tr | Fr | 2 block stages
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
+    const size_t rep_bytes = ((size_t)(ta.rep_rows * S + ta.max_halo) * sizeof(L) + 15) / 16 * 16;
+    unsigned char* const Tr = smem + 128;
+    unsigned char* const Fr = smem + 128 + rep_bytes;
+    const size_t stage_bytes = (size_t)ta.max_block;
+    unsigned char* const stage0 = smem + 128 + 2 * rep_bytes;
+    unsigned char* const stage1 = stage0 + stage_bytes;
+    L* const T0row = reinterpret_cast<L*>(Tr);
+    L* const Thalo = reinterpret_cast<L*>(Tr) + ta.rep_rows * S;
+    L* const Fcol = reinterpret_cast<L*>(Fr);
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    for (int i = threadIdx.x; i < ta.rep_rows * S; i += TPB) Fcol[i] = lzero<L>();
+    __syncthreads();
+    unsigned long long target = 0;
+    long long done = 0;
+    if (!grid_barrier(a.status, target, spin_limit)) return;
+    const int64_t first = blockIdx.x;
+    const int n_my = first < ta.n_tiles ? (int)((ta.n_tiles - 1 - first) / gridDim.x + 1) : 0;
+    const bool resident = n_my <= 2;
+    const long long total = (long long)n_steps * n_my;
+    const uint64_t policy = policy_evict_first();
+    uint32_t ph0 = 0u, ph1 = 0u;
+    bool pend0 = false, pend1 = false;
+    auto tile_at = [&](int p) { return first + (int64_t)p * gridDim.x; };
+    auto buf_of = [&](long long kk, int p) { return resident ? p : (int)(kk & 1); };
+    auto issue = [&](long long kk, int p) {
+        const int buf = buf_of(kk, p);
+        if (threadIdx.x == 0) {
+            const int64_t t = tile_at(p);
+            const int64_t o0 = ta.block_off[t], o1 = ta.block_off[t + 1];
+            fence_proxy_async();
+            mbar_expect_tx(&bar[buf], (uint32_t)(o1 - o0));
+            bulk_g2s(buf ? stage1 : stage0, ta.blocks + o0, (uint32_t)(o1 - o0), &bar[buf], policy);
+        }
+        if (buf) pend1 = true; else pend0 = true;
+    };
+    // (a copy whose wait gave up stays pending, so that the drain at exit waits for it again)
+    auto land = [&](int buf) -> bool {
+        bool ok = true;
+        const bool pend = buf ? pend1 : pend0;
+        if (pend && threadIdx.x == 0) ok = mbar_wait(&bar[buf], buf ? ph1 : ph0, spin_limit);
+        const bool failed = __syncthreads_or(!ok) != 0;
+        if (pend && !failed) {
+            if (buf) { ph1 ^= 1u; pend1 = false; }
+            else { ph0 ^= 1u; pend0 = false; }
+        }
+        return !failed;
+    };
+    auto fail_timeout = [&]() {
+        if (threadIdx.x == 0) atomicOr(&a.status->flags, STATUS_TIMEOUT);
+    };
+    auto view_of = [&](long long kk, int p) { return tile_view<R, NV>(buf_of(kk, p) ? stage1 : stage0); };
+    // owned temperatures into row 0 (thread l fetches owned node l), halo ones after the rows
+    auto fetch = [&](long long kk, int p, const L* Tin) {
+        const TileView<R> v = view_of(kk, p);
+        const int64_t base = tile_at(p) * ta.B;
+        const int own = (int)min((int64_t)ta.B, a.N_free - base);
+        if ((int)threadIdx.x < own) cp_async<sizeof(L)>(T0row + threadIdx.x, Tin + base + threadIdx.x);
+        for (int h = threadIdx.x; h < v.nh; h += TPB) cp_async<sizeof(L)>(Thalo + h, Tin + v.halo[h]);
+        cp_async_commit();
+    };
+    bool stop = false;
+    if (total > 0) {
+        for (int p = 0; p < 2 && p < n_my; ++p) issue(p, p);
+        if (!land(0)) { fail_timeout(); stop = true; }
+        else fetch(0, 0, a.T);
+    }
+    long long kk = 0;
+    for (long long s = 0; s < n_steps && !stop; ++s) {
+        const L* Tin = (s & 1) ? a.T2 : a.T;
+        L* Tout = (s & 1) ? a.T : a.T2;
+        for (int i = 0; i < n_my; ++i, ++kk) {
+            const TileView<R> v = view_of(kk, i);
+            const int64_t t = tile_at(i);
+            const int64_t base = t * ta.B;
+            const int own = (int)min((int64_t)ta.B, a.N_free - base);
+            const int deg = v.deg;
+            const int l = threadIdx.x;
+            L T0 = lzero<L>();
+            NodeVals<R, L> v0{};
+            cp_async_wait_all();
+            if (l < own) {   // this thread's own fetch has landed: copy it into the other rows
+                T0 = T0row[l];
+#pragma unroll
+                for (int r = 1; r < DMAX; ++r)
+                    if (r < deg) T0row[r * S + l] = T0;
+                v0 = node_load<R, L, MODE>(a, base + l);
+            }
+            __syncthreads();   // Tr of this tile complete; Fr clear
+            with_k_laws<MODE>(a, tile_regions<MODE>(a, t), [&](const auto& kl) {
+                rep_elements_k<R, L, NV, TPB>(kl, v, Tr, Fr);
+            });
+            __syncthreads();   // loads complete; this stage and Tr are free
+            if (i + 1 < n_my) {
+                if (!land(buf_of(kk + 1, i + 1))) { fail_timeout(); stop = true; break; }
+                fetch(kk + 1, i + 1, Tin);
+            }
+            if (!resident && kk + 2 < total) issue(kk + 2, i + 2 < n_my ? i + 2 : i + 2 - n_my);
+            if (l < own) {   // node phase: column l in rank order, cleared for the next tile
+                L F = lzero<L>();
+#pragma unroll
+                for (int r = 0; r < DMAX; ++r)
+                    if (r < deg) {
+                        F = F + Fcol[r * S + l];
+                        Fcol[r * S + l] = lzero<L>();
+                    }
+                node_update_v<R, L, MODE>(a, base + l, T0, F, v0, Tout, a.step0 + s);
+            }
+        }
+        if (stop) break;
+        cp_async_wait_all();
+        const bool ok = grid_barrier(a.status, target, spin_limit);
+        done = s + 1;
+        if (!ok) break;
+        if (s + 1 < n_steps && n_my > 0) {
+            if (!land(buf_of(kk, 0))) { fail_timeout(); break; }
+            fetch(kk, 0, Tout);
+        }
+    }
+    cp_async_wait_all();
+    if (threadIdx.x == 0) {
+        if (pend0) mbar_wait(&bar[0], ph0, spin_limit);
+        if (pend1) mbar_wait(&bar[1], ph1, spin_limit);
+    }
+    if (done & 1) {
+        const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.N_free; i += stride) a.T[i] = a.T2[i];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.status->steps_done = a.step0 + done;
+}
+
 // MODE bit 0: Kahan-compensated state; bit 1: built with the time-varying
 // source, thermal-dose, tabulated-law and region paths (launched only when a
 // context enables one)
 template <typename R, typename L, int NV, int MODE>
 auto tiled_kernel(const TileArgs<R>& ta) {
+    if constexpr (sizeof(L) == sizeof(R)) {   // one lane: the replicated rows would not fit four
+        if (ta.rep) return ta.threads == 256 ? k_tiled_rep<R, L, NV, MODE, 256> : k_tiled_rep<R, L, NV, MODE, kTiledThreads>;
+    }
     return !ta.staged           ? k_tiled_direct<R, L, NV, MODE>
            : ta.threads == 256  ? k_tiled<R, L, NV, MODE, 256>
            : ta.threads == 1024 ? k_tiled<R, L, NV, MODE, 1024>
@@ -883,10 +1099,12 @@ cudaError_t launch_tiled_f32x4(const StepArgs<float, F4>& a, const TileArgs<floa
                  : launch_tiled_impl<float, F4, 4, false>(a, t, n_steps, cfg, s);
 }
 
+// staged: 0 direct, 1 staged, 2 staged with replicated rows
 template <typename R, typename L, int NV, bool KAHAN>
 const void* pick_tiled_k(int staged, int threads) {
     TileArgs<R> ta{};
-    ta.staged = staged;
+    ta.staged = staged != 0;
+    ta.rep = staged == 2;
     ta.threads = threads;
     return (const void*)tiled_kernel<R, L, NV, KAHAN ? 1 : 0>(ta);
 }

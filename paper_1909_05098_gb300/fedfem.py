@@ -23,7 +23,7 @@ OK, E_ARG, E_MESH, E_STATE, E_UNSTABLE_DT, E_RANGE, E_TIMEOUT, E_CUDA, E_OOM, E_
 TET4, HEX8 = 4, 8
 FP64, FP32_KAHAN, FP32_PLAIN = 0, 1, 2
 ORDER_INPUT, ORDER_MORTON, ORDER_RCM = 0, 1, 2
-KERNEL_TWO_PHASE, KERNEL_PERSISTENT, KERNEL_TILED, KERNEL_TILED_STAGED = 0, 1, 2, 3
+KERNEL_TWO_PHASE, KERNEL_PERSISTENT, KERNEL_TILED, KERNEL_TILED_STAGED, KERNEL_TILED_REP = 0, 1, 2, 3, 4
 DOSE_CEM43, DOSE_ARRHENIUS = 0, 1
 HEX_ONE_POINT, HEX_FULL = 0, 1
 LUMP_ELEMENT, LUMP_UNIFORM = 0, 1

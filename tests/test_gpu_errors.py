@@ -90,7 +90,8 @@ def test_range_violation_stops_every_kernel_at_the_same_step():
     p.T_hi = 38.0                                  # the source crosses this after some steps
     dt = 0.5 * critical_dt(Oracle(p), 20.0, 38.0)
     done = {}
-    for kern in (f.KERNEL_TWO_PHASE, f.KERNEL_PERSISTENT, f.KERNEL_TILED, f.KERNEL_TILED_STAGED):
+    for kern in (f.KERNEL_TWO_PHASE, f.KERNEL_PERSISTENT, f.KERNEL_TILED, f.KERNEL_TILED_STAGED,
+                 f.KERNEL_TILED_REP):
         s = _solver(p, kernel=kern)
         try:
             s.step(dt, 400)
@@ -108,7 +109,7 @@ def test_range_violation_stops_every_kernel_at_the_same_step():
 def test_barrier_timeout_is_reported_and_the_context_recovers():
     f = ff()
     p = cube_hex_td_convective(n=24).problem
-    for kern in (f.KERNEL_PERSISTENT, f.KERNEL_TILED):
+    for kern in (f.KERNEL_PERSISTENT, f.KERNEL_TILED, f.KERNEL_TILED_REP):
         s = _solver(p, kernel=kern)
         try:
             dt = 0.5 * s.dt_cr

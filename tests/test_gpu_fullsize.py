@@ -54,7 +54,7 @@ def ellipsoid():
 
 def _kernels():
     f = ff()
-    return [(f.KERNEL_PERSISTENT, 0), (f.KERNEL_TILED, 0), (f.KERNEL_TILED_STAGED, 384)]
+    return [(f.KERNEL_PERSISTENT, 0), (f.KERNEL_TILED, 0), (f.KERNEL_TILED_STAGED, 384), (f.KERNEL_TILED_REP, 512)]
 
 
 def test_cube128_sampled_oracle_parity(cube128):
@@ -111,7 +111,7 @@ def test_ellipsoid_sampled_oracle_parity(ellipsoid):
     ref = sampled_run(p, dt, n, samples)
     f = ff()
     for prec, tol in ((f.FP64, TOL64), (f.FP32_KAHAN, TOL32)):
-        for kern, B in ((f.KERNEL_PERSISTENT, 0), (f.KERNEL_TILED, 0)):
+        for kern, B in ((f.KERNEL_PERSISTENT, 0), (f.KERNEL_TILED, 0), (f.KERNEL_TILED_REP, 0)):
             T, _ = _run(p, dt, n, prec, kern, T0=p.T0, tile_nodes=B)
             err = max_abs(T[samples], ref)
             print(f"ellipsoid prec {prec} kernel {kern}: sampled max|dT| = {err:.3e}")

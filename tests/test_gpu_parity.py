@@ -54,7 +54,8 @@ def test_every_kernel_and_order_is_bit_identical(cube):
     for prec in (f.FP64, f.FP32_KAHAN):
         base, _ = run_gpu(w.problem, dt, 300, prec, order=f.ORDER_MORTON, kernel=f.KERNEL_PERSISTENT)
         for order in (f.ORDER_INPUT, f.ORDER_MORTON, f.ORDER_RCM):
-            for kernel in (f.KERNEL_TWO_PHASE, f.KERNEL_PERSISTENT, f.KERNEL_TILED, f.KERNEL_TILED_STAGED):
+            for kernel in (f.KERNEL_TWO_PHASE, f.KERNEL_PERSISTENT, f.KERNEL_TILED, f.KERNEL_TILED_STAGED,
+                           f.KERNEL_TILED_REP):
                 T, _ = run_gpu(w.problem, dt, 300, prec, order=order, kernel=kernel)
                 assert np.array_equal(T, base), (prec, order, kernel)
 
@@ -72,11 +73,14 @@ def test_tiled_kernel_odd_even_steps_and_tets(n_steps):
         base, _ = run_gpu(p, dt, n_steps, f.FP32_KAHAN, kernel=f.KERNEL_PERSISTENT)
         # hex tiles larger than the block (threads own two nodes); tets (about 24
         # elements per node) with smaller tiles so that the load table fits
-        big = ((f.KERNEL_TILED_STAGED, 0, 1000), (f.KERNEL_TILED_STAGED, 1024, 1280)) if p.elem_type == 8 else \
-              ((f.KERNEL_TILED_STAGED, 1024, 200),)
+        big = ((f.KERNEL_TILED_STAGED, 0, 1000), (f.KERNEL_TILED_STAGED, 1024, 1280),
+               (f.KERNEL_TILED_REP, 0, 512)) if p.elem_type == 8 else \
+              ((f.KERNEL_TILED_STAGED, 1024, 200), (f.KERNEL_TILED_REP, 256, 128))
+        # the replicated-row kernel: default tiles, tiles smaller than the block, 256 threads
+        rep = ((f.KERNEL_TILED_REP, 0, 0), (f.KERNEL_TILED_REP, 0, 96), (f.KERNEL_TILED_REP, 256, 72))
         for kern, blk, B in ((f.KERNEL_TILED, 0, 0), (f.KERNEL_TILED, 0, 64), (f.KERNEL_TILED, 0, 160),
                              (f.KERNEL_TILED_STAGED, 0, 0), (f.KERNEL_TILED_STAGED, 0, 96),
-                             (f.KERNEL_TILED_STAGED, 256, 72)) + big:
+                             (f.KERNEL_TILED_STAGED, 256, 72)) + rep + big:
             s = f.Solver(p, precision=f.FP32_KAHAN)
             try:
                 f.fedfem_set_tile(s.ctx, kern, blk, B, 0)
@@ -125,7 +129,8 @@ def test_uniform_field_bit_unchanged_on_gpu():
     p.conv_T_inf = 37.0
     f = ff()
     for prec in (f.FP64, f.FP32_KAHAN, f.FP32_PLAIN):
-        for kernel in (f.KERNEL_TWO_PHASE, f.KERNEL_PERSISTENT, f.KERNEL_TILED, f.KERNEL_TILED_STAGED):
+        for kernel in (f.KERNEL_TWO_PHASE, f.KERNEL_PERSISTENT, f.KERNEL_TILED, f.KERNEL_TILED_STAGED,
+                       f.KERNEL_TILED_REP):
             T, _ = run_gpu(p, 1.0, 200, prec, kernel=kernel)
             assert np.all(T == 37.0), (prec, kernel)
 
