@@ -100,7 +100,8 @@ typedef struct {
     int kernel;        /* FEDFEM_KERNEL_* */
     int block;         /* threads per block: 64..1024, multiple of 32 (0 = default); the
                           staged tiled kernel is built for 256, 512 (default) and 1024, the
-                          replicated-row kernel for 256 and 512 (default) */
+                          replicated-row kernel for 128, 256 and 512 (default 512 for hex8 and
+                          256 for tet4, halved in FP64) */
     int tile_nodes;    /* TILED: owned nodes per tile, multiple of 8 (0 = default: the library
                           picks a size near 512 (hex) / 256 (tet), smaller when such tiles
                           do not fit in shared memory, that gives every resident block the

@@ -385,9 +385,15 @@ size_t tile_smem(const Tiles& t, size_t rs, size_t ls, int* max_block, int kind,
 }
 
 // threads per block of the staged kernels: the block knob if it names a built
-// size (the replicated-row kernel: 256 or 512)
+// size.  The replicated-row kernel is built for 128, 256 and 512; its rows have
+// one entry per thread, so its default shrinks with the rows' size: 512 for
+// hex8 (8 rows), 256 for tet4 (up to 32 rows), halved in FP64.
 int staged_threads(const fedfem_ctx* c) {
-    if (c->tile.kernel == FEDFEM_KERNEL_TILED_REP) return c->tile.block == 256 ? 256 : tiled_threads();
+    if (c->tile.kernel == FEDFEM_KERNEL_TILED_REP) {
+        if (c->tile.block == 128 || c->tile.block == 256 || c->tile.block == 512) return c->tile.block;
+        const int d = c->nv == 8 ? 512 : 256;
+        return c->precision == FEDFEM_FP64 ? d / 2 : d;
+    }
     return c->tile.block == 256 || c->tile.block == 1024 ? c->tile.block : tiled_threads();
 }
 

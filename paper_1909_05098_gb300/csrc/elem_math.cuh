@@ -8,13 +8,13 @@
 //    A = G^T M G with M = V_tet E^-1 E^-T.
 //
 // M is symmetric: stored as m00 m11 m22 m01 m02 m12.  G T is formed from
-// differences of nodal temperatures only (G 1 = 0, so this is the same
-// product; a uniform field gives exactly zero load).  For the hexahedron each
-// gradient component is the sum of the four edge differences along that
-// natural direction.  k_e is the mean of the nodal k(T_n) (Eq. 13).  Every
-// kernel variant calls these functions; fused multiply-adds are written out
-// explicitly and the library is built without automatic contraction, so all
-// variants round alike.
+// differences of nodal temperatures, or of equally grouped sums of them (G 1 =
+// 0, so this is the same product; a uniform field gives exactly zero load).
+// k_e is the mean of the nodal k(T_n) (Eq. 13).  Every kernel variant calls
+// these functions; fused multiply-adds are written out explicitly and the
+// library is built without automatic contraction, so all variants round
+// alike.  FP32 work on pairs of values uses the packed f32x2 instructions,
+// whose lanes round exactly as the scalar instructions do.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -24,16 +24,54 @@ namespace fedfem {
 template <typename R>
 __device__ __forceinline__ R fmadd(R a, R b, R c) { return fma(a, b, c); }
 
+// Packed FP32 pairs: one f32x2 instruction (Blackwell) computes both lanes,
+// each rounded to nearest exactly as the scalar instruction rounds it, so a
+// packed computation gives the same bits as the scalar one in the same order.
+__device__ __forceinline__ unsigned long long pack2(float2 a) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y));
+    return r;
+}
+__device__ __forceinline__ float2 unpack2(unsigned long long r) {
+    float2 a;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(r));
+    return a;
+}
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+    unsigned long long r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pack2(a)), "l"(pack2(b)));
+    return unpack2(r);
+}
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pack2(a)), "l"(pack2(b)));
+    return unpack2(r);
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+    unsigned long long r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pack2(a)), "l"(pack2(b)));
+    return unpack2(r);
+}
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {   // a * b + c, one rounding
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(pack2(a)), "l"(pack2(b)), "l"(pack2(c)));
+    return unpack2(r);
+}
+
 // Four independent problems (scenario lanes) that share a mesh: every
 // operation acts on each lane exactly as the scalar code acts on one problem,
-// so a lane's result is bit-identical to running that problem alone.
+// so a lane's result is bit-identical to running that problem alone.  The
+// lanes go through the packed instructions two at a time.
 struct __align__(16) F4 {
     float x, y, z, w;
 };
 __device__ __forceinline__ F4 f4(float v) { return F4{v, v, v, v}; }
-__device__ __forceinline__ F4 operator+(F4 a, F4 b) { return F4{a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w}; }
-__device__ __forceinline__ F4 operator-(F4 a, F4 b) { return F4{a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w}; }
-__device__ __forceinline__ F4 operator*(F4 a, F4 b) { return F4{a.x * b.x, a.y * b.y, a.z * b.z, a.w * b.w}; }
+__device__ __forceinline__ F4 join(float2 a, float2 b) { return F4{a.x, a.y, b.x, b.y}; }
+__device__ __forceinline__ float2 lo2(F4 a) { return make_float2(a.x, a.y); }
+__device__ __forceinline__ float2 hi2(F4 a) { return make_float2(a.z, a.w); }
+__device__ __forceinline__ F4 operator+(F4 a, F4 b) { return join(add2(lo2(a), lo2(b)), add2(hi2(a), hi2(b))); }
+__device__ __forceinline__ F4 operator-(F4 a, F4 b) { return join(sub2(lo2(a), lo2(b)), sub2(hi2(a), hi2(b))); }
+__device__ __forceinline__ F4 operator*(F4 a, F4 b) { return join(mul2(lo2(a), lo2(b)), mul2(hi2(a), hi2(b))); }
 __device__ __forceinline__ F4 operator/(F4 a, F4 b) { return F4{a.x / b.x, a.y / b.y, a.z / b.z, a.w / b.w}; }
 
 // the explicit increment's quotient r / C: FP64 state divides exactly (IEEE);
@@ -50,7 +88,7 @@ __device__ __forceinline__ F4 operator-(F4 a, float b) { return a - f4(b); }
 __device__ __forceinline__ F4 operator-(float a, F4 b) { return f4(a) - b; }
 __device__ __forceinline__ F4 operator*(float a, F4 b) { return f4(a) * b; }
 __device__ __forceinline__ F4 fmadd(F4 a, F4 b, F4 c) {
-    return F4{fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y), fmaf(a.z, b.z, c.z), fmaf(a.w, b.w, c.w)};
+    return join(fma2(lo2(a), lo2(b), lo2(c)), fma2(hi2(a), hi2(b), hi2(c)));
 }
 __device__ __forceinline__ F4 fmadd(float a, F4 b, F4 c) { return fmadd(f4(a), b, c); }
 __device__ __forceinline__ F4 fmadd(float a, F4 b, float c) { return fmadd(f4(a), b, f4(c)); }
@@ -69,15 +107,39 @@ struct Law {           // p(T) = p0 + dp (T - T_ref)
     __device__ __forceinline__ L at(L T) const { return fmadd(dp, T - T_ref, p0); }
 };
 
+// hex8 gradient g = sum_n s_n T_n, corner signs (x,y,z): 0(-,-,-) 1(+,-,-)
+// 2(+,+,-) 3(-,+,-) 4(-,-,+) 5(+,-,+) 6(+,+,+) 7(-,+,+).  With the x-pair sums
+// a = (t0 + t3, t1 + t2) and b = (t4 + t7, t5 + t6):
+//   gx = (a.y + b.y) - (a.x + b.x),
+//   gy = ((t3 - t0) + (t7 - t4)) + ((t2 - t1) + (t6 - t5)),
+//   gz = (b.x - a.x) + (b.y - a.y);
+// every term is a difference of equally grouped sums, so a uniform field
+// gives exactly zero.  FP32 computes the pairs with f32x2 instructions.
+template <typename L>
+__device__ __forceinline__ void hex8_gradient(const L t[8], L& gx, L& gy, L& gz) {
+    const L ax = t[0] + t[3], ay = t[1] + t[2], bx = t[4] + t[7], by = t[5] + t[6];
+    gx = (ay + by) - (ax + bx);
+    gy = ((t[3] - t[0]) + (t[7] - t[4])) + ((t[2] - t[1]) + (t[6] - t[5]));
+    gz = (bx - ax) + (by - ay);
+}
+template <>
+__device__ __forceinline__ void hex8_gradient<float>(const float t[8], float& gx, float& gy, float& gz) {
+    const float2 p01 = make_float2(t[0], t[1]), p32 = make_float2(t[3], t[2]);
+    const float2 p45 = make_float2(t[4], t[5]), p76 = make_float2(t[7], t[6]);
+    const float2 a = add2(p01, p32), b = add2(p45, p76);
+    const float2 w = add2(a, b), v = sub2(b, a);
+    const float2 u = add2(sub2(p32, p01), sub2(p76, p45));
+    gx = w.y - w.x;
+    gy = u.x + u.y;
+    gz = v.x + v.y;
+}
+
 // hex8: t[8] nodal temperatures, m[6], k_e already formed -> F[8]
 // (R: element-matrix type; L: temperature type, R itself or F4 lanes)
 template <typename R, typename L = R>
 __device__ __forceinline__ void hex8_loads(const L t[8], const R m[6], L ke, L F[8]) {
-    // corner signs (x,y,z): 0(-,-,-) 1(+,-,-) 2(+,+,-) 3(-,+,-) 4(-,-,+) 5(+,-,+) 6(+,+,+) 7(-,+,+);
-    // g = sum_n s_n T_n, grouped as edge differences
-    const L gx = ((t[1] - t[0]) + (t[2] - t[3])) + ((t[5] - t[4]) + (t[6] - t[7]));
-    const L gy = ((t[3] - t[0]) + (t[2] - t[1])) + ((t[7] - t[4]) + (t[6] - t[5]));
-    const L gz = ((t[4] - t[0]) + (t[5] - t[1])) + ((t[6] - t[2]) + (t[7] - t[3]));
+    L gx, gy, gz;
+    hex8_gradient<L>(t, gx, gy, gz);
     const L qx = ke * fmadd(m[0], gx, fmadd(m[3], gy, m[4] * gz));
     const L qy = ke * fmadd(m[3], gx, fmadd(m[1], gy, m[5] * gz));
     const L qz = ke * fmadd(m[4], gx, fmadd(m[5], gy, m[2] * gz));
@@ -97,13 +159,38 @@ __device__ __forceinline__ void tet4_loads(const L t[4], const R m[6], L ke, L F
     F[1] = q0; F[2] = q1; F[3] = q2;
 }
 
-// k_e of Eq. 13: mean over the element's nodes of k(T_n)  (K: a law with at())
+// k_e of Eq. 13: mean over the element's nodes of k(T_n)  (K: a law with at()).
+// The nodal values are summed as ((k0 + k3) + (k4 + k7)) + ((k1 + k2) + (k5 + k6))
+// (hex8) or (k0 + k2) + (k1 + k3) (tet4), the pair order of the packed FP32 path.
+template <int NV, typename L>
+__device__ __forceinline__ L sum_nodal(const L k[NV]) {
+    if constexpr (NV == 8) return ((k[0] + k[3]) + (k[4] + k[7])) + ((k[1] + k[2]) + (k[5] + k[6]));
+    else return (k[0] + k[2]) + (k[1] + k[3]);
+}
 template <typename R, int NV, typename L = R, typename K>
 __device__ __forceinline__ L element_k(const L t[NV], const K& k) {
-    L s = k.at(t[0]);
+    L kn[NV];
 #pragma unroll
-    for (int n = 1; n < NV; ++n) s = s + k.at(t[n]);
-    return R(1) / R(NV) * s;
+    for (int n = 0; n < NV; ++n) kn[n] = k.at(t[n]);
+    return R(1) / R(NV) * sum_nodal<NV, L>(kn);
+}
+// a linear law on FP32 temperatures: k(T) of two nodes per instruction
+template <typename R, int NV, typename L = R>
+__device__ __forceinline__ float element_k(const float t[NV], const Law<float>& k) {
+    const float2 tr = make_float2(k.T_ref, k.T_ref), dp = make_float2(k.dp, k.dp), p0 = make_float2(k.p0, k.p0);
+    if constexpr (NV == 8) {
+        const float2 k01 = fma2(dp, sub2(make_float2(t[0], t[1]), tr), p0);
+        const float2 k32 = fma2(dp, sub2(make_float2(t[3], t[2]), tr), p0);
+        const float2 k45 = fma2(dp, sub2(make_float2(t[4], t[5]), tr), p0);
+        const float2 k76 = fma2(dp, sub2(make_float2(t[7], t[6]), tr), p0);
+        const float2 s = add2(add2(k01, k32), add2(k45, k76));
+        return 0.125f * (s.x + s.y);
+    } else {
+        const float2 k01 = fma2(dp, sub2(make_float2(t[0], t[1]), tr), p0);
+        const float2 k23 = fma2(dp, sub2(make_float2(t[2], t[3]), tr), p0);
+        const float2 s = add2(k01, k23);
+        return 0.25f * (s.x + s.y);
+    }
 }
 
 }  // namespace fedfem

@@ -901,17 +901,15 @@ __global__ void __launch_bounds__(TPB, StagedOccupancy<L, TPB>::min_blocks)
         }
         if (buf) pend1 = true; else pend0 = true;
     };
-    // (a copy whose wait gave up stays pending, so that the drain at exit waits for it again)
+    // every thread waits for stage buf's copy itself (no block barrier); false when its bounded
+    // wait gave up: the copy then stays pending (the drain at exit waits for it again), the
+    // thread skips what would read the stage, and the block agrees to stop at its next barrier
     auto land = [&](int buf) -> bool {
-        bool ok = true;
-        const bool pend = buf ? pend1 : pend0;
-        if (pend && threadIdx.x == 0) ok = mbar_wait(&bar[buf], buf ? ph1 : ph0, spin_limit);
-        const bool failed = __syncthreads_or(!ok) != 0;
-        if (pend && !failed) {
-            if (buf) { ph1 ^= 1u; pend1 = false; }
-            else { ph0 ^= 1u; pend0 = false; }
-        }
-        return !failed;
+        if (!(buf ? pend1 : pend0)) return true;
+        if (!mbar_wait(&bar[buf], buf ? ph1 : ph0, spin_limit)) return false;
+        if (buf) { ph1 ^= 1u; pend1 = false; }
+        else { ph0 ^= 1u; pend0 = false; }
+        return true;
     };
     auto fail_timeout = [&]() {
         if (threadIdx.x == 0) atomicOr(&a.status->flags, STATUS_TIMEOUT);
@@ -926,11 +924,11 @@ __global__ void __launch_bounds__(TPB, StagedOccupancy<L, TPB>::min_blocks)
         for (int h = threadIdx.x; h < v.nh; h += TPB) cp_async<sizeof(L)>(Thalo + h, Tin + v.halo[h]);
         cp_async_commit();
     };
-    bool stop = false;
+    bool stop = false, failed = false;
     if (total > 0) {
         for (int p = 0; p < 2 && p < n_my; ++p) issue(p, p);
-        if (!land(0)) { fail_timeout(); stop = true; }
-        else fetch(0, 0, a.T);
+        if (land(0)) fetch(0, 0, a.T);
+        else failed = true;
     }
     long long kk = 0;
     for (long long s = 0; s < n_steps && !stop; ++s) {
@@ -953,14 +951,14 @@ __global__ void __launch_bounds__(TPB, StagedOccupancy<L, TPB>::min_blocks)
                     if (r < deg) T0row[r * S + l] = T0;
                 v0 = node_load<R, L, MODE>(a, base + l);
             }
-            __syncthreads();   // Tr of this tile complete; Fr clear
+            if (__syncthreads_or(failed)) { fail_timeout(); stop = true; break; }   // Tr complete; Fr clear
             with_k_laws<MODE>(a, tile_regions<MODE>(a, t), [&](const auto& kl) {
                 rep_elements_k<R, L, NV, TPB>(kl, v, Tr, Fr);
             });
             __syncthreads();   // loads complete; this stage and Tr are free
-            if (i + 1 < n_my) {
-                if (!land(buf_of(kk + 1, i + 1))) { fail_timeout(); stop = true; break; }
-                fetch(kk + 1, i + 1, Tin);
+            if (i + 1 < n_my) {   // the next tile of this step: its stage, then its temperatures
+                if (land(buf_of(kk + 1, i + 1))) fetch(kk + 1, i + 1, Tin);
+                else failed = true;
             }
             if (!resident && kk + 2 < total) issue(kk + 2, i + 2 < n_my ? i + 2 : i + 2 - n_my);
             if (l < own) {   // node phase: column l in rank order, cleared for the next tile
@@ -979,12 +977,14 @@ __global__ void __launch_bounds__(TPB, StagedOccupancy<L, TPB>::min_blocks)
         const bool ok = grid_barrier(a.status, target, spin_limit);
         done = s + 1;
         if (!ok) break;
-        if (s + 1 < n_steps && n_my > 0) {
-            if (!land(buf_of(kk, 0))) { fail_timeout(); break; }
-            fetch(kk, 0, Tout);
+        if (s + 1 < n_steps && n_my > 0) {   // the first tile of the next step reads this step's result
+            if (land(buf_of(kk, 0))) fetch(kk, 0, Tout);
+            else failed = true;
         }
     }
     cp_async_wait_all();
+    if (failed && !stop) fail_timeout();   // a wait after the last tile gave up
+    // copies nobody consumed (early stop): let them land before the block exits
     if (threadIdx.x == 0) {
         if (pend0) mbar_wait(&bar[0], ph0, spin_limit);
         if (pend1) mbar_wait(&bar[1], ph1, spin_limit);
@@ -1002,7 +1002,10 @@ __global__ void __launch_bounds__(TPB, StagedOccupancy<L, TPB>::min_blocks)
 template <typename R, typename L, int NV, int MODE>
 auto tiled_kernel(const TileArgs<R>& ta) {
     if constexpr (sizeof(L) == sizeof(R)) {   // one lane: the replicated rows would not fit four
-        if (ta.rep) return ta.threads == 256 ? k_tiled_rep<R, L, NV, MODE, 256> : k_tiled_rep<R, L, NV, MODE, kTiledThreads>;
+        if (ta.rep)
+            return ta.threads == 128   ? k_tiled_rep<R, L, NV, MODE, 128>
+                   : ta.threads == 256 ? k_tiled_rep<R, L, NV, MODE, 256>
+                                       : k_tiled_rep<R, L, NV, MODE, kTiledThreads>;
     }
     return !ta.staged           ? k_tiled_direct<R, L, NV, MODE>
            : ta.threads == 256  ? k_tiled<R, L, NV, MODE, 256>

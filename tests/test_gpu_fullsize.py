@@ -52,9 +52,12 @@ def ellipsoid():
     return w, dt
 
 
-def _kernels():
+def _kernels(prec=None):
+    """Kernel and tile size pairs; the replicated-row kernel with the bench's
+    512-node tiles in FP32 (its FP64 build has 256-thread rows: default tiles)."""
     f = ff()
-    return [(f.KERNEL_PERSISTENT, 0), (f.KERNEL_TILED, 0), (f.KERNEL_TILED_STAGED, 384), (f.KERNEL_TILED_REP, 512)]
+    rep_B = 0 if prec == f.FP64 else 512
+    return [(f.KERNEL_PERSISTENT, 0), (f.KERNEL_TILED, 0), (f.KERNEL_TILED_STAGED, 384), (f.KERNEL_TILED_REP, rep_B)]
 
 
 def test_cube128_sampled_oracle_parity(cube128):
@@ -70,7 +73,7 @@ def test_cube128_sampled_oracle_parity(cube128):
     ref = sampled_run(p, dt, n, samples)
     f = ff()
     for prec, tol in ((f.FP64, TOL64), (f.FP32_KAHAN, TOL32)):
-        for kern, B in _kernels():
+        for kern, B in _kernels(prec):
             T, info = _run(p, dt, n, prec, kern, T0=p.T0, tile_nodes=B)
             err = max_abs(T[samples], ref)
             print(f"cube128 prec {prec} kernel {kern}: sampled max|dT| = {err:.3e}")
@@ -95,7 +98,7 @@ def test_cube128_uniform_field_bit_unchanged(cube128):
     p.sources = []
     p.conv_T_inf = 37.0
     f = ff()
-    for kern, B in _kernels():
+    for kern, B in _kernels(f.FP32_KAHAN):
         T, _ = _run(p, dt, 50, f.FP32_KAHAN, kern, tile_nodes=B)
         assert np.all(T == 37.0), kern
 
