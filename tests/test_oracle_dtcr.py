@@ -125,3 +125,31 @@ def test_uniform_lumping_shifts_the_cube_spectrum_by_a_constant():
     share = (10 * h) ** 3 / 11 ** 3
     lam = 4 * alpha / h ** 2 * S.max() + pf.w_b * pf.c_b * share / (m.rho0 * m.c0 * h ** 3)
     assert critical_dt(p) == pytest.approx(2.0 / lam, rel=1e-10)
+
+
+@pytest.mark.parametrize("n", [3, 5, 8, 11])
+def test_box_spectrum_equals_dense_eigenvalue(n):
+    """Separation of variables (sine modes in x and y, a tridiagonal problem in
+    z) gives the same lambda_max as the dense eigenvalue solver on the
+    assembled matrices of the film-topped, five-face-Dirichlet hex box."""
+    from oracle.box_spectrum import critical_dt_hex_box
+    from synth.scenarios import cube_hex_td_convective
+    p = cube_hex_td_convective(n=n).problem
+    assert critical_dt_hex_box(p, n, 1e-3) == pytest.approx(critical_dt(p), rel=1e-12)
+
+
+def test_box_spectrum_without_film_or_perfusion_approaches_the_symbol_maximum():
+    """Without film or perfusion the largest eigenvalue grows with n towards
+    the one-point hex symbol's supremum 4 alpha / h^2 (the symbol
+    (4 alpha / h^2) sum_d sin^2(theta_d / 2) prod_{d' != d} cos^2(theta_d' / 2)
+    reaches 1 at theta = (pi, 0, 0), which the Dirichlet box never quite
+    samples), staying below it."""
+    from oracle.box_spectrum import lambda_max_hex_box
+    k0, rc, h = 0.5, 4.0e6, 1e-3
+    top = 4.0 * k0 / rc / h ** 2
+    prev = 0.0
+    for n in (8, 16, 32, 64):
+        lam = lambda_max_hex_box(n, h, k0, rc, 0.0, 0.0)
+        assert prev < lam < top
+        prev = lam
+    assert prev > 0.99 * top
