@@ -6,7 +6,10 @@ the unit cube, exact gradient energy for affine fields, and the hourglass
 null-space of the one-point hexahedron; the fully integrated hexahedron
 (2 x 2 x 2 Gauss points) against the textbook unit-cube matrix, exact
 energies and volumes of distorted elements, and a null space of constants
-only.
+only; the hourglass-stabilised one-point hexahedron against the plain rule
+at zero strength, linear fields left with exactly the one-point energy on
+distorted elements, the closed-form hourglass energy 3 eps h on a cube, and
+a null space of constants only.
 """
 from __future__ import annotations
 
@@ -64,6 +67,38 @@ def hex8_full(xe: np.ndarray):
     return A, dmin, V
 
 
+# The four hourglass patterns of the hexahedron: products of the corner signs
+# (s_x s_y, s_y s_z, s_z s_x, s_x s_y s_z), orthogonal to the constant and to
+# each s_d; the one-point rule gives them no energy.
+HEX8_HOURGLASS = np.stack([HEX8_NATURAL[:, 0] * HEX8_NATURAL[:, 1], HEX8_NATURAL[:, 1] * HEX8_NATURAL[:, 2],
+                           HEX8_NATURAL[:, 2] * HEX8_NATURAL[:, 0],
+                           HEX8_NATURAL[:, 0] * HEX8_NATURAL[:, 1] * HEX8_NATURAL[:, 2]])   # (4, 8)
+
+
+def hex8_hourglass(xe: np.ndarray, eps: float):
+    """One-point hexahedron with hourglass stabilisation (the paper keeps
+    Eq. 14 and defers hourglass control to another work).  The hourglass
+    vectors are made blind to linear fields,
+        gamma_a = h_a - sum_i (h_a . x_i) b_i,
+    with x_i the corners' i-th coordinates and b_i the i-th row of the
+    one-point B (Eq. 14), so that gamma_a . T = 0 for every T linear in x
+    (b_i . x_j = delta_ij); then
+        A = A_1pt + c sum_a gamma_a gamma_a^T,  c = eps trace(A_1pt) / 32,
+    so that on a parallelepiped (gamma_a = h_a, |h_a|^2 = 8) the added
+    matrix has eps times the trace of the one-point matrix.  Constant and
+    linear fields keep exactly the one-point energy; the four hourglass modes
+    get a positive one.  Returns (A, det J, V_e) like hex8_reduced."""
+    A1, detJ, V = hex8_reduced(xe)
+    dN = hex8_dN_dxi_centre()                                   # (3, 8)
+    J = np.einsum("...ni,jn->...ij", xe, dN)
+    B = np.einsum("...ji,jn->...in", np.linalg.inv(J), dN)     # (..., 3, 8): b_i rows
+    hx = np.einsum("an,...ni->...ai", HEX8_HOURGLASS, xe)        # (..., 4, 3): h_a . x_i
+    gamma = HEX8_HOURGLASS - np.einsum("...ai,...in->...an", hx, B)   # (..., 4, 8)
+    c = eps * np.trace(A1, axis1=-2, axis2=-1) / 32.0
+    A = A1 + c[..., None, None] * np.einsum("...an,...am->...nm", gamma, gamma)
+    return A, detJ, V
+
+
 def tet4_linear(xe: np.ndarray):
     """Linear tetrahedron, Eq. 15 and Eq. 16.
 
@@ -80,15 +115,19 @@ def tet4_linear(xe: np.ndarray):
     return A, detE, V
 
 
-def element_matrices(elem_type: int, xyz: np.ndarray, conn: np.ndarray, hex_rule: str = "one-point"):
+def element_matrices(elem_type: int, xyz: np.ndarray, conn: np.ndarray, hex_rule: str = "one-point",
+                     hourglass_eps: float = 0.0):
     """A_e, the orientation determinant and V_e for every element of a mesh
-    (hex_rule: "one-point", Eq. 14, or "full", 2 x 2 x 2 Gauss points).
+    (hex_rule: "one-point", Eq. 14; "full", 2 x 2 x 2 Gauss points; or
+    "hourglass", the one-point rule with hourglass stabilisation hourglass_eps).
 
     Raises ValueError for an element with det <= 0 (inverted or degenerate),
     which the method cannot use (Algorithm 1, pre-computation)."""
     xe = xyz[conn]
     if elem_type == 8 and hex_rule == "full":
         A, det, V = hex8_full(xe)
+    elif elem_type == 8 and hex_rule == "hourglass":
+        A, det, V = hex8_hourglass(xe, hourglass_eps)
     elif elem_type == 8:
         A, det, V = hex8_reduced(xe)
     elif elem_type == 4:

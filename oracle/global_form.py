@@ -96,7 +96,8 @@ class Oracle:
         self.N = N
         self.conn = np.asarray(p.conn, dtype=np.int64)
         self.A_e, self.det_e, self.V_e = element_matrices(p.elem_type, p.xyz, self.conn,
-                                                          getattr(p, "hex_rule", "one-point"))
+                                                          getattr(p, "hex_rule", "one-point"),
+                                                          getattr(p, "hourglass_eps", 0.0))
         self.V = lumped_volumes(self.conn, self.V_e, N)
         self.hA = p.conv_h * lumped_face_areas(p.xyz, np.asarray(p.conv_faces, dtype=np.int64), N)
         lumping = getattr(p, "lumping", "element")

@@ -113,8 +113,10 @@ class Problem:
     regions: Optional[np.ndarray] = None
     region_materials: tuple = ()
     region_perfusion: tuple = ()
-    # hex8 integration: "one-point" (Eq. 14, the paper's) or "full" (2 x 2 x 2 Gauss)
+    # hex8 integration: "one-point" (Eq. 14, the paper's), "full" (2 x 2 x 2 Gauss) or
+    # "hourglass" (one point plus hourglass stabilisation of strength hourglass_eps)
     hex_rule: str = "one-point"
+    hourglass_eps: float = 0.0
     # perfusion and metabolic heat per node: "element" (V_e / nv shares, as C)
     # or "uniform" (V / N for every node, the paper's verification runs)
     lumping: str = "element"

@@ -167,3 +167,55 @@ def test_full_hex_kirchhoff_bar_is_unchanged():
     target = u(37.0) + (u(65.0) - u(37.0)) * m.grid_index[:, 0] / n
     expect = 37.0 + (-mat.k0 + np.sqrt(mat.k0 ** 2 + 2 * mat.dk * target)) / mat.dk
     np.testing.assert_allclose(T, expect, rtol=0, atol=1e-10)
+
+
+# --- hourglass-stabilised one-point hexahedron ---------------------------------
+
+def _distorted_hex(seed):
+    from oracle.elements import HEX8_NATURAL
+    rng = np.random.default_rng(seed)
+    return 0.5e-3 * (HEX8_NATURAL + 1.0) + rng.uniform(-0.12e-3, 0.12e-3, (8, 3))
+
+
+def test_hourglass_strength_zero_is_the_one_point_rule():
+    from oracle.elements import hex8_hourglass, hex8_reduced
+    xe = _distorted_hex(1)
+    assert np.array_equal(hex8_hourglass(xe, 0.0)[0], hex8_reduced(xe)[0])
+
+
+def test_hourglass_term_leaves_linear_fields_alone_on_distorted_hexes():
+    """gamma_a is orthogonal to every linear field, so A T = A_1pt T for
+    T = a + b . x on any element (the patch test the one-point rule passes)."""
+    from oracle.elements import hex8_hourglass, hex8_reduced
+    rng = np.random.default_rng(2)
+    for seed in range(5):
+        xe = _distorted_hex(seed)
+        A, _, _ = hex8_hourglass(xe, 0.3)
+        A1, _, _ = hex8_reduced(xe)
+        for _ in range(3):
+            T = rng.normal() + xe @ rng.normal(size=3) * 1e3
+            np.testing.assert_allclose(A @ T, A1 @ T, rtol=0, atol=1e-13 * np.abs(A).max() * np.abs(T).max())
+        np.testing.assert_allclose(A.sum(axis=1), 0.0, atol=1e-15 * np.abs(A).max())
+
+
+def test_hourglass_energy_on_a_cube_is_three_eps_h():
+    """Cube of edge h: A_1pt = (h/16) sum_d s_d s_d^T has trace 3h/2, so
+    c = eps (3h/2) / 32; each hourglass pattern h_a has gamma_a = h_a and
+    h_a . h_a = 8, giving the energy c * 64 = 3 eps h; different patterns do
+    not couple, and the one-point part gives them nothing."""
+    from oracle.elements import HEX8_HOURGLASS, HEX8_NATURAL, hex8_hourglass
+    h, eps = 2e-3, 0.25
+    xe = 0.5 * h * (HEX8_NATURAL + 1.0)
+    A, _, _ = hex8_hourglass(xe, eps)
+    E = HEX8_HOURGLASS @ A @ HEX8_HOURGLASS.T
+    np.testing.assert_allclose(E, 3 * eps * h * np.eye(4), rtol=1e-13, atol=1e-18)
+
+
+def test_hourglass_element_null_space_is_constants_only():
+    from oracle.elements import hex8_hourglass, hex8_reduced
+    for seed in range(4):
+        xe = _distorted_hex(10 + seed)
+        w = np.linalg.eigvalsh(hex8_hourglass(xe, 0.1)[0])
+        w1 = np.linalg.eigvalsh(hex8_reduced(xe)[0])
+        assert abs(w[0]) < 1e-12 * w[-1] and w[1] > 1e-6 * w[-1]    # one zero: the constant
+        assert np.sum(np.abs(w1) < 1e-12 * w1[-1]) == 5                # the plain rule: constant + 4 hourglass
