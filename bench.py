@@ -389,15 +389,19 @@ def run_ours(args):
     w = cube_hex_td_convective(n=args.n)
     p = w.problem
     stream = torch.cuda.Stream(device=dev)
-    solver = ff.Solver(p, precision=ff.FP32_KAHAN, device=local, stream=stream.cuda_stream,
-                       kernel=ff.KERNEL_PERSISTENT)
-    dt = 0.5 * solver.dt_cr
+    def make_solver(order):
+        return ff.Solver(p, precision=ff.FP32_KAHAN, device=local, stream=stream.cuda_stream,
+                         kernel=ff.KERNEL_PERSISTENT, order=order)
+
     tuned = None
-    if args.kernel == "auto":
-        from paper_1909_05098_gb300.autotune import tune
-        tuned = tune(solver, dt, use_cache=False, stream=stream)
+    if args.kernel == "auto":   # kernel, block, tile size and element order (Morton or RCM)
+        from paper_1909_05098_gb300.autotune import tune_order
+        solver, tuned = tune_order(make_solver, lambda sv: 0.5 * sv.dt_cr, use_cache=False, stream=stream)
+        dt = 0.5 * solver.dt_cr
         kernel = tuned["kernel"]
     else:
+        solver = make_solver(ff.ORDER_MORTON)
+        dt = 0.5 * solver.dt_cr
         kernel = {v: k for k, v in names.items()}[args.kernel]
         ff.fedfem_set_tile(solver.ctx, kernel, args.block, args.tile_nodes, 0)
     solver.step(dt, 1)      # plans tiles if needed
@@ -481,9 +485,10 @@ def run_ours(args):
                    "time_steps_per_bench_step": S, "kernel": names[kernel],
                    "tile_nodes": info["tile_nodes"], "grid_blocks": info["grid_blocks"],
                    "autotune": None if tuned is None else
-                   {names[t["kernel"]] + (f"/{t['tile_nodes']}" if t["tile_nodes"] else "") +
-                    (f"x{t['block']}" if t.get("block") else ""):
+                   {("rcm:" if t.get("order") == ff.ORDER_RCM else "") + names[t["kernel"]] +
+                    (f"/{t['tile_nodes']}" if t["tile_nodes"] else "") + (f"x{t['block']}" if t.get("block") else ""):
                     round(t.get("us_per_step", -1), 1) for t in tuned["trials"]},
+                   "order": "RCM" if tuned and tuned.get("order") == ff.ORDER_RCM else "Morton",
                    "block_threads": info["block_threads"],
                    "precision": "FP32+Kahan",
                    "dt_s": dt, "dt_cr_s": solver.dt_cr,
@@ -821,10 +826,35 @@ def run_suite(args):
                "algorithmic_gbs": info["algorithmic_bytes_per_step"] / (us * 1e3),
                "hbm_frac": info["algorithmic_bytes_per_step"] / (us * 1e3) / peak,
                "setup_s": setup_s, "max_err_C": err}
+        if prec == ff.FP64:
+            # FP64 operations of one step (FMA = 2): hex8 77 per element (k_e 32, gradient 17, flux 18,
+            # loads 10), tet4 40; per free node 15 plus one add per element it sums (8 hex, 24 tet)
+            nv = info["elem_type"]
+            flops = (77 if nv == 8 else 40) * info["n_elems"] + (15 + (8 if nv == 8 else 24)) * info["n_free"]
+            row["fp64_tflops"] = flops / (us * 1e-6) / 1e12
+            row["fp64_frac_of_measured"] = row["fp64_tflops"] / fp64_tflops
         log(json.dumps(row))
         rows.append(row)
         s.close()
         return dt
+
+    # the FP64 rate the FP64 variants are bound by: eight independent FMA chains per
+    # thread, 4 blocks of 256 threads per SM, timed with CUDA events (best of 5)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    sink = torch.zeros(4 * sms, dtype=torch.float64, device="cuda")
+    iters = 20000
+    ff.fedfem_fp64_fma_loop(1000, 4 * sms, 256, sink.data_ptr(), stream.cuda_stream)
+    best = None
+    for _ in range(5):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ff.fedfem_fp64_fma_loop(iters, 4 * sms, 256, sink.data_ptr(), stream.cuda_stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        best = ms if best is None else min(best, ms)
+    fp64_tflops = 16.0 * iters * 4 * sms * 256 / (best * 1e-3) / 1e12
+    log(json.dumps({"fp64_fma_tflops": fp64_tflops, "ms": best}))
 
     # 11^3 hex cube, FP64, 2000 steps, against the oracle
     from oracle import Oracle
@@ -845,6 +875,11 @@ def run_suite(args):
         return f
     measure("tet ellipsoid 60/45/35 mm, h = 1 mm", w2.problem, ff.FP32_KAHAN, 1000, ref=gpu64(w2.problem))
     measure("tet ellipsoid 60/45/35 mm, h = 1 mm", w2.problem, ff.FP64, 1000)
+    # the same recipe at h = 1.44 mm, whose counts (about 142k nodes, 0.8M tets) are the ones stated
+    # for this workload beside its 1 mm spacing
+    w2c = ellipsoid_tet_td(h=1.44e-3)
+    measure("tet ellipsoid 60/45/35 mm, h = 1.44 mm", w2c.problem, ff.FP32_KAHAN, 1000, ref=gpu64(w2c.problem))
+    measure("tet ellipsoid 60/45/35 mm, h = 1.44 mm", w2c.problem, ff.FP64, 1000)
     # 128^3 hex cube, FP64 variant
     w3 = cube_hex_td_convective(n=128)
     measure("hex cube 128^3 elements", w3.problem, ff.FP64, 200)
@@ -870,7 +905,8 @@ def run_suite(args):
     p5.region_perfusion = (pf, Perfusion(w_b=0.2 * pf.w_b, c_b=pf.c_b, T_a=pf.T_a, Q_m=2.0 * pf.Q_m),
                            Perfusion(w_b=4.0 * pf.w_b, c_b=pf.c_b, T_a=pf.T_a, Q_m=0.0))
     measure("hex cube 128^3 elements, three tissue regions", p5, ff.FP32_KAHAN, 200)
-    print(json.dumps({"workload": "suite", "n_gpus": 1, "data": "synthetic", "hbm_peak_gbs": peak, "rows": rows}))
+    print(json.dumps({"workload": "suite", "n_gpus": 1, "data": "synthetic", "hbm_peak_gbs": peak,
+                      "fp64_fma_tflops_measured": fp64_tflops, "rows": rows}))
 
 
 def main():

@@ -158,6 +158,22 @@ int fedfem_set_mesh(fedfem_ctx* ctx, int elem_type, int64_t n_nodes, const doubl
  * the next fedfem_precompute. */
 int fedfem_set_hex_integration(fedfem_ctx* ctx, int rule);
 
+/* Hourglass control of the one-point hexahedron (Section 2.3.3 keeps Eq. 14's
+ * single point and leaves the remedy for its zero-energy modes to another
+ * work).  eps > 0 adds to each one-point element matrix
+ *   c sum_a gamma_a gamma_a^T,  c = eps trace(A_1pt) / 32,
+ * where gamma_a = h_a - sum_i (h_a . x_i) b_i are the four hourglass patterns
+ * h_a (products of the corner signs s_x s_y, s_y s_z, s_z s_x, s_x s_y s_z)
+ * made blind to linear fields (x_i: the corners' i-th coordinates, b_i: the
+ * i-th row of Eq. 14's B).  Linear fields keep exactly the one-point energy;
+ * on a parallelepiped the added matrix carries eps times the trace of the
+ * one-point one.  Each element stores 12 weights w_ad (gamma_a = h_a -
+ * sum_d w_ad s_d), computed in FP64 with the geometry; the critical step
+ * includes the added term.  eps = 0 (default) turns it off.  Ignored for
+ * tet4; E_UNSUPPORTED at fedfem_precompute with the full rule.  Takes effect
+ * at the next fedfem_precompute.  E_ARG for eps < 0 or not finite. */
+int fedfem_set_hourglass_control(fedfem_ctx* ctx, double eps);
+
 /* Element order used internally (FEDFEM_ORDER_*; default MORTON). */
 int fedfem_set_order(fedfem_ctx* ctx, int order);
 
@@ -392,6 +408,15 @@ void fedfem_destroy(fedfem_ctx* ctx);
 
 /* Library version string. */
 const char* fedfem_version(void);
+
+/* Measurement helper (the paper has no counterpart): launches `blocks` x
+ * `threads` threads that each run `iterations` rounds of eight independent
+ * FP64 fused multiply-adds, 16 * iterations * blocks * threads FLOPs in all,
+ * asynchronously on `stream`; timing it with CUDA events gives the FP64 rate
+ * the FP64 time-loop kernels are bound by.  sink_dev: device array of at
+ * least `blocks` doubles (written only in a case that never occurs).
+ * FEDFEM_E_ARG for a bad size, FEDFEM_E_CUDA when the launch fails. */
+int fedfem_fp64_fma_loop(long long iterations, int blocks, int threads, double* sink_dev, void* stream);
 
 /* Sizes of the layout fedfem_plan_layout returns. */
 typedef struct {

@@ -1,8 +1,8 @@
 """Autotuner for the time-loop launch knobs.
 
-Every kernel family and tile size gives bit-identical temperatures (the
-per-node summation order is fixed by the input mesh), so the choice is purely
-one of speed.  ``tune`` times each candidate on the live context with CUDA
+Every kernel family, tile size and element order gives bit-identical
+temperatures (the per-node summation order is fixed by the input mesh), so
+the choice is purely one of speed.  ``tune`` times each candidate on the live context with CUDA
 events, restores the context's state afterwards (checkpoint API), applies the
 fastest candidate and caches it under a signature of the mesh, precision and
 device.
@@ -33,6 +33,7 @@ def candidates(elem_type: int, precision: int):
     # replicated rows: at most one owned node per thread (512 or 256 threads)
     if elem_type == ff.HEX8:
         rep = [(0, b) for b in ((0, 448, 480, 512) if precision != ff.FP64 else (0, 256))]
+        rep += [(256, b) for b in ((224, 256) if precision != ff.FP64 else (128,))]
     else:
         rep = [(256, b) for b in (0, 96, 128, 192)]
     out += [(ff.KERNEL_TILED_REP, blk, b, 0) for blk, b in rep]
@@ -50,7 +51,7 @@ def variant(solver) -> str:
         if getattr(p, "regions", None) is not None:
             parts.append(f"regions{len(p.region_materials)}")
         if getattr(p, "hex_rule", "one-point") != "one-point":
-            parts.append("hexfull")
+            parts.append("hex" + getattr(p, "hex_rule"))
         if getattr(p, "lumping", "element") != "element":
             parts.append("uniform")
         if len(getattr(p, "schedule_factor", ())):
@@ -127,3 +128,33 @@ def tune(solver, dt: float, steps: int = 30, use_cache: bool = True, stream=None
         cache[sig] = result
         _save_cache(cache)
     return dict(result, trials=trials, cached=False)
+
+
+def tune_order(make_solver, dt_of, orders=None, **kw):
+    """The element (and node) order is fixed when a context is built, so it is
+    tuned by building one solver per order: ``make_solver(order)`` returns a
+    fedfem.Solver, ``dt_of(solver)`` the step to time with.  Each is tuned with
+    ``tune(**kw)``; the fastest solver is kept (the others are closed) and
+    returned with its result, which gains an "order" key and the trials of
+    every order.  Results do not depend on the order (each node sums its
+    loads in input element order), so the choice is one of speed."""
+    if orders is None:
+        orders = (ff.ORDER_MORTON, ff.ORDER_RCM)
+    best, best_r, trials = None, None, []
+    for order in orders:
+        s = make_solver(order)
+        try:
+            r = tune(s, dt_of(s), **kw)
+        except Exception:
+            s.close()
+            raise
+        trials += [dict(t, order=order) for t in r.get("trials", [])]
+        r = dict(r, order=order)
+        if best is None or r["us_per_step"] < best_r["us_per_step"]:
+            if best is not None:
+                best.close()
+            best, best_r = s, r
+        else:
+            s.close()
+    best_r["trials"] = trials
+    return best, best_r

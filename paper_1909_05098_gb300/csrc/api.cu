@@ -47,6 +47,7 @@ struct fedfem_ctx {
     bool dose_on = false;
     int dose_model = FEDFEM_DOSE_CEM43;
     int hex_rule = FEDFEM_HEX_ONE_POINT;
+    double hg_eps = 0.0;                          // hourglass stabilisation of the one-point hex (0: off)
     double dose_A = 0.0, dose_Ea = 0.0;           // Arrhenius frequency factor (1/s), activation energy (J/mol)
     int n_reg = 0;                                // heterogeneous tissue regions (0: mat everywhere)
     int lumping = FEDFEM_LUMP_ELEMENT;            // perfusion / metabolic heat per node
@@ -77,6 +78,8 @@ struct fedfem_ctx {
     unsigned char* emat = nullptr;             // regions: per internal element
     double* A28_64 = nullptr;                  // fully integrated hex8: 28 planes of E
     float* A28_32 = nullptr;
+    double* W64 = nullptr;                     // hourglass-stabilised hex8: 12 planes of E
+    float* W32 = nullptr;
     double *Cq64 = nullptr, *matk64 = nullptr;   // regions: node coefficients (4 x N_free), k laws (3 each)
     float *Cq32 = nullptr, *matk32 = nullptr;
     double* dose = nullptr;                       // CEM43 minutes per free node
@@ -156,6 +159,7 @@ void free_device(fedfem_ctx* c) {
     c->tab64 = nullptr; c->tab32 = nullptr;
     c->emat = nullptr; c->Cq64 = c->matk64 = nullptr; c->Cq32 = c->matk32 = nullptr;
     c->A28_64 = nullptr; c->A28_32 = nullptr;
+    c->W64 = nullptr; c->W32 = nullptr;
     c->dose = nullptr;
     c->T = nullptr; c->T2 = nullptr; c->Tlo = nullptr; c->slots = nullptr; c->node_of = nullptr; c->T_dir = nullptr;
     c->io = nullptr; c->st = nullptr;
@@ -326,6 +330,8 @@ StepArgs<R, L> make_args(fedfem_ctx* c, const R* M, const R* V, const R* Q, cons
     for (int j = 0; j < c->tab_n; ++j) a.tab_T[j] = (R)c->tab_T[j];
     a.tab = std::is_same<R, double>::value ? (const R*)c->tab64 : (const R*)c->tab32;
     a.A28 = std::is_same<R, double>::value ? (const R*)c->A28_64 : (const R*)c->A28_32;
+    a.W12 = std::is_same<R, double>::value ? (const R*)c->W64 : (const R*)c->W32;
+    a.hg_eps4 = (R)(0.25 * c->hg_eps);
     if (c->n_cq > 0 && c->emat) {
         a.emat = c->emat;
         a.emat_tile = c->t_emat;
@@ -350,10 +356,10 @@ cudaError_t talloc(fedfem_ctx* c, P** p, size_t bytes) {
 // halo nodes, most elements at one owned node}, the 6 element-matrix rows
 // (padded element count each), the 16-bit local connectivity (nv per padded
 // element), the halo node ids; 16-byte multiple
-int64_t tile_block_bytes(const Tiles& t, int64_t i, size_t rs) {
+int64_t tile_block_bytes(const Tiles& t, int64_t i, size_t rs, bool hg = false) {
     const int64_t ne = t.e_off[i + 1] - t.e_off[i], ne_pad = (ne + 7) / 8 * 8;
     const int64_t nh = t.h_off[i + 1] - t.h_off[i];
-    const int64_t b = 16 + 6 * ne_pad * (int64_t)rs + ne_pad * t.nv * 2 + nh * 4;
+    const int64_t b = 16 + (hg ? 18 : 6) * ne_pad * (int64_t)rs + ne_pad * t.nv * 2 + nh * 4;
     return (b + 15) / 16 * 16;
 }
 
@@ -374,9 +380,9 @@ size_t rep_bytes(const Tiles& t, size_t ls, int S) {
 // with replicated rows of stride S): two block stages when staged; the tile
 // temperatures and the per-node load table (max_deg rows of B), or the two
 // replicated-row arrays
-size_t tile_smem(const Tiles& t, size_t rs, size_t ls, int* max_block, int kind, int S) {
+size_t tile_smem(const Tiles& t, size_t rs, size_t ls, int* max_block, int kind, int S, bool hg) {
     int64_t mb = 0;
-    for (int64_t i = 0; i < t.n_tiles; ++i) mb = std::max(mb, tile_block_bytes(t, i, rs));
+    for (int64_t i = 0; i < t.n_tiles; ++i) mb = std::max(mb, tile_block_bytes(t, i, rs, hg));
     *max_block = (int)mb;
     if (kind == 2) return 128 + 2 * rep_bytes(t, ls, S) + 2 * (size_t)mb;
     const size_t ts = ((size_t)t.max_local * ls + 15) / 16 * 16;
@@ -415,6 +421,7 @@ int plan_tiles(fedfem_ctx* c) {
     const int S = staged_threads(c);    // replicated-row stride: one owned node per thread
     const size_t rs = c->precision == FEDFEM_FP64 ? sizeof(double) : sizeof(float);
     const size_t ls = rs * c->n_lanes;
+    const bool hg = c->W64 || c->W32;   // blocks carry the hourglass weights
     if (kind == 2 && c->n_lanes > 1) return fail(c, FEDFEM_E_UNSUPPORTED, "the replicated-row kernel takes one lane");
     const int64_t NF = c->L.N_free;
     if (NF == 0) return fail(c, FEDFEM_E_ARG, "no free nodes");
@@ -439,7 +446,7 @@ int plan_tiles(fedfem_ctx* c) {
         for (;;) {   // the default size halves while its tiles do not fit (meshes whose tiles hold many elements)
             m = build_tiles(c->L, B0, t);
             if (!m.empty()) return fail(c, FEDFEM_E_ARG, m);
-            size_t smem = tile_smem(t, rs, ls, &mb, kind, S);
+            size_t smem = tile_smem(t, rs, ls, &mb, kind, S, hg);
             per_sm = tiled_blocks_per_sm(c->precision, c->nv, kind, S, c->n_lanes, smem);
             if (c->tile.blocks_per_sm > 0) per_sm = std::min(per_sm, c->tile.blocks_per_sm);
             if (per_sm >= 1 || c->tile.tile_nodes > 0 || B0 <= 32) break;
@@ -456,7 +463,7 @@ int plan_tiles(fedfem_ctx* c) {
             Tiles tw;
             if (!build_tiles(c->L, (int)Bw, tw).empty()) continue;
             int mbw = 0;
-            int pw = tiled_blocks_per_sm(c->precision, c->nv, kind, S, c->n_lanes, tile_smem(tw, rs, ls, &mbw, kind, S));
+            int pw = tiled_blocks_per_sm(c->precision, c->nv, kind, S, c->n_lanes, tile_smem(tw, rs, ls, &mbw, kind, S, hg));
             if (c->tile.blocks_per_sm > 0) pw = std::min(pw, c->tile.blocks_per_sm);
             if (pw != per_sm) continue;
             B = (int)Bw;
@@ -468,7 +475,7 @@ int plan_tiles(fedfem_ctx* c) {
         m = build_tiles(c->L, B, t);
         if (!m.empty()) return fail(c, FEDFEM_E_ARG, m);
     }
-    const size_t smem = tile_smem(t, rs, ls, &mb, kind, S);
+    const size_t smem = tile_smem(t, rs, ls, &mb, kind, S, hg);
     if (kind == 2 && t.max_deg > (c->nv == 8 ? 8 : 32))
         return fail(c, FEDFEM_E_UNSUPPORTED, "the replicated-row kernel takes at most 8 (hex) or 32 (tet) elements per node");
     if (kind == 2 && ls * ((size_t)std::max(1, t.max_deg) * S + tile_max_halo(t)) > 65536)
@@ -477,14 +484,17 @@ int plan_tiles(fedfem_ctx* c) {
         return fail(c, FEDFEM_E_UNSUPPORTED, "tile does not fit in shared memory; use smaller tile_nodes");
     free_tiles(c);
     cudaStream_t st = c->stream;
-    // element matrices back to the host once, to pack them per tile
+    // element matrices (and hourglass weights) back to the host once, to pack them per tile
     const int64_t E = c->E;
-    std::vector<unsigned char> Mh(rs * 6 * E);
+    std::vector<unsigned char> Mh(rs * 6 * E), Wh(hg ? rs * 12 * E : 0);
     CU(cudaMemcpyAsync(Mh.data(), c->precision == FEDFEM_FP64 ? (void*)c->M64 : (void*)c->M32, rs * 6 * E,
                        cudaMemcpyDeviceToHost, st), "tile pack");
+    if (hg)
+        CU(cudaMemcpyAsync(Wh.data(), c->precision == FEDFEM_FP64 ? (void*)c->W64 : (void*)c->W32, rs * 12 * E,
+                           cudaMemcpyDeviceToHost, st), "tile pack");
     CU(cudaStreamSynchronize(st), "tile pack");
     std::vector<int64_t> off(t.n_tiles + 1, 0);
-    for (int64_t i = 0; i < t.n_tiles; ++i) off[i + 1] = off[i] + tile_block_bytes(t, i, rs);
+    for (int64_t i = 0; i < t.n_tiles; ++i) off[i + 1] = off[i] + tile_block_bytes(t, i, rs, hg);
     std::vector<unsigned char> blob(off[t.n_tiles], 0);
     for (int64_t i = 0; i < t.n_tiles; ++i) {
         unsigned char* b = blob.data() + off[i];
@@ -496,7 +506,13 @@ int plan_tiles(fedfem_ctx* c) {
         for (int q = 0; q < 6; ++q)
             for (int64_t j = 0; j < ne; ++j)
                 std::memcpy(Mb + rs * (6 * j + q), Mh.data() + rs * (q * E + t.e_glob[e0 + j]), rs);
-        uint16_t* lc = (uint16_t*)(Mb + rs * 6 * ne_pad);
+        if (hg) {   // an element's 12 weights together, after the matrices
+            unsigned char* Wb = Mb + rs * 6 * ne_pad;
+            for (int q = 0; q < 12; ++q)
+                for (int64_t j = 0; j < ne; ++j)
+                    std::memcpy(Wb + rs * (12 * j + q), Wh.data() + rs * (q * E + t.e_glob[e0 + j]), rs);
+        }
+        uint16_t* lc = (uint16_t*)(Mb + rs * (hg ? 18 : 6) * ne_pad);
         if (kind == 2) {   // byte offsets into the replicated rows (see TileArgs::rep)
             const int64_t own = std::min<int64_t>(t.B, NF - i * (int64_t)t.B);
             const int id_mask = (1 << t.rank_shift) - 1, D = std::max(1, t.max_deg);
@@ -553,6 +569,7 @@ TileArgs<R> make_tile_args(fedfem_ctx* c) {
     t.rep = tile_kind(c) == 2;
     t.rep_rows = std::max(1, h.max_deg);
     t.max_halo = c->t_max_halo;
+    t.hourglass = (c->W64 || c->W32) ? 1 : 0;
     return t;
 }
 
@@ -956,6 +973,14 @@ int fedfem_set_lumping(fedfem_ctx* c, int mode) {
     return FEDFEM_OK;
 }
 
+int fedfem_set_hourglass_control(fedfem_ctx* c, double eps) {
+    if (!c) return FEDFEM_E_ARG;
+    if (!(eps >= 0.0) || !is_finite(eps)) return fail(c, FEDFEM_E_ARG, "hourglass strength must be >= 0");
+    c->hg_eps = eps;
+    invalidate(c);
+    return FEDFEM_OK;
+}
+
 int fedfem_set_hex_integration(fedfem_ctx* c, int rule) {
     if (!c) return FEDFEM_E_ARG;
     if (rule != FEDFEM_HEX_ONE_POINT && rule != FEDFEM_HEX_FULL) return fail(c, FEDFEM_E_ARG, "unknown hex rule");
@@ -1160,6 +1185,13 @@ int fedfem_precompute(fedfem_ctx* c, double T_lo, double T_hi, double* dt_cr_out
     pa.n_faces = c->conv_nv ? (int64_t)fint.size() / c->conv_nv : 0;
     pa.face_nv = c->conv_nv; pa.faces = faces; pa.face_share = face_share;
     pa.conv_off = conv_off; pa.conv_face = conv_face; pa.h_film = c->conv_h;
+    if (nv == 8 && c->hg_eps > 0.0 && c->hex_rule == FEDFEM_HEX_FULL)
+        return fail(c, FEDFEM_E_UNSUPPORTED, "hourglass control applies to the one-point hexahedron");
+    if (nv == 8 && c->hg_eps > 0.0) {   // hourglass weights, computed with the one-point matrices
+        CU(dalloc(c, &c->W64, sizeof(double) * 12 * std::max<int64_t>(1, E)), "alloc");
+        pa.W64 = c->W64;
+        pa.hg_eps4 = 0.25 * c->hg_eps;
+    }
     CU(launch_geometry(pa, st), "geometry kernel");
     if (nv == 8 && c->hex_rule == FEDFEM_HEX_FULL) {   // A_e by 2 x 2 x 2 Gauss points, exact V_e
         CU(dalloc(c, &c->A28_64, sizeof(double) * 28 * std::max<int64_t>(1, E)), "alloc");
@@ -1283,6 +1315,10 @@ int fedfem_precompute(fedfem_ctx* c, double T_lo, double T_hi, double* dt_cr_out
             CU(dalloc(c, &c->A28_32, sizeof(float) * 28 * std::max<int64_t>(1, E)), "alloc");
             CU(launch_to_f32(c->A28_64, c->A28_32, 28 * E, st), "convert");
         }
+        if (c->W64) {
+            CU(dalloc(c, &c->W32, sizeof(float) * 12 * std::max<int64_t>(1, E)), "alloc");
+            CU(launch_to_f32(c->W64, c->W32, 12 * E, st), "convert");
+        }
         CU(launch_to_f32(c->V64, c->V32, NF, st), "convert");
         CU(launch_pack_lanes(c->Q64, c->Q32, NL, NF, st), "convert");
         CU(launch_to_f32(c->hA64, c->hA32, NC, st), "convert");
@@ -1316,6 +1352,7 @@ int fedfem_precompute(fedfem_ctx* c, double T_lo, double T_hi, double* dt_cr_out
     if (c->precision != FEDFEM_FP64) {
         release(c, c->M64, sizeof(double) * 6 * E); c->M64 = nullptr;
         if (c->A28_64) { release(c, c->A28_64, sizeof(double) * 28 * std::max<int64_t>(1, E)); c->A28_64 = nullptr; }
+        if (c->W64) { release(c, c->W64, sizeof(double) * 12 * std::max<int64_t>(1, E)); c->W64 = nullptr; }
         release(c, c->V64, sizeof(double) * NF); c->V64 = nullptr;
         release(c, c->Q64, sizeof(double) * NF * NL); c->Q64 = nullptr;
         release(c, c->hA64, sizeof(double) * NC); c->hA64 = nullptr;
@@ -1592,7 +1629,7 @@ int fedfem_get_info(fedfem_ctx* c, fedfem_info* info) {
     const int64_t node_state = c->precision == FEDFEM_FP32_KAHAN ? 4 * R : 2 * R;   // T (+lo) read+write
     const int64_t E = c->E, NF = L.N_free, NC = L.N_free - L.N_plain;
     const int64_t NL = c->n_lanes;   // lanes share V, hA and the element data
-    const int64_t nm = (c->A28_64 || c->A28_32) ? 28 : 6;   // element matrix values
+    const int64_t nm = (c->A28_64 || c->A28_32) ? 28 : (c->W64 || c->W32) ? 18 : 6;   // element matrix values
     info->algorithmic_bytes_per_step = E * (4 * c->nv + nm * R) + NF * (NL * (node_state + R) + R) + NC * R;
     // a source schedule reads the source part of Q too; the dose is read and written in FP64
     const int64_t extra = (c->sched_f.empty() ? 0 : NF * NL * R) + (c->dose ? NF * 16 : 0) +

@@ -148,6 +148,51 @@ __device__ __forceinline__ void hex8_loads(const L t[8], const R m[6], L ke, L F
     F[4] = -a + qz;  F[5] = b + qz;  F[6] = a + qz;  F[7] = -b + qz;
 }
 
+// Hourglass-stabilised one-point hex8.  The four hourglass patterns are the
+// sign products h_1 = s_x s_y, h_2 = s_y s_z, h_3 = s_z s_x, h_4 = s_x s_y s_z;
+// their amplitudes, made blind to linear fields with the per-element
+// weights w (gamma_a = h_a - sum_d w_ad s_d, row-major a x d), are
+// q_a = h_a . T - sum_d w_ad g_d with g_d = s_d . T.  With the strength
+// c = eps4 trace(M) (eps4 = eps / 4, so that on a parallelepiped the added
+// matrix has eps times the trace of the one-point one):
+//   F = k_e [ s^T (M g - c W^T q) + c H^T q ].
+// Every h_a . T is a sum of four nodal differences (a uniform field gives
+// exactly zero).
+template <typename R, typename L = R>
+__device__ __forceinline__ void hex8_hourglass_loads(const L t[8], const R m[6], const R w[12], R eps4, L ke,
+                                                     L F[8]) {
+    L g0, g1, g2;
+    hex8_gradient<L>(t, g0, g1, g2);
+    // corner signs (x,y,z): 0(-,-,-) 1(+,-,-) 2(+,+,-) 3(-,+,-) 4(-,-,+) 5(+,-,+) 6(+,+,+) 7(-,+,+)
+    const L h0 = ((t[0] - t[1]) + (t[2] - t[3])) + ((t[4] - t[5]) + (t[6] - t[7]));   // s_x s_y
+    const L h1 = ((t[0] - t[2]) + (t[1] - t[3])) + ((t[6] - t[4]) + (t[7] - t[5]));   // s_y s_z
+    const L h2 = ((t[0] - t[1]) + (t[3] - t[2])) + ((t[5] - t[4]) + (t[6] - t[7]));   // s_z s_x
+    const L h3 = ((t[1] - t[0]) + (t[3] - t[2])) + ((t[4] - t[5]) + (t[6] - t[7]));   // s_x s_y s_z
+    const R c = eps4 * ((m[0] + m[1]) + m[2]);
+    const L q0 = c * (h0 - fmadd(w[0], g0, fmadd(w[1], g1, w[2] * g2)));
+    const L q1 = c * (h1 - fmadd(w[3], g0, fmadd(w[4], g1, w[5] * g2)));
+    const L q2 = c * (h2 - fmadd(w[6], g0, fmadd(w[7], g1, w[8] * g2)));
+    const L q3 = c * (h3 - fmadd(w[9], g0, fmadd(w[10], g1, w[11] * g2)));
+    // gradient flux less the hourglass vectors' linear parts: M g - W^T (c q)
+    const L rx = fmadd(w[0], q0, fmadd(w[3], q1, fmadd(w[6], q2, w[9] * q3)));
+    const L ry = fmadd(w[1], q0, fmadd(w[4], q1, fmadd(w[7], q2, w[10] * q3)));
+    const L rz = fmadd(w[2], q0, fmadd(w[5], q1, fmadd(w[8], q2, w[11] * q3)));
+    const L qx = ke * (fmadd(m[0], g0, fmadd(m[3], g1, m[4] * g2)) - rx);
+    const L qy = ke * (fmadd(m[3], g0, fmadd(m[1], g1, m[5] * g2)) - ry);
+    const L qz = ke * (fmadd(m[4], g0, fmadd(m[5], g1, m[2] * g2)) - rz);
+    const L p0 = ke * q0, p1 = ke * q1, p2 = ke * q2, p3 = ke * q3;
+    const L a = qx + qy, b = qx - qy;
+    // s^T (qx, qy, qz) + H^T (p0 .. p3), corner by corner
+    F[0] = (-a - qz) + ((p0 + p1) + (p2 - p3));
+    F[1] = (b - qz) + ((p3 - p0) + (p1 - p2));
+    F[2] = (a - qz) + ((p0 - p1) - (p2 + p3));
+    F[3] = (-b - qz) + ((p2 + p3) - (p0 + p1));
+    F[4] = (-a + qz) + ((p0 + p3) - (p1 + p2));
+    F[5] = (b + qz) + ((p2 - p0) - (p1 + p3));
+    F[6] = (a + qz) + ((p0 + p1) + (p2 + p3));
+    F[7] = (-b + qz) + ((p1 - p0) - (p2 + p3));
+}
+
 // tet4: t[4], m[6], k_e -> F[4]
 template <typename R, typename L = R>
 __device__ __forceinline__ void tet4_loads(const L t[4], const R m[6], L ke, L F[4]) {

@@ -155,6 +155,11 @@ struct StepArgs {
     // A_ab, a < b, of each element matrix as planes of E (pair order a-major);
     // the diagonal is implied by the zero row sums.  Null: the factored M.
     const R* A28;
+    // hourglass-stabilised one-point hex8: the 12 weights w_ad of each element
+    // (planes of E, a-major) and eps / 4; null: no stabilisation.  The tiled
+    // kernels read the weights from their tile blocks instead.
+    const R* W12;
+    R hg_eps4;
 };
 
 // Launchers (step.cu).  mode: FEDFEM_FP64 / FEDFEM_FP32_KAHAN / FEDFEM_FP32_PLAIN.
@@ -170,6 +175,7 @@ struct LaunchCfg {
 // Packed per-tile blocks of the tiled kernels, each 16-byte aligned (copied
 // whole into shared memory by one bulk (TMA) copy in the staged kernel):
 //   int32 header {ne, ne_pad, nh, deg}; M: ne_pad x 6 R (one element's six values together);
+//   with hourglass stabilisation: ne_pad x 12 R hourglass weights;
 //   local connectivity: ne_pad x nv uint16 (id | rank << rank_shift);
 //   halo ids: nh int32.
 template <typename R>
@@ -190,6 +196,7 @@ struct TileArgs {
     int rep;
     int rep_rows;                    // rows of the temperature copies and of the load table (largest rank count)
     int max_halo;                    // largest halo of any tile
+    int hourglass;                   // 1: each element's 12 hourglass weights follow its 6 matrix values in the block
 };
 
 struct F4;
@@ -237,6 +244,8 @@ struct PreArgs {
     const double* x; const double* y; const double* z;      // internal node order
     double* M64;                 // 6 planes of E
     double* A28;                 // fully integrated hex8: 28 planes of E (pairs a < b of A_e), else null
+    double* W64;                 // hourglass-stabilised hex8: 12 planes of E (weights w_ad), else null
+    double hg_eps4;              // its strength / 4
     double* Vshare;              // E + 1 (last = 0): V_e / nv
     int* bad_elem;               // smallest internal element with det <= 0 (init INT_MAX)
     const int32_t* sell_off; const int32_t* sell_ids;

@@ -90,6 +90,21 @@ __global__ void k_geometry(PreArgs a) {
     const double w = (a.nv == 8) ? det * 0.125 : det / 6.0;   // hex: det J / 8; tet: V_tet
     const double Ve = (a.nv == 8) ? 8.0 * det : det / 6.0;
     const int64_t E = a.E;
+    if (a.nv == 8 && a.W64) {   // hourglass weights w_ad = (1/8) sum_i (h_a . x_i) (J^-1)_di
+        double hx[4][3] = {};
+        for (int n = 0; n < 8; ++n) {
+            const double sx = (n == 1 || n == 2 || n == 5 || n == 6) ? 1.0 : -1.0;
+            const double sy = (n == 2 || n == 3 || n == 6 || n == 7) ? 1.0 : -1.0;
+            const double sz = (n >= 4) ? 1.0 : -1.0;
+            const double h[4] = {sx * sy, sy * sz, sz * sx, sx * sy * sz};
+            const double X[3] = {a.x[c[n]], a.y[c[n]], a.z[c[n]]};
+            for (int q = 0; q < 4; ++q)
+                for (int i = 0; i < 3; ++i) hx[q][i] += h[q] * X[i];
+        }
+        for (int q = 0; q < 4; ++q)
+            for (int d = 0; d < 3; ++d)
+                a.W64[(3 * q + d) * E + e] = 0.125 * (hx[q][0] * inv[d][0] + hx[q][1] * inv[d][1] + hx[q][2] * inv[d][2]);
+    }
     a.M64[0 * E + e] = w * P[0][0];
     a.M64[1 * E + e] = w * P[1][1];
     a.M64[2 * E + e] = w * P[2][2];
@@ -299,6 +314,12 @@ __global__ void k_lz_elem(LzArgs a) {
                 F[n] -= w;
             }
         for (int n = 0; n < 8; ++n) a.slots[e * 8 + n] = a.k0 * F[n];
+    } else if (a.p.nv == 8 && a.p.W64) {   // hourglass-stabilised one-point rule
+        double t[8], F[8], w[12];
+        for (int n = 0; n < 8; ++n) t[n] = a.u[c[n]];
+        for (int q = 0; q < 12; ++q) w[q] = a.p.W64[q * E + e];
+        hex8_hourglass_loads<double>(t, m, w, a.p.hg_eps4, a.k0, F);
+        for (int n = 0; n < 8; ++n) a.slots[e * 8 + n] = F[n];
     } else if (a.p.nv == 8) {
         double t[8], F[8];
         for (int n = 0; n < 8; ++n) t[n] = a.u[c[n]];
@@ -560,3 +581,32 @@ cudaError_t launch_read_state(int precision, int n_lanes, int lane, int64_t N, c
 }
 
 }  // namespace fedfem
+
+// ---- FP64 pipe throughput (measurement helper) ----------------------------
+// Eight independent chains of fused multiply-adds per thread, so that every
+// FP64 unit has work each cycle; the sum goes to a sink so that nothing is
+// optimised away.  FLOPs = 2 * 8 * iterations * threads.
+namespace fedfem {
+namespace {
+__global__ void k_fp64_fma_loop(long long iterations, double* sink) {
+    const double b = 0.9999999999, c = 1e-9;
+    double x[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) x[q] = 1.0 + 1e-3 * (q + (double)threadIdx.x * 1e-6);
+    for (long long k = 0; k < iterations; ++k) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) x[q] = fma(x[q], b, c);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) s += x[q];
+    if (s == 12345.678) sink[blockIdx.x] = s;   // never true; keeps the chains live
+}
+}  // namespace
+}  // namespace fedfem
+
+extern "C" int fedfem_fp64_fma_loop(long long iterations, int blocks, int threads, double* sink_dev, void* stream) {
+    if (iterations < 1 || blocks < 1 || threads < 32 || threads > 1024 || !sink_dev) return FEDFEM_E_ARG;
+    fedfem::k_fp64_fma_loop<<<blocks, threads, 0, (cudaStream_t)stream>>>(iterations, sink_dev);
+    return cudaGetLastError() == cudaSuccess ? FEDFEM_OK : FEDFEM_E_CUDA;
+}

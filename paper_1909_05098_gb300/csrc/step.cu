@@ -151,11 +151,22 @@ __device__ __forceinline__ void element_phase(const StepArgs<R>& a, int64_t e) {
     R ke;
     with_k_laws<MODE>(a, a.emat, [&](const auto& kl) { ke = element_k<R, NV>(t, kl(e)); });
     R F[NV];
-    bool full = false;
-    if constexpr ((MODE & 2) != 0 && NV == 8) full = a.A28 != nullptr;
+    bool full = false, hg = false;
+    if constexpr ((MODE & 2) != 0 && NV == 8) {
+        full = a.A28 != nullptr;
+        hg = a.W12 != nullptr;
+    }
     if constexpr (NV == 8) {
-        if (full) hex8_full_loads<R>(a, e, t, ke, F);
-        else hex8_loads<R>(t, m, ke, F);
+        if (full) {
+            hex8_full_loads<R>(a, e, t, ke, F);
+        } else if (hg) {
+            R w[12];
+#pragma unroll
+            for (int q = 0; q < 12; ++q) w[q] = a.W12[q * E + e];
+            hex8_hourglass_loads<R>(t, m, w, a.hg_eps4, ke, F);
+        } else {
+            hex8_loads<R>(t, m, ke, F);
+        }
     } else {
         tet4_loads<R>(t, m, ke, F);
     }
@@ -440,18 +451,45 @@ template <typename R>
 struct TileView {
     int ne, ne_pad, nh, deg;
     const R* M;                 // ne_pad x 6: an element's six values together
+    const R* W;                 // ne_pad x 12 hourglass weights (hg blocks), else null
     const uint16_t* lc;         // nv entries per element
     const int32_t* halo;        // nh global node ids
 };
 template <typename R, int NV>
-__device__ __forceinline__ TileView<R> tile_view(const unsigned char* blk) {
+__device__ __forceinline__ TileView<R> tile_view(const unsigned char* blk, int hg = 0) {
     const int4 hdr = *reinterpret_cast<const int4*>(blk);
     TileView<R> v;
     v.ne = hdr.x; v.ne_pad = hdr.y; v.nh = hdr.z; v.deg = hdr.w;
     v.M = reinterpret_cast<const R*>(blk + 16);
-    v.lc = reinterpret_cast<const uint16_t*>(blk + 16 + 6 * (size_t)v.ne_pad * sizeof(R));
+    v.W = hg ? v.M + 6 * (size_t)v.ne_pad : nullptr;
+    v.lc = reinterpret_cast<const uint16_t*>(blk + 16 + (hg ? 18 : 6) * (size_t)v.ne_pad * sizeof(R));
     v.halo = reinterpret_cast<const int32_t*>(v.lc + NV * v.ne_pad);
     return v;
+}
+
+// element loads inside a tile: the plain factored rule, or (kernels built with
+// the extensions, blocks carrying weights) the hourglass-stabilised one
+template <bool EXT, typename R, typename L, int NV>
+__device__ __forceinline__ void tile_loads(const TileView<R>& v, int j, const L tt[NV], const R m[6], L ke, R eps4,
+                                           L F[NV]) {
+    if constexpr (NV == 8) {
+        if constexpr (EXT) {
+            if (v.W) {
+                R w[12];
+#pragma unroll
+                for (int q = 0; q < 12; q += 2) {
+                    const typename Vec2<R>::type p = reinterpret_cast<const typename Vec2<R>::type*>(v.W + 12 * j)[q / 2];
+                    w[q] = p.x;
+                    w[q + 1] = p.y;
+                }
+                hex8_hourglass_loads<R, L>(tt, m, w, eps4, ke, F);
+                return;
+            }
+        }
+        hex8_loads<R, L>(tt, m, ke, F);
+    } else {
+        tet4_loads<R, L>(tt, m, ke, F);
+    }
 }
 
 template <int NV>
@@ -527,9 +565,9 @@ __device__ __forceinline__ const unsigned char* tile_regions(const StepArgs<R, L
 
 // element phase of one tile: loads of every tile element; each owned corner's
 // load goes to Fn[rank * B + local id]
-template <typename R, typename L, int NV, bool SHARED, typename KL>
+template <typename R, typename L, int NV, bool SHARED, bool EXT, typename KL>
 __device__ __forceinline__ void tile_elements_k(const KL& kl, const TileView<R>& v, int own, int B, int rank_shift,
-                                                const L* Ts, L* Fn) {
+                                                const L* Ts, L* Fn, R eps4) {
     const int id_mask = (1 << rank_shift) - 1;
     for (int j = threadIdx.x; j < v.ne; j += blockDim.x) {
         int c[NV];
@@ -546,8 +584,7 @@ __device__ __forceinline__ void tile_elements_k(const KL& kl, const TileView<R>&
         }
         const L ke = element_k<R, NV, L>(tt, kl(j));
         L F[NV];
-        if (NV == 8) hex8_loads<R, L>(tt, m, ke, F);
-        else tet4_loads<R, L>(tt, m, ke, F);
+        tile_loads<EXT, R, L, NV>(v, j, tt, m, ke, eps4, F);
         LConn<NV>::template reload<SHARED>(v.lc, j, c);
 #pragma unroll
         for (int n = 0; n < NV; ++n) {
@@ -560,7 +597,9 @@ __device__ __forceinline__ void tile_elements_k(const KL& kl, const TileView<R>&
 template <typename R, typename L, int NV, int MODE, bool SHARED>
 __device__ __forceinline__ void tile_elements(const StepArgs<R, L>& a, const unsigned char* em, const TileView<R>& v,
                                               int own, int B, int rank_shift, const L* Ts, L* Fn) {
-    with_k_laws<MODE>(a, em, [&](const auto& kl) { tile_elements_k<R, L, NV, SHARED>(kl, v, own, B, rank_shift, Ts, Fn); });
+    with_k_laws<MODE>(a, em, [&](const auto& kl) {
+        tile_elements_k<R, L, NV, SHARED, (MODE & 2) != 0>(kl, v, own, B, rank_shift, Ts, Fn, a.hg_eps4);
+    });
 }
 
 // node phase: sum each owned node's column (rank order), clear it, Eq. 19.
@@ -630,7 +669,7 @@ __global__ void __launch_bounds__(256, DirectOccupancy<L>::min_blocks) k_tiled_d
         const L* Tin = (s & 1) ? a.T2 : a.T;
         L* Tout = (s & 1) ? a.T : a.T2;
         for (int64_t t = blockIdx.x; t < ta.n_tiles; t += gridDim.x) {
-            const TileView<R> v = tile_view<R, NV>(ta.blocks + ta.block_off[t]);
+            const TileView<R> v = tile_view<R, NV>(ta.blocks + ta.block_off[t], ta.hourglass);
             const int64_t base = t * ta.B;
             const int own = (int)min((int64_t)ta.B, a.N_free - base);
             tile_fetch<L, false>(v.halo, v.nh, base, own, Tin, Ts);
@@ -725,7 +764,7 @@ __global__ void __launch_bounds__(TPB, StagedOccupancy<L, TPB>::min_blocks)
     auto fail_timeout = [&]() {
         if (threadIdx.x == 0) atomicOr(&a.status->flags, STATUS_TIMEOUT);
     };
-    auto view_of = [&](long long kk, int p) { return tile_view<R, NV>(buf_of(kk, p) ? stage1 : stage0); };
+    auto view_of = [&](long long kk, int p) { return tile_view<R, NV>(buf_of(kk, p) ? stage1 : stage0, ta.hourglass); };
     // temperatures of tile kk (its stage has landed) into Ts, asynchronously
     auto fetch = [&](long long kk, int p, const L* Tin) {
         const TileView<R> v = view_of(kk, p);
@@ -822,9 +861,9 @@ struct RepCodes<4> {
 };
 
 // element phase of one replicated-row tile
-template <typename R, typename L, int NV, int TPB, typename KL>
+template <typename R, typename L, int NV, int TPB, bool EXT, typename KL>
 __device__ __forceinline__ void rep_elements_k(const KL& kl, const TileView<R>& v, const unsigned char* Tr,
-                                               unsigned char* Fr) {
+                                               unsigned char* Fr, R eps4) {
     for (int j = threadIdx.x; j < v.ne; j += TPB) {
         uint32_t o[NV];
         RepCodes<NV>::load(v.lc, j, o);
@@ -840,8 +879,7 @@ __device__ __forceinline__ void rep_elements_k(const KL& kl, const TileView<R>& 
         }
         const L ke = element_k<R, NV, L>(tt, kl(j));
         L F[NV];
-        if (NV == 8) hex8_loads<R, L>(tt, m, ke, F);
-        else tet4_loads<R, L>(tt, m, ke, F);
+        tile_loads<EXT, R, L, NV>(v, j, tt, m, ke, eps4, F);
 #pragma unroll
         for (int n = 0; n < NV; ++n) *reinterpret_cast<L*>(Fr + o[n]) = F[n];
     }
@@ -914,7 +952,7 @@ __global__ void __launch_bounds__(TPB, StagedOccupancy<L, TPB>::min_blocks)
     auto fail_timeout = [&]() {
         if (threadIdx.x == 0) atomicOr(&a.status->flags, STATUS_TIMEOUT);
     };
-    auto view_of = [&](long long kk, int p) { return tile_view<R, NV>(buf_of(kk, p) ? stage1 : stage0); };
+    auto view_of = [&](long long kk, int p) { return tile_view<R, NV>(buf_of(kk, p) ? stage1 : stage0, ta.hourglass); };
     // owned temperatures into row 0 (thread l fetches owned node l), halo ones after the rows
     auto fetch = [&](long long kk, int p, const L* Tin) {
         const TileView<R> v = view_of(kk, p);
@@ -953,7 +991,7 @@ __global__ void __launch_bounds__(TPB, StagedOccupancy<L, TPB>::min_blocks)
             }
             if (__syncthreads_or(failed)) { fail_timeout(); stop = true; break; }   // Tr complete; Fr clear
             with_k_laws<MODE>(a, tile_regions<MODE>(a, t), [&](const auto& kl) {
-                rep_elements_k<R, L, NV, TPB>(kl, v, Tr, Fr);
+                rep_elements_k<R, L, NV, TPB, (MODE & 2) != 0>(kl, v, Tr, Fr, a.hg_eps4);
             });
             __syncthreads();   // loads complete; this stage and Tr are free
             if (i + 1 < n_my) {   // the next tile of this step: its stage, then its temperatures
@@ -1017,8 +1055,8 @@ template <typename R, typename L, int NV, bool KAHAN>
 cudaError_t launch_tiled_impl(const StepArgs<R, L>& a, const TileArgs<R>& ta, int64_t n_steps, LaunchCfg& cfg,
                               cudaStream_t s) {
     constexpr int M = KAHAN ? 1 : 0;
-    auto kern = (a.Qs || a.dose || a.n_tab > 0 || a.emat) ? tiled_kernel<R, L, NV, M | 2>(ta)
-                                                          : tiled_kernel<R, L, NV, M>(ta);
+    auto kern = (a.Qs || a.dose || a.n_tab > 0 || a.emat || ta.hourglass) ? tiled_kernel<R, L, NV, M | 2>(ta)
+                                                                          : tiled_kernel<R, L, NV, M>(ta);
     const int b = ta.staged ? ta.threads : 256;
     cudaError_t err = cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)ta.smem_bytes);
@@ -1046,7 +1084,7 @@ inline int blocks_for(int64_t n, int t) {
 template <typename R, int NV, bool KAHAN>
 cudaError_t launch_impl(const StepArgs<R>& a, int64_t n_steps, LaunchCfg& cfg, cudaStream_t s) {
     constexpr int M = KAHAN ? 1 : 0;
-    const bool ext = a.Qs || a.dose || a.n_tab > 0 || a.emat || a.A28;
+    const bool ext = a.Qs || a.dose || a.n_tab > 0 || a.emat || a.A28 || a.W12;
     if (cfg.kernel == FEDFEM_KERNEL_TWO_PHASE) {
         const int b = cfg.block > 0 ? std::min(cfg.block, 256) : 256;
         auto node = ext ? k_node<R, M | 2> : k_node<R, M>;

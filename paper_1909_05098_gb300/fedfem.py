@@ -107,6 +107,8 @@ _SIGS = {
     "fedfem_last_error": ([_ctx_p], C.c_char_p),
     "fedfem_destroy": ([_ctx_p], None),
     "fedfem_version": ([], C.c_char_p),
+    "fedfem_set_hourglass_control": ([_ctx_p, C.c_double], C.c_int),
+    "fedfem_fp64_fma_loop": ([C.c_longlong, C.c_int, C.c_int, C.c_void_p, C.c_void_p], C.c_int),
     "fedfem_debug_set": ([_ctx_p, C.c_int, _i64], C.c_int),
     "fedfem_plan_layout": ([C.c_int, _i64, _dp, _i64, _ip, _ip, C.c_int, _i64, _ip, _i64, C.c_int, _ip, C.c_int,
                             C.POINTER(fedfem_layout_info)] + [C.c_void_p] * 10, C.c_int),
@@ -182,6 +184,13 @@ def _i(a):
 
 def fedfem_version() -> str:
     return _lib.fedfem_version().decode()
+
+
+def fedfem_fp64_fma_loop(iterations: int, blocks: int, threads: int, sink_dev: int, stream=None):
+    """FP64 throughput probe: 16 * iterations * blocks * threads FLOPs on `stream`."""
+    rc = _lib.fedfem_fp64_fma_loop(iterations, blocks, threads, C.c_void_p(sink_dev), C.c_void_p(stream))
+    if rc != OK:
+        raise FedfemError(rc, "fedfem_fp64_fma_loop")
 
 
 def fedfem_create(device: int = 0, precision: int = FP32_KAHAN, cuda_stream: int | None = None):
@@ -491,6 +500,10 @@ def fedfem_set_hex_integration(ctx, rule):
     _check(ctx, _lib.fedfem_set_hex_integration(ctx, int(rule)))
 
 
+def fedfem_set_hourglass_control(ctx, eps: float):
+    _check(ctx, _lib.fedfem_set_hourglass_control(ctx, float(eps)))
+
+
 def fedfem_set_lumping(ctx, mode):
     _check(ctx, _lib.fedfem_set_lumping(ctx, int(mode)))
 
@@ -536,6 +549,8 @@ class Solver:
             fedfem_set_order(self.ctx, order)
             if getattr(p, "hex_rule", "one-point") == "full":
                 fedfem_set_hex_integration(self.ctx, HEX_FULL)
+            elif getattr(p, "hex_rule", "one-point") == "hourglass":
+                fedfem_set_hourglass_control(self.ctx, p.hourglass_eps)
             if getattr(p, "lumping", "element") == "uniform":
                 fedfem_set_lumping(self.ctx, LUMP_UNIFORM)
             apply_material(self.ctx, p.material)

@@ -40,9 +40,23 @@ def _run(p, dt, n, prec, kernel, T0=None, tile_nodes=0):
 
 @pytest.fixture(scope="module")
 def cube128():
+    from oracle.box_spectrum import critical_dt_hex_box
     w = cube_hex_td_convective(n=128)
-    dt = 0.5 * critical_dt(cube_hex_td_convective(n=32).problem)   # lambda_max grows slowly with n
+    # the cube's own critical step, by separation of variables (equal to the dense
+    # solver's on small boxes, tests/test_oracle_dtcr.py)
+    dt = 0.5 * critical_dt_hex_box(w.problem, 128, 1e-3)
     return w, dt
+
+
+def test_cube128_dt_cr_matches_oracle(cube128):
+    w, dt = cube128
+    f = ff()
+    s = f.Solver(w.problem, precision=f.FP32_KAHAN)
+    try:
+        print(f"cube128 dt_cr GPU {s.dt_cr:.12g} oracle {2 * dt:.12g}")
+        assert s.dt_cr == pytest.approx(2 * dt, rel=1e-8)
+    finally:
+        s.close()
 
 
 @pytest.fixture(scope="module")
