@@ -790,9 +790,10 @@ def run_suite(args):
     stream = torch.cuda.Stream()
     rows = []
 
-    def measure(label, p, prec, steps, reps=3, ref=None, dose=False):
+    def measure(label, p, prec, steps, reps=3, ref=None, dose=False, mf=False):
         t0 = time.perf_counter()
-        s = ff.Solver(p, precision=prec, stream=stream.cuda_stream, kernel=ff.KERNEL_PERSISTENT, dose=dose)
+        s = ff.Solver(p, precision=prec, stream=stream.cuda_stream, kernel=ff.KERNEL_PERSISTENT, dose=dose,
+                      matrix_free=mf)
         setup_s = time.perf_counter() - t0
         dt = 0.5 * s.dt_cr
         tuned = tune(s, dt, use_cache=False, stream=stream, steps=min(steps, 50))
@@ -825,7 +826,10 @@ def run_suite(args):
                "sim_s_per_wall_s": dt / (us * 1e-6),
                "algorithmic_gbs": info["algorithmic_bytes_per_step"] / (us * 1e3),
                "hbm_frac": info["algorithmic_bytes_per_step"] / (us * 1e3) / peak,
-               "setup_s": setup_s, "max_err_C": err}
+               "setup_s": setup_s, "max_err_C": err, "matrix_free": mf,
+               "autotune": {names[t["kernel"]] + (f"/{t['tile_nodes']}" if t["tile_nodes"] else "") +
+                            (f"x{t['block']}" if t.get("block") else ""): round(t["us_per_step"], 1)
+                            for t in tuned.get("trials", []) if "us_per_step" in t}}
         if prec == ff.FP64:
             # FP64 operations of one step (FMA = 2): hex8 77 per element (k_e 32, gradient 17, flux 18,
             # loads 10), tet4 40; per free node 15 plus one add per element it sums (8 hex, 24 tet)
@@ -875,11 +879,15 @@ def run_suite(args):
         return f
     measure("tet ellipsoid 60/45/35 mm, h = 1 mm", w2.problem, ff.FP32_KAHAN, 1000, ref=gpu64(w2.problem))
     measure("tet ellipsoid 60/45/35 mm, h = 1 mm", w2.problem, ff.FP64, 1000)
+    measure("tet ellipsoid 60/45/35 mm, h = 1 mm, matrix-free geometry", w2.problem, ff.FP32_KAHAN, 1000,
+            ref=gpu64(w2.problem), mf=True)
     # the same recipe at h = 1.44 mm, whose counts (about 142k nodes, 0.8M tets) are the ones stated
     # for this workload beside its 1 mm spacing
     w2c = ellipsoid_tet_td(h=1.44e-3)
     measure("tet ellipsoid 60/45/35 mm, h = 1.44 mm", w2c.problem, ff.FP32_KAHAN, 1000, ref=gpu64(w2c.problem))
     measure("tet ellipsoid 60/45/35 mm, h = 1.44 mm", w2c.problem, ff.FP64, 1000)
+    measure("tet ellipsoid 60/45/35 mm, h = 1.44 mm, matrix-free geometry", w2c.problem, ff.FP32_KAHAN, 1000,
+            ref=gpu64(w2c.problem), mf=True)
     # 128^3 hex cube, FP64 variant
     w3 = cube_hex_td_convective(n=128)
     measure("hex cube 128^3 elements", w3.problem, ff.FP64, 200)

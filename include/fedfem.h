@@ -174,6 +174,23 @@ int fedfem_set_hex_integration(fedfem_ctx* ctx, int rule);
  * at the next fedfem_precompute.  E_ARG for eps < 0 or not finite. */
 int fedfem_set_hourglass_control(fedfem_ctx* ctx, double eps);
 
+/* Matrix-free element geometry for tet4 meshes with FP32 state (the pre-
+ * computation of Eq. 15-16 moved into the time loop; the paper pre-computes
+ * A_e once, its aim (v) in the introduction).  on = 1: the tiled kernels
+ * (FEDFEM_KERNEL_TILED, FEDFEM_KERNEL_TILED_STAGED) read each tile's node
+ * coordinates (FP32, relative to the centre of the mesh's bounding box,
+ * rounded once from the FP64 input) instead of the 6 matrix values of every
+ * element, and
+ * recompute M_e = V_tet E^-1 E^-T from the corners of each element in FP32
+ * every step: 24 bytes fewer per element and step, about 60 more arithmetic
+ * operations.  Results agree with the stored-matrix kernels to rounding (not
+ * bit for bit) and are the same bits for both kernels and every tile size;
+ * the critical step is unchanged (pre-computed in FP64).  Other
+ * kernels, FP64 state and hex8 meshes give E_UNSUPPORTED (at the next step
+ * for kernels and precision; at once for a hex8 mesh already set).  on = 0
+ * (default): stored matrices. */
+int fedfem_set_matrix_free(fedfem_ctx* ctx, int on);
+
 /* Element order used internally (FEDFEM_ORDER_*; default MORTON). */
 int fedfem_set_order(fedfem_ctx* ctx, int order);
 

@@ -58,6 +58,8 @@ def variant(solver) -> str:
             parts.append("schedule")
     if getattr(solver, "dose_model", False):
         parts.append("dose")
+    if getattr(solver, "matrix_free", False):
+        parts.append("mf")
     return "+".join(parts)
 
 

@@ -48,6 +48,7 @@ struct fedfem_ctx {
     int dose_model = FEDFEM_DOSE_CEM43;
     int hex_rule = FEDFEM_HEX_ONE_POINT;
     double hg_eps = 0.0;                          // hourglass stabilisation of the one-point hex (0: off)
+    int matrix_free = 0;                          // tet4 FP32: element matrices recomputed in the tiled kernels
     double dose_A = 0.0, dose_Ea = 0.0;           // Arrhenius frequency factor (1/s), activation energy (J/mol)
     int n_reg = 0;                                // heterogeneous tissue regions (0: mat everywhere)
     int lumping = FEDFEM_LUMP_ELEMENT;            // perfusion / metabolic heat per node
@@ -356,10 +357,11 @@ cudaError_t talloc(fedfem_ctx* c, P** p, size_t bytes) {
 // halo nodes, most elements at one owned node}, the 6 element-matrix rows
 // (padded element count each), the 16-bit local connectivity (nv per padded
 // element), the halo node ids; 16-byte multiple
-int64_t tile_block_bytes(const Tiles& t, int64_t i, size_t rs, bool hg = false) {
+int64_t tile_block_bytes(const Tiles& t, int64_t i, size_t rs, bool hg = false, bool mf = false) {
     const int64_t ne = t.e_off[i + 1] - t.e_off[i], ne_pad = (ne + 7) / 8 * 8;
     const int64_t nh = t.h_off[i + 1] - t.h_off[i];
-    const int64_t b = 16 + (hg ? 18 : 6) * ne_pad * (int64_t)rs + ne_pad * t.nv * 2 + nh * 4;
+    const int64_t geo = mf ? 16 * ((int64_t)t.B + nh) : (hg ? 18 : 6) * ne_pad * (int64_t)rs;
+    const int64_t b = 16 + geo + ne_pad * t.nv * 2 + nh * 4;
     return (b + 15) / 16 * 16;
 }
 
@@ -380,9 +382,9 @@ size_t rep_bytes(const Tiles& t, size_t ls, int S) {
 // with replicated rows of stride S): two block stages when staged; the tile
 // temperatures and the per-node load table (max_deg rows of B), or the two
 // replicated-row arrays
-size_t tile_smem(const Tiles& t, size_t rs, size_t ls, int* max_block, int kind, int S, bool hg) {
+size_t tile_smem(const Tiles& t, size_t rs, size_t ls, int* max_block, int kind, int S, bool hg, bool mf) {
     int64_t mb = 0;
-    for (int64_t i = 0; i < t.n_tiles; ++i) mb = std::max(mb, tile_block_bytes(t, i, rs, hg));
+    for (int64_t i = 0; i < t.n_tiles; ++i) mb = std::max(mb, tile_block_bytes(t, i, rs, hg, mf));
     *max_block = (int)mb;
     if (kind == 2) return 128 + 2 * rep_bytes(t, ls, S) + 2 * (size_t)mb;
     const size_t ts = ((size_t)t.max_local * ls + 15) / 16 * 16;
@@ -422,6 +424,9 @@ int plan_tiles(fedfem_ctx* c) {
     const size_t rs = c->precision == FEDFEM_FP64 ? sizeof(double) : sizeof(float);
     const size_t ls = rs * c->n_lanes;
     const bool hg = c->W64 || c->W32;   // blocks carry the hourglass weights
+    const bool mf = c->matrix_free != 0;  // blocks carry local coordinates instead of the matrices
+    if (mf && (c->nv != 4 || c->precision == FEDFEM_FP64 || kind == 2))
+        return fail(c, FEDFEM_E_UNSUPPORTED, "matrix-free geometry: tet4, FP32 state, the tiled and staged tiled kernels");
     if (kind == 2 && c->n_lanes > 1) return fail(c, FEDFEM_E_UNSUPPORTED, "the replicated-row kernel takes one lane");
     const int64_t NF = c->L.N_free;
     if (NF == 0) return fail(c, FEDFEM_E_ARG, "no free nodes");
@@ -446,7 +451,7 @@ int plan_tiles(fedfem_ctx* c) {
         for (;;) {   // the default size halves while its tiles do not fit (meshes whose tiles hold many elements)
             m = build_tiles(c->L, B0, t);
             if (!m.empty()) return fail(c, FEDFEM_E_ARG, m);
-            size_t smem = tile_smem(t, rs, ls, &mb, kind, S, hg);
+            size_t smem = tile_smem(t, rs, ls, &mb, kind, S, hg, mf);
             per_sm = tiled_blocks_per_sm(c->precision, c->nv, kind, S, c->n_lanes, smem);
             if (c->tile.blocks_per_sm > 0) per_sm = std::min(per_sm, c->tile.blocks_per_sm);
             if (per_sm >= 1 || c->tile.tile_nodes > 0 || B0 <= 32) break;
@@ -463,7 +468,7 @@ int plan_tiles(fedfem_ctx* c) {
             Tiles tw;
             if (!build_tiles(c->L, (int)Bw, tw).empty()) continue;
             int mbw = 0;
-            int pw = tiled_blocks_per_sm(c->precision, c->nv, kind, S, c->n_lanes, tile_smem(tw, rs, ls, &mbw, kind, S, hg));
+            int pw = tiled_blocks_per_sm(c->precision, c->nv, kind, S, c->n_lanes, tile_smem(tw, rs, ls, &mbw, kind, S, hg, mf));
             if (c->tile.blocks_per_sm > 0) pw = std::min(pw, c->tile.blocks_per_sm);
             if (pw != per_sm) continue;
             B = (int)Bw;
@@ -475,7 +480,7 @@ int plan_tiles(fedfem_ctx* c) {
         m = build_tiles(c->L, B, t);
         if (!m.empty()) return fail(c, FEDFEM_E_ARG, m);
     }
-    const size_t smem = tile_smem(t, rs, ls, &mb, kind, S, hg);
+    const size_t smem = tile_smem(t, rs, ls, &mb, kind, S, hg, mf);
     if (kind == 2 && t.max_deg > (c->nv == 8 ? 8 : 32))
         return fail(c, FEDFEM_E_UNSUPPORTED, "the replicated-row kernel takes at most 8 (hex) or 32 (tet) elements per node");
     if (kind == 2 && ls * ((size_t)std::max(1, t.max_deg) * S + tile_max_halo(t)) > 65536)
@@ -494,14 +499,45 @@ int plan_tiles(fedfem_ctx* c) {
                            cudaMemcpyDeviceToHost, st), "tile pack");
     CU(cudaStreamSynchronize(st), "tile pack");
     std::vector<int64_t> off(t.n_tiles + 1, 0);
-    for (int64_t i = 0; i < t.n_tiles; ++i) off[i + 1] = off[i] + tile_block_bytes(t, i, rs, hg);
+    for (int64_t i = 0; i < t.n_tiles; ++i) off[i + 1] = off[i] + tile_block_bytes(t, i, rs, hg, mf);
     std::vector<unsigned char> blob(off[t.n_tiles], 0);
+    // matrix-free blocks: one origin for every tile, so that a node's stored
+    // coordinates (and every element matrix recomputed from them) do not
+    // depend on the tiling
+    double mf_origin[3] = {0.0, 0.0, 0.0};
+    if (mf) {
+        for (int d = 0; d < 3; ++d) {
+            double lo = c->xyz[d], hi = c->xyz[d];
+            for (int64_t n = 1; n < c->N; ++n) {
+                lo = std::min(lo, c->xyz[3 * n + d]);
+                hi = std::max(hi, c->xyz[3 * n + d]);
+            }
+            mf_origin[d] = 0.5 * (lo + hi);
+        }
+    }
     for (int64_t i = 0; i < t.n_tiles; ++i) {
         unsigned char* b = blob.data() + off[i];
         const int64_t e0 = t.e_off[i], ne = t.e_off[i + 1] - e0, ne_pad = (ne + 7) / 8 * 8;
         const int64_t h0 = t.h_off[i], nh = t.h_off[i + 1] - h0;
         const int32_t hdr[4] = {(int32_t)ne, (int32_t)ne_pad, (int32_t)nh, t.deg[i]};
         std::memcpy(b, hdr, 16);
+        if (mf) {   // node coordinates relative to the mesh's bounding-box centre, rounded once from FP64
+            const int64_t base = i * (int64_t)t.B, own = std::min<int64_t>(t.B, NF - base);
+            const double* a0 = mf_origin;
+            float* X = (float*)(b + 16);
+            auto put = [&](int64_t slot, int64_t internal) {
+                const double* x = &c->xyz[3 * (int64_t)c->L.node_of[internal]];
+                for (int d = 0; d < 3; ++d) X[4 * slot + d] = (float)(x[d] - a0[d]);
+                X[4 * slot + 3] = 0.0f;
+            };
+            for (int64_t l = 0; l < own; ++l) put(l, base + l);
+            for (int64_t h = 0; h < nh; ++h) put(own + h, t.halo[h0 + h]);   // local id own + h
+            uint16_t* lc = (uint16_t*)(b + 16 + 16 * ((int64_t)t.B + nh));
+            std::memcpy(lc, t.lconn.data() + e0 * t.nv, sizeof(uint16_t) * ne * t.nv);
+            int32_t* hh = (int32_t*)(lc + t.nv * ne_pad);
+            std::memcpy(hh, t.halo.data() + h0, sizeof(int32_t) * nh);
+            continue;
+        }
         unsigned char* Mb = b + 16;
         for (int q = 0; q < 6; ++q)
             for (int64_t j = 0; j < ne; ++j)
@@ -570,6 +606,7 @@ TileArgs<R> make_tile_args(fedfem_ctx* c) {
     t.rep_rows = std::max(1, h.max_deg);
     t.max_halo = c->t_max_halo;
     t.hourglass = (c->W64 || c->W32) ? 1 : 0;
+    t.mf = c->matrix_free;
     return t;
 }
 
@@ -584,6 +621,8 @@ int prepare_launch(fedfem_ctx* c, LaunchCfg& cfg) {
     const bool tiled = cfg.kernel == FEDFEM_KERNEL_TILED || cfg.kernel == FEDFEM_KERNEL_TILED_STAGED ||
                        cfg.kernel == FEDFEM_KERNEL_TILED_REP;
     if (c->n_lanes > 1 && !tiled) return fail(c, FEDFEM_E_UNSUPPORTED, "scenario lanes need a tiled kernel");
+    if (!tiled && c->matrix_free)
+        return fail(c, FEDFEM_E_UNSUPPORTED, "matrix-free geometry runs on the tiled kernels");
     if (tiled && (c->A28_64 || c->A28_32))
         return fail(c, FEDFEM_E_UNSUPPORTED, "the fully integrated hexahedron runs on the two-phase and persistent kernels");
     if (tiled) return plan_tiles(c);
@@ -970,6 +1009,15 @@ int fedfem_set_lumping(fedfem_ctx* c, int mode) {
     if (mode != FEDFEM_LUMP_ELEMENT && mode != FEDFEM_LUMP_UNIFORM) return fail(c, FEDFEM_E_ARG, "unknown lumping");
     c->lumping = mode;
     invalidate(c);
+    return FEDFEM_OK;
+}
+
+int fedfem_set_matrix_free(fedfem_ctx* c, int on) {
+    if (!c) return FEDFEM_E_ARG;
+    if (on != 0 && on != 1) return fail(c, FEDFEM_E_ARG, "matrix-free: 0 or 1");
+    if (on && c->has_mesh && c->nv != 4) return fail(c, FEDFEM_E_UNSUPPORTED, "matrix-free geometry is for tet4 meshes");
+    c->matrix_free = on;
+    free_tiles(c);
     return FEDFEM_OK;
 }
 
@@ -1631,6 +1679,8 @@ int fedfem_get_info(fedfem_ctx* c, fedfem_info* info) {
     const int64_t NL = c->n_lanes;   // lanes share V, hA and the element data
     const int64_t nm = (c->A28_64 || c->A28_32) ? 28 : (c->W64 || c->W32) ? 18 : 6;   // element matrix values
     info->algorithmic_bytes_per_step = E * (4 * c->nv + nm * R) + NF * (NL * (node_state + R) + R) + NC * R;
+    if (c->matrix_free)   // coordinates (each node once) instead of the element matrices
+        info->algorithmic_bytes_per_step += 12 * c->N - E * nm * R;
     // a source schedule reads the source part of Q too; the dose is read and written in FP64
     const int64_t extra = (c->sched_f.empty() ? 0 : NF * NL * R) + (c->dose ? NF * 16 : 0) +
                           (c->n_cq > 0 ? NF * 4 * R + E : 0);   // regions: node coefficients, element ids

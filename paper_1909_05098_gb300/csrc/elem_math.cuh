@@ -193,6 +193,29 @@ __device__ __forceinline__ void hex8_hourglass_loads(const L t[8], const R m[6],
     F[7] = (-b + qz) + ((p1 - p0) - (p2 + p3));
 }
 
+// tet4 factored matrix from corner coordinates (Eq. 15-16, recomputed in the
+// time loop instead of read from memory): with the edges a = x1 - x0,
+// b = x2 - x0, c = x3 - x0 (the columns of E), the rows of E^-1 are
+// (b x c, c x a, a x b) / det E and det E = a . (b x c), so
+//   M = V_tet E^-1 E^-T = (r_i . r_j) / (6 det E),  r = (b x c, c x a, a x b).
+// x: the four corners (w unused), relative to any common anchor.
+__device__ __forceinline__ void tet4_matrix(const float4 x[4], float m[6]) {
+    const float ax = x[1].x - x[0].x, ay = x[1].y - x[0].y, az = x[1].z - x[0].z;
+    const float bx = x[2].x - x[0].x, by = x[2].y - x[0].y, bz = x[2].z - x[0].z;
+    const float cx = x[3].x - x[0].x, cy = x[3].y - x[0].y, cz = x[3].z - x[0].z;
+    const float r0x = fmaf(by, cz, -bz * cy), r0y = fmaf(bz, cx, -bx * cz), r0z = fmaf(bx, cy, -by * cx);
+    const float r1x = fmaf(cy, az, -cz * ay), r1y = fmaf(cz, ax, -cx * az), r1z = fmaf(cx, ay, -cy * ax);
+    const float r2x = fmaf(ay, bz, -az * by), r2y = fmaf(az, bx, -ax * bz), r2z = fmaf(ax, by, -ay * bx);
+    const float det = fmaf(ax, r0x, fmaf(ay, r0y, az * r0z));
+    const float s = 1.0f / (6.0f * det);
+    m[0] = s * fmaf(r0x, r0x, fmaf(r0y, r0y, r0z * r0z));
+    m[1] = s * fmaf(r1x, r1x, fmaf(r1y, r1y, r1z * r1z));
+    m[2] = s * fmaf(r2x, r2x, fmaf(r2y, r2y, r2z * r2z));
+    m[3] = s * fmaf(r0x, r1x, fmaf(r0y, r1y, r0z * r1z));
+    m[4] = s * fmaf(r0x, r2x, fmaf(r0y, r2y, r0z * r2z));
+    m[5] = s * fmaf(r1x, r2x, fmaf(r1y, r2y, r1z * r2z));
+}
+
 // tet4: t[4], m[6], k_e -> F[4]
 template <typename R, typename L = R>
 __device__ __forceinline__ void tet4_loads(const L t[4], const R m[6], L ke, L F[4]) {

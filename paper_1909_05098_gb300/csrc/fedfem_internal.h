@@ -176,6 +176,9 @@ struct LaunchCfg {
 // whole into shared memory by one bulk (TMA) copy in the staged kernel):
 //   int32 header {ne, ne_pad, nh, deg}; M: ne_pad x 6 R (one element's six values together);
 //   with hourglass stabilisation: ne_pad x 12 R hourglass weights;
+//   matrix-free (tet4, FP32): instead of the matrices, room for (B + nh) float4 local node
+//   coordinates indexed by local id (owned, then halo; x, y, z relative to the centre of the mesh's
+//   bounding box, the same for every tile);
 //   local connectivity: ne_pad x nv uint16 (id | rank << rank_shift);
 //   halo ids: nh int32.
 template <typename R>
@@ -197,6 +200,7 @@ struct TileArgs {
     int rep_rows;                    // rows of the temperature copies and of the load table (largest rank count)
     int max_halo;                    // largest halo of any tile
     int hourglass;                   // 1: each element's 12 hourglass weights follow its 6 matrix values in the block
+    int mf;                          // 1: matrix-free tet4 blocks: local coordinates instead of element matrices
 };
 
 struct F4;

@@ -450,19 +450,30 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 template <typename R>
 struct TileView {
     int ne, ne_pad, nh, deg;
-    const R* M;                 // ne_pad x 6: an element's six values together
+    const R* M;                 // ne_pad x 6: an element's six values together (null in matrix-free blocks)
     const R* W;                 // ne_pad x 12 hourglass weights (hg blocks), else null
+    const float4* X;            // matrix-free blocks: local node coordinates by local id, else null
     const uint16_t* lc;         // nv entries per element
     const int32_t* halo;        // nh global node ids
 };
+// hg: blocks carry hourglass weights; mf_B > 0: matrix-free blocks of tiles of
+// mf_B owned nodes (coordinates instead of element matrices)
 template <typename R, int NV>
-__device__ __forceinline__ TileView<R> tile_view(const unsigned char* blk, int hg = 0) {
+__device__ __forceinline__ TileView<R> tile_view(const unsigned char* blk, int hg = 0, int mf_B = 0) {
     const int4 hdr = *reinterpret_cast<const int4*>(blk);
     TileView<R> v;
     v.ne = hdr.x; v.ne_pad = hdr.y; v.nh = hdr.z; v.deg = hdr.w;
-    v.M = reinterpret_cast<const R*>(blk + 16);
-    v.W = hg ? v.M + 6 * (size_t)v.ne_pad : nullptr;
-    v.lc = reinterpret_cast<const uint16_t*>(blk + 16 + (hg ? 18 : 6) * (size_t)v.ne_pad * sizeof(R));
+    if (mf_B > 0) {
+        v.M = nullptr;
+        v.W = nullptr;
+        v.X = reinterpret_cast<const float4*>(blk + 16);
+        v.lc = reinterpret_cast<const uint16_t*>(blk + 16 + 16 * (size_t)(mf_B + v.nh));
+    } else {
+        v.M = reinterpret_cast<const R*>(blk + 16);
+        v.W = hg ? v.M + 6 * (size_t)v.ne_pad : nullptr;
+        v.X = nullptr;
+        v.lc = reinterpret_cast<const uint16_t*>(blk + 16 + (hg ? 18 : 6) * (size_t)v.ne_pad * sizeof(R));
+    }
     v.halo = reinterpret_cast<const int32_t*>(v.lc + NV * v.ne_pad);
     return v;
 }
@@ -576,11 +587,23 @@ __device__ __forceinline__ void tile_elements_k(const KL& kl, const TileView<R>&
 #pragma unroll
         for (int n = 0; n < NV; ++n) tt[n] = Ts[c[n] & id_mask];
         R m[6];
+        bool mf = false;
+        if constexpr (EXT && NV == 4 && sizeof(R) == sizeof(float)) {   // matrix-free: M from the corners
+            if (v.X) {
+                float4 xs[4];
 #pragma unroll
-        for (int q = 0; q < 6; q += 2) {   // three 2-wide loads (8- or 16-byte aligned)
-            const typename Vec2<R>::type p = reinterpret_cast<const typename Vec2<R>::type*>(v.M + 6 * j)[q / 2];
-            m[q] = p.x;
-            m[q + 1] = p.y;
+                for (int n = 0; n < 4; ++n) xs[n] = v.X[c[n] & id_mask];
+                tet4_matrix(xs, reinterpret_cast<float*>(m));
+                mf = true;
+            }
+        }
+        if (!mf) {
+#pragma unroll
+            for (int q = 0; q < 6; q += 2) {   // three 2-wide loads (8- or 16-byte aligned)
+                const typename Vec2<R>::type p = reinterpret_cast<const typename Vec2<R>::type*>(v.M + 6 * j)[q / 2];
+                m[q] = p.x;
+                m[q + 1] = p.y;
+            }
         }
         const L ke = element_k<R, NV, L>(tt, kl(j));
         L F[NV];
@@ -669,7 +692,7 @@ __global__ void __launch_bounds__(256, DirectOccupancy<L>::min_blocks) k_tiled_d
         const L* Tin = (s & 1) ? a.T2 : a.T;
         L* Tout = (s & 1) ? a.T : a.T2;
         for (int64_t t = blockIdx.x; t < ta.n_tiles; t += gridDim.x) {
-            const TileView<R> v = tile_view<R, NV>(ta.blocks + ta.block_off[t], ta.hourglass);
+            const TileView<R> v = tile_view<R, NV>(ta.blocks + ta.block_off[t], ta.hourglass, ta.mf ? ta.B : 0);
             const int64_t base = t * ta.B;
             const int own = (int)min((int64_t)ta.B, a.N_free - base);
             tile_fetch<L, false>(v.halo, v.nh, base, own, Tin, Ts);
@@ -764,7 +787,7 @@ __global__ void __launch_bounds__(TPB, StagedOccupancy<L, TPB>::min_blocks)
     auto fail_timeout = [&]() {
         if (threadIdx.x == 0) atomicOr(&a.status->flags, STATUS_TIMEOUT);
     };
-    auto view_of = [&](long long kk, int p) { return tile_view<R, NV>(buf_of(kk, p) ? stage1 : stage0, ta.hourglass); };
+    auto view_of = [&](long long kk, int p) { return tile_view<R, NV>(buf_of(kk, p) ? stage1 : stage0, ta.hourglass, ta.mf ? ta.B : 0); };
     // temperatures of tile kk (its stage has landed) into Ts, asynchronously
     auto fetch = [&](long long kk, int p, const L* Tin) {
         const TileView<R> v = view_of(kk, p);
@@ -952,7 +975,7 @@ __global__ void __launch_bounds__(TPB, StagedOccupancy<L, TPB>::min_blocks)
     auto fail_timeout = [&]() {
         if (threadIdx.x == 0) atomicOr(&a.status->flags, STATUS_TIMEOUT);
     };
-    auto view_of = [&](long long kk, int p) { return tile_view<R, NV>(buf_of(kk, p) ? stage1 : stage0, ta.hourglass); };
+    auto view_of = [&](long long kk, int p) { return tile_view<R, NV>(buf_of(kk, p) ? stage1 : stage0, ta.hourglass, ta.mf ? ta.B : 0); };
     // owned temperatures into row 0 (thread l fetches owned node l), halo ones after the rows
     auto fetch = [&](long long kk, int p, const L* Tin) {
         const TileView<R> v = view_of(kk, p);
@@ -1055,8 +1078,8 @@ template <typename R, typename L, int NV, bool KAHAN>
 cudaError_t launch_tiled_impl(const StepArgs<R, L>& a, const TileArgs<R>& ta, int64_t n_steps, LaunchCfg& cfg,
                               cudaStream_t s) {
     constexpr int M = KAHAN ? 1 : 0;
-    auto kern = (a.Qs || a.dose || a.n_tab > 0 || a.emat || ta.hourglass) ? tiled_kernel<R, L, NV, M | 2>(ta)
-                                                                          : tiled_kernel<R, L, NV, M>(ta);
+    auto kern = (a.Qs || a.dose || a.n_tab > 0 || a.emat || ta.hourglass || ta.mf) ? tiled_kernel<R, L, NV, M | 2>(ta)
+                                                                                   : tiled_kernel<R, L, NV, M>(ta);
     const int b = ta.staged ? ta.threads : 256;
     cudaError_t err = cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)ta.smem_bytes);

@@ -108,6 +108,7 @@ _SIGS = {
     "fedfem_destroy": ([_ctx_p], None),
     "fedfem_version": ([], C.c_char_p),
     "fedfem_set_hourglass_control": ([_ctx_p, C.c_double], C.c_int),
+    "fedfem_set_matrix_free": ([_ctx_p, C.c_int], C.c_int),
     "fedfem_fp64_fma_loop": ([C.c_longlong, C.c_int, C.c_int, C.c_void_p, C.c_void_p], C.c_int),
     "fedfem_debug_set": ([_ctx_p, C.c_int, _i64], C.c_int),
     "fedfem_plan_layout": ([C.c_int, _i64, _dp, _i64, _ip, _ip, C.c_int, _i64, _ip, _i64, C.c_int, _ip, C.c_int,
@@ -504,6 +505,10 @@ def fedfem_set_hourglass_control(ctx, eps: float):
     _check(ctx, _lib.fedfem_set_hourglass_control(ctx, float(eps)))
 
 
+def fedfem_set_matrix_free(ctx, on: bool):
+    _check(ctx, _lib.fedfem_set_matrix_free(ctx, 1 if on else 0))
+
+
 def fedfem_set_lumping(ctx, mode):
     _check(ctx, _lib.fedfem_set_lumping(ctx, int(mode)))
 
@@ -539,14 +544,19 @@ class Solver:
     _T_inf, flux_nodes/_q, T0, T_lo, T_hi."""
 
     def __init__(self, problem, precision=FP32_KAHAN, device=0, stream=None, order=ORDER_MORTON,
-                 kernel=KERNEL_PERSISTENT, T_lo=None, T_hi=None, dose=False):
+                 kernel=KERNEL_PERSISTENT, T_lo=None, T_hi=None, dose=False, matrix_free=False):
         self.ctx = fedfem_create(device, precision, stream)
         self.problem = problem
         self.dose_model = dose
+        self.matrix_free = matrix_free
+        if matrix_free and kernel not in (KERNEL_TILED, KERNEL_TILED_STAGED):
+            kernel = KERNEL_TILED_STAGED      # the kernels that recompute the element matrices
         try:
             p = problem
             fedfem_set_mesh(self.ctx, p.elem_type, p.xyz, p.conn)
             fedfem_set_order(self.ctx, order)
+            if matrix_free:
+                fedfem_set_matrix_free(self.ctx, True)
             if getattr(p, "hex_rule", "one-point") == "full":
                 fedfem_set_hex_integration(self.ctx, HEX_FULL)
             elif getattr(p, "hex_rule", "one-point") == "hourglass":

@@ -219,3 +219,23 @@ def test_hourglass_element_null_space_is_constants_only():
         w1 = np.linalg.eigvalsh(hex8_reduced(xe)[0])
         assert abs(w[0]) < 1e-12 * w[-1] and w[1] > 1e-6 * w[-1]    # one zero: the constant
         assert np.sum(np.abs(w1) < 1e-12 * w1[-1]) == 5                # the plain rule: constant + 4 hourglass
+
+
+def test_element_matrices_do_not_depend_on_where_the_element_sits():
+    """A_e depends on the corners only through their differences (Eq. 15-16),
+    so computing it from coordinates relative to any anchor (as a tile's local
+    coordinates are) gives the same matrix: a rigid translation by 6 cm
+    changes no entry beyond the rounding of the translated coordinates."""
+    from oracle.elements import HEX8_NATURAL, hex8_reduced, tet4_linear
+    rng = np.random.default_rng(9)
+    shift = np.array([0.061, -0.044, 0.037])
+    for _ in range(5):
+        xt = rng.uniform(0, 1e-3, (4, 3))
+        xt[1:] += np.eye(3) * 1e-3                                  # well shaped, positive orientation
+        A, _, _ = tet4_linear(xt)
+        B, _, _ = tet4_linear(xt + shift)
+        np.testing.assert_allclose(B, A, rtol=0, atol=1e-11 * np.abs(A).max())
+        xh = 0.5e-3 * (HEX8_NATURAL + 1.0) + rng.uniform(-0.1e-3, 0.1e-3, (8, 3))
+        A, _, _ = hex8_reduced(xh)
+        B, _, _ = hex8_reduced(xh + shift)
+        np.testing.assert_allclose(B, A, rtol=0, atol=1e-11 * np.abs(A).max())
