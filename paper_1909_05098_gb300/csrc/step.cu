@@ -52,14 +52,22 @@ struct Vec<double> {
 };
 
 // Property P (0 rho, 1 c, 2 k) of a piecewise-linear table at T.  The table
-// points increase, so the interval j is the number of interior points <= T
-// (compares against launch arguments); its start, value and slope are then
-// three cached loads.
+// points increase, so the interval j is the number of interior points <= T:
+// the bin of T gives a lower bound and two compares against launch arguments
+// finish it (or, without bins, compares against every interior point); its
+// start, value and slope are then three cached loads.
 template <int P, typename R, typename L>
 __device__ __forceinline__ R tab_law(const StepArgs<R, L>& a, R T) {
     int j = 0;
+    if (a.tab_nbin > 0) {
+        const int b = min(max((int)((T - a.tab_lo) * a.tab_inv_w), 0), a.tab_nbin - 1);
+        j = a.tab_bin[b];
 #pragma unroll
-    for (int q = 1; q < kMaxTable - 1; ++q) j += (q < a.n_tab - 1 && T >= a.tab_T[q]) ? 1 : 0;
+        for (int k = 0; k < 2; ++k) j += (j + 1 < a.n_tab - 1 && T >= a.tab_T[j + 1]) ? 1 : 0;
+    } else {
+#pragma unroll
+        for (int q = 1; q < kMaxTable - 1; ++q) j += (q < a.n_tab - 1 && T >= a.tab_T[q]) ? 1 : 0;
+    }
     const R* t = a.tab + j;
     return fmadd(__ldg(t + (4 + P) * kMaxTable), T - __ldg(t), __ldg(t + (1 + P) * kMaxTable));
 }
@@ -450,9 +458,12 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 template <typename R>
 struct TileView {
     int ne, ne_pad, nh, deg;
-    const R* M;                 // ne_pad x 6: an element's six values together (null in matrix-free blocks)
-    const R* W;                 // ne_pad x 12 hourglass weights (hg blocks), else null
-    const float4* X;            // matrix-free blocks: local node coordinates by local id, else null
+    // (every pointer is derived from the block, never null, so that shared-memory
+    // blocks keep shared-space loads; hg and mf say which parts exist)
+    bool hg, mf;
+    const R* M;                 // ne_pad x 6: an element's six values together (absent in matrix-free blocks)
+    const R* W;                 // hg blocks: ne_pad x 12 hourglass weights
+    const float4* X;            // mf blocks: local node coordinates by local id
     const uint16_t* lc;         // nv entries per element
     const int32_t* halo;        // nh global node ids
 };
@@ -463,20 +474,24 @@ __device__ __forceinline__ TileView<R> tile_view(const unsigned char* blk, int h
     const int4 hdr = *reinterpret_cast<const int4*>(blk);
     TileView<R> v;
     v.ne = hdr.x; v.ne_pad = hdr.y; v.nh = hdr.z; v.deg = hdr.w;
-    if (mf_B > 0) {
-        v.M = nullptr;
-        v.W = nullptr;
-        v.X = reinterpret_cast<const float4*>(blk + 16);
-        v.lc = reinterpret_cast<const uint16_t*>(blk + 16 + 16 * (size_t)(mf_B + v.nh));
-    } else {
-        v.M = reinterpret_cast<const R*>(blk + 16);
-        v.W = hg ? v.M + 6 * (size_t)v.ne_pad : nullptr;
-        v.X = nullptr;
-        v.lc = reinterpret_cast<const uint16_t*>(blk + 16 + (hg ? 18 : 6) * (size_t)v.ne_pad * sizeof(R));
-    }
+    v.hg = hg != 0 && mf_B == 0;
+    v.mf = mf_B > 0;
+    v.M = reinterpret_cast<const R*>(blk + 16);
+    v.W = v.M + 6 * (size_t)v.ne_pad;
+    v.X = reinterpret_cast<const float4*>(blk + 16);
+    const size_t geo = v.mf ? 16 * (size_t)(mf_B + v.nh) : (v.hg ? 18 : 6) * (size_t)v.ne_pad * sizeof(R);
+    v.lc = reinterpret_cast<const uint16_t*>(blk + 16 + geo);
     v.halo = reinterpret_cast<const int32_t*>(v.lc + NV * v.ne_pad);
     return v;
 }
+
+// the block variants a kernel build can meet: only the builds with the
+// extensions (MODE bit 1) read hourglass weights or coordinates, so the plain
+// builds see constants and keep their code
+template <int MODE, typename R>
+__device__ __forceinline__ int view_hg(const TileArgs<R>& ta) { return (MODE & 2) != 0 ? ta.hourglass : 0; }
+template <int MODE, typename R>
+__device__ __forceinline__ int view_mf(const TileArgs<R>& ta) { return (MODE & 2) != 0 && ta.mf ? ta.B : 0; }
 
 // element loads inside a tile: the plain factored rule, or (kernels built with
 // the extensions, blocks carrying weights) the hourglass-stabilised one
@@ -485,7 +500,7 @@ __device__ __forceinline__ void tile_loads(const TileView<R>& v, int j, const L 
                                            L F[NV]) {
     if constexpr (NV == 8) {
         if constexpr (EXT) {
-            if (v.W) {
+            if (v.hg) {
                 R w[12];
 #pragma unroll
                 for (int q = 0; q < 12; q += 2) {
@@ -589,7 +604,7 @@ __device__ __forceinline__ void tile_elements_k(const KL& kl, const TileView<R>&
         R m[6];
         bool mf = false;
         if constexpr (EXT && NV == 4 && sizeof(R) == sizeof(float)) {   // matrix-free: M from the corners
-            if (v.X) {
+            if (v.mf) {
                 float4 xs[4];
 #pragma unroll
                 for (int n = 0; n < 4; ++n) xs[n] = v.X[c[n] & id_mask];
@@ -692,7 +707,7 @@ __global__ void __launch_bounds__(256, DirectOccupancy<L>::min_blocks) k_tiled_d
         const L* Tin = (s & 1) ? a.T2 : a.T;
         L* Tout = (s & 1) ? a.T : a.T2;
         for (int64_t t = blockIdx.x; t < ta.n_tiles; t += gridDim.x) {
-            const TileView<R> v = tile_view<R, NV>(ta.blocks + ta.block_off[t], ta.hourglass, ta.mf ? ta.B : 0);
+            const TileView<R> v = tile_view<R, NV>(ta.blocks + ta.block_off[t], view_hg<MODE>(ta), view_mf<MODE>(ta));
             const int64_t base = t * ta.B;
             const int own = (int)min((int64_t)ta.B, a.N_free - base);
             tile_fetch<L, false>(v.halo, v.nh, base, own, Tin, Ts);
@@ -787,7 +802,7 @@ __global__ void __launch_bounds__(TPB, StagedOccupancy<L, TPB>::min_blocks)
     auto fail_timeout = [&]() {
         if (threadIdx.x == 0) atomicOr(&a.status->flags, STATUS_TIMEOUT);
     };
-    auto view_of = [&](long long kk, int p) { return tile_view<R, NV>(buf_of(kk, p) ? stage1 : stage0, ta.hourglass, ta.mf ? ta.B : 0); };
+    auto view_of = [&](long long kk, int p) { return tile_view<R, NV>(buf_of(kk, p) ? stage1 : stage0, view_hg<MODE>(ta), view_mf<MODE>(ta)); };
     // temperatures of tile kk (its stage has landed) into Ts, asynchronously
     auto fetch = [&](long long kk, int p, const L* Tin) {
         const TileView<R> v = view_of(kk, p);
@@ -975,7 +990,7 @@ __global__ void __launch_bounds__(TPB, StagedOccupancy<L, TPB>::min_blocks)
     auto fail_timeout = [&]() {
         if (threadIdx.x == 0) atomicOr(&a.status->flags, STATUS_TIMEOUT);
     };
-    auto view_of = [&](long long kk, int p) { return tile_view<R, NV>(buf_of(kk, p) ? stage1 : stage0, ta.hourglass, ta.mf ? ta.B : 0); };
+    auto view_of = [&](long long kk, int p) { return tile_view<R, NV>(buf_of(kk, p) ? stage1 : stage0, view_hg<MODE>(ta), view_mf<MODE>(ta)); };
     // owned temperatures into row 0 (thread l fetches owned node l), halo ones after the rows
     auto fetch = [&](long long kk, int p, const L* Tin) {
         const TileView<R> v = view_of(kk, p);
