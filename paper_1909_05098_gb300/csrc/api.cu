@@ -295,9 +295,6 @@ int reset_status(fedfem_ctx* c) {
     return FEDFEM_OK;
 }
 
-template <typename R, typename L>
-void table_bins(const fedfem_ctx* c, StepArgs<R, L>& a);
-
 template <typename R, typename L = R>
 StepArgs<R, L> make_args(fedfem_ctx* c, const R* M, const R* V, const R* Q, const R* hA, double dt,
                          const R* Qs = nullptr) {
@@ -332,7 +329,6 @@ StepArgs<R, L> make_args(fedfem_ctx* c, const R* M, const R* V, const R* Q, cons
     a.step0 = c->steps_issued;
     a.n_tab = c->tab_n;
     for (int j = 0; j < c->tab_n; ++j) a.tab_T[j] = (R)c->tab_T[j];
-    table_bins(c, a);
     a.tab = std::is_same<R, double>::value ? (const R*)c->tab64 : (const R*)c->tab32;
     a.A28 = std::is_same<R, double>::value ? (const R*)c->A28_64 : (const R*)c->A28_32;
     a.W12 = std::is_same<R, double>::value ? (const R*)c->W64 : (const R*)c->W32;
@@ -345,41 +341,6 @@ StepArgs<R, L> make_args(fedfem_ctx* c, const R* M, const R* V, const R* Q, cons
         a.Cq = std::is_same<R, double>::value ? (const R*)c->Cq64 : (const R*)c->Cq32;
     }
     return a;
-}
-
-// Bins of the table's interval search (see StepArgs::tab_nbin): they cover
-// [T_lo, T_hi] and every interior point with a margin, are at most 2/5 of the
-// smallest gap between interior points wide (so a bin and its neighbours hold
-// at most one point), and store the interior points at or below the bin's
-// start less a guard of 1/1000 bin, counted against the table values as the
-// kernels see them (state precision).  No bins when 256 are not enough.
-template <typename R, typename L>
-void table_bins(const fedfem_ctx* c, StepArgs<R, L>& a) {
-    a.tab_nbin = 0;
-    const int n = c->tab_n;
-    if (n < 3) return;   // no interior point: interval 0 always
-    double lo = c->T_lo, hi = c->T_hi, gap = INFINITY;
-    for (int q = 1; q < n - 1; ++q) {
-        lo = std::min(lo, c->tab_T[q]);
-        hi = std::max(hi, c->tab_T[q]);
-        if (q + 1 < n - 1) gap = std::min(gap, c->tab_T[q + 1] - c->tab_T[q]);
-    }
-    const double margin = 0.01 * (hi - lo) + 1e-6;
-    lo -= margin;
-    hi += margin;
-    int nb = 16;
-    while (nb < kMaxTableBins && (hi - lo) / nb > 0.4 * gap) nb *= 2;
-    const double w = (hi - lo) / nb;
-    if (w > 0.4 * gap) return;
-    for (int b = 0; b < nb; ++b) {
-        const R start = (R)(lo + b * w - 1e-3 * w);
-        int j = 0;
-        for (int q = 1; q < n - 1; ++q) j += (R)c->tab_T[q] <= start ? 1 : 0;
-        a.tab_bin[b] = (unsigned char)j;
-    }
-    a.tab_lo = (R)lo;
-    a.tab_inv_w = (R)(1.0 / w);
-    a.tab_nbin = nb;
 }
 
 template <typename P>

@@ -95,7 +95,6 @@ struct DevStatus {
 // temperature state -- R itself, or F4 for four scenario lanes.
 constexpr int kMaxSegments = 8;   // pieces of a source schedule
 constexpr int kMaxTable = 8;      // points of a piecewise-linear property table
-constexpr int kMaxTableBins = 256;  // bins of its interval search
 constexpr int kMaxRegions = 16;   // tissue regions of a heterogeneous mesh
 
 template <typename R, typename L = R>
@@ -141,14 +140,6 @@ struct StepArgs {
     int n_tab;
     R tab_T[kMaxTable];
     const R* tab;
-    // interval search by bins: bin b = (T - tab_lo) * tab_inv_w (clamped to
-    // [0, tab_nbin)) holds a lower bound of the interval index (the interior
-    // points at or below the bin's start, less a guard); at most one interior
-    // point lies within a bin and its neighbours, so two upward steps finish
-    // the search exactly.  tab_nbin = 0: the plain search over all points.
-    int tab_nbin;
-    R tab_lo, tab_inv_w;
-    unsigned char tab_bin[kMaxTableBins];
     // heterogeneous tissue (emat non-null): each element's region, in internal
     // element order (emat) and in tile-element order (emat_tile, tile t's
     // elements from emat_off[t]); each region's k law (T_ref, k0, dk) in

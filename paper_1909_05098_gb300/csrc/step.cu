@@ -52,22 +52,14 @@ struct Vec<double> {
 };
 
 // Property P (0 rho, 1 c, 2 k) of a piecewise-linear table at T.  The table
-// points increase, so the interval j is the number of interior points <= T:
-// the bin of T gives a lower bound and two compares against launch arguments
-// finish it (or, without bins, compares against every interior point); its
-// start, value and slope are then three cached loads.
+// points increase, so the interval j is the number of interior points <= T
+// (compares against launch arguments); its start, value and slope are then
+// three cached loads.
 template <int P, typename R, typename L>
 __device__ __forceinline__ R tab_law(const StepArgs<R, L>& a, R T) {
     int j = 0;
-    if (a.tab_nbin > 0) {
-        const int b = min(max((int)((T - a.tab_lo) * a.tab_inv_w), 0), a.tab_nbin - 1);
-        j = a.tab_bin[b];
 #pragma unroll
-        for (int k = 0; k < 2; ++k) j += (j + 1 < a.n_tab - 1 && T >= a.tab_T[j + 1]) ? 1 : 0;
-    } else {
-#pragma unroll
-        for (int q = 1; q < kMaxTable - 1; ++q) j += (q < a.n_tab - 1 && T >= a.tab_T[q]) ? 1 : 0;
-    }
+    for (int q = 1; q < kMaxTable - 1; ++q) j += (q < a.n_tab - 1 && T >= a.tab_T[q]) ? 1 : 0;
     const R* t = a.tab + j;
     return fmadd(__ldg(t + (4 + P) * kMaxTable), T - __ldg(t), __ldg(t + (1 + P) * kMaxTable));
 }
@@ -990,7 +982,9 @@ __global__ void __launch_bounds__(TPB, StagedOccupancy<L, TPB>::min_blocks)
     auto fail_timeout = [&]() {
         if (threadIdx.x == 0) atomicOr(&a.status->flags, STATUS_TIMEOUT);
     };
-    auto view_of = [&](long long kk, int p) { return tile_view<R, NV>(buf_of(kk, p) ? stage1 : stage0, view_hg<MODE>(ta), view_mf<MODE>(ta)); };
+    auto view_of = [&](long long kk, int p) {   // (no matrix-free blocks: the host refuses them here)
+        return tile_view<R, NV>(buf_of(kk, p) ? stage1 : stage0, view_hg<MODE>(ta), 0);
+    };
     // owned temperatures into row 0 (thread l fetches owned node l), halo ones after the rows
     auto fetch = [&](long long kk, int p, const L* Tin) {
         const TileView<R> v = view_of(kk, p);
