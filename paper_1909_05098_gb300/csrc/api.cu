@@ -74,8 +74,6 @@ struct fedfem_ctx {
     int32_t *sell_off = nullptr, *sell_ids = nullptr;
     double *V64 = nullptr, *Q64 = nullptr, *hA64 = nullptr, *Qs64 = nullptr;
     float *V32 = nullptr, *Q32 = nullptr, *hA32 = nullptr, *Qs32 = nullptr;
-    double* tab64 = nullptr;   // device copy of the property table (7 x kMaxTable), state precision
-    float* tab32 = nullptr;
     unsigned char* emat = nullptr;             // regions: per internal element
     double* A28_64 = nullptr;                  // fully integrated hex8: 28 planes of E
     float* A28_32 = nullptr;
@@ -157,7 +155,6 @@ void free_device(fedfem_ctx* c) {
     c->dev_bytes = 0;
     c->conn4 = nullptr; c->M64 = nullptr; c->M32 = nullptr; c->sell_off = c->sell_ids = nullptr;
     c->V64 = c->Q64 = c->hA64 = c->Qs64 = nullptr; c->V32 = c->Q32 = c->hA32 = c->Qs32 = nullptr;
-    c->tab64 = nullptr; c->tab32 = nullptr;
     c->emat = nullptr; c->Cq64 = c->matk64 = nullptr; c->Cq32 = c->matk32 = nullptr;
     c->A28_64 = nullptr; c->A28_32 = nullptr;
     c->W64 = nullptr; c->W32 = nullptr;
@@ -329,7 +326,11 @@ StepArgs<R, L> make_args(fedfem_ctx* c, const R* M, const R* V, const R* Q, cons
     a.step0 = c->steps_issued;
     a.n_tab = c->tab_n;
     for (int j = 0; j < c->tab_n; ++j) a.tab_T[j] = (R)c->tab_T[j];
-    a.tab = std::is_same<R, double>::value ? (const R*)c->tab64 : (const R*)c->tab32;
+    for (int P = 0; P < 3 && c->tab_n > 1; ++P) {
+        a.tab_p0[P] = (R)c->tab_p[P][0];
+        a.tab_s0[P] = (R)tab_slope(c, P, 0);
+        for (int q = 1; q + 1 < c->tab_n; ++q) a.tab_d[P][q] = (R)(tab_slope(c, P, q) - tab_slope(c, P, q - 1));
+    }
     a.A28 = std::is_same<R, double>::value ? (const R*)c->A28_64 : (const R*)c->A28_32;
     a.W12 = std::is_same<R, double>::value ? (const R*)c->W64 : (const R*)c->W32;
     a.hg_eps4 = (R)(0.25 * c->hg_eps);
@@ -1314,26 +1315,6 @@ int fedfem_precompute(fedfem_ctx* c, double T_lo, double T_hi, double* dt_cr_out
             CU(cudaMemcpy(c->Cq64 + 3 * NF, b.data(), sizeof(double) * NF, cudaMemcpyHostToDevice), "copy");
             beta_ref = c->Cq64 + 3 * NF;
         }
-    }
-    if (c->tab_n > 0) {   // [T_j | rho_j | c_j | k_j | slopes of rho, c, k], kMaxTable each
-        double h[7 * kMaxTable] = {};
-        for (int j = 0; j < c->tab_n; ++j) {
-            h[j] = c->tab_T[j];
-            for (int P = 0; P < 3; ++P) {
-                h[(1 + P) * kMaxTable + j] = c->tab_p[P][j];
-                h[(4 + P) * kMaxTable + j] = j + 1 < c->tab_n ? tab_slope(c, P, j) : 0.0;
-            }
-        }
-        float f[7 * kMaxTable];
-        for (int q = 0; q < 7 * kMaxTable; ++q) f[q] = (float)h[q];
-        if (c->precision == FEDFEM_FP64) {
-            CU(dalloc(c, &c->tab64, sizeof(h)), "alloc");
-            CU(cudaMemcpyAsync(c->tab64, h, sizeof(h), cudaMemcpyHostToDevice, st), "copy");
-        } else {
-            CU(dalloc(c, &c->tab32, sizeof(f)), "alloc");
-            CU(cudaMemcpyAsync(c->tab32, f, sizeof(f), cudaMemcpyHostToDevice, st), "copy");
-        }
-        CU(cudaStreamSynchronize(st), "copy");   // h and f are on this stack frame
     }
     CU(cudaStreamSynchronize(st), "nodal kernel");
     LanczosResult lr;

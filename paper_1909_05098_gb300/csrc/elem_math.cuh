@@ -93,6 +93,11 @@ __device__ __forceinline__ F4 fmadd(F4 a, F4 b, F4 c) {
 __device__ __forceinline__ F4 fmadd(float a, F4 b, F4 c) { return fmadd(f4(a), b, c); }
 __device__ __forceinline__ F4 fmadd(float a, F4 b, float c) { return fmadd(f4(a), b, f4(c)); }
 __device__ __forceinline__ F4 fmadd(F4 a, F4 b, float c) { return fmadd(a, b, f4(c)); }
+// max(x, 0): the ramp of one kink of a piecewise-linear law
+__device__ __forceinline__ float ramp(float x) { return fmaxf(x, 0.0f); }
+__device__ __forceinline__ double ramp(double x) { return fmax(x, 0.0); }
+__device__ __forceinline__ float2 ramp(float2 x) { return make_float2(fmaxf(x.x, 0.0f), fmaxf(x.y, 0.0f)); }
+__device__ __forceinline__ F4 ramp(F4 x) { return F4{ramp(x.x), ramp(x.y), ramp(x.z), ramp(x.w)}; }
 __device__ __forceinline__ bool all_in(F4 v, float lo, float hi) {
     return (v.x >= lo && v.x <= hi) && (v.y >= lo && v.y <= hi) && (v.z >= lo && v.z <= hi) && (v.w >= lo && v.w <= hi);
 }

@@ -133,13 +133,15 @@ struct StepArgs {
     double dose_lnA, dose_EaR;
     float dose_c43, dose_a2, dose_g2;   // FP32 state: the rate as 2^(c43 s (T - 43) + a2 - g2 / T_K)
     // piecewise-linear laws (n_tab > 0): property P (0 rho, 1 c, 2 k) is
-    // p_P[j] + s_P[j] (T - T_j) on the interval j that holds T (the first one
-    // below the table, the last one above it).  tab: device array of 7 rows of
-    // kMaxTable, [T_j | p_rho | p_c | p_k | s_rho | s_c | s_k]; tab_T: the T_j
-    // again, as launch arguments, for the interval search.
+    // linear on each interval between the points tab_T (the end intervals
+    // extended beyond the table), written by its kinks:
+    //   p(T) = tab_p0[P] + tab_s0[P] (T - T_0) + sum_q tab_d[P][q] max(T - T_q, 0)
+    // over the interior points q = 1 .. n_tab - 2, tab_d the change of slope
+    // at T_q.  All launch arguments, so that an evaluation reads no memory.
     int n_tab;
     R tab_T[kMaxTable];
-    const R* tab;
+    R tab_p0[3], tab_s0[3];
+    R tab_d[3][kMaxTable];
     // heterogeneous tissue (emat non-null): each element's region, in internal
     // element order (emat) and in tile-element order (emat_tile, tile t's
     // elements from emat_off[t]); each region's k law (T_ref, k0, dk) in

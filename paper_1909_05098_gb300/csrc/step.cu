@@ -51,21 +51,18 @@ struct Vec<double> {
     }
 };
 
-// Property P (0 rho, 1 c, 2 k) of a piecewise-linear table at T.  The table
-// points increase, so the interval j is the number of interior points <= T
-// (compares against launch arguments); its start, value and slope are then
-// three cached loads.
-template <int P, typename R, typename L>
-__device__ __forceinline__ R tab_law(const StepArgs<R, L>& a, R T) {
-    int j = 0;
+// Property P (0 rho, 1 c, 2 k) of a piecewise-linear table at T, from its
+// first interval and the slope change at each interior point (the same
+// function as the value and slope of the interval that holds T; the end
+// intervals extend beyond the table).  Every term reads launch arguments;
+// the point count is the same for every thread, so its test is uniform.
+template <int P, typename R, typename L, typename X>
+__device__ __forceinline__ X tab_law(const StepArgs<R, L>& a, X T) {
+    X v = fmadd(a.tab_s0[P], T - a.tab_T[0], a.tab_p0[P]);
 #pragma unroll
-    for (int q = 1; q < kMaxTable - 1; ++q) j += (q < a.n_tab - 1 && T >= a.tab_T[q]) ? 1 : 0;
-    const R* t = a.tab + j;
-    return fmadd(__ldg(t + (4 + P) * kMaxTable), T - __ldg(t), __ldg(t + (1 + P) * kMaxTable));
-}
-template <int P, typename R, typename L>
-__device__ __forceinline__ F4 tab_law(const StepArgs<R, L>& a, F4 T) {
-    return F4{tab_law<P>(a, T.x), tab_law<P>(a, T.y), tab_law<P>(a, T.z), tab_law<P>(a, T.w)};
+    for (int q = 1; q < kMaxTable - 1; ++q)
+        if (q < a.n_tab - 1) v = fmadd(a.tab_d[P][q], ramp(T - a.tab_T[q]), v);
+    return v;
 }
 
 // k(T) from the property table
@@ -75,6 +72,55 @@ struct TabKLaw {
     template <typename X>
     __device__ __forceinline__ X at(X T) const { return tab_law<2>(a, T); }
 };
+
+// Eq. 13's k_e under a table law: k at every corner as tab_law<2> computes
+// it (the same operations in the same order, so the same bits), with one
+// uniform test per interior point for the whole element; FP32 corners go in
+// pairs through the packed instructions, paired as in sum_nodal.
+template <typename R, int NV, typename L, typename R2, typename L2>
+__device__ __forceinline__ L element_k(const L t[NV], const TabKLaw<R2, L2>& kl) {
+    const StepArgs<R2, L2>& a = kl.a;
+    if constexpr (std::is_same<L, float>::value) {
+        constexpr int NP = NV / 2;
+        float2 tp[NP];
+        if constexpr (NV == 8) {
+            tp[0] = make_float2(t[0], t[1]); tp[1] = make_float2(t[3], t[2]);
+            tp[2] = make_float2(t[4], t[5]); tp[3] = make_float2(t[7], t[6]);
+        } else {
+            tp[0] = make_float2(t[0], t[1]); tp[1] = make_float2(t[2], t[3]);
+        }
+        const float2 T0 = make_float2(a.tab_T[0], a.tab_T[0]);
+        const float2 s0 = make_float2(a.tab_s0[2], a.tab_s0[2]), p0 = make_float2(a.tab_p0[2], a.tab_p0[2]);
+        float2 kp[NP];
+#pragma unroll
+        for (int i = 0; i < NP; ++i) kp[i] = fma2(s0, sub2(tp[i], T0), p0);
+#pragma unroll
+        for (int q = 1; q < kMaxTable - 1; ++q)
+            if (q < a.n_tab - 1) {
+                const float2 Tq = make_float2(a.tab_T[q], a.tab_T[q]), dq = make_float2(a.tab_d[2][q], a.tab_d[2][q]);
+#pragma unroll
+                for (int i = 0; i < NP; ++i) kp[i] = fma2(dq, ramp(sub2(tp[i], Tq)), kp[i]);
+            }
+        if constexpr (NV == 8) {
+            const float2 s = add2(add2(kp[0], kp[1]), add2(kp[2], kp[3]));
+            return 0.125f * (s.x + s.y);
+        } else {
+            const float2 s = add2(kp[0], kp[1]);
+            return 0.25f * (s.x + s.y);
+        }
+    } else {
+        L kn[NV];
+#pragma unroll
+        for (int n = 0; n < NV; ++n) kn[n] = fmadd(a.tab_s0[2], t[n] - a.tab_T[0], a.tab_p0[2]);
+#pragma unroll
+        for (int q = 1; q < kMaxTable - 1; ++q)
+            if (q < a.n_tab - 1) {
+#pragma unroll
+                for (int n = 0; n < NV; ++n) kn[n] = fmadd(a.tab_d[2][q], ramp(t[n] - a.tab_T[q]), kn[n]);
+            }
+        return R(1) / R(NV) * sum_nodal<NV, L>(kn);
+    }
+}
 
 // The element k laws of a context, as functions of the element index j: the
 // material's law (Plain), each element's region law (Region), or the table
@@ -359,7 +405,7 @@ __device__ __forceinline__ bool grid_barrier(DevStatus* st, unsigned long long& 
 }
 
 template <typename R, int NV, int MODE>
-__global__ void __launch_bounds__(256) k_persistent(StepArgs<R> a, long long n_steps, long long spin_limit) {
+__device__ __forceinline__ void persistent_steps(const StepArgs<R>& a, long long n_steps, long long spin_limit) {
     unsigned long long target = 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -374,6 +420,18 @@ __global__ void __launch_bounds__(256) k_persistent(StepArgs<R> a, long long n_s
         if (!ok) break;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) a.status->steps_done = a.step0 + done;
+}
+template <typename R, int NV, int MODE>
+__global__ void __launch_bounds__(256) k_persistent(StepArgs<R> a, long long n_steps, long long spin_limit) {
+    persistent_steps<R, NV, MODE>(a, n_steps, spin_limit);
+}
+// The extension build asks for at least 4 (FP32) or 3 (FP64) blocks per SM:
+// without the bound the compiler keeps its per-element plane offsets live
+// across the whole step loop (172 registers, one block per SM).
+template <typename R, int NV, int MODE>
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 3)
+    k_persistent_ext(StepArgs<R> a, long long n_steps, long long spin_limit) {
+    persistent_steps<R, NV, MODE>(a, n_steps, spin_limit);
 }
 
 // ---- tiled persistent kernels ------------------------------------------------
@@ -1128,7 +1186,7 @@ cudaError_t launch_impl(const StepArgs<R>& a, int64_t n_steps, LaunchCfg& cfg, c
         return cudaGetLastError();
     }
     // persistent: one cooperative launch, grid = resident blocks
-    auto kern = ext ? k_persistent<R, NV, M | 2> : k_persistent<R, NV, M>;
+    auto kern = ext ? k_persistent_ext<R, NV, M | 2> : k_persistent<R, NV, M>;
     const int b = 256;
     int per_sm = 0;
     cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, b, 0);
