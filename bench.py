@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--tile-nodes", type=int, default=0)
     ap.add_argument("--block", type=int, default=0, help="threads per block (0 = the kernel's default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="cube", choices=["cube", "planning", "surrogate", "suite"],
+    ap.add_argument("--workload", default="cube", choices=["cube", "planning", "surrogate", "suite", "paper-sizes"],
                     help="cube: the 128^3 throughput cube (default); planning: 64 uneven tet meshes x 4 "
                          "scenarios in one batched launch, compared with the plain per-run GPU path")
     ap.add_argument("--meshes", type=int, default=64)
@@ -917,6 +917,80 @@ def run_suite(args):
                       "fp64_fma_tflops_measured": fp64_tflops, "rows": rows}))
 
 
+# the per-step times the paper states for its largest timing mesh (7872 nodes,
+# 40021 tetrahedra; 2000 steps of 0.005 s): the method in C++ with OpenMP on
+# an Intel i7-6700, and ABAQUS with and without its parallel execution
+PAPER_TIMING_CONTEXT = {"nodes": 7872, "elements": 40021, "hardware": "Intel Core i7-6700, 3.40 GHz",
+                        "method_td_openmp_ms_per_step": 3.022, "method_ti_openmp_ms_per_step": 1.074,
+                        "method_td_serial_ms_per_step": 5.001, "abaqus_td_parallel_ms_per_step": 325.50,
+                        "abaqus_td_serial_ms_per_step": 829.75}
+
+
+def run_paper_sizes(args):
+    """The paper's timing study in kind (Section 3.2, Fig. 8, Table 6): six
+    tet meshes of its node counts (the ellipsoid recipe scaled to them),
+    temperature-dependent (TD) and constant (TI) properties, 2000 steps of
+    0.005 s, autotuned kernel, device-resident, CUDA events (best of 3).
+    FP32+Kahan and FP64; each FP32 row reports max|dT| against the FP64 GPU
+    run.  The paper's own per-step times (another machine, a CPU) are
+    context only."""
+    import torch
+    from paper_1909_05098_gb300.build import build
+    build()
+    from paper_1909_05098_gb300 import fedfem as ff
+    from paper_1909_05098_gb300.autotune import tune
+    from synth.scenarios import PAPER_TIMING_SIZES, paper_size_ellipsoid
+    torch.cuda.set_device(0)
+    log = lambda m: print(m, file=sys.stderr, flush=True)
+    names = {ff.KERNEL_TWO_PHASE: "two_phase", ff.KERNEL_PERSISTENT: "persistent", ff.KERNEL_TILED: "tiled",
+             ff.KERNEL_TILED_STAGED: "tiled_staged", ff.KERNEL_TILED_REP: "tiled_rep"}
+    stream = torch.cuda.Stream()
+    dt, steps = 0.005, 2000
+    rows = []
+    for n_target, e_paper in PAPER_TIMING_SIZES:
+        for td in (True, False):
+            p = paper_size_ellipsoid(n_target, temperature_dependent=td).problem
+            fields = {}
+            for prec in (ff.FP64, ff.FP32_KAHAN):
+                s = ff.Solver(p, precision=prec, stream=stream.cuda_stream, kernel=ff.KERNEL_PERSISTENT)
+                tuned = tune(s, dt, use_cache=False, stream=stream, steps=50)
+                s.init()
+                s.step(dt, steps)
+                s.sync()
+                fields[prec] = s.temperature()
+                best = None
+                for _ in range(3):
+                    s.init()
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    s.step(dt, steps)
+                    b.record(stream)
+                    s.sync()
+                    torch.cuda.synchronize()
+                    ms = a.elapsed_time(b)
+                    best = ms if best is None else min(best, ms)
+                info = s.info()
+                s.close()
+                us = 1e3 * best / steps
+                row = {"paper_nodes": n_target, "paper_elements": e_paper, "nodes": info["n_nodes"],
+                       "elements": info["n_elems"], "properties": "TD" if td else "TI",
+                       "precision": {ff.FP64: "FP64", ff.FP32_KAHAN: "FP32+Kahan"}[prec],
+                       "kernel": names[tuned["kernel"]], "tile_nodes": info["tile_nodes"],
+                       "us_per_step": us, "node_steps_per_s": info["n_nodes"] / (us * 1e-6),
+                       "sim_s_per_wall_s": dt / (us * 1e-6),
+                       "max_err_vs_fp64_C": (float(np.max(np.abs(fields[prec] - fields[ff.FP64])))
+                                             if prec != ff.FP64 else None)}
+                log(json.dumps(row))
+                rows.append(row)
+    big = [r for r in rows if r["paper_nodes"] == PAPER_TIMING_CONTEXT["nodes"] and r["precision"] == "FP32+Kahan"]
+    ctx = dict(PAPER_TIMING_CONTEXT)
+    for r in big:
+        key = "method_td_openmp_ms_per_step" if r["properties"] == "TD" else "method_ti_openmp_ms_per_step"
+        ctx[f"ratio_{r['properties'].lower()}_paper_cpu_over_this_gpu"] = ctx[key] * 1e3 / r["us_per_step"]
+    print(json.dumps({"workload": "paper-sizes", "n_gpus": 1, "data": "synthetic", "dt_s": dt, "steps": steps,
+                      "rows": rows, "paper_context": ctx}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -927,6 +1001,8 @@ def main():
         run_surrogate(args)
     elif args.workload == "suite":
         run_suite(args)
+    elif args.workload == "paper-sizes":
+        run_paper_sizes(args)
     else:
         run_ours(args)
 

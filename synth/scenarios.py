@@ -112,6 +112,43 @@ def cube_hex_td_convective(n: int = 128, h: float = 1e-3, n_steps: int = 10000) 
                     prob, n_steps)
 
 
+# the six mesh densities (nodes, tetrahedra) of the paper's timing study
+# (Section 3.2, Fig. 8 and Table 6)
+PAPER_TIMING_SIZES = ((1445, 6738), (1840, 8724), (2644, 12852), (3339, 16371), (5304, 26550), (7872, 40021))
+
+
+def paper_size_ellipsoid(target_nodes: int, temperature_dependent: bool = True, h: float = 1e-3,
+                         seed: int = ELLIPSOID_SEED) -> Workload:
+    """The ellipsoid recipe (jittered Kuhn tets, three seeded sources,
+    perfusion) with its 60/45/35 mm shape scaled until the node count is the
+    first one at or above target_nodes; temperature-dependent k, c or the
+    constant tissue values.  Like the paper's liver, only the bottom is held
+    at 37 degC: the surface nodes below half the short semi-axis under the
+    centre; the rest of the surface is insulated.  The paper's timing study
+    runs 2000 steps of 0.005 s."""
+    shape = np.asarray(ELLIPSOID_AXES)
+    lo, hi = 0.01, 1.5
+    for _ in range(30):   # bisection on the node count
+        s = 0.5 * (lo + hi)
+        if ellipsoid_node_count(shape * s, h) < target_nodes:
+            lo = s
+        else:
+            hi = s
+    axes = tuple(float(v) for v in shape * hi)
+    m = tet_ellipsoid(axes, h, 0.2 * h, seed)
+    rng = np.random.default_rng(seed + 1)
+    src = _sample_sources(rng, axes, 3)
+    z = m.xyz[m.surface_nodes, 2]
+    zc = 0.5 * (m.xyz[:, 2].min() + m.xyz[:, 2].max())
+    dn = m.surface_nodes[z < zc - 0.5 * axes[2]]
+    mat = TISSUE_TD if temperature_dependent else TISSUE_CONST
+    prob = Problem(4, m.xyz, m.conn, mat, PERFUSION, sources=src,
+                   dirichlet_nodes=dn, dirichlet_T=np.full(len(dn), 37.0),
+                   T0=37.0, T_lo=25.0, T_hi=400.0)
+    return Workload(f"tet4 ellipsoid scaled to {len(m.xyz)} nodes, {'TD' if temperature_dependent else 'TI'}",
+                    prob, 2000)
+
+
 @dataclass
 class PlanningMesh:
     seed: int
