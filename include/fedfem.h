@@ -339,10 +339,13 @@ int fedfem_precompute(fedfem_ctx* ctx, double T_lo, double T_hi, double* dt_cr_o
 
 /* Initial field (the initialisation of Algorithm 1): T0 has n_nodes values in input order,
  * or is NULL for T0_uniform everywhere.  Dirichlet nodes take their values.
- * Clears the device status and the step counter. */
+ * Clears the device status and the step counter.  A non-finite value gives
+ * FEDFEM_E_ARG and leaves the state as it was (the values are checked on the
+ * device after the copy; the call returns once the check is read back). */
 int fedfem_init(fedfem_ctx* ctx, const double* T0, double T0_uniform);
 
-/* As fedfem_init, T0 a device pointer to n_nodes doubles (input order). */
+/* As fedfem_init, T0 a device pointer to n_nodes doubles (input order); the
+ * same check. */
 int fedfem_init_device(fedfem_ctx* ctx, const double* T0_dev);
 
 /* Advance n_steps explicit steps of size dt (Algorithm 1's time loop),

@@ -1424,14 +1424,34 @@ static int init_common(fedfem_ctx* c, bool per_lane = false) {
     return FEDFEM_OK;
 }
 
+// any non-finite value among the n staged values sets the status word bad_input
+__global__ void k_check_finite(const double* v, int64_t n, DevStatus* st) {
+    bool bad = false;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        bad |= !isfinite(v[i]);
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&st->bad_input, 1ULL);
+}
+
+// FEDFEM_OK when every one of the n staged initial values is finite: one pass on
+// the device and an 8-byte read, instead of a host pass over the caller's array
+int check_initial_field(fedfem_ctx* c, const double* v, int64_t n) {
+    CU(cudaMemsetAsync(&c->st->bad_input, 0, sizeof(unsigned long long), c->stream), "check T0");
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 8LL * c->sm_count));
+    k_check_finite<<<grid, 256, 0, c->stream>>>(v, n, c->st);
+    CU(cudaGetLastError(), "check T0");
+    unsigned long long bad = 0;
+    CU(cudaMemcpyAsync(&bad, &c->st->bad_input, sizeof bad, cudaMemcpyDeviceToHost, c->stream), "check T0");
+    CU(cudaStreamSynchronize(c->stream), "check T0");
+    return bad ? fail(c, FEDFEM_E_ARG, "non-finite initial temperature") : FEDFEM_OK;
+}
+
 int fedfem_init(fedfem_ctx* c, const double* T0, double T0_uniform) {
     if (!c) return FEDFEM_E_ARG;
     if (!c->pre) return fail(c, FEDFEM_E_STATE, "precompute first");
     CU(cudaSetDevice(c->device), "set device");
     if (T0) {
-        for (int64_t i = 0; i < c->N; ++i)
-            if (!is_finite(T0[i])) return fail(c, FEDFEM_E_ARG, "non-finite initial temperature");
         CU(cudaMemcpyAsync(c->io, T0, sizeof(double) * c->N, cudaMemcpyHostToDevice, c->stream), "copy T0");
+        if (int r = check_initial_field(c, c->io, c->N)) return r;
     } else {
         if (!is_finite(T0_uniform)) return fail(c, FEDFEM_E_ARG, "non-finite initial temperature");
         std::vector<double> u(c->N, T0_uniform);
@@ -1446,6 +1466,7 @@ int fedfem_init_device(fedfem_ctx* c, const double* T0_dev) {
     if (!c->pre) return fail(c, FEDFEM_E_STATE, "precompute first");
     CU(cudaSetDevice(c->device), "set device");
     CU(cudaMemcpyAsync(c->io, T0_dev, sizeof(double) * c->N, cudaMemcpyDeviceToDevice, c->stream), "copy T0");
+    if (int r = check_initial_field(c, c->io, c->N)) return r;
     return init_common(c);
 }
 
@@ -1455,6 +1476,7 @@ int fedfem_init_lanes_device(fedfem_ctx* c, const double* T0_dev) {
     CU(cudaSetDevice(c->device), "set device");
     CU(cudaMemcpyAsync(c->io, T0_dev, sizeof(double) * c->N * c->n_lanes, cudaMemcpyDeviceToDevice, c->stream),
        "copy T0");
+    if (int r = check_initial_field(c, c->io, c->N * c->n_lanes)) return r;
     return init_common(c, true);
 }
 

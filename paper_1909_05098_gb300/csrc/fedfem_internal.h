@@ -85,7 +85,8 @@ struct DevStatus {
     long long fail_step;             // step index (since init) of the first failure
     unsigned long long barrier;      // monotone arrival counter of the grid barrier
     long long steps_done;            // steps completed since init
-    long long pad[2];
+    unsigned long long bad_input;    // nonzero: the last checked initial field held a non-finite value
+    long long pad;
 };
 
 // ---------------------------------------------------------------------------

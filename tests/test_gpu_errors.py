@@ -180,6 +180,39 @@ def test_device_pointer_init_and_read():
         s.close()
 
 
+def test_non_finite_initial_field_is_refused_and_changes_nothing():
+    """The initial field is checked on the device after its copy: one NaN or
+    infinity anywhere (here the last node, and a node in the middle) gives
+    E_ARG through the host and the device entry points, and the field and
+    the step counter stay those of the last good init."""
+    import torch
+    f = ff()
+    p = cube_hex_fp64().problem
+    s = _solver(p, f.FP64)
+    try:
+        dt = 0.5 * s.dt_cr
+        s.step(dt, 5)
+        assert s.sync() == 5
+        before = s.temperature()
+        dev = torch.device("cuda", 0)
+        for pos, bad in ((p.n_nodes - 1, np.nan), (p.n_nodes // 2, np.inf)):
+            T0 = np.full(p.n_nodes, 37.0)
+            T0[pos] = bad
+            with pytest.raises(f.FedfemError) as e:
+                f.fedfem_init(s.ctx, T0)
+            assert e.value.code == f.E_ARG
+            Td = torch.tensor(T0, dtype=torch.float64, device=dev)
+            torch.cuda.synchronize()
+            with pytest.raises(f.FedfemError) as e:
+                f.fedfem_init_device(s.ctx, Td.data_ptr())
+            assert e.value.code == f.E_ARG
+            assert np.array_equal(s.temperature(), before)
+        s.step(dt, 3)                              # the context goes on from the last good state
+        assert s.sync() == 8
+    finally:
+        s.close()
+
+
 def test_refused_tile_size_leaves_the_context_usable():
     """A tile whose shared memory no block can hold is refused with
     E_UNSUPPORTED; the refusal must not surface as an error in later calls."""
