@@ -131,3 +131,37 @@ def test_table_arguments_are_checked():
         assert f.fedfem_precompute(s.ctx, 0.0, 60.0) > 0.0
     finally:
         s.close()
+
+
+# eight points (the most a table takes): six kinks between 38 and 48 degC,
+# slopes changing sign, all inside the range the heated cube crosses
+TAB8 = Material.tabulated((30.0, 38.0, 40.0, 42.0, 44.0, 46.0, 48.0, 70.0),
+                          (1060.0, 1058.0, 1050.0, 1052.0, 1040.0, 1035.0, 1030.0, 1000.0),
+                          (3600.0, 3650.0, 3700.0, 3640.0, 3560.0, 3500.0, 3480.0, 3300.0),
+                          (0.50, 0.52, 0.56, 0.55, 0.62, 0.70, 0.69, 0.74))
+
+
+def test_eight_point_table_every_kink_every_kernel():
+    """Every interior point of the largest table is a kink the field crosses:
+    FP64 within 1e-9 and FP32+Kahan within 1e-3 of the oracle, all kernels
+    the same bits."""
+    f = ff()
+    p = copy.copy(cube_hex_fp64().problem)
+    p.material = TAB8
+    p.T_lo, p.T_hi = 0.0, 200.0
+    orc = Oracle(p)
+    dt = 0.5 * critical_dt(orc, p.T_lo, p.T_hi)
+    n = 800
+    ref = orc.run(dt, n)
+    assert ref.max() > 48.0                         # the last interior kink is crossed
+    for prec, tol in ((f.FP64, TOL64), (f.FP32_KAHAN, TOL32)):
+        base = None
+        for kern in (f.KERNEL_PERSISTENT, f.KERNEL_TWO_PHASE, f.KERNEL_TILED, f.KERNEL_TILED_STAGED,
+                     f.KERNEL_TILED_REP):
+            T, _ = run_gpu(p, dt, n, prec, kernel=kern)
+            err = max_abs(T, ref)
+            print(f"eight-point table prec {prec} kernel {kern}: max|dT| = {err:.3e}")
+            assert err <= tol
+            if base is None:
+                base = T
+            assert np.array_equal(T, base), kern
