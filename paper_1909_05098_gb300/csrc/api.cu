@@ -1425,7 +1425,7 @@ static int init_common(fedfem_ctx* c, bool per_lane = false) {
 }
 
 // any non-finite value among the n staged values sets the status word bad_input
-__global__ void k_check_finite(const double* v, int64_t n, DevStatus* st) {
+static __global__ void k_check_finite(const double* v, int64_t n, DevStatus* st) {
     bool bad = false;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         bad |= !isfinite(v[i]);
@@ -1434,7 +1434,7 @@ __global__ void k_check_finite(const double* v, int64_t n, DevStatus* st) {
 
 // FEDFEM_OK when every one of the n staged initial values is finite: one pass on
 // the device and an 8-byte read, instead of a host pass over the caller's array
-int check_initial_field(fedfem_ctx* c, const double* v, int64_t n) {
+static int check_initial_field(fedfem_ctx* c, const double* v, int64_t n) {
     CU(cudaMemsetAsync(&c->st->bad_input, 0, sizeof(unsigned long long), c->stream), "check T0");
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 8LL * c->sm_count));
     k_check_finite<<<grid, 256, 0, c->stream>>>(v, n, c->st);
