@@ -301,8 +301,9 @@ int fedfem_set_source_schedule(fedfem_ctx* ctx, int n, const double* t_end, cons
  * no formula): cumulative equivalent minutes at 43 degC of Sapareto and
  * Dewey, CEM43 += (dt / 60) R^(43 - T) with R = 1/2 at or above 43 degC and
  * 1/4 below, T the node's temperature at the start of each step (the hi part
- * in FP32+Kahan), accumulated in FP64 inside the node update of every
- * kernel (every scenario lane separately); the power is evaluated in the
+ * in FP32+Kahan), accumulated inside the node update of every kernel (every
+ * scenario lane separately): in FP64 with FP64 state, as a compensated FP32
+ * pair (about 2^-48 relative) with FP32 state; the power is evaluated in the
  * state's precision.  on != 0 enables it from the next fedfem_precompute;
  * fedfem_init resets it to 0; checkpoints carry it. */
 int fedfem_enable_dose(fedfem_ctx* ctx, int on);
@@ -312,8 +313,8 @@ int fedfem_enable_dose(fedfem_ctx* ctx, int on);
 /* The dose model (default CEM43).  FEDFEM_DOSE_ARRHENIUS: the thermal damage
  * integral of Henriques and Moritz, Omega += dt A exp(-Ea / (R T_K)), A the
  * frequency factor (1/s), Ea the activation energy (J/mol), R = 8.314462618
- * J/(mol K), T_K = T + 273.15, at each step's start temperature, summed in
- * FP64 (the exponential in the state's precision); fedfem_read_dose then
+ * J/(mol K), T_K = T + 273.15, at each step's start temperature, summed as
+ * the CEM43 dose is (the exponential in the state's precision); fedfem_read_dose then
  * returns Omega (dimensionless; 1 is the usual coagulation threshold).
  * FEDFEM_DOSE_CEM43 ignores A and Ea.  E_ARG for another model or A, Ea not
  * finite and positive.  Takes effect at the next fedfem_step; fedfem_init

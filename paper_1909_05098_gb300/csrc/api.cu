@@ -307,6 +307,7 @@ StepArgs<R, L> make_args(fedfem_ctx* c, const R* M, const R* V, const R* Q, cons
     a.dose = c->dose;
     a.dose_model = c->dose_model;
     a.dose_dt = c->dose_model == FEDFEM_DOSE_ARRHENIUS ? dt : dt / 60.0;
+    a.dose_dt32 = (float)a.dose_dt;
     a.dose_lnA = c->dose_model == FEDFEM_DOSE_ARRHENIUS ? std::log(c->dose_A) : 0.0;
     a.dose_EaR = c->dose_Ea / kGasConstant;
     const bool arr = c->dose_model == FEDFEM_DOSE_ARRHENIUS;
@@ -1064,7 +1065,15 @@ int fedfem_read_dose_lane(fedfem_ctx* c, int lane, double* out) {
     std::vector<double> d(std::max<int64_t>(1, NF * NL));
     CU(cudaStreamSynchronize(c->stream), "dose read");
     CU(cudaMemcpy(d.data(), c->dose, sizeof(double) * NF * NL, cudaMemcpyDeviceToHost), "dose read");
-    for (int64_t i = 0; i < NF; ++i) out[c->L.node_of[i]] = d[i * NL + lane];
+    if (c->precision == FEDFEM_FP64) {
+        for (int64_t i = 0; i < NF; ++i) out[c->L.node_of[i]] = d[i * NL + lane];
+    } else {   // FP32 state: each slot holds the pair (hi, lo)
+        const float* h = reinterpret_cast<const float*>(d.data());
+        for (int64_t i = 0; i < NF; ++i) {
+            const int64_t q = 2 * (i * NL + lane);
+            out[c->L.node_of[i]] = (double)h[q] + (double)h[q + 1];
+        }
+    }
     // Dirichlet nodes sit at their fixed temperature for the whole elapsed time
     for (int64_t i = NF; i < c->N; ++i) {
         const int64_t o = c->L.node_of[i];
@@ -1684,7 +1693,7 @@ int fedfem_get_info(fedfem_ctx* c, fedfem_info* info) {
     info->algorithmic_bytes_per_step = E * (4 * c->nv + nm * R) + NF * (NL * (node_state + R) + R) + NC * R;
     if (c->matrix_free)   // coordinates (each node once) instead of the element matrices
         info->algorithmic_bytes_per_step += 12 * c->N - E * nm * R;
-    // a source schedule reads the source part of Q too; the dose is read and written in FP64
+    // a source schedule reads the source part of Q too; the dose (8 bytes per node) is read and written
     const int64_t extra = (c->sched_f.empty() ? 0 : NF * NL * R) + (c->dose ? NF * 16 : 0) +
                           (c->n_cq > 0 ? NF * 4 * R + E : 0);   // regions: node coefficients, element ids
     info->algorithmic_bytes_per_step += extra;

@@ -127,9 +127,12 @@ struct StepArgs {
     R seg_f[kMaxSegments];
     // thermal dose, dose[i * lanes + l] += dose_dt * rate(T_il): CEM43 minutes
     // (dose_model 0, dose_dt = dt / 60) or the Arrhenius damage integral
-    // (dose_model 1, dose_dt = dt, rate = exp(dose_lnA - dose_EaR / T_K))
+    // (dose_model 1, dose_dt = dt, rate = exp(dose_lnA - dose_EaR / T_K)).
+    // FP64 state sums in the double; FP32 state keeps each 8-byte slot as a
+    // compensated FP32 pair (hi, lo), the dose being hi + lo.
     double* dose;
     double dose_dt;
+    float dose_dt32;                 // dose_dt rounded to FP32 (FP32 state)
     int dose_model;
     double dose_lnA, dose_EaR;
     float dose_c43, dose_a2, dose_g2;   // FP32 state: the rate as 2^(c43 s (T - 43) + a2 - g2 / T_K)

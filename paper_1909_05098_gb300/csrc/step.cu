@@ -263,7 +263,7 @@ __device__ __forceinline__ R schedule_factor(const StepArgs<R, L>& a, long long 
 // minute; or the Arrhenius damage rate (model 1), A exp(-Ea / (R_gas T_K)) =
 // exp(lnA - EaR / (T + 273.15)), per second.  The power is taken in the
 // state's precision (FP32 state: exp2f, whose relative error is far below
-// that of the FP32 temperature it is taken of); sums are FP64.
+// that of the FP32 temperature it is taken of).
 __device__ __forceinline__ double dose_rate(int model, double lnA, double EaR, double T) {
     if (model == 1) return exp(lnA - EaR / (T + 273.15));
     return exp2(T >= 43.0 ? T - 43.0 : 2.0 * (T - 43.0));
@@ -272,9 +272,19 @@ __device__ __forceinline__ double dose_rate(int model, double lnA, double EaR, d
 // 2^(c43 s (T - 43) + a2 - g2 / T_K), s = 1 at or above 43 degC and 2 below;
 // CEM43: c43 = 1, a2 = g2 = 0 (exactly the CEM43 exponent); Arrhenius:
 // c43 = 0, a2 = log2 A, g2 = (Ea / R) / ln 2
-__device__ __forceinline__ double dose_rate(float c43, float a2, float g2, float T) {
+__device__ __forceinline__ float dose_rate(float c43, float a2, float g2, float T) {
     const float e = c43 * (T >= 43.0f ? T - 43.0f : 2.0f * (T - 43.0f));
-    return (double)exp2f((e + a2) - g2 * __frcp_rn(T + 273.15f));
+    return exp2f((e + a2) - g2 * __frcp_rn(T + 273.15f));
+}
+// The FP32 dose (hi, lo) plus an increment: y = inc + lo, then hi + y as an
+// exact sum of two FP32 values (Knuth's TwoSum, valid whatever their sizes:
+// the increment of a heating node can exceed the dose so far), so the pair
+// carries the running dose to about 2^-48 relative with FP32 instructions only.
+__device__ __forceinline__ float2 dose_sum(float2 d, float inc) {
+    const float y = inc + d.y;
+    const float s = d.x + y;
+    const float yy = s - d.x;
+    return make_float2(s, (d.x - (s - yy)) + (y - yy));
 }
 template <typename L>
 __device__ __forceinline__ void dose_add(const StepArgs<double, L>& a, int64_t i, double T) {
@@ -282,19 +292,21 @@ __device__ __forceinline__ void dose_add(const StepArgs<double, L>& a, int64_t i
 }
 template <typename L>
 __device__ __forceinline__ void dose_add(const StepArgs<float, L>& a, int64_t i, float T) {
-    a.dose[i] += a.dose_dt * dose_rate(a.dose_c43, a.dose_a2, a.dose_g2, T);
+    float2* d = reinterpret_cast<float2*>(a.dose) + i;
+    *d = dose_sum(*d, a.dose_dt32 * dose_rate(a.dose_c43, a.dose_a2, a.dose_g2, T));
 }
-// four scenario lanes: the node's four doses are contiguous
+// four scenario lanes: the node's four (hi, lo) pairs are contiguous, each
+// lane summed exactly as one lane alone
 template <typename L>
 __device__ __forceinline__ void dose_add(const StepArgs<float, L>& a, int64_t i, F4 T) {
-    double2* d = reinterpret_cast<double2*>(a.dose + 4 * i);
-    double2 p = d[0], q = d[1];
-    p.x += a.dose_dt * dose_rate(a.dose_c43, a.dose_a2, a.dose_g2, T.x);
-    p.y += a.dose_dt * dose_rate(a.dose_c43, a.dose_a2, a.dose_g2, T.y);
-    q.x += a.dose_dt * dose_rate(a.dose_c43, a.dose_a2, a.dose_g2, T.z);
-    q.y += a.dose_dt * dose_rate(a.dose_c43, a.dose_a2, a.dose_g2, T.w);
-    d[0] = p;
-    d[1] = q;
+    float4* d = reinterpret_cast<float4*>(a.dose) + 2 * i;
+    const float4 p = d[0], q = d[1];
+    const float2 d0 = dose_sum(make_float2(p.x, p.y), a.dose_dt32 * dose_rate(a.dose_c43, a.dose_a2, a.dose_g2, T.x));
+    const float2 d1 = dose_sum(make_float2(p.z, p.w), a.dose_dt32 * dose_rate(a.dose_c43, a.dose_a2, a.dose_g2, T.y));
+    const float2 d2 = dose_sum(make_float2(q.x, q.y), a.dose_dt32 * dose_rate(a.dose_c43, a.dose_a2, a.dose_g2, T.z));
+    const float2 d3 = dose_sum(make_float2(q.z, q.w), a.dose_dt32 * dose_rate(a.dose_c43, a.dose_a2, a.dose_g2, T.w));
+    d[0] = make_float4(d0.x, d0.y, d1.x, d1.y);
+    d[1] = make_float4(d2.x, d2.y, d3.x, d3.y);
 }
 
 template <typename R, typename L, int MODE>
