@@ -165,3 +165,31 @@ def test_eight_point_table_every_kink_every_kernel():
             if base is None:
                 base = T
             assert np.array_equal(T, base), kern
+
+
+def test_field_below_the_first_table_point_extrapolates_the_first_interval():
+    """A table that starts above the initial 37 degC (points at 40, 45 and 60
+    degC): most of the cube stays below its first point for the whole run,
+    where every property follows the first interval's line, and the heated
+    centre crosses into and past the table; FP64 and FP32+Kahan against the
+    oracle, every kernel the same bits."""
+    f = ff()
+    p = copy.copy(cube_hex_fp64().problem)
+    p.material = Material.tabulated((40.0, 45.0, 60.0), (1050.0, 1040.0, 1020.0), (3700.0, 3650.0, 3500.0),
+                                    (0.55, 0.60, 0.66))
+    p.T_lo, p.T_hi = 0.0, 200.0
+    orc = Oracle(p)
+    dt = 0.5 * critical_dt(orc, p.T_lo, p.T_hi)
+    n = 800
+    ref = orc.run(dt, n)
+    assert ref.min() < 40.0 < 45.0 < ref.max()      # below the table and past its interior point
+    for prec, tol in ((f.FP64, TOL64), (f.FP32_KAHAN, TOL32)):
+        base = None
+        for kern in (f.KERNEL_PERSISTENT, f.KERNEL_TILED_STAGED, f.KERNEL_TILED_REP):
+            T, _ = run_gpu(p, dt, n, prec, kernel=kern)
+            err = max_abs(T, ref)
+            print(f"table above T0, prec {prec} kernel {kern}: max|dT| = {err:.3e}")
+            assert err <= tol
+            if base is None:
+                base = T
+            assert np.array_equal(T, base), kern
