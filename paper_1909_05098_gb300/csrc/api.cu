@@ -10,6 +10,8 @@
 #include <type_traits>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "fedfem_internal.h"
 
 using namespace fedfem;
@@ -658,6 +660,16 @@ cudaError_t launch_all(fedfem_ctx* c, double dt, int64_t n_steps, LaunchCfg& cfg
 
 }  // namespace
 
+// One NVTX range per public call, named after it, so that a profiler's
+// timeline shows which library call the kernels and copies belong to (no
+// cost unless a tool is attached).
+struct ApiRange {
+    explicit ApiRange(const char* name) { nvtxRangePushA(name); }
+    ~ApiRange() { nvtxRangePop(); }
+    ApiRange(const ApiRange&) = delete;
+    ApiRange& operator=(const ApiRange&) = delete;
+};
+
 extern "C" {
 
 int fedfem_plan_layout(int elem_type, int64_t n_nodes, const double* xyz, int64_t n_elems, const int32_t* conn,
@@ -756,6 +768,7 @@ const char* fedfem_last_error(const fedfem_ctx* c) { return c ? c->err.c_str() :
 
 int fedfem_set_mesh(fedfem_ctx* c, int elem_type, int64_t n_nodes, const double* xyz, int64_t n_elems,
                     const int32_t* conn) {
+    ApiRange nvtx_range("fedfem_set_mesh");
     if (!c) return FEDFEM_E_ARG;
     if (elem_type != FEDFEM_HEX8 && elem_type != FEDFEM_TET4) return fail(c, FEDFEM_E_ARG, "elem_type must be 4 or 8");
     if (n_nodes <= 0 || n_elems <= 0 || !xyz || !conn) return fail(c, FEDFEM_E_ARG, "empty mesh or null array");
@@ -1109,6 +1122,7 @@ int fedfem_debug_set(fedfem_ctx* c, int key, int64_t value) {
 }
 
 int fedfem_precompute(fedfem_ctx* c, double T_lo, double T_hi, double* dt_cr_out) {
+    ApiRange nvtx_range("fedfem_precompute");
     if (!c) return FEDFEM_E_ARG;
     if (!c->has_mesh || !c->has_mat) return fail(c, FEDFEM_E_STATE, "set_mesh and set_material first");
     if (!(is_finite(T_lo) && is_finite(T_hi) && T_lo < T_hi)) return fail(c, FEDFEM_E_ARG, "need T_lo < T_hi");
@@ -1455,6 +1469,7 @@ static int check_initial_field(fedfem_ctx* c, const double* v, int64_t n) {
 }
 
 int fedfem_init(fedfem_ctx* c, const double* T0, double T0_uniform) {
+    ApiRange nvtx_range("fedfem_init");
     if (!c) return FEDFEM_E_ARG;
     if (!c->pre) return fail(c, FEDFEM_E_STATE, "precompute first");
     CU(cudaSetDevice(c->device), "set device");
@@ -1471,6 +1486,7 @@ int fedfem_init(fedfem_ctx* c, const double* T0, double T0_uniform) {
 }
 
 int fedfem_init_device(fedfem_ctx* c, const double* T0_dev) {
+    ApiRange nvtx_range("fedfem_init_device");
     if (!c || !T0_dev) return fail(c, FEDFEM_E_ARG, "null T0");
     if (!c->pre) return fail(c, FEDFEM_E_STATE, "precompute first");
     CU(cudaSetDevice(c->device), "set device");
@@ -1502,6 +1518,7 @@ int fedfem_read_lanes_device(fedfem_ctx* c, double* out_dev) {
 }
 
 int fedfem_step(fedfem_ctx* c, double dt, int64_t n_steps) {
+    ApiRange nvtx_range("fedfem_step");
     if (!c) return FEDFEM_E_ARG;
     if (!c->inited) return fail(c, FEDFEM_E_STATE, "init first");
     if (!(dt > 0) || !is_finite(dt) || n_steps < 0) return fail(c, FEDFEM_E_ARG, "need dt > 0 and n_steps >= 0");
@@ -1559,6 +1576,7 @@ int fedfem_replay_graph(fedfem_ctx* c) {
 }
 
 int fedfem_sync(fedfem_ctx* c, int64_t* steps_done) {
+    ApiRange nvtx_range("fedfem_sync");
     if (!c) return FEDFEM_E_ARG;
     if (!c->inited) return fail(c, FEDFEM_E_STATE, "init first");
     CU(cudaSetDevice(c->device), "set device");
@@ -1581,6 +1599,7 @@ int fedfem_sync(fedfem_ctx* c, int64_t* steps_done) {
 }
 
 int fedfem_read_temperature_device(fedfem_ctx* c, double* out_dev) {
+    ApiRange nvtx_range("fedfem_read_temperature_device");
     if (!c || !out_dev) return fail(c, FEDFEM_E_ARG, "null output");
     if (!c->inited) return fail(c, FEDFEM_E_STATE, "init first");
     CU(cudaSetDevice(c->device), "set device");
@@ -1603,6 +1622,7 @@ int fedfem_read_temperature_lane(fedfem_ctx* c, int lane, double* out) {
 }
 
 int fedfem_read_temperature(fedfem_ctx* c, double* out) {
+    ApiRange nvtx_range("fedfem_read_temperature");
     if (!c || !out) return fail(c, FEDFEM_E_ARG, "null output");
     if (!c->inited) return fail(c, FEDFEM_E_STATE, "init first");
     CU(cudaSetDevice(c->device), "set device");
@@ -1625,6 +1645,7 @@ struct StateHeader {
 static const uint64_t kMagic = 0x5453464d45464546ULL;   // "FEFEMFST"
 
 int fedfem_get_state(fedfem_ctx* c, void* buf, size_t* bytes) {
+    ApiRange nvtx_range("fedfem_get_state");
     if (!c || !bytes) return fail(c, FEDFEM_E_ARG, "null size pointer");
     if (!c->inited) return fail(c, FEDFEM_E_STATE, "init first");
     const size_t tb = (c->precision == FEDFEM_FP64 ? sizeof(double) : sizeof(float)) * c->N * c->n_lanes;
@@ -1647,6 +1668,7 @@ int fedfem_get_state(fedfem_ctx* c, void* buf, size_t* bytes) {
 }
 
 int fedfem_set_state(fedfem_ctx* c, const void* buf, size_t bytes) {
+    ApiRange nvtx_range("fedfem_set_state");
     if (!c || !buf) return fail(c, FEDFEM_E_ARG, "null state");
     if (!c->pre) return fail(c, FEDFEM_E_STATE, "precompute first");
     if (bytes < sizeof(StateHeader)) return fail(c, FEDFEM_E_ARG, "state too short");
