@@ -22,7 +22,7 @@ def candidates(elem_type: int, precision: int):
     """(kernel, block, tile_nodes, blocks_per_sm); 0 = the library's default."""
     out = [(ff.KERNEL_PERSISTENT, 0, 0, 0)]
     sizes = (0, 128, 256, 384) if elem_type == ff.HEX8 else (0, 64, 96, 128, 192)
-    staged = (0, 384, 512, 576, 640) if elem_type == ff.HEX8 else (0, 128, 192, 256, 320)
+    staged = (0, 384, 512, 576, 640) if elem_type == ff.HEX8 else (0, 128, 192, 224, 256)
     staged1024 = (1024, 1280) if elem_type == ff.HEX8 else (512,)   # one block of 1024 threads per SM
     if precision == ff.FP64:
         sizes = tuple(s // 2 for s in sizes if s)[:2] + (0,)

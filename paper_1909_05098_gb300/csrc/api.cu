@@ -384,7 +384,7 @@ size_t rep_bytes(const Tiles& t, size_t ls, int S) {
 
 // dynamic shared memory of the tiled kernels (kind: 0 direct, 1 staged, 2 staged
 // with replicated rows of stride S): two block stages when staged; the tile
-// temperatures and the per-node load table (max_deg rows of B), or the two
+// temperatures and the per-node load table (max_deg rows of B + 1), or the two
 // replicated-row arrays
 size_t tile_smem(const Tiles& t, size_t rs, size_t ls, int* max_block, int kind, int S, bool hg, bool mf) {
     int64_t mb = 0;
@@ -392,7 +392,7 @@ size_t tile_smem(const Tiles& t, size_t rs, size_t ls, int* max_block, int kind,
     *max_block = (int)mb;
     if (kind == 2) return 128 + 2 * rep_bytes(t, ls, S) + 2 * (size_t)mb;
     const size_t ts = ((size_t)t.max_local * ls + 15) / 16 * 16;
-    const size_t b = (kind ? 128 + 2 * (size_t)mb : 0) + ts + ls * (size_t)std::max(1, t.max_deg) * t.B;
+    const size_t b = (kind ? 128 + 2 * (size_t)mb : 0) + ts + ls * (size_t)std::max(1, t.max_deg) * (t.B + 1);
     return (b + 15) / 16 * 16;
 }
 

@@ -274,6 +274,69 @@ std::string build_layout(const MeshInput& in, Layout& L, bool* mesh_error) {
 
 namespace fedfem {
 
+// Order of one tet tile's elements for the warps of the tiled kernels (each
+// run of 32 consecutive elements is one warp): warp by warp, the next element
+// is the one, among the first K not yet placed, that adds the fewest
+// shared-memory bank collisions to the warp's accesses, corner by corner:
+// temperature loads at the local id, load stores at rank x (B + 1) + id for
+// owned corners.  Sums are taken in rank order, so the order changes no
+// result.  lid, rnk: nv entries per element in the tile's sorted order.
+static void bank_order(const std::vector<int32_t>& lid, const std::vector<uint8_t>& rnk, int nv, int64_t ne,
+                       int64_t own, int64_t B, std::vector<int32_t>& perm) {
+    constexpr int K = 48;
+    perm.clear();
+    // each corner's load word and store word (-1: a halo corner, no store), computed once
+    std::vector<int32_t> lw(ne * nv), sw(ne * nv);
+    for (int64_t q = 0; q < ne * nv; ++q) {
+        lw[q] = lid[q];
+        sw[q] = lid[q] < own ? (int32_t)(rnk[q] * (B + 1) + lid[q]) : -1;
+    }
+    // doubly linked list of the unplaced elements in sorted order; index ne is the sentinel
+    std::vector<int32_t> nxt(ne + 1), prv(ne + 1);
+    for (int64_t j = 0; j <= ne; ++j) {
+        nxt[j] = (int32_t)((j + 1) % (ne + 1));
+        prv[j] = (int32_t)((j + ne) % (ne + 1));
+    }
+    // the first word that took each bank in the warp being filled, per corner (-1: free)
+    std::vector<int32_t> la(nv * 32), sa(nv * 32);
+    for (int64_t placed = 0; placed < ne;) {
+        std::fill(la.begin(), la.end(), -1);
+        std::fill(sa.begin(), sa.end(), -1);
+        for (int slot = 0; slot < 32 && placed < ne; ++slot, ++placed) {
+            int32_t best = -1;
+            int best_cost = 1 << 30;
+            int seen = 0;
+            for (int32_t j = nxt[ne]; j != ne && seen < K; j = nxt[j], ++seen) {
+                const int32_t* l = &lw[(int64_t)j * nv];
+                const int32_t* w = &sw[(int64_t)j * nv];
+                int cost = 0;
+                for (int k = 0; k < nv; ++k) {
+                    const int32_t a = la[k * 32 + (l[k] & 31)];
+                    cost += a >= 0 && a != l[k];
+                    if (w[k] >= 0) {
+                        const int32_t b = sa[k * 32 + (w[k] & 31)];
+                        cost += b >= 0 && b != w[k];
+                    }
+                }
+                if (cost < best_cost) {
+                    best_cost = cost;
+                    best = j;
+                    if (cost == 0) break;
+                }
+            }
+            perm.push_back(best);
+            nxt[prv[best]] = nxt[best];
+            prv[nxt[best]] = prv[best];
+            const int32_t* l = &lw[(int64_t)best * nv];
+            const int32_t* w = &sw[(int64_t)best * nv];
+            for (int k = 0; k < nv; ++k) {
+                if (la[k * 32 + (l[k] & 31)] < 0) la[k * 32 + (l[k] & 31)] = l[k];
+                if (w[k] >= 0 && sa[k * 32 + (w[k] & 31)] < 0) sa[k * 32 + (w[k] & 31)] = w[k];
+            }
+        }
+    }
+}
+
 std::string build_tiles(const Layout& L, int B, Tiles& T) {
     T = Tiles();
     const int nv = L.nv;
@@ -288,6 +351,8 @@ std::string build_tiles(const Layout& L, int B, Tiles& T) {
     std::vector<int32_t> touched;
     std::vector<int32_t> lid;                      // local ids, combined with the ranks at the end
     std::vector<uint8_t> rank;
+    std::vector<int32_t> tl, perm;                 // one tile: local ids (sorted element order), warp order
+    std::vector<uint8_t> tr;
     for (int64_t t = 0; t < T.n_tiles; ++t) {
         const int64_t base = t * B, own = std::min<int64_t>(B, NF - base);
         // elements touching the owned nodes, from the nodes' slot lists
@@ -334,12 +399,26 @@ std::string build_tiles(const Layout& L, int B, Tiles& T) {
         }
         if (dmax > 255) return "a node has more than 255 elements";
         T.deg[t] = dmax;
-        for (int64_t j = 0; j < ne; ++j) {
-            T.e_glob.push_back(elems[j]);
+        tl.resize(ne * nv);
+        tr.resize(ne * nv);
+        for (int64_t j = 0; j < ne; ++j)
             for (int k = 0; k < nv; ++k) {
                 const int32_t l = local_of[L.conn[(int64_t)elems[j] * nv + k]];
-                lid.push_back(l);
-                rank.push_back((uint8_t)(l < own ? rank_of[j * nv + k] : 0));
+                tl[j * nv + k] = l;
+                tr[j * nv + k] = (uint8_t)(l < own ? rank_of[j * nv + k] : 0);
+            }
+        if (nv == 4) {
+            bank_order(tl, tr, nv, ne, own, B, perm);
+        } else {
+            perm.resize(ne);
+            for (int64_t j = 0; j < ne; ++j) perm[j] = (int32_t)j;
+        }
+        for (int64_t q = 0; q < ne; ++q) {
+            const int64_t j = perm[q];
+            T.e_glob.push_back(elems[j]);
+            for (int k = 0; k < nv; ++k) {
+                lid.push_back(tl[j * nv + k]);
+                rank.push_back(tr[j * nv + k]);
             }
         }
         T.halo.insert(T.halo.end(), touched.begin(), touched.end());

@@ -652,7 +652,9 @@ __device__ __forceinline__ const unsigned char* tile_regions(const StepArgs<R, L
 }
 
 // element phase of one tile: loads of every tile element; each owned corner's
-// load goes to Fn[rank * B + local id]
+// load goes to Fn[rank * B + local id], B the load table's row stride (the
+// tile size plus one: odd, so that the rank rows of one node fall in
+// different shared-memory banks)
 template <typename R, typename L, int NV, bool SHARED, bool EXT, typename KL>
 __device__ __forceinline__ void tile_elements_k(const KL& kl, const TileView<R>& v, int own, int B, int rank_shift,
                                                 const L* Ts, L* Fn, R eps4) {
@@ -761,7 +763,7 @@ __global__ void __launch_bounds__(256, DirectOccupancy<L>::min_blocks) k_tiled_d
     extern __shared__ __align__(128) unsigned char smem[];
     L* Ts = reinterpret_cast<L*>(smem);
     L* Fn = reinterpret_cast<L*>(smem + ((size_t)ta.max_local * sizeof(L) + 15) / 16 * 16);
-    zero_table(Fn, ta.max_deg * ta.B);
+    zero_table(Fn, ta.max_deg * (ta.B + 1));
     unsigned long long target = 0;
     long long done = 0;
     if (!grid_barrier(a.status, target, spin_limit)) return;   // also orders the zeroing before first use
@@ -777,9 +779,9 @@ __global__ void __launch_bounds__(256, DirectOccupancy<L>::min_blocks) k_tiled_d
             L T0 = lzero<L>();
             NodeVals<R, L> v0{};
             first_node<R, L, MODE>(a, base, own, Ts, T0, v0);
-            tile_elements<R, L, NV, MODE, false>(a, tile_regions<MODE>(a, t), v, own, ta.B, ta.rank_shift, Ts, Fn);
+            tile_elements<R, L, NV, MODE, false>(a, tile_regions<MODE>(a, t), v, own, ta.B + 1, ta.rank_shift, Ts, Fn);
             __syncthreads();   // loads complete; Ts is free for the next tile
-            tile_nodes<R, L, MODE>(a, base, own, v.deg, ta.B, Fn, T0, v0, Tin, Tout, a.step0 + s);
+            tile_nodes<R, L, MODE>(a, base, own, v.deg, ta.B + 1, Fn, T0, v0, Tin, Tout, a.step0 + s);
             __syncthreads();   // table cleared before the next tile writes it
         }
         const bool ok = grid_barrier(a.status, target, spin_limit);
@@ -817,7 +819,7 @@ __global__ void __launch_bounds__(TPB, StagedOccupancy<L, TPB>::min_blocks)
         mbar_init(&bar[1], 1);
         fence_mbar_init();
     }
-    zero_table(Fn, ta.max_deg * ta.B);
+    zero_table(Fn, ta.max_deg * (ta.B + 1));
     __syncthreads();
     unsigned long long target = 0;
     long long done = 0;
@@ -893,14 +895,14 @@ __global__ void __launch_bounds__(TPB, StagedOccupancy<L, TPB>::min_blocks)
             L T0 = lzero<L>();
             NodeVals<R, L> v0{};
             first_node<R, L, MODE>(a, base, own, Ts, T0, v0);
-            tile_elements<R, L, NV, MODE, true>(a, tile_regions<MODE>(a, t), v, own, ta.B, ta.rank_shift, Ts, Fn);
+            tile_elements<R, L, NV, MODE, true>(a, tile_regions<MODE>(a, t), v, own, ta.B + 1, ta.rank_shift, Ts, Fn);
             __syncthreads();   // loads complete; this stage and Ts are free
             if (i + 1 < n_my) {   // the next tile of this step: its stage, then its temperatures
                 if (!land(buf_of(kk + 1, i + 1))) { fail_timeout(); stop = true; break; }
                 fetch(kk + 1, i + 1, Tin);
             }
             if (!resident && kk + 2 < total) issue(kk + 2, i + 2 < n_my ? i + 2 : i + 2 - n_my);
-            tile_nodes<R, L, MODE>(a, base, own, deg, ta.B, Fn, T0, v0, Tin, Tout, a.step0 + s);
+            tile_nodes<R, L, MODE>(a, base, own, deg, ta.B + 1, Fn, T0, v0, Tin, Tout, a.step0 + s);
         }
         if (stop) break;
         cp_async_wait_all();
